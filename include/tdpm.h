@@ -1,0 +1,239 @@
+/*
+ * tdpm.h -- C-ABI of the tensor-decomposed DPM scoring library (sm_103a / GB300).
+ *
+ * The library scores deformable part models (Sec. 2 of "Tensor-based approach to accelerate deformable part models"):
+ *   step 1  correlate every root and part filter with every level of a HOG feature pyramid, either with the full
+ *           h x w x 32 filter (Sec. 2, score equation) or with its CP decomposition (Sec. 4, I o T = sum_r ((I o a_r)
+ *           o b_r) o c_r; joint mode shares a_r, b_r, c_r across the filters of one shape and recombines per filter);
+ *   step 2  generalised distance transform with argmax of every part score map (Sec. 2, argmax equation);
+ *   step 3  shift the transformed part maps to their anchors and add them to the root map (Sec. 2, score equation);
+ *   step 4  keep the positions whose score reaches the threshold tau (Algorithm 1, steps 15-16).
+ *
+ * Conventions shared by every entry point
+ *   - Status: 0 (TDPM_OK) or a negative TDPM_ERR_* code; no C++ exception or abort crosses the ABI. The message of the
+ *     last failure on the calling thread is returned by tdpm_last_error().
+ *   - Features: 32 channels per cell, NHWC FP32 ("[H][W][32]", cell (y, x) channel c at ((y*W)+x)*32+c).
+ *   - Filters: [h][w][32] FP32, same cell/channel order. A filter is correlated at every valid placement: the score
+ *     map of an h x w filter on an H x W level is (H-h+1) x (W-w+1); a level the filter does not fit is skipped.
+ *   - Deformation: d[4] = coefficients of (dx, dx^2, dy, dy^2), displacement = part position - anchor, in part-level
+ *     cells. d[1] and d[3] must be > 0.
+ *   - Pyramid: level j >= lambda holds root positions; its parts are scored on level j - lambda (twice the
+ *     resolution). Part i of a root placed at (y, x) is anchored at (2y + anchor_y, 2x + anchor_x). A root position is
+ *     scored only when the root filter and every anchored part placement lie inside their maps.
+ *   - Ties: the part position is the lexicographically smallest (row, column) among the maximisers.
+ *   - Streams: a `void* stream` is a cudaStream_t (NULL = legacy default stream). Device pointers passed in must stay
+ *     valid until the work enqueued on that stream has completed.
+ *   - Thread safety: one internal mutex per context; calls on one context are serialised.
+ */
+#ifndef TDPM_H
+#define TDPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TDPM_FEAT_DIM 32
+#define TDPM_MAX_PARTS 16
+
+typedef int32_t tdpm_status;
+#define TDPM_OK 0
+#define TDPM_ERR_ARG (-1)      /* bad argument (NULL pointer, out-of-range value) */
+#define TDPM_ERR_SHAPE (-2)    /* inconsistent sizes */
+#define TDPM_ERR_OOM (-3)      /* device memory budget or cudaMalloc exhausted */
+#define TDPM_ERR_CAPACITY (-4) /* caller buffer too small; the required count is still reported */
+#define TDPM_ERR_TIMEOUT (-5)  /* a bounded wait expired */
+#define TDPM_ERR_CUDA (-6)     /* CUDA runtime error */
+#define TDPM_ERR_STATE (-7)    /* unknown id or call out of order */
+#define TDPM_ERR_IO (-8)       /* file error or corrupt factor file */
+
+/* correlation form, Sec. 2 (full filter) and Sec. 4 (CP-decomposed filter) */
+#define TDPM_FORM_FULL 0
+#define TDPM_FORM_DECOMPOSED 1
+
+/* arithmetic of the correlation: operands in FP32, BF16 or FP8 e4m3 (per-tensor scale); FP32 accumulation always */
+#define TDPM_PREC_FP32 0
+#define TDPM_PREC_BF16 1
+#define TDPM_PREC_FP8 2
+
+/* decomposition mode: one CP per filter (Sec. 4, per-filter rank R) or one CP per stacked shape group with shared
+ * factors a_r, b_r, c_r and per-filter weights Lambda[k][r] */
+#define TDPM_DECOMP_PER_FILTER 0
+#define TDPM_DECOMP_JOINT 1
+
+typedef struct tdpm_ctx tdpm_ctx;
+
+/* ---------------------------------------------------------------- model (Sec. 2: root f0, parts f_i, costs d_i) */
+typedef struct {
+    int32_t h, w;
+    const float *data; /* host [h][w][32]; copied by tdpm_load_model */
+} tdpm_filter;
+
+typedef struct {
+    tdpm_filter filter;
+    int32_t anchor_y, anchor_x; /* part-level cells, relative to twice the root position */
+    float deform[4];            /* coefficients of (dx, dx^2, dy, dy^2); deform[1], deform[3] > 0 */
+} tdpm_part;
+
+typedef struct {
+    tdpm_filter root;
+    float bias;
+    int32_t n_parts; /* 0 .. TDPM_MAX_PARTS */
+    const tdpm_part *parts;
+} tdpm_component;
+
+typedef struct {
+    int32_t n_components; /* mixture components (Sec. 2), scored independently */
+    const tdpm_component *components;
+} tdpm_model_desc;
+
+/* ---------------------------------------------------------------- feature pyramid (device memory, caller-owned) */
+typedef struct {
+    int32_t H, W;
+    const float *data; /* device NHWC FP32 [H][W][32] */
+} tdpm_level;
+
+typedef struct {
+    int32_t n_levels;
+    int32_t lambda; /* levels per octave: root level j uses part level j - lambda */
+    const tdpm_level *levels;
+} tdpm_pyramid;
+
+/* ---------------------------------------------------------------- detections (Algorithm 1 result set D) */
+typedef struct {
+    int32_t component, level, y, x; /* root placement (top-left cell) */
+    float score;                    /* s = f0.phi(p0) + sum_i (f_i.phi(p_i) - d_i.psi(p_i, p0)) + bias */
+    int32_t n_parts;
+    int32_t part_y[TDPM_MAX_PARTS], part_x[TDPM_MAX_PARTS]; /* best part placements on level - lambda */
+} tdpm_detection;
+
+typedef struct {
+    int32_t n_groups;       /* shape groups decomposed */
+    int32_t total_rank;     /* sum over groups of the number of rank-1 terms */
+    int32_t total_iters;    /* ALS cycles over all decompositions */
+    double max_rel_error;   /* max over filters of ||f - CP(f)||_F / ||f||_F */
+    double mean_rel_error;  /* mean of the same */
+    double gain;            /* formula (1) over the whole model: full products / decomposed products */
+} tdpm_decomp_report;
+
+/* ================================================================================================= context */
+
+/* Create a context on CUDA device `device`. mem_budget_bytes caps the device memory the context allocates for score
+ * buffers (0 = no cap). The context owns every allocation it makes; tdpm_destroy frees them. */
+tdpm_status tdpm_create(tdpm_ctx **out, int32_t device, size_t mem_budget_bytes);
+void tdpm_destroy(tdpm_ctx *ctx);
+/* Message of the last failed call made by this thread (empty if none). Valid until the thread's next call. */
+const char *tdpm_last_error(void);
+/* Library build string (compiler, architecture). */
+const char *tdpm_version(void);
+
+/* ================================================================================================= model */
+
+/* Copy a model (Sec. 2) to the context: host filters are copied (caller keeps ownership) and uploaded. Filters are
+ * numbered in model order: component 0 root, its parts, component 1 root, ... Filters with the same role (root or
+ * part) and shape form one shape group. Errors: ERR_ARG (NULL, n_parts > TDPM_MAX_PARTS, deform[1] or deform[3] <= 0,
+ * non-positive sizes). */
+tdpm_status tdpm_load_model(tdpm_ctx *ctx, const tdpm_model_desc *desc, int32_t *model_id);
+
+/* n_filters, n_groups of a loaded model. */
+tdpm_status tdpm_model_info(tdpm_ctx *ctx, int32_t model_id, int32_t *n_filters, int32_t *n_groups);
+
+/* Shape group g: role (0 root, 1 part), h, w, number of filters, current rank (0 = not decomposed); filter_ids gets
+ * the model-order ids of its filters (capacity entries at most). */
+tdpm_status tdpm_group_info(tdpm_ctx *ctx, int32_t model_id, int32_t group, int32_t *role, int32_t *h, int32_t *w,
+                            int32_t *n_filters, int32_t *rank, int32_t *filter_ids, int32_t capacity);
+
+/* CP-decompose the model's filters (Sec. 4): host FP64 alternating least squares, one exact least-squares solve per
+ * factor per cycle, stopping after max_iters cycles or when the fit changes by at most tol * ||T||_F. mode
+ * TDPM_DECOMP_PER_FILTER gives every filter `rank` terms (rank >= h*w uses the exact slice decomposition);
+ * TDPM_DECOMP_JOINT gives every shape group `rank` shared terms. The factors are kept in FP64 and uploaded in FP32 and
+ * BF16. Errors: ERR_ARG (rank <= 0, bad mode), ERR_STATE (unknown model). */
+tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_t mode, int32_t max_iters, double tol,
+                           uint64_t seed, tdpm_decomp_report *report);
+
+/* FP64 factors of shape group g: A [h][R], B [w][R], C [32][R], Lambda [n_filters][R] (row-major). Any output may be
+ * NULL. Errors: ERR_STATE (not decomposed). */
+tdpm_status tdpm_get_factors(tdpm_ctx *ctx, int32_t model_id, int32_t group, double *A, double *B, double *C,
+                             double *Lambda);
+
+/* Save / load the decomposition of a model (versioned binary file with FP64 factors and a checksum). Loading checks
+ * that the shapes match the model. Errors: ERR_IO. */
+tdpm_status tdpm_save_factors(tdpm_ctx *ctx, int32_t model_id, const char *path);
+tdpm_status tdpm_load_factors(tdpm_ctx *ctx, int32_t model_id, const char *path);
+
+/* ================================================================================================= scoring */
+
+/* Steps 1-3 for every component and root level of one pyramid: correlation in `form` and `precision`, distance
+ * transform of every part map, shift-and-sum into per-(component, level) score maps. Enqueued on `stream`; returns
+ * before the GPU finishes. The score buffers live in the context until tdpm_release(scores_id).
+ * Errors: ERR_ARG, ERR_STATE (decomposed form before tdpm_decompose), ERR_OOM (budget). */
+tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyr, int32_t form,
+                                      int32_t precision, void *stream, int32_t *scores_id);
+
+/* Step 4: every scored position with s >= tau, ordered by (component, level, y, x), copied to the host array `out`
+ * (capacity records). Blocks until `stream` has finished. *n_out = number of detections, even when it exceeds
+ * capacity (then ERR_CAPACITY and the first `capacity` records are written). */
+tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detection *out, size_t capacity,
+                        size_t *n_out, void *stream);
+
+/* Map kinds for tdpm_get_maps */
+#define TDPM_MAP_FILTER_SCORE 0 /* index_a = filter id, index_b = level: correlation map [H-h+1][W-w+1] FP32 */
+#define TDPM_MAP_FINAL_SCORE 1  /* index_a = component, index_b = root level: score map [Y][X] FP32 */
+#define TDPM_MAP_PART_DT 2      /* index_a = part filter id, index_b = root level: transformed part map at the
+                                   anchored positions [Y][X] FP32 */
+#define TDPM_MAP_PART_ARG 3     /* same indices: argmax (part_y << 16) | part_x, int32 [Y][X] */
+
+/* Copy one map of a scores set to host memory (blocks on `stream`). rows/cols receive its size; a map that was not
+ * computed (filter does not fit, empty domain) has 0 rows. Errors: ERR_CAPACITY (bytes too small), ERR_STATE. */
+tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_t index_a, int32_t index_b,
+                          void *out_host, size_t capacity_bytes, int32_t *rows, int32_t *cols, void *stream);
+
+/* Free a scores set. */
+tdpm_status tdpm_release(tdpm_ctx *ctx, int32_t scores_id);
+
+/* ================================================================================================= stateless ops */
+
+/* Generalised distance transform of one score map (Sec. 2 argmax equation), on device buffers:
+ *   D[i][k] = max_{qy,qx} S[qy][qx] - d . (qx - px, (qx - px)^2, qy - py, (qy - py)^2),
+ *   px = x_off + x_step*k (k < nx), py = y_off + y_step*i (i < ny), both inside the map;
+ *   arg[i][k] = (qy << 16) | qx, the lexicographically smallest maximiser.
+ * S: device [H][W] FP32 (H, W <= 32767); D: device [ny][nx] FP32; arg: device [ny][nx] int32; scratch: device
+ * buffer of at least tdpm_dt_scratch_bytes(H, nx) bytes (intermediate x-pass result), owned by the caller.
+ * Errors: ERR_ARG (d[1] or d[3] <= 0, sampled positions outside the map, NULL pointers). */
+size_t tdpm_dt_scratch_bytes(int32_t H, int32_t nx);
+tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int32_t x_off, int32_t x_step, int32_t nx,
+                    int32_t y_off, int32_t y_step, int32_t ny, float *D, int32_t *arg, void *scratch, void *stream);
+
+/* Correlation of K filters of one shape with one feature level (step 1, Sec. 2), on device buffers:
+ *   out[k][y][x] = sum_{dy<h,dx<w,c<32} filt[k][dy][dx][c] * feat[y+dy][x+dx][c], y < H-h+1, x < W-w+1.
+ * feat: device NHWC FP32; filt: HOST [K][h][w][32] FP32 (uploaded per call); out: device [K][H-h+1][W-w+1] FP32.
+ * precision FP32 runs the FP32 SIMT kernel, BF16 the tcgen05 tensor-core kernel on BF16-rounded operands. */
+tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float *filt_host, int32_t K, int32_t h,
+                           int32_t w, int32_t precision, float *out, void *stream);
+
+/* ================================================================================================= instrumentation */
+
+/* Number of CUDA kernels this process has launched through the library (all contexts). */
+uint64_t tdpm_kernel_launches(void);
+
+/* When enabled, every stage the context enqueues is bracketed by CUDA events recorded on the stage's own stream, and
+ * the device time is accumulated per stage name ("corr_f32", "zproj", "sep", "dt_x", "dt_y", "assemble", "detect",
+ * ...). Disabled by default. */
+tdpm_status tdpm_profile_enable(tdpm_ctx *ctx, int32_t enable);
+
+/* Stage `index` of the accumulated profile (waits for the recorded events): its name (NUL-terminated, truncated to
+ * name_cap), total device milliseconds and number of launches. *n_stages receives the number of stages; an index out
+ * of range only sets *n_stages. */
+tdpm_status tdpm_profile_read(tdpm_ctx *ctx, int32_t index, char *name, size_t name_cap, double *total_ms,
+                              int64_t *launches, int32_t *n_stages);
+
+/* Clear the accumulated profile. */
+tdpm_status tdpm_profile_reset(tdpm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDPM_H */

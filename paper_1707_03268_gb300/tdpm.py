@@ -1,0 +1,343 @@
+"""ctypes binding of libtdpm (include/tdpm.h): the same entry points, argument marshalling only.
+
+Every step of the scoring path runs in the library's CUDA kernels; this module only converts Python objects (numpy
+host arrays, torch CUDA tensors, streams) into the C structs and pointers, and turns non-zero status codes into
+``TdpmError``. Importing it loads ``_build/libtdpm.so`` and fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+FEAT_DIM = 32
+MAX_PARTS = 16
+
+OK, ERR_ARG, ERR_SHAPE, ERR_OOM, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_STATE, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7, -8
+FORM_FULL, FORM_DECOMPOSED = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+DECOMP_PER_FILTER, DECOMP_JOINT = 0, 1
+MAP_FILTER_SCORE, MAP_FINAL_SCORE, MAP_PART_DT, MAP_PART_ARG = 0, 1, 2, 3
+
+_c_i32 = ctypes.c_int32
+_c_f32p = ctypes.POINTER(ctypes.c_float)
+
+
+class TdpmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tdpm status {status}: {msg}")
+        self.status = status
+
+
+class Filter(ctypes.Structure):
+    _fields_ = [("h", _c_i32), ("w", _c_i32), ("data", _c_f32p)]
+
+
+class Part(ctypes.Structure):
+    _fields_ = [("filter", Filter), ("anchor_y", _c_i32), ("anchor_x", _c_i32), ("deform", ctypes.c_float * 4)]
+
+
+class Component(ctypes.Structure):
+    _fields_ = [("root", Filter), ("bias", ctypes.c_float), ("n_parts", _c_i32), ("parts", ctypes.POINTER(Part))]
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("n_components", _c_i32), ("components", ctypes.POINTER(Component))]
+
+
+class Level(ctypes.Structure):
+    _fields_ = [("H", _c_i32), ("W", _c_i32), ("data", ctypes.c_void_p)]
+
+
+class PyramidDesc(ctypes.Structure):
+    _fields_ = [("n_levels", _c_i32), ("lambda_", _c_i32), ("levels", ctypes.POINTER(Level))]
+
+
+class Detection(ctypes.Structure):
+    _fields_ = [("component", _c_i32), ("level", _c_i32), ("y", _c_i32), ("x", _c_i32), ("score", ctypes.c_float),
+                ("n_parts", _c_i32), ("part_y", _c_i32 * MAX_PARTS), ("part_x", _c_i32 * MAX_PARTS)]
+
+
+class DecompReport(ctypes.Structure):
+    _fields_ = [("n_groups", _c_i32), ("total_rank", _c_i32), ("total_iters", _c_i32),
+                ("max_rel_error", ctypes.c_double), ("mean_rel_error", ctypes.c_double), ("gain", ctypes.c_double)]
+
+
+DETECTION_DTYPE = np.dtype([("component", np.int32), ("level", np.int32), ("y", np.int32), ("x", np.int32),
+                            ("score", np.float32), ("n_parts", np.int32), ("part_y", np.int32, MAX_PARTS),
+                            ("part_x", np.int32, MAX_PARTS)])
+assert DETECTION_DTYPE.itemsize == ctypes.sizeof(Detection)
+
+# every symbol include/tdpm.h declares, with (restype, argtypes)
+_VP = ctypes.c_void_p
+SIGNATURES = {
+    "tdpm_create": (_c_i32, [ctypes.POINTER(_VP), _c_i32, ctypes.c_size_t]),
+    "tdpm_destroy": (None, [_VP]),
+    "tdpm_last_error": (ctypes.c_char_p, []),
+    "tdpm_version": (ctypes.c_char_p, []),
+    "tdpm_load_model": (_c_i32, [_VP, ctypes.POINTER(ModelDesc), ctypes.POINTER(_c_i32)]),
+    "tdpm_model_info": (_c_i32, [_VP, _c_i32, ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i32)]),
+    "tdpm_group_info": (_c_i32, [_VP, _c_i32, _c_i32] + [ctypes.POINTER(_c_i32)] * 6 + [_c_i32]),
+    "tdpm_decompose": (_c_i32, [_VP, _c_i32, _c_i32, _c_i32, _c_i32, ctypes.c_double, ctypes.c_uint64,
+                                ctypes.POINTER(DecompReport)]),
+    "tdpm_get_factors": (_c_i32, [_VP, _c_i32, _c_i32] + [ctypes.POINTER(ctypes.c_double)] * 4),
+    "tdpm_save_factors": (_c_i32, [_VP, _c_i32, ctypes.c_char_p]),
+    "tdpm_load_factors": (_c_i32, [_VP, _c_i32, ctypes.c_char_p]),
+    "tdpm_build_pyramid_scores": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _c_i32, _VP,
+                                           ctypes.POINTER(_c_i32)]),
+    "tdpm_detect": (_c_i32, [_VP, _c_i32, ctypes.c_float, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _VP]),
+    "tdpm_get_maps": (_c_i32, [_VP, _c_i32, _c_i32, _c_i32, _c_i32, _VP, ctypes.c_size_t, ctypes.POINTER(_c_i32),
+                               ctypes.POINTER(_c_i32), _VP]),
+    "tdpm_release": (_c_i32, [_VP, _c_i32]),
+    "tdpm_dt_scratch_bytes": (ctypes.c_size_t, [_c_i32, _c_i32]),
+    "tdpm_dt": (_c_i32, [_VP, _c_i32, _c_i32, _c_f32p, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _VP, _VP, _VP,
+                         _VP]),
+    "tdpm_correlate": (_c_i32, [_VP, _c_i32, _c_i32, _c_f32p, _c_i32, _c_i32, _c_i32, _c_i32, _VP, _VP]),
+    "tdpm_kernel_launches": (ctypes.c_uint64, []),
+    "tdpm_profile_enable": (_c_i32, [_VP, _c_i32]),
+    "tdpm_profile_read": (_c_i32, [_VP, _c_i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_i32)]),
+    "tdpm_profile_reset": (_c_i32, [_VP]),
+}
+
+_LIB: Optional[ctypes.CDLL] = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtdpm.so (built by ``paper_1707_03268_gb300.build``); raise if it is missing."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libtdpm.so is not built ({_build.LIB}); run __graft_entry__.build() first")
+        L = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(st: int) -> None:
+    if st != OK:
+        raise TdpmError(st, lib().tdpm_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch tensor (or an int)."""
+    return t if isinstance(t, int) else int(t.data_ptr())
+
+
+# --------------------------------------------------------------------------------------------------- context
+def tdpm_create(device: int = 0, mem_budget_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().tdpm_create(ctypes.byref(h), int(device), int(mem_budget_bytes)))
+    return h.value
+
+
+def tdpm_destroy(ctx: int) -> None:
+    lib().tdpm_destroy(ctx)
+
+
+def tdpm_last_error() -> str:
+    return lib().tdpm_last_error().decode(errors="replace")
+
+
+def tdpm_version() -> str:
+    return lib().tdpm_version().decode()
+
+
+# --------------------------------------------------------------------------------------------------- model
+def _filter(arr: np.ndarray, keep: list) -> Filter:
+    a = np.ascontiguousarray(arr, dtype=np.float32)
+    assert a.ndim == 3 and a.shape[2] == FEAT_DIM
+    keep.append(a)
+    return Filter(a.shape[0], a.shape[1], a.ctypes.data_as(_c_f32p))
+
+
+def tdpm_load_model(ctx: int, model) -> int:
+    """Load a model given as an object with ``components`` (each with ``root``, ``parts`` [filt, anchor, deform],
+    ``bias``), e.g. ``synth.Model``."""
+    keep: list = []
+    comps = (Component * len(model.components))()
+    for i, c in enumerate(model.components):
+        parts = (Part * max(1, len(c.parts)))()
+        for k, p in enumerate(c.parts):
+            parts[k] = Part(_filter(p.filt, keep), int(p.anchor[0]), int(p.anchor[1]),
+                            (ctypes.c_float * 4)(*[float(v) for v in p.deform]))
+        keep.append(parts)
+        comps[i] = Component(_filter(c.root, keep), float(c.bias), len(c.parts), parts)
+    desc = ModelDesc(len(model.components), comps)
+    mid = _c_i32()
+    _check(lib().tdpm_load_model(ctx, ctypes.byref(desc), ctypes.byref(mid)))
+    return mid.value
+
+
+def tdpm_model_info(ctx: int, model_id: int) -> Tuple[int, int]:
+    nf, ng = _c_i32(), _c_i32()
+    _check(lib().tdpm_model_info(ctx, model_id, ctypes.byref(nf), ctypes.byref(ng)))
+    return nf.value, ng.value
+
+
+def tdpm_group_info(ctx: int, model_id: int, group: int) -> dict:
+    role, h, w, n, rank = (_c_i32() for _ in range(5))
+    _check(lib().tdpm_group_info(ctx, model_id, group, ctypes.byref(role), ctypes.byref(h), ctypes.byref(w),
+                                 ctypes.byref(n), ctypes.byref(rank), None, 0))
+    ids = (_c_i32 * n.value)()
+    _check(lib().tdpm_group_info(ctx, model_id, group, None, None, None, None, None, ids, n.value))
+    return {"role": role.value, "h": h.value, "w": w.value, "n_filters": n.value, "rank": rank.value,
+            "filter_ids": list(ids)}
+
+
+def tdpm_decompose(ctx: int, model_id: int, rank: int, mode: int = DECOMP_PER_FILTER, max_iters: int = 500,
+                   tol: float = 1e-10, seed: int = 0) -> dict:
+    rep = DecompReport()
+    _check(lib().tdpm_decompose(ctx, model_id, int(rank), int(mode), int(max_iters), float(tol), int(seed),
+                                ctypes.byref(rep)))
+    return {f: getattr(rep, f) for f, _ in DecompReport._fields_}
+
+
+def tdpm_get_factors(ctx: int, model_id: int, group: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:
+    info = tdpm_group_info(ctx, model_id, group)
+    R, h, w, K = info["rank"], info["h"], info["w"], info["n_filters"]
+    A, B, C, Lam = (np.zeros((n, R)) for n in (h, w, FEAT_DIM, K))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().tdpm_get_factors(ctx, model_id, group, A.ctypes.data_as(dp), B.ctypes.data_as(dp),
+                                  C.ctypes.data_as(dp), Lam.ctypes.data_as(dp)))
+    return A, B, C, Lam
+
+
+def tdpm_save_factors(ctx: int, model_id: int, path: str) -> None:
+    _check(lib().tdpm_save_factors(ctx, model_id, path.encode()))
+
+
+def tdpm_load_factors(ctx: int, model_id: int, path: str) -> None:
+    _check(lib().tdpm_load_factors(ctx, model_id, path.encode()))
+
+
+# --------------------------------------------------------------------------------------------------- scoring
+class DevicePyramid:
+    """Levels of a feature pyramid as torch CUDA tensors ([H][W][32] FP32, contiguous) plus lambda."""
+
+    def __init__(self, levels: Sequence, lam: int):
+        self.levels = list(levels)
+        self.lam = int(lam)
+        arr = (Level * len(self.levels))()
+        for i, t in enumerate(self.levels):
+            assert t.dim() == 3 and t.shape[2] == FEAT_DIM and t.is_contiguous() and t.is_cuda
+            arr[i] = Level(int(t.shape[0]), int(t.shape[1]), _ptr(t))
+        self._arr = arr
+        self.desc = PyramidDesc(len(self.levels), self.lam, arr)
+
+
+def tdpm_build_pyramid_scores(ctx: int, model_id: int, pyramid: DevicePyramid, form: int = FORM_FULL,
+                              precision: int = PREC_FP32, stream=None) -> int:
+    sid = _c_i32()
+    _check(lib().tdpm_build_pyramid_scores(ctx, model_id, ctypes.byref(pyramid.desc), int(form), int(precision),
+                                           _stream_ptr(stream), ctypes.byref(sid)))
+    return sid.value
+
+
+def tdpm_detect(ctx: int, scores_id: int, tau: float, capacity: int = 1 << 20, stream=None,
+                out: Optional[np.ndarray] = None) -> np.ndarray:
+    """Detections with score >= tau as a structured array (DETECTION_DTYPE), ordered by (component, level, y, x).
+    Raises TdpmError(ERR_CAPACITY) when more than ``capacity`` exist."""
+    if out is None or out.shape[0] < capacity:
+        out = np.zeros(capacity, dtype=DETECTION_DTYPE)
+    n = ctypes.c_size_t()
+    st = lib().tdpm_detect(ctx, scores_id, float(tau), out.ctypes.data if capacity else None, int(capacity),
+                           ctypes.byref(n), _stream_ptr(stream))
+    _check(st)
+    return out[: n.value]
+
+
+def tdpm_get_maps(ctx: int, scores_id: int, kind: int, index_a: int, index_b: int, stream=None) -> np.ndarray:
+    rows, cols = _c_i32(), _c_i32()
+    st = lib().tdpm_get_maps(ctx, scores_id, kind, index_a, index_b, None, 0, ctypes.byref(rows), ctypes.byref(cols),
+                             _stream_ptr(stream))
+    if rows.value == 0:
+        return np.zeros((0, 0), dtype=np.int32 if kind == MAP_PART_ARG else np.float32)
+    if st not in (OK, ERR_CAPACITY):
+        _check(st)
+    out = np.zeros((rows.value, cols.value), dtype=np.int32 if kind == MAP_PART_ARG else np.float32)
+    _check(lib().tdpm_get_maps(ctx, scores_id, kind, index_a, index_b, out.ctypes.data, out.nbytes,
+                               ctypes.byref(rows), ctypes.byref(cols), _stream_ptr(stream)))
+    return out
+
+
+def tdpm_release(ctx: int, scores_id: int) -> None:
+    _check(lib().tdpm_release(ctx, scores_id))
+
+
+# --------------------------------------------------------------------------------------------------- ops
+def tdpm_dt_scratch_bytes(H: int, nx: int) -> int:
+    return int(lib().tdpm_dt_scratch_bytes(int(H), int(nx)))
+
+
+def tdpm_dt(S, d: Sequence[float], x_off: int, x_step: int, nx: int, y_off: int, y_step: int, ny: int, D, arg,
+            scratch, stream=None) -> None:
+    """Distance transform of device map S (torch [H][W] FP32) into D [ny][nx] FP32 and arg [ny][nx] int32."""
+    H, W = int(S.shape[0]), int(S.shape[1])
+    dd = (ctypes.c_float * 4)(*[float(v) for v in d])
+    _check(lib().tdpm_dt(_ptr(S), H, W, dd, x_off, x_step, nx, y_off, y_step, ny, _ptr(D), _ptr(arg), _ptr(scratch),
+                         _stream_ptr(stream)))
+
+
+def tdpm_correlate(feat, filters: np.ndarray, out, precision: int = PREC_FP32, stream=None) -> None:
+    """out[k] = correlation of filters[k] ([K][h][w][32] host FP32) with the device level feat ([H][W][32])."""
+    f = np.ascontiguousarray(filters, dtype=np.float32)
+    K, h, w, _ = f.shape
+    _check(lib().tdpm_correlate(_ptr(feat), int(feat.shape[0]), int(feat.shape[1]), f.ctypes.data_as(_c_f32p), K, h, w,
+                                int(precision), _ptr(out), _stream_ptr(stream)))
+
+
+def unpack_arg(a: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """Split packed (row << 16) | column argmax values."""
+    a = np.asarray(a, dtype=np.int64)
+    return (a >> 16).astype(np.int32), (a & 0xFFFF).astype(np.int32)
+
+
+# --------------------------------------------------------------------------------------------------- instrumentation
+def tdpm_kernel_launches() -> int:
+    return int(lib().tdpm_kernel_launches())
+
+
+def tdpm_profile_enable(ctx: int, enable: bool = True) -> None:
+    _check(lib().tdpm_profile_enable(ctx, 1 if enable else 0))
+
+
+def tdpm_profile_read(ctx: int) -> dict:
+    """{stage name: (total device ms, launches)} accumulated since the last reset."""
+    n = _c_i32()
+    _check(lib().tdpm_profile_read(ctx, -1, None, 0, None, None, ctypes.byref(n)))
+    out = {}
+    for i in range(n.value):
+        name = ctypes.create_string_buffer(64)
+        ms, cnt = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().tdpm_profile_read(ctx, i, name, 64, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(n)))
+        out[name.value.decode()] = (ms.value, cnt.value)
+    return out
+
+
+def tdpm_profile_reset(ctx: int) -> None:
+    _check(lib().tdpm_profile_reset(ctx))

@@ -1,0 +1,315 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the same seeded inputs.
+
+Tolerances (from the arithmetic): FP32 scores within 1e-5 of max |score|; BF16 operands with FP32 accumulation
+within 1e-2; distance-transform argmax bit-exact on the strict suite (integer maps, power-of-two costs: every
+operation is exact in FP32) and, on general maps, equal to the oracle's except where the oracle's own values of the
+two choices are within FP32 rounding (ties); detections at >= 99.5% position agreement.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from helpers import agreement, check_argmax, det_keys, device_pyramid, rel_err
+from oracle import oracle as orc
+from paper_1707_03268_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def T(torch):
+    from paper_1707_03268_gb300 import tdpm
+    return tdpm
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    c = T.tdpm_create(0)
+    yield c
+    T.tdpm_destroy(c)
+
+
+def _tau(name):
+    with open(os.path.join(GOLDEN, "thresholds.json")) as f:
+        return json.load(f)[name]["tau"]
+
+
+# ------------------------------------------------------------------------------------------------ step 1 kernels
+@pytest.mark.parametrize("H,W,h,w,K", [(13, 29, 6, 6, 3), (30, 40, 6, 11, 1), (60, 80, 6, 6, 8), (9, 17, 5, 11, 70),
+                                       (40, 16, 7, 7, 65), (11, 5, 11, 5, 2), (1, 40, 1, 3, 4)])
+def test_correlate_fp32_matches_oracle(torch, T, H, W, h, w, K):
+    rng = np.random.default_rng(H * 1000 + W * 10 + K)
+    feat = rng.uniform(0, 0.2, size=(H, W, 32)).astype(np.float32)
+    filt = rng.normal(0, 0.05, size=(K, h, w, 32)).astype(np.float32)
+    out = torch.full((K, H - h + 1, W - w + 1), float("nan"), device="cuda")
+    T.tdpm_correlate(torch.from_numpy(feat).cuda(), filt, out)
+    got = out.cpu().numpy()
+    for k in range(K):
+        ref = orc.correlate(feat, filt[k])
+        assert rel_err(got[k], ref) <= 1e-5, k
+
+
+# ------------------------------------------------------------------------------------------------ step 2 kernels
+def _run_dt(torch, T, S, d, x_off=0, x_step=1, nx=None, y_off=0, y_step=1, ny=None):
+    H, W = S.shape
+    nx = nx if nx is not None else (W - x_off + x_step - 1) // x_step
+    ny = ny if ny is not None else (H - y_off + y_step - 1) // y_step
+    Sd = torch.from_numpy(np.ascontiguousarray(S, dtype=np.float32)).cuda()
+    D = torch.empty((ny, nx), device="cuda")
+    A = torch.empty((ny, nx), dtype=torch.int32, device="cuda")
+    scratch = torch.empty(T.tdpm_dt_scratch_bytes(H, nx), dtype=torch.uint8, device="cuda")
+    T.tdpm_dt(Sd, d, x_off, x_step, nx, y_off, y_step, ny, D, A, scratch)
+    torch.cuda.synchronize()
+    gy, gx = T.unpack_arg(A.cpu().numpy())
+    return D.cpu().numpy(), gy, gx, (x_off, x_step, nx, y_off, y_step, ny)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 37), (45, 1), (7, 9), (33, 70), (64, 31), (75, 120)])
+def test_dt_strict_suite_bit_exact(torch, T, H, W):
+    rng = np.random.default_rng(H * 7 + W)
+    for trial in range(3):
+        S = synth.make_integer_map(rng, H, W)
+        d = synth.make_pow2_deform(rng)
+        Do, Iy, Ix = orc.dt2d(S.astype(np.float64), d.astype(np.float64))
+        for (xo, xs, yo, ys) in [(0, 1, 0, 1), (1, 2, 0, 2), (W // 3, 3, H // 2, 1)]:
+            if xo >= W or yo >= H:
+                continue
+            D, gy, gx, (xo, xs, nx, yo, ys, ny) = _run_dt(torch, T, S, d, xo, xs, None, yo, ys, None)
+            ys_idx = yo + ys * np.arange(ny)
+            xs_idx = xo + xs * np.arange(nx)
+            np.testing.assert_array_equal(D.astype(np.float64), Do[np.ix_(ys_idx, xs_idx)])
+            np.testing.assert_array_equal(gy, Iy[np.ix_(ys_idx, xs_idx)])
+            np.testing.assert_array_equal(gx, Ix[np.ix_(ys_idx, xs_idx)])
+
+
+@pytest.mark.parametrize("H,W", [(55, 75), (90, 160), (8, 300), (300, 9)])
+def test_dt_float_maps_match_oracle(torch, T, H, W):
+    rng = np.random.default_rng(H + 3 * W)
+    S = rng.normal(0, 1.0, size=(H, W)).astype(np.float32)
+    for d in [rng.uniform(0.001, 0.1, 4), np.array([-0.05, 0.002, 0.03, 0.001]), np.array([0.5, 3.0, -0.2, 2.0])]:
+        d = d.astype(np.float32)
+        d64 = d.astype(np.float64)
+        Do, Iy, Ix = orc.dt2d(S.astype(np.float64), d64)
+        D, gy, gx, _ = _run_dt(torch, T, S, d)
+        assert np.max(np.abs(D - Do)) <= 1e-5 * max(1.0, np.max(np.abs(Do)))
+        py, px = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+        ties, bad = check_argmax(S.astype(np.float64), d64, gy, gx, Iy, Ix, py, px)
+        assert bad == 0, (ties, bad)
+
+
+def test_dt_fed_oracle_score_maps(torch, T):
+    """The transform fed the oracle's own part score maps (rounded to FP32) returns the oracle's argmax."""
+    wl = synth.config_c1()
+    comp = wl.model.components[0]
+    part_level = wl.pyramids[0].levels[0]
+    total_ties = 0
+    for p in comp.parts:
+        S = orc.correlate(part_level, p.filt).astype(np.float32)
+        d64 = p.deform.astype(np.float64)
+        Do, Iy, Ix = orc.dt2d(S.astype(np.float64), d64)
+        D, gy, gx, _ = _run_dt(torch, T, S, p.deform)
+        H, W = S.shape
+        py, px = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+        ties, bad = check_argmax(S.astype(np.float64), d64, gy, gx, Iy, Ix, py, px)
+        assert bad == 0
+        total_ties += ties
+        assert np.max(np.abs(D - Do)) <= 1e-5 * np.max(np.abs(Do))
+    assert total_ties <= 0.001 * 8 * S.size
+
+
+def test_dt_rejects_bad_arguments(torch, T):
+    S = torch.zeros((4, 4), device="cuda")
+    D = torch.zeros((4, 4), device="cuda")
+    A = torch.zeros((4, 4), dtype=torch.int32, device="cuda")
+    sc = torch.zeros(T.tdpm_dt_scratch_bytes(4, 4), dtype=torch.uint8, device="cuda")
+    with pytest.raises(T.TdpmError):
+        T.tdpm_dt(S, [0.1, 0.0, 0.1, 0.1], 0, 1, 4, 0, 1, 4, D, A, sc)
+    with pytest.raises(T.TdpmError):
+        T.tdpm_dt(S, [0.1, 0.1, 0.1, 0.1], 1, 1, 4, 0, 1, 4, D, A, sc)
+
+
+# ------------------------------------------------------------------------------------------------ whole path
+def _compare_pipeline(torch, T, ctx, wl, form, prec, filters=None, score_tol=1e-5, tau=None, model_id=None,
+                      check_parts=True, min_agree=0.995):
+    pyr = wl.pyramids[0]
+    mid = model_id if model_id is not None else T.tdpm_load_model(ctx, wl.model)
+    dp = device_pyramid(pyr, torch)
+    sid = T.tdpm_build_pyramid_scores(ctx, mid, dp, form, prec)
+    scored = orc.score_pyramid(wl.model, pyr, filters=filters)
+    worst = 0.0
+    for m in scored:
+        got = T.tdpm_get_maps(ctx, sid, T.MAP_FINAL_SCORE, m["component"], m["level"])
+        assert got.shape == m["score"].shape
+        worst = max(worst, rel_err(got, m["score"]))
+    assert worst <= score_tol, worst
+    if tau is None:
+        tau = float(np.percentile(orc.all_scores(scored), 99))
+    ref = orc.detect(scored, tau)
+    dets = T.tdpm_detect(ctx, sid, tau)
+    agree = agreement(det_keys(dets), det_keys(ref))
+    assert agree >= min_agree, agree
+    bad_parts = 0
+    if check_parts:
+        ref_by_key = {d[:4]: d for d in ref}
+        fid = 0
+        part_fid = {}
+        for c, comp in enumerate(wl.model.components):
+            for i in range(len(comp.parts)):
+                part_fid[(c, i)] = fid + 1 + i
+            fid += 1 + len(comp.parts)
+        for d in dets:
+            key = (int(d["component"]), int(d["level"]), int(d["y"]), int(d["x"]))
+            if key not in ref_by_key:
+                continue
+            r = ref_by_key[key]
+            comp = wl.model.components[key[0]]
+            for i, p in enumerate(comp.parts):
+                gy, gx = int(d["part_y"][i]), int(d["part_x"][i])
+                if (gy, gx) == (r[5][i], r[6][i]):
+                    continue
+                pf = p.filt if filters is None else filters[part_fid[(key[0], i)]]
+                S = orc.correlate(pyr.levels[key[1] - pyr.lam], pf)
+                ay, ax = 2 * key[2] + p.anchor[0], 2 * key[3] + p.anchor[1]
+                dd = p.deform.astype(np.float64)
+                dv = lambda qy, qx: S[qy, qx] - (dd[0] * (qx - ax) + dd[1] * (qx - ax) ** 2 + dd[2] * (qy - ay) +
+                                                 dd[3] * (qy - ay) ** 2)
+                if dv(r[5][i], r[6][i]) - dv(gy, gx) > score_tol * max(1.0, abs(dv(r[5][i], r[6][i]))) * 10:
+                    bad_parts += 1
+    assert bad_parts == 0
+    T.tdpm_release(ctx, sid)
+    return mid, worst, agree
+
+
+def test_c1_full_fp32_end_to_end(torch, T, ctx):
+    wl = synth.config_c1()
+    mid, worst, agree = _compare_pipeline(torch, T, ctx, wl, T.FORM_FULL, T.PREC_FP32, tau=_tau("c1"))
+    # filter maps themselves
+    dp = device_pyramid(wl.pyramids[0], torch)
+    sid = T.tdpm_build_pyramid_scores(ctx, mid, dp, T.FORM_FULL, T.PREC_FP32)
+    root = T.tdpm_get_maps(ctx, sid, T.MAP_FILTER_SCORE, 0, 1)
+    assert rel_err(root, orc.correlate(wl.pyramids[0].levels[1], wl.model.components[0].root)) <= 1e-5
+    for i, p in enumerate(wl.model.components[0].parts):
+        got = T.tdpm_get_maps(ctx, sid, T.MAP_FILTER_SCORE, 1 + i, 0)
+        assert rel_err(got, orc.correlate(wl.pyramids[0].levels[0], p.filt)) <= 1e-5
+    T.tdpm_release(ctx, sid)
+
+
+def test_c2_full_fp32_end_to_end(torch, T, ctx):
+    wl = synth.config_c2()
+    _compare_pipeline(torch, T, ctx, wl, T.FORM_FULL, T.PREC_FP32, tau=_tau("c2"))
+
+
+def _factor_filters(T, ctx, mid, model):
+    """Filters rebuilt by the oracle from the library's exported FP64 factors (model order)."""
+    n_f, n_g = T.tdpm_model_info(ctx, mid)
+    out = [None] * n_f
+    for g in range(n_g):
+        info = T.tdpm_group_info(ctx, mid, g)
+        A, B, C, Lam = T.tdpm_get_factors(ctx, mid, g)
+        F = orc.joint_reconstruct(Lam, A, B, C)
+        for k, fid in enumerate(info["filter_ids"]):
+            out[fid] = F[k]
+    return out
+
+
+@pytest.mark.parametrize("rank,mode", [(4, 0), (8, 0), (3, 1), (16, 1)])
+def test_c1_decomposed_fp32_matches_oracle_on_same_factors(torch, T, ctx, rank, mode):
+    wl = synth.config_c1()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    rep = T.tdpm_decompose(ctx, mid, rank, mode, max_iters=200, seed=5)
+    assert rep["max_rel_error"] < 1.0
+    filters = _factor_filters(T, ctx, mid, wl.model)
+    _compare_pipeline(torch, T, ctx, wl, T.FORM_DECOMPOSED, T.PREC_FP32, filters=filters, model_id=mid)
+
+
+def test_c2_decomposed_bf16_matches_oracle_on_same_factors(torch, T, ctx):
+    wl = synth.config_c2()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    T.tdpm_decompose(ctx, mid, 8, T.DECOMP_PER_FILTER, max_iters=100, seed=1)
+    filters = _factor_filters(T, ctx, mid, wl.model)
+    _compare_pipeline(torch, T, ctx, wl, T.FORM_DECOMPOSED, T.PREC_BF16, filters=filters, model_id=mid,
+                      score_tol=1e-2, check_parts=False, min_agree=0.95)
+
+
+def test_full_rank_decomposition_equals_full_form(torch, T, ctx):
+    wl = synth.config_c1()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    rep = T.tdpm_decompose(ctx, mid, 10 ** 6, T.DECOMP_PER_FILTER)
+    assert rep["max_rel_error"] <= 1e-7
+    _compare_pipeline(torch, T, ctx, wl, T.FORM_DECOMPOSED, T.PREC_FP32, model_id=mid, tau=_tau("c1"))
+
+
+def test_detect_thresholds_and_capacity(torch, T, ctx):
+    wl = synth.config_c1()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    sid = T.tdpm_build_pyramid_scores(ctx, mid, device_pyramid(wl.pyramids[0], torch))
+    scored = orc.score_pyramid(wl.model, wl.pyramids[0])
+    n_all = sum(m["score"].size for m in scored)
+    assert len(T.tdpm_detect(ctx, sid, -math.inf)) == n_all
+    assert len(T.tdpm_detect(ctx, sid, math.inf)) == 0
+    with pytest.raises(T.TdpmError) as ei:
+        T.tdpm_detect(ctx, sid, -math.inf, capacity=10)
+    assert ei.value.status == T.ERR_CAPACITY
+    T.tdpm_release(ctx, sid)
+
+
+def test_levels_too_small_are_skipped(torch, T, ctx):
+    rng = np.random.default_rng(3)
+    comp = synth.make_component(rng, (6, 11), [(6, 6)] * 2)
+    pyr = synth.make_pyramid(rng, [(12, 20), (5, 9), (6, 10)], lam=1)  # level 1 too small for the root
+    model = synth.Model([comp])
+    mid = T.tdpm_load_model(ctx, model)
+    sid = T.tdpm_build_pyramid_scores(ctx, mid, device_pyramid(pyr, torch))
+    scored = orc.score_pyramid(model, pyr)
+    for j in (1, 2):
+        got = T.tdpm_get_maps(ctx, sid, T.MAP_FINAL_SCORE, 0, j)
+        ref = [m for m in scored if m["level"] == j]
+        assert got.shape == (ref[0]["score"].shape if ref else (0, 0))
+    T.tdpm_release(ctx, sid)
+
+
+def test_library_decomposition_matches_oracle_als_on_planted_rank(torch, T, ctx):
+    """Both ALS implementations reach the planted tensor (relative errors agree within 1e-6)."""
+    rng = np.random.default_rng(8)
+    R = 3
+    U = [rng.standard_normal((n, R)) for n in (6, 6, 32)]
+    F = (orc.cp_reconstruct(np.ones(R), U) * 0.02).astype(np.float32)
+    comp = synth.Component(root=F, parts=[], bias=0.0)
+    mid = T.tdpm_load_model(ctx, synth.Model([comp]))
+    rep = T.tdpm_decompose(ctx, mid, R, T.DECOMP_PER_FILTER, max_iters=2000, tol=0.0, seed=2)
+    w, V, _ = orc.cp_als(F, R, max_iters=2000, tol=0.0, eps=1e-13, seed=2)
+    e_orc = np.linalg.norm(F - orc.cp_reconstruct(w, V)) / np.linalg.norm(F)
+    assert abs(rep["max_rel_error"] - e_orc) <= 1e-6
+
+
+def test_save_and_load_factors_roundtrip(torch, T, ctx, tmp_path):
+    wl = synth.config_c1()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    T.tdpm_decompose(ctx, mid, 4, T.DECOMP_PER_FILTER, max_iters=50)
+    path = str(tmp_path / "f.bin")
+    T.tdpm_save_factors(ctx, mid, path)
+    before = [T.tdpm_get_factors(ctx, mid, g) for g in range(T.tdpm_model_info(ctx, mid)[1])]
+    mid2 = T.tdpm_load_model(ctx, wl.model)
+    T.tdpm_load_factors(ctx, mid2, path)
+    after = [T.tdpm_get_factors(ctx, mid2, g) for g in range(T.tdpm_model_info(ctx, mid2)[1])]
+    for a, b in zip(before, after):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+    with open(path, "r+b") as f:
+        f.seek(40)
+        f.write(b"\x01\x02")
+    with pytest.raises(T.TdpmError):
+        T.tdpm_load_factors(ctx, mid2, path)
