@@ -1,0 +1,322 @@
+// Step 1 on the 5th-generation tensor cores (tcgen05, sm_103a): BF16 operands, FP32 accumulation in TMEM.
+//
+// One kernel serves two contractions of the path:
+//   * full correlation (Sec. 2 score equation): S[k][y][x] = sum_{dy,dx,c} F_k[dy][dx][c] phi[y+dy][x+dx][c], an
+//     implicit GEMM with M = positions, N = filters, K = taps x 32 channels, walked tap by tap;
+//   * the channel stage of the decomposed form (Sec. 4, correlation with c_r): Z[r][cell] = sum_c C[c][r] phi[cell][c],
+//     the same kernel with a single 1x1 tap and N = rank-1 terms.
+//
+// Positions are flattened over the full level width (p = y*W + x, so a 128-row M tile is one contiguous run of cells
+// and rows with x >= W-w+1 are computed and dropped). Features are stored as BF16 in a channel-chunk-planar layout
+// [4][H*W][8] (16 bytes per cell per chunk): a TMA box {8 ch, 128 cells, 4 chunks} at cell p0 + dy*W + dx lands in
+// shared memory as the no-swizzle K-major canonical layout of the A operand (core matrix = 8 cells x 16 bytes;
+// 8-row groups 128 bytes apart, K chunks 2048 bytes apart). Filter taps are stored [tap][4][N][8] and each tap's
+// N-tile slice is fetched with four 1-D bulk copies into the same layout for B. One thread issues the copies, one
+// issues the MMAs, and all four warps drain TMEM (32x32b loads) and store coalesced rows of the output maps.
+// Every mbarrier wait is bounded: on expiry the kernel raises the context's error flag and carries on to a clean exit.
+#include <cuda.h>
+
+#include "internal.h"
+
+namespace tdpm {
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_THREADS = 128;
+constexpr int TC_STAGES = 4;
+constexpr uint32_t A_STAGE_BYTES = TC_M * 64;  // 128 cells x 32 channels x 2 bytes
+constexpr uint32_t A_PLANE_BYTES = TC_M * 16;  // one 8-channel chunk of 128 cells
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with `parity` to complete; give up after ~2^31 cycles (about a second), raising *err.
+__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int *err)
+{
+    if (mbar_try_wait(bar, parity)) return;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1ll << 31)) {
+            atomicExch(err, 1);
+            return;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor, no swizzle, K-major: lbo = byte distance between core matrices along K,
+// sbo = byte distance between 8-row core-matrix groups along M (or N).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <class Job>
+__device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].begin <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// grid: one CTA per (job, M tile, N tile); filt: [taps][4][Npad][8] BF16; NT = N tile width (multiple of 16, <= 256)
+__global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__restrict__ jobs, int n_jobs,
+                                                                const uint16_t *__restrict__ filt, int K, int Npad,
+                                                                int NT, int n_tiles_n, int h, int w, uint32_t tmem_cols,
+                                                                int *err)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const uint32_t b_stage_bytes = (uint32_t)NT * 64;
+    uint8_t *a_smem = sm;
+    uint8_t *b_smem = sm + TC_STAGES * A_STAGE_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + TC_STAGES * b_stage_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * TC_STAGES + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES), done = smem_u32(bars + 2 * TC_STAGES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ji = find_job(jobs, n_jobs, blockIdx.x);
+    const TcJob *J = jobs + ji;
+    const int local = blockIdx.x - J->begin;
+    const int nt = local % n_tiles_n, mt = local / n_tiles_n;
+    const int p0 = mt * TC_M, n0 = nt * NT;
+    const int W = J->W, Ho = J->Ho, Wo = J->Wo;
+    const int taps = h * w;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer: one A box and four B chunk copies per tap
+        for (int t = 0; t < taps; ++t) {
+            const int s = t % TC_STAGES;
+            if (t >= TC_STAGES) mbar_wait(empty0 + 8 * s, ((t / TC_STAGES) - 1) & 1, err);
+            const uint32_t full = full0 + 8 * s;
+            mbar_expect_tx(full, A_STAGE_BYTES + b_stage_bytes);
+            const int dy = t / w, dx = t - dy * w;
+            tma_load_3d(smem_u32(a_smem + s * A_STAGE_BYTES), &J->tmap, 0, p0 + dy * W + dx, 0, full);
+            const uint32_t bdst = smem_u32(b_smem + s * b_stage_bytes);
+            for (int kc = 0; kc < 4; ++kc)
+                bulk_load(bdst + kc * NT * 16, filt + (((size_t)t * 4 + kc) * Npad + n0) * 8, (uint32_t)NT * 16, full);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: two K=16 steps per tap (channel chunks {0,1} and {2,3})
+        const uint32_t idesc = instr_desc(TC_M, NT);
+        for (int t = 0; t < taps; ++t) {
+            const int s = t % TC_STAGES;
+            mbar_wait(full0 + 8 * s, (t / TC_STAGES) & 1, err);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_base = smem_u32(a_smem + s * A_STAGE_BYTES);
+            const uint32_t b_base = smem_u32(b_smem + s * b_stage_bytes);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t ad = smem_desc(a_base + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
+                const uint64_t bd = smem_desc(b_base + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
+                mma_bf16(tmem, ad, bd, idesc, (t | ks) != 0);
+            }
+            mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(done);
+    }
+    __syncwarp();
+
+    // epilogue: TMEM lane m holds position p0 + m; columns are the N tile's filters
+    mbar_wait(done, 0, err);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int p = p0 + warp * 32 + lane;
+    const int y = p / W, x = p - y * W;
+    const bool valid = (y < Ho) && (x < Wo);
+    float *out = J->out + (size_t)y * Wo + x;
+    const size_t plane = (size_t)Ho * Wo;
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int k = n0 + c0 + j;
+                if (k < K) out[(size_t)k * plane] = __uint_as_float(r[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// FP32 NHWC [cells][32] -> BF16 [4][cells][8]: one thread per (cell, chunk)
+__global__ void to_bf16_planar_kernel(const float *__restrict__ src, uint16_t *__restrict__ dst, long long cells)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cells * 4) return;
+    const long long cell = i >> 2;
+    const int kc = (int)(i & 3);
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(src + cell * FD + kc * 8));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(src + cell * FD + kc * 8 + 4));
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t wv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v[2 * j]), hi = __float2bfloat16_rn(v[2 * j + 1]);
+        wv[j] = (uint32_t)(*reinterpret_cast<const uint16_t *>(&lo)) |
+                ((uint32_t)(*reinterpret_cast<const uint16_t *>(&hi)) << 16);
+    }
+    *reinterpret_cast<uint4 *>(dst + ((size_t)kc * cells + cell) * 8) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+}
+
+}  // namespace
+
+int corr_tc_tile_m() { return TC_M; }
+
+int corr_tc_n_tile(int Npad) { return Npad / ((Npad + 255) / 256); }
+
+size_t corr_tc_smem_bytes(int NT) { return TC_STAGES * (A_STAGE_BYTES + (size_t)NT * 64) + 8 * (2 * TC_STAGES + 1) + 16; }
+
+cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc, int K, int Npad,
+                           int h, int w, int *d_err, cudaStream_t s)
+{
+    if (total_tiles <= 0) return cudaSuccess;
+    const int n_tiles_n = (Npad + 255) / 256;
+    const int NT = Npad / n_tiles_n;
+    if (NT % 16 != 0 || NT < 16 || NT > 256 || NT * n_tiles_n != Npad) return cudaErrorInvalidValue;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)NT) cols <<= 1;
+    // keep residency within TMEM: at most 512 / cols CTAs per SM, enforced through the shared memory request
+    const int max_ctas = 512 / (int)cols;
+    size_t smem = corr_tc_smem_bytes(NT);
+    const size_t floor_bytes = 233472 / (size_t)(max_ctas + 1);
+    if (smem < floor_bytes) smem = floor_bytes;
+    if (smem > 232448) smem = 232448;
+    cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    corr_tc_kernel<<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, K, Npad, NT, n_tiles_n, h, w, cols,
+                                                         d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16_planar(const float *src, uint16_t *dst, long long cells, cudaStream_t s)
+{
+    if (cells <= 0) return cudaSuccess;
+    note_launches(1);
+    to_bf16_planar_kernel<<<(unsigned)((cells * 4 + 255) / 256), 256, 0, s>>>(src, dst, cells);
+    return cudaGetLastError();
+}
+
+// Tensor map over one BF16 planar level: dims {8 channels, cells, 4 chunks}, box {8, 128, 4}, zero fill outside.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells)
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return false;
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    const cuuint64_t dims[3] = {8, (cuuint64_t)cells, 4};
+    const cuuint64_t strides[2] = {16, (cuuint64_t)cells * 16};
+    const cuuint32_t box[3] = {8, (cuuint32_t)TC_M, 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t *>(planar), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tdpm
