@@ -39,7 +39,7 @@ L2_BYTES = 129 * 1024 * 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tdpm", choices=["tdpm", "reference"])
     ap.add_argument("--form", default="decomposed", choices=["decomposed", "full"])
@@ -116,8 +116,13 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
         groups.setdefault((0,) + comp.root.shape[:2], []).append(comp.root)
         for p in comp.parts:
             groups.setdefault((1,) + p.filt.shape[:2], []).append(p.filt)
-    fb = 2 if precision == "bf16" else 4
-    out = {"corr_f32": [0, 0], "zproj": [0, 0], "sep": [0, 0], "dt": [0, 0], "assemble": [0, 0]}
+    bf = precision == "bf16"
+    fb = 2 if bf else 4
+    corr = "corr_tc" if bf else "corr_f32"
+    zproj = "zproj_tc" if bf else "zproj_f32"
+    out = {corr: [0, 0], zproj: [0, 0], "sep": [0, 0], "dt": [0, 0], "assemble": [0, 0], "to_bf16": [0, 0]}
+    if bf:
+        out["to_bf16"][0] = sum(H * W * 32 * (4 + 2) for (H, W) in sizes)
     for (role, h, w), fl in groups.items():
         K = len(fl)
         R = (rank * K if not joint else rank) if rank < h * w else h * w * K
@@ -128,11 +133,11 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
             if Ho <= 0 or Wo <= 0:
                 continue
             if form == "full":
-                out["corr_f32"][0] += H * W * 32 * 4 + K * Ho * Wo * 4
-                out["corr_f32"][1] += 2 * h * w * 32 * K * Ho * Wo
+                out[corr][0] += H * W * 32 * fb + K * Ho * Wo * 4
+                out[corr][1] += 2 * h * w * 32 * K * Ho * Wo
             else:
-                out["zproj"][0] += H * W * 32 * fb + R * H * W * 4
-                out["zproj"][1] += 2 * 32 * R * H * W
+                out[zproj][0] += H * W * 32 * fb + R * H * W * 4
+                out[zproj][1] += 2 * 32 * R * H * W
                 out["sep"][0] += R * H * W * 4 + K * Ho * Wo * 4
                 per_filter_terms = R if joint else R // K
                 out["sep"][1] += 2 * K * Ho * Wo * per_filter_terms * (h + w + 1)
@@ -167,6 +172,42 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
 def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     """FP32 FMA roofline: 152 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+TENSOR_STAGES = ("corr_tc", "zproj_tc")
+ALU_STAGES = ("corr_f32", "zproj_f32", "sep")
+
+
+def stage_roofline(name, ms_per_image, launches_per_image, model, peaks, sm_mhz):
+    """Roofline of one stage: achieved algorithmic throughput against the peak of whichever resource binds it
+    (the one whose peak would take longest for the stage's algorithmic bytes or flops)."""
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    src_hbm = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
+    b, f = model[name]["bytes"], model[name]["flops"]
+    s = ms_per_image / 1e3
+    t_hbm = b / (hbm * 1e9)
+    cand = [("hbm", t_hbm)]
+    if name in TENSOR_STAGES:
+        tp = float(peaks.get("bf16_tflops", 1900.0))
+        cand.append(("tensor", f / (tp * 1e12)))
+    elif name in ALU_STAGES:
+        cand.append(("alu", f / (fp32_alu_peak_tflops(sm_mhz) * 1e12)))
+    bound = max(cand, key=lambda c: c[1])[0]
+    out = {"kernel": name, "bound": bound, "launches_per_image": launches_per_image, "ms_per_image": ms_per_image,
+           "traffic": None, "algorithmic_bytes_per_image": b, "algorithmic_flops_per_image": f}
+    if bound == "hbm":
+        out.update(achieved=b / s / 1e9, peak=hbm, unit="GB/s", peak_source=src_hbm)
+    elif bound == "tensor":
+        tp = float(peaks.get("bf16_tflops", 1900.0))
+        out.update(achieved=f / s / 1e12, peak=tp, unit="TFLOP/s",
+                   peak_source="MEASURED_PEAKS.json bf16_tflops burst (of measured)" if "bf16_tflops" in peaks
+                   else "fallback 1900 TFLOP/s")
+    else:
+        pk = fp32_alu_peak_tflops(sm_mhz)
+        out.update(achieved=f / s / 1e12, peak=pk, unit="TFLOP/s",
+                   peak_source="derived: 152 SM x 128 FP32 lanes x 2 flop x median SM clock under load")
+    out["frac"] = out["achieved"] / out["peak"]
+    return out
 
 
 # ------------------------------------------------------------------------------------------------ reference arm
@@ -327,22 +368,11 @@ def main():
             peaks = json.load(f)
     except Exception:
         pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     steps_prof = prof_run_steps(prof_run)
-    stage_s = dom_ms / steps_prof / 1e3  # device time of the stage per image
-    if dom_name in model and dom_name != "corr_f32":
-        achieved = model[dom_name]["bytes"] / stage_s / 1e9
-        roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": None, "launches_per_image": dom_n / steps_prof,
-                    "algorithmic_bytes_per_image": model[dom_name]["bytes"],
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"}
-    elif dom_name == "corr_f32":
-        achieved = model["corr_f32"]["flops"] / stage_s / 1e12
-        peak = fp32_alu_peak_tflops((clk or {}).get("sm_mhz") or 1920.0)
-        roofline = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "launches_per_image": dom_n / steps_prof,
-                    "algorithmic_flops_per_image": model["corr_f32"]["flops"],
-                    "peak_source": "152 SM x 128 FP32 lanes x 2 x median SM clock"}
+    sm_mhz = (clk or {}).get("sm_mhz") or 1920.0
+    rooflines = {name: stage_roofline(name, ms / steps_prof, n / steps_prof, model, peaks, sm_mhz)
+                 for name, (ms, n) in stages.items() if name in model}
+    roofline = rooflines.get(dom_name)
 
     # ---- end to end through the public API: pyramid H2D from pinned host memory, detections D2H
     host_levels = [torch.from_numpy(l).pin_memory() for l in pyr.levels]
@@ -406,7 +436,8 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": main_run["launches"], "stages_ms_per_image": {k: v[0] / prof_run_steps(prof_run)
                                                                           for k, v in stages.items()},
-            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "compare": compare,
+            "roofline": roofline, "rooflines": rooflines, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "compare": compare,
             "decomposition_report": rep, "wall_s_timed": main_run["wall_s"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -22,8 +22,6 @@ __device__ __forceinline__ int find_job(const Job *jobs, int n, long long idx)
     return lo;
 }
 
-__device__ __forceinline__ float bf16_to_f32(uint16_t v) { return __uint_as_float(((uint32_t)v) << 16); }
-
 // ------------------------------------------------------------------------------------------------------------ K8
 // CTA tile: CT_TY rows x CT_TX columns of output positions x CT_TK filters. Thread (tx, tf) owns the CT_TY positions
 // of column x0+tx and the 8 filters k0+8tf..k0+8tf+7: 64 FP32 accumulators. The level's halo tile sits in shared
@@ -109,11 +107,11 @@ __global__ void __launch_bounds__(CT_THREADS) corr_f32_kernel(const CorrJob *__r
 }
 
 // ------------------------------------------------------------------------------------------------------------ K2
-// One thread per cell, ZP_RCHUNK projections per CTA: z_r = sum_c C[c][r] phi[cell][c].
+// One thread per cell, ZP_RCHUNK projections per CTA: z_r = sum_c C[c][r] phi[cell][c] (FP32 path).
 constexpr int ZP_CELLS = 128, ZP_RCHUNK = 64;
 
 __global__ void __launch_bounds__(ZP_CELLS) zproj_kernel(const ZJob *__restrict__ jobs, int n_jobs,
-                                                         const float *__restrict__ Ct, int R, int bf16)
+                                                         const float *__restrict__ Ct, int R)
 {
     __shared__ __align__(16) float cs[ZP_RCHUNK][FD];
     const int ji = find_job(jobs, n_jobs, blockIdx.x);
@@ -129,25 +127,11 @@ __global__ void __launch_bounds__(ZP_CELLS) zproj_kernel(const ZJob *__restrict_
     const int cell = ct * ZP_CELLS + threadIdx.x;
     float f[FD];
     if (cell < J.cells) {
-        if (bf16) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(J.feat_bf + (size_t)cell * FD);
+        const float4 *src = reinterpret_cast<const float4 *>(J.feat + (size_t)cell * FD);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint4 u = __ldg(src + i);
-                const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    f[i * 8 + 2 * j] = bf16_to_f32((uint16_t)(wv[j] & 0xffffu));
-                    f[i * 8 + 2 * j + 1] = bf16_to_f32((uint16_t)(wv[j] >> 16));
-                }
-            }
-        } else {
-            const float4 *src = reinterpret_cast<const float4 *>(J.feat + (size_t)cell * FD);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 v = __ldg(src + i);
-                f[4 * i] = v.x; f[4 * i + 1] = v.y; f[4 * i + 2] = v.z; f[4 * i + 3] = v.w;
-            }
+        for (int i = 0; i < 8; ++i) {
+            const float4 v = __ldg(src + i);
+            f[4 * i] = v.x; f[4 * i + 1] = v.y; f[4 * i + 2] = v.z; f[4 * i + 3] = v.w;
         }
     }
     __syncthreads();
@@ -161,81 +145,110 @@ __global__ void __launch_bounds__(ZP_CELLS) zproj_kernel(const ZJob *__restrict_
 }
 
 // ------------------------------------------------------------------------------------------------------------ K3/K4
-// CTA tile: SP_TY x SP_TX output positions, one per thread, for FC filters. For every rank-1 term r the CTA stages
-// the Z_r halo, runs the y pass with a_r into shared memory, the x pass with b_r in registers, and adds
-// Lambda[k][r] * U_r to each filter's accumulator.
-constexpr int SP_TX = 32, SP_TY = 8, SP_THREADS = SP_TX * SP_TY, SP_FC_JOINT = 16, SP_MAXHW = 16;
+// A warp owns 32 consecutive columns x SP_ROWS rows of output positions for FC filters (CTA = 4 warps stacked along
+// y, 32 x 32 positions). For every rank-1 term r of the filter chunk each lane loads the column strips
+// Z_r[y0 .. y0+SP_ROWS+h-2][x] and [x+32] into registers, runs the y pass with a_r in registers (sliding window),
+// exchanges the SP_ROWS x 64 intermediate row through shared memory, runs the x pass with b_r, and adds
+// Lambda[k][r] * U_r to each filter's accumulators. No block-wide barrier is needed.
+constexpr int SP_ROWS = 8, SP_WARPS = 4, SP_FC_JOINT = 8, SP_MAXW = 16;
 
-template <int FC>
-__global__ void __launch_bounds__(SP_THREADS) sep_kernel(const SepJob *__restrict__ jobs, int n_jobs,
-                                                         const float *__restrict__ A, const float *__restrict__ B,
-                                                         const float *__restrict__ lam,
-                                                         const int *__restrict__ rank_off, int K, int R, int h, int w)
+template <int FC, int HH>
+__global__ void __launch_bounds__(SP_WARPS * 32) sep_kernel(const SepJob *__restrict__ jobs, int n_jobs,
+                                                            const float *__restrict__ A, const float *__restrict__ B,
+                                                            const float *__restrict__ lam,
+                                                            const int *__restrict__ rank_off, int K, int R, int h,
+                                                            int w)
 {
-    extern __shared__ __align__(16) float sm[];
-    const int HX = SP_TX + w - 1, HY = SP_TY + h - 1;
-    float *zh = sm;                // [HY][HX]
-    float *th = zh + HY * HX;      // [SP_TY][HX]
-    float *co = th + SP_TY * HX;   // a[h], b[w], lam[FC]
-
+    __shared__ float tsm[SP_WARPS][SP_ROWS][64 + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ji = find_job(jobs, n_jobs, blockIdx.x);
     const SepJob J = jobs[ji];
     int local = blockIdx.x - J.begin;
     const int f_chunks = (FC == 1) ? K : (K + FC - 1) / FC;
     const int fc = local % f_chunks;
     local /= f_chunks;
-    const int x0 = (local % J.tiles_x) * SP_TX, y0 = (local / J.tiles_x) * SP_TY;
+    const int x0 = (local % J.tiles_x) * 32, y0 = (local / J.tiles_x) * (SP_ROWS * SP_WARPS) + warp * SP_ROWS;
+    if (y0 >= J.Ho) return;
     const int k0 = fc * FC;
     int r_begin = 0, r_end = R;
     if (FC == 1) { r_begin = rank_off[k0]; r_end = rank_off[k0 + 1]; }
-
-    const int tx = threadIdx.x % SP_TX, ty = threadIdx.x / SP_TX;
+    const int x = x0 + lane;
     const size_t plane = (size_t)J.H * J.W;
-    float acc[FC];
-#pragma unroll
-    for (int f = 0; f < FC; ++f) acc[f] = 0.f;
-
-    for (int r = r_begin; r < r_end; ++r) {
-        __syncthreads();
-        const float *Zr = J.Z + (size_t)r * plane;
-        for (int i = threadIdx.x; i < HY * HX; i += SP_THREADS) {
-            const int yy = i / HX, xx = i - yy * HX;
-            const int gy = y0 + yy, gx = x0 + xx;
-            zh[i] = (gy < J.H && gx < J.W) ? __ldg(Zr + (size_t)gy * J.W + gx) : 0.f;
-        }
-        if (threadIdx.x < h) co[threadIdx.x] = A[threadIdx.x * R + r];
-        else if (threadIdx.x < h + w) co[threadIdx.x] = B[(threadIdx.x - h) * R + r];
-        else if (threadIdx.x < h + w + FC) {
-            const int f = threadIdx.x - h - w;
-            co[threadIdx.x] = (FC == 1) ? lam[r] : ((k0 + f < K) ? lam[(size_t)(k0 + f) * R + r] : 0.f);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < SP_TY * HX; i += SP_THREADS) {
-            const int yy = i / HX, xx = i - yy * HX;
-            float t = 0.f;
-            for (int dy = 0; dy < h; ++dy) t = fmaf(co[dy], zh[(yy + dy) * HX + xx], t);
-            th[i] = t;
-        }
-        __syncthreads();
-        float u = 0.f;
-        for (int dx = 0; dx < w; ++dx) u = fmaf(co[h + dx], th[ty * HX + tx + dx], u);
-#pragma unroll
-        for (int f = 0; f < FC; ++f) acc[f] = fmaf(co[h + w + f], u, acc[f]);
-    }
-    const int y = y0 + ty, x = x0 + tx;
-    if (y >= J.Ho || x >= J.Wo) return;
+    const bool inA = x < J.W, inB = x + 32 < J.W;
+    float acc[FC][SP_ROWS];
 #pragma unroll
     for (int f = 0; f < FC; ++f)
-        if (k0 + f < K) J.out[((size_t)(k0 + f) * J.Ho + y) * J.Wo + x] = acc[f];
+#pragma unroll
+        for (int i = 0; i < SP_ROWS; ++i) acc[f][i] = 0.f;
+    float (*ts)[64 + 1] = tsm[warp];
+
+    for (int r = r_begin; r < r_end; ++r) {
+        const float *Zr = J.Z + (size_t)r * plane;
+        float a[HH];
+#pragma unroll
+        for (int dy = 0; dy < HH; ++dy) a[dy] = (dy < h) ? __ldg(A + dy * R + r) : 0.f;
+        float zA[SP_ROWS + HH - 1], zB[SP_ROWS + HH - 1];
+#pragma unroll
+        for (int i = 0; i < SP_ROWS + HH - 1; ++i) {
+            const int yy = y0 + i;
+            const bool ry = yy < J.H;
+            zA[i] = (ry && inA) ? __ldg(Zr + (size_t)yy * J.W + x) : 0.f;
+            zB[i] = (ry && inB) ? __ldg(Zr + (size_t)yy * J.W + x + 32) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < SP_ROWS; ++i) {
+            float tA = 0.f, tB = 0.f;
+#pragma unroll
+            for (int dy = 0; dy < HH; ++dy) {
+                tA = fmaf(a[dy], zA[i + dy], tA);
+                tB = fmaf(a[dy], zB[i + dy], tB);
+            }
+            ts[i][lane] = tA;
+            ts[i][lane + 32] = tB;
+        }
+        __syncwarp();
+        float lf[FC];
+#pragma unroll
+        for (int f = 0; f < FC; ++f)
+            lf[f] = (FC == 1) ? __ldg(lam + r) : ((k0 + f < K) ? __ldg(lam + (size_t)(k0 + f) * R + r) : 0.f);
+        float bw[SP_MAXW];
+#pragma unroll
+        for (int dx = 0; dx < SP_MAXW; ++dx) bw[dx] = (dx < w) ? __ldg(B + dx * R + r) : 0.f;
+#pragma unroll
+        for (int i = 0; i < SP_ROWS; ++i) {
+            float u = 0.f;
+#pragma unroll
+            for (int dx = 0; dx < SP_MAXW; ++dx)
+                if (dx < w) u = fmaf(bw[dx], ts[i][lane + dx], u);
+#pragma unroll
+            for (int f = 0; f < FC; ++f) acc[f][i] = fmaf(lf[f], u, acc[f][i]);
+        }
+        __syncwarp();
+    }
+    if (x >= J.Wo) return;
+#pragma unroll
+    for (int f = 0; f < FC; ++f) {
+        if (k0 + f >= K) break;
+        float *o = J.out + (size_t)(k0 + f) * J.Ho * J.Wo + x;
+#pragma unroll
+        for (int i = 0; i < SP_ROWS; ++i)
+            if (y0 + i < J.Ho) o[(size_t)(y0 + i) * J.Wo] = acc[f][i];
+    }
 }
 
-__global__ void to_bf16_kernel(const float *__restrict__ src, uint16_t *__restrict__ dst, long long n)
+template <int FC>
+cudaError_t launch_sep_fc(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
+                          const float *lam, const int *rank_off, int K, int R, int h, int w, cudaStream_t s)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        __nv_bfloat16 b = __float2bfloat16_rn(src[i]);
-        dst[i] = *reinterpret_cast<uint16_t *>(&b);
+    const dim3 grid(total_tiles), block(SP_WARPS * 32);
+    switch (h) {
+    case 5: sep_kernel<FC, 5><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
+    case 6: sep_kernel<FC, 6><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
+    case 7: sep_kernel<FC, 7><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
+    case 11: sep_kernel<FC, 11><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
+    default: sep_kernel<FC, 16><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
     }
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -260,41 +273,26 @@ cudaError_t launch_corr_f32(const CorrJob *d_jobs, int n_jobs, int total_tiles, 
 int zproj_simt_cells_per_tile() { return ZP_CELLS; }
 int zproj_simt_r_chunk() { return ZP_RCHUNK; }
 
-cudaError_t launch_zproj_simt(const ZJob *d_jobs, int n_jobs, int total_tiles, const float *Ct, int R, bool bf16_feat,
-                              cudaStream_t s)
+cudaError_t launch_zproj_simt(const ZJob *d_jobs, int n_jobs, int total_tiles, const float *Ct, int R, cudaStream_t s)
 {
     if (total_tiles <= 0) return cudaSuccess;
     note_launches(1);
-    zproj_kernel<<<total_tiles, ZP_CELLS, 0, s>>>(d_jobs, n_jobs, Ct, R, bf16_feat ? 1 : 0);
+    zproj_kernel<<<total_tiles, ZP_CELLS, 0, s>>>(d_jobs, n_jobs, Ct, R);
     return cudaGetLastError();
 }
 
-int sep_tile_x() { return SP_TX; }
-int sep_tile_y() { return SP_TY; }
+int sep_tile_x() { return 32; }
+int sep_tile_y() { return SP_ROWS * SP_WARPS; }
 int sep_filters_per_cta(bool joint) { return joint ? SP_FC_JOINT : 1; }
 
-cudaError_t launch_sep_simt(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
-                            const float *lam, const int *rank_off, int K, int R, int h, int w, bool joint,
-                            cudaStream_t s)
+cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
+                       const float *lam, const int *rank_off, int K, int R, int h, int w, bool joint, cudaStream_t s)
 {
     if (total_tiles <= 0) return cudaSuccess;
-    if (h > SP_MAXHW || w > SP_MAXHW) return cudaErrorInvalidValue;
-    const int HX = SP_TX + w - 1, HY = SP_TY + h - 1;
-    const size_t smem = sizeof(float) * (HY * HX + SP_TY * HX + h + w + SP_FC_JOINT);
+    if (h < 1 || h > 16 || w < 1 || w > SP_MAXW) return cudaErrorInvalidValue;
     note_launches(1);
-    if (joint)
-        sep_kernel<SP_FC_JOINT><<<total_tiles, SP_THREADS, smem, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w);
-    else
-        sep_kernel<1><<<total_tiles, SP_THREADS, smem, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_to_bf16(const float *src, uint16_t *dst, long long n, cudaStream_t s)
-{
-    if (n <= 0) return cudaSuccess;
-    note_launches(1);
-    to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
-    return cudaGetLastError();
+    if (joint) return launch_sep_fc<SP_FC_JOINT>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
+    return launch_sep_fc<1>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
 }
 
 }  // namespace tdpm

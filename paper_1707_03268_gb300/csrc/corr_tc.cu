@@ -15,6 +15,7 @@
 // issues the MMAs, and all four warps drain TMEM (32x32b loads) and store coalesced rows of the output maps.
 // Every mbarrier wait is bounded: on expiry the kernel raises the context's error flag and carries on to a clean exit.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include "internal.h"
 
@@ -50,13 +51,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase)
     return ok != 0;
 }
 
-// Wait for the phase with `parity` to complete; give up after ~2^31 cycles (about a second), raising *err.
+// Wait for the phase with `parity` to complete. Gives up after ~2^30 cycles (about half a second), raising *err;
+// once any CTA has raised *err, later waits return at once, so a failing launch ends within about a second.
 __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int *err)
 {
     if (mbar_try_wait(bar, parity)) return;
+    if (*reinterpret_cast<volatile int *>(err)) return;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1ll << 31)) {
+        if (clock64() - t0 > (1ll << 30)) {
             atomicExch(err, 1);
             return;
         }
@@ -234,31 +237,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
-// FP32 NHWC [cells][32] -> BF16 [4][cells][8]: one thread per (cell, chunk)
-__global__ void to_bf16_planar_kernel(const float *__restrict__ src, uint16_t *__restrict__ dst, long long cells)
+// FP32 NHWC [cells][32] -> BF16 [4][cells][8] for many levels: one thread per (cell, chunk) item
+__global__ void to_bf16_planar_kernel(const ConvJob *__restrict__ jobs, int n_jobs, long long total)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cells * 4) return;
-    const long long cell = i >> 2;
-    const int kc = (int)(i & 3);
-    const float4 a = __ldg(reinterpret_cast<const float4 *>(src + cell * FD + kc * 8));
-    const float4 b = __ldg(reinterpret_cast<const float4 *>(src + cell * FD + kc * 8 + 4));
+    if (i >= total) return;
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].begin <= i) lo = mid; else hi = mid - 1;
+    }
+    const ConvJob &J = jobs[lo];
+    const long long item = i - J.begin;
+    const long long cell = item >> 2;
+    const int kc = (int)(item & 3);
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(J.src + cell * FD + kc * 8));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(J.src + cell * FD + kc * 8 + 4));
     const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     uint32_t wv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v[2 * j]), hi = __float2bfloat16_rn(v[2 * j + 1]);
-        wv[j] = (uint32_t)(*reinterpret_cast<const uint16_t *>(&lo)) |
-                ((uint32_t)(*reinterpret_cast<const uint16_t *>(&hi)) << 16);
+        const __nv_bfloat16 lo16 = __float2bfloat16_rn(v[2 * j]), hi16 = __float2bfloat16_rn(v[2 * j + 1]);
+        wv[j] = (uint32_t)(*reinterpret_cast<const uint16_t *>(&lo16)) |
+                ((uint32_t)(*reinterpret_cast<const uint16_t *>(&hi16)) << 16);
     }
-    *reinterpret_cast<uint4 *>(dst + ((size_t)kc * cells + cell) * 8) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    *reinterpret_cast<uint4 *>(J.dst + ((size_t)kc * J.cells + cell) * 8) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
 }
 
 }  // namespace
 
 int corr_tc_tile_m() { return TC_M; }
 
-int corr_tc_n_tile(int Npad) { return Npad / ((Npad + 255) / 256); }
+int corr_tc_n_tiles(int Npad) { return (Npad + 255) / 256; }
+
+int corr_tc_pad(int K)
+{
+    const int n_tiles = (K + 255) / 256;
+    int nt = (K + n_tiles - 1) / n_tiles;
+    nt = (nt + 15) / 16 * 16;
+    return nt * n_tiles;
+}
 
 size_t corr_tc_smem_bytes(int NT) { return TC_STAGES * (A_STAGE_BYTES + (size_t)NT * 64) + 8 * (2 * TC_STAGES + 1) + 16; }
 
@@ -285,11 +303,11 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_bf16_planar(const float *src, uint16_t *dst, long long cells, cudaStream_t s)
+cudaError_t launch_to_bf16_planar(const ConvJob *d_jobs, int n_jobs, long long total, cudaStream_t s)
 {
-    if (cells <= 0) return cudaSuccess;
+    if (total <= 0 || n_jobs <= 0) return cudaSuccess;
     note_launches(1);
-    to_bf16_planar_kernel<<<(unsigned)((cells * 4 + 255) / 256), 256, 0, s>>>(src, dst, cells);
+    to_bf16_planar_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(d_jobs, n_jobs, total);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,154 @@
+// Host-side state of a tdpm context (shared by model.cu and pipeline.cu; not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace tdpm {
+
+tdpm_status fail(tdpm_status st, const std::string &msg);
+void clear_error();
+
+#define CUDA_TRY(expr)                                                                                           \
+    do {                                                                                                         \
+        cudaError_t _e = (expr);                                                                                 \
+        if (_e != cudaSuccess) return ::tdpm::fail(TDPM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------------------------------------------------------ model
+struct FilterH {
+    int h, w, role, comp, part, group, gidx;
+    std::vector<float> data;  // [h][w][32]
+};
+
+struct PartH {
+    int fid, vy, vx;
+    float d[4];
+};
+
+struct CompH {
+    int root_fid;
+    float bias;
+    std::vector<PartH> parts;
+};
+
+// Filters of one role (root / part) and one shape. Device copies of the full filters and, once decomposed, of the
+// CP factors (Sec. 4): A [h][R], B [w][R], C [32][R], Lambda [K][R].
+struct Group {
+    int role = 0, h = 0, w = 0, K = 0;
+    std::vector<int> fids;
+    int Kpad = 0;                        // FP32 SIMT layout padding (multiple of 64)
+    float *d_filt_t = nullptr;           // [h*w*32][Kpad] FP32
+    int Npad_tc = 0;                     // tensor-core layout padding
+    uint16_t *d_filt_tc = nullptr;       // [h*w][4][Npad_tc][8] BF16
+    // decomposition, FP64 master copies
+    int R = 0, joint = 0;
+    std::vector<double> A, B, C, Lam;
+    std::vector<int> rank_off;           // per-filter mode: filter k owns terms [rank_off[k], rank_off[k+1])
+    std::vector<double> rel_err;         // per filter
+    // device copies: [0] FP32, [1] BF16-rounded values held in FP32
+    float *d_A[2] = {nullptr, nullptr}, *d_B[2] = {nullptr, nullptr}, *d_Ct[2] = {nullptr, nullptr},
+          *d_lam[2] = {nullptr, nullptr};
+    int *d_rank_off = nullptr;
+    int Rpad_tc = 0;
+    uint16_t *d_C_tc = nullptr;          // [1][4][Rpad_tc][8] BF16: the channel factor as a 1x1 "filter bank"
+
+    void free_factors();
+    void free_all();
+};
+
+struct Model {
+    std::vector<FilterH> filters;
+    std::vector<CompH> comps;
+    std::vector<Group> groups;
+    bool decomposed = false;
+    int decomp_mode = 0;
+    int version = 0;                     // bumped whenever the factors change (invalidates cached plans)
+};
+
+// ------------------------------------------------------------------------------------------------------ scores
+struct MapRef {
+    size_t off = 0;  // byte offset in the arena
+    int rows = 0, cols = 0;
+};
+
+struct Plan;  // pipeline.cu
+
+// One device arena (score maps, intermediates, job tables) with its pinned host copy of the job tables and, once
+// captured, a CUDA graph of the whole enqueue for the plan it was last filled for.
+struct Arena {
+    char *dev = nullptr;
+    char *host = nullptr;
+    size_t bytes = 0, host_bytes = 0;
+    uint64_t plan_uid = 0;               // plan whose job tables the host blob currently holds (0: none)
+    std::vector<const void *> levels;    // level pointers patched into the blob
+    cudaGraphExec_t graph = nullptr;
+    int uses = 0;
+};
+
+struct Scores {
+    int model_id = 0;
+    std::shared_ptr<Plan> plan;
+    Arena arena;
+    tdpm_detection *d_records = nullptr;
+    size_t rec_cap = 0;
+    cudaEvent_t done = nullptr;
+};
+
+struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+};
+
+}  // namespace tdpm
+
+struct tdpm_ctx {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    std::mutex mu;
+    int next_id = 1;
+    std::map<int, std::unique_ptr<tdpm::Model>> models;
+    std::map<int, std::unique_ptr<tdpm::Scores>> scores;
+    std::map<std::string, std::shared_ptr<tdpm::Plan>> plans;
+    std::vector<tdpm::Arena> free_arenas;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    int *d_err = nullptr;                // raised by bounded device waits
+    int *h_err = nullptr;                // pinned mirror
+    bool use_graphs = true;
+    // profiling
+    bool prof = false;
+    std::vector<tdpm::Pending> pending;
+    std::vector<std::pair<std::string, std::pair<double, long long>>> stages;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace tdpm {
+
+tdpm_status set_device(tdpm_ctx *ctx);
+Model *get_model(tdpm_ctx *ctx, int id);
+void free_scores(tdpm_ctx *ctx, Scores &s);
+void arena_free(tdpm_ctx *ctx, Arena &a);
+void drop_plans_of_model(tdpm_ctx *ctx, int model_id);
+
+template <class T>
+tdpm_status upload(T **dst, const std::vector<T> &src)
+{
+    CUDA_TRY(cudaMalloc(dst, sizeof(T) * std::max<size_t>(src.size(), 1)));
+    if (!src.empty()) CUDA_TRY(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return TDPM_OK;
+}
+
+uint16_t bf16_bits(float x);
+float bf16_round(float x);
+
+}  // namespace tdpm

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libtdpm (not part of the C-ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,32 +16,48 @@ constexpr int MAXP = TDPM_MAX_PARTS;
 // Every stage runs as ONE launch over all (level, map) jobs of a pyramid. A CTA (or a warp) finds its job by binary
 // search of its linear index in the jobs' begin prefixes.
 
-// Step 1, full form: one (shape group, level) pair. Output maps are [K][Ho][Wo] contiguous per filter.
+// Step 1, full form, FP32 SIMT: one (shape group, level) pair. Output maps are [K][Ho][Wo] contiguous per filter.
 struct CorrJob {
     const float *feat;        // FP32 NHWC level
-    const uint16_t *feat_bf;  // BF16 copy of the level: NHWC (SIMT paths) or tensor-core layout (tcgen05 paths)
     float *out;               // [K][Ho][Wo]
     int H, W, Ho, Wo;
     int tiles_x, tiles_y;     // position tiles of this job
     int begin;                // first linear tile index of this job
 };
 
-// Step 1, decomposed form, stage Z: per-cell projections Z[r][cell] = sum_c C[c][r] phi[cell][c].
+// Step 1 on tensor cores (full form, or the channel stage of the decomposed form with a 1x1 tap): one (group,
+// level) pair. The tensor map describes the level's BF16 planar copy [4][H*W][8].
+struct alignas(64) TcJob {
+    CUtensorMap tmap;
+    float *out;               // [N][Ho][Wo] (channel stage: [R][H][W])
+    int H, W, Ho, Wo;
+    int begin;                // first linear CTA index (M tiles x N tiles)
+    int pad[3];
+};
+
+// Step 1, decomposed form, stage Z on the FP32 SIMT path: Z[r][cell] = sum_c C[c][r] phi[cell][c].
 struct ZJob {
     const float *feat;
-    const uint16_t *feat_bf;
     float *Z;                 // [R][H*W]
     int cells;                // H*W
     int begin;                // first linear tile index
 };
 
-// Step 1, decomposed form, stage U+S: separable passes of Z and recombination into filter maps.
+// Step 1, decomposed form, separable passes + recombination.
 struct SepJob {
     const float *Z;           // [R][H][W]
     float *out;               // [K][Ho][Wo]
     int H, W, Ho, Wo;
     int tiles_x, tiles_y;
     int begin;
+};
+
+// FP32 NHWC level -> BF16 planar [4][cells][8].
+struct ConvJob {
+    const float *src;
+    uint16_t *dst;
+    long long cells;
+    long long begin;          // first (cell, chunk) item of this job
 };
 
 // Step 2: one part score map, transformed at sampled positions.
@@ -73,10 +90,9 @@ struct AsmJob {
 };
 
 // --------------------------------------------------------------------------------------------------- launchers
-// Every launcher adds the number of kernels it launched to the process-wide counter (tdpm_kernel_launches).
+// Every launcher adds the number of kernels it launched to the process-wide counter (tdpm_kernel_launches) and
+// returns the launch error (cudaSuccess when the launch was accepted).
 void note_launches(int n);
-
-// All launchers enqueue on `s` and return the launch error (cudaSuccess when the launch was accepted).
 
 // K8: FP32 SIMT direct correlation. filt_t: [h*w*32][Kpad] (filter index fastest), Kpad a multiple of 64.
 cudaError_t launch_corr_f32(const CorrJob *d_jobs, int n_jobs, int total_tiles, const float *filt_t, int K, int Kpad,
@@ -85,27 +101,27 @@ int corr_f32_tile_x();
 int corr_f32_tile_y();
 int corr_f32_tile_k();
 
-// K1: tcgen05 BF16 implicit-GEMM correlation. feat_bf in the tensor-core layout written by convert_levels_tc.
-cudaError_t launch_corr_tc(const CorrJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc, int K, int Npad,
-                           int h, int w, cudaStream_t s);
+// K1: tcgen05 BF16 implicit-GEMM correlation. filt_tc: [h*w][4][Npad][8] BF16, Npad = n_tiles * NT, NT <= 256 and a
+// multiple of 16 (corr_tc_pad). d_err: device flag raised when a bounded wait expires.
+cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc, int K, int Npad,
+                           int h, int w, int *d_err, cudaStream_t s);
 int corr_tc_tile_m();
-int corr_tc_n_tile(int K);
+int corr_tc_pad(int K);            // padded N for K filters
+int corr_tc_n_tiles(int Npad);     // N tiles of one launch
+bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells);
 
-// Conversions: FP32 NHWC -> BF16 NHWC (n elements), and FP32 NHWC -> BF16 tensor-core layout [4][H][W][8].
-cudaError_t launch_to_bf16(const float *src, uint16_t *dst, long long n, cudaStream_t s);
-cudaError_t launch_to_bf16_planar(const float *src, uint16_t *dst, int H, int W, cudaStream_t s);
+// FP32 NHWC -> BF16 planar for many levels in one launch (total = sum of 4 * cells).
+cudaError_t launch_to_bf16_planar(const ConvJob *d_jobs, int n_jobs, long long total, cudaStream_t s);
 
-// K2: Z projection, SIMT. Ct: [R][32] FP32 (BF16 precision: already rounded to BF16 values).
-cudaError_t launch_zproj_simt(const ZJob *d_jobs, int n_jobs, int total_tiles, const float *Ct, int R, bool bf16_feat,
-                              cudaStream_t s);
+// K2: Z projection, SIMT FP32. Ct: [R][32] FP32.
+cudaError_t launch_zproj_simt(const ZJob *d_jobs, int n_jobs, int total_tiles, const float *Ct, int R, cudaStream_t s);
 int zproj_simt_cells_per_tile();
 int zproj_simt_r_chunk();
 
-// K3+K4: separable passes + recombination, SIMT. A: [h][R], B: [w][R]; lam: per-rank weights (per-filter mode,
-// rank range [rank_off[k], rank_off[k+1])) or dense Lambda [K][R] (joint mode).
-cudaError_t launch_sep_simt(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
-                            const float *lam, const int *rank_off, int K, int R, int h, int w, bool joint,
-                            cudaStream_t s);
+// K3+K4: separable passes along y (a_r) and x (b_r) + recombination. A: [h][R], B: [w][R]; per-filter mode: lam[R]
+// per-term weights, filter k owns terms [rank_off[k], rank_off[k+1]); joint mode: lam = Lambda [K][R].
+cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
+                       const float *lam, const int *rank_off, int K, int R, int h, int w, bool joint, cudaStream_t s);
 int sep_tile_x();
 int sep_tile_y();
 int sep_filters_per_cta(bool joint);

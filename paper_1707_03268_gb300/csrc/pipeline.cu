@@ -1,0 +1,931 @@
+// C-ABI, part 2: scoring a pyramid (steps 1-3), detection (step 4), maps, instrumentation and stateless ops.
+//
+// A Plan is computed once per (model version, form, precision, pyramid shape): the arena layout (every score map,
+// intermediate and job table at a fixed offset) and the launch list (one launch per stage over all levels). A device
+// arena holds one scores set; its pinned host blob carries the job tables. Reusing an arena for the same plan only
+// patches the caller's level pointers in the blob, and from the second use on the whole enqueue (table upload plus
+// every kernel) is replayed as one CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+namespace tdpm {
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+std::atomic<unsigned long long> g_plan_uid{1};
+
+int fdiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
+
+struct Bump {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t o = align256(off);
+        off = o + bytes;
+        return o;
+    }
+};
+}  // namespace
+
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+struct GroupLevel {
+    int j;
+    size_t out_off, z_off;
+    int Ho, Wo;
+};
+
+struct DtPlan {
+    int fid, jroot, l, Hs, Ws, X, Y, vx, vy;
+    float d[4];
+    size_t s_off, v_off, iv_off, d_off, a_off;
+};
+
+struct AsmPlan {
+    int c, j, Y, X, root_W;
+    float bias;
+    size_t out_off, root_off;
+    std::vector<int> dt;
+};
+
+struct Plan {
+    uint64_t uid = 0;
+    int model_id = 0, form = 0, precision = 0, L = 0, lam = 0;
+    bool bf = false, dec = false;
+    std::vector<std::pair<int, int>> sizes;
+    size_t arena_bytes = 0, blob_off = 0, blob_bytes = 0;
+    std::vector<size_t> bf_off;
+    std::vector<std::vector<GroupLevel>> glv;
+    std::vector<DtPlan> dts;
+    std::vector<AsmPlan> asms;
+    std::map<std::pair<int, int>, MapRef> filter_maps, final_maps, dt_maps, arg_maps;
+    long long total = 0;
+    int n_det_blocks = 0;
+    size_t counts_off = 0, offsets_off = 0, total_off = 0;
+    // job tables, offsets inside the blob
+    size_t conv_off = 0;
+    long long conv_items = 0;
+    std::vector<size_t> g_jobs_off, g_sep_off;
+    std::vector<int> g_tiles, g_sep_tiles;
+    size_t dt_off = 0, asm_off = 0;
+    int x_warps = 0, y_warps = 0, max_W = 1, max_H = 1;
+    std::vector<std::pair<size_t, int>> patches;  // blob offsets of caller level pointers
+};
+
+namespace {
+
+std::string plan_key(int model_id, const Model &m, int form, int prec, const tdpm_pyramid *pyr)
+{
+    std::string k = std::to_string(model_id) + ":" + std::to_string(m.version) + ":" + std::to_string(form) + ":" +
+                    std::to_string(prec) + ":" + std::to_string(pyr->lambda);
+    for (int j = 0; j < pyr->n_levels; ++j)
+        k += ":" + std::to_string(pyr->levels[j].H) + "x" + std::to_string(pyr->levels[j].W);
+    return k;
+}
+
+std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid *pyr, int form, int prec)
+{
+    auto P = std::make_shared<Plan>();
+    P->uid = g_plan_uid.fetch_add(1);
+    P->model_id = model_id; P->form = form; P->precision = prec;
+    P->L = pyr->n_levels; P->lam = pyr->lambda;
+    P->bf = prec == TDPM_PREC_BF16;
+    P->dec = form == TDPM_FORM_DECOMPOSED;
+    const int L = P->L, lam = P->lam;
+    for (int j = 0; j < L; ++j) P->sizes.push_back({pyr->levels[j].H, pyr->levels[j].W});
+    Bump bump;
+    if (P->bf) {
+        P->bf_off.resize(L);
+        for (int j = 0; j < L; ++j) P->bf_off[j] = bump.take(sizeof(uint16_t) * (size_t)P->sizes[j].first * P->sizes[j].second * FD);
+    }
+    P->glv.resize(m.groups.size());
+    for (size_t gi = 0; gi < m.groups.size(); ++gi) {
+        const Group &g = m.groups[gi];
+        const int j0 = g.role == 0 ? lam : 0, j1 = g.role == 0 ? L : L - lam;
+        for (int j = j0; j < j1; ++j) {
+            const int H = P->sizes[j].first, W = P->sizes[j].second;
+            const int Ho = H - g.h + 1, Wo = W - g.w + 1;
+            if (Ho <= 0 || Wo <= 0) continue;
+            GroupLevel gl{j, 0, 0, Ho, Wo};
+            gl.out_off = bump.take(sizeof(float) * (size_t)g.K * Ho * Wo);
+            if (P->dec) gl.z_off = bump.take(sizeof(float) * (size_t)g.R * H * W);
+            P->glv[gi].push_back(gl);
+            for (int k = 0; k < g.K; ++k)
+                P->filter_maps[{g.fids[k], j}] = MapRef{gl.out_off + sizeof(float) * (size_t)k * Ho * Wo, Ho, Wo};
+        }
+    }
+    for (size_t c = 0; c < m.comps.size(); ++c) {
+        const CompH &C = m.comps[c];
+        const FilterH &Rf = m.filters[C.root_fid];
+        for (int j = lam; j < L; ++j) {
+            const int l = j - lam;
+            // root positions where the root and every anchored part placement fit
+            int Y = P->sizes[j].first - Rf.h + 1, X = P->sizes[j].second - Rf.w + 1;
+            for (const PartH &Pp : C.parts) {
+                const FilterH &Pf = m.filters[Pp.fid];
+                const int Hs = P->sizes[l].first - Pf.h + 1, Ws = P->sizes[l].second - Pf.w + 1;
+                if (Hs <= 0 || Ws <= 0) { Y = 0; X = 0; break; }
+                Y = std::min(Y, fdiv2(Hs - 1 - Pp.vy) + 1);
+                X = std::min(X, fdiv2(Ws - 1 - Pp.vx) + 1);
+            }
+            if (Y <= 0 || X <= 0) continue;
+            AsmPlan ap;
+            ap.c = (int)c; ap.j = j; ap.Y = Y; ap.X = X; ap.bias = C.bias;
+            const MapRef &Rm = P->filter_maps.at({C.root_fid, j});
+            ap.root_off = Rm.off;
+            ap.root_W = Rm.cols;
+            ap.out_off = bump.take(sizeof(float) * (size_t)Y * X);
+            P->final_maps[{(int)c, j}] = MapRef{ap.out_off, Y, X};
+            for (const PartH &Pp : C.parts) {
+                const FilterH &Pf = m.filters[Pp.fid];
+                DtPlan dp;
+                dp.fid = Pp.fid; dp.jroot = j; dp.l = l;
+                dp.Hs = P->sizes[l].first - Pf.h + 1; dp.Ws = P->sizes[l].second - Pf.w + 1;
+                dp.X = X; dp.Y = Y; dp.vx = Pp.vx; dp.vy = Pp.vy;
+                std::memcpy(dp.d, Pp.d, sizeof(dp.d));
+                dp.s_off = P->filter_maps.at({Pp.fid, l}).off;
+                dp.v_off = bump.take(sizeof(float) * (size_t)dp.Hs * X);
+                dp.iv_off = bump.take(sizeof(int32_t) * (size_t)dp.Hs * X);
+                dp.d_off = bump.take(sizeof(float) * (size_t)Y * X);
+                dp.a_off = bump.take(sizeof(int32_t) * (size_t)Y * X);
+                P->dt_maps[{Pp.fid, j}] = MapRef{dp.d_off, Y, X};
+                P->arg_maps[{Pp.fid, j}] = MapRef{dp.a_off, Y, X};
+                ap.dt.push_back((int)P->dts.size());
+                P->dts.push_back(dp);
+            }
+            P->asms.push_back(std::move(ap));
+        }
+    }
+    for (const AsmPlan &a : P->asms) P->total += (long long)a.Y * a.X;
+    P->n_det_blocks = (int)((P->total + detect_positions_per_block() - 1) / detect_positions_per_block());
+    P->counts_off = bump.take(sizeof(int) * std::max(1, P->n_det_blocks));
+    P->offsets_off = bump.take(sizeof(int) * std::max(1, P->n_det_blocks));
+    P->total_off = bump.take(sizeof(long long));
+    P->blob_off = align256(bump.off);
+
+    // job tables inside the blob
+    Bump jb;
+    if (P->bf) {
+        P->conv_off = jb.take(sizeof(ConvJob) * L);
+        for (int j = 0; j < L; ++j) P->conv_items += 4ll * P->sizes[j].first * P->sizes[j].second;
+    }
+    const size_t ng = m.groups.size();
+    P->g_jobs_off.assign(ng, 0); P->g_sep_off.assign(ng, 0); P->g_tiles.assign(ng, 0); P->g_sep_tiles.assign(ng, 0);
+    for (size_t gi = 0; gi < ng; ++gi) {
+        const Group &g = m.groups[gi];
+        const size_t nj = std::max<size_t>(1, P->glv[gi].size());
+        const size_t job_bytes = P->bf ? sizeof(TcJob) : (P->dec ? sizeof(ZJob) : sizeof(CorrJob));
+        P->g_jobs_off[gi] = jb.take(job_bytes * nj);
+        if (P->dec) P->g_sep_off[gi] = jb.take(sizeof(SepJob) * nj);
+        int tiles = 0, sep_tiles = 0;
+        for (const GroupLevel &gl : P->glv[gi]) {
+            const int H = P->sizes[gl.j].first, W = P->sizes[gl.j].second;
+            if (P->bf) {
+                const int Npad = P->dec ? g.Rpad_tc : g.Npad_tc;
+                const long long span = P->dec ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
+                tiles += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad);
+            } else if (P->dec) {
+                tiles += ((H * W + zproj_simt_cells_per_tile() - 1) / zproj_simt_cells_per_tile()) *
+                         ((g.R + zproj_simt_r_chunk() - 1) / zproj_simt_r_chunk());
+            } else {
+                tiles += ((gl.Wo + corr_f32_tile_x() - 1) / corr_f32_tile_x()) *
+                         ((gl.Ho + corr_f32_tile_y() - 1) / corr_f32_tile_y()) * (g.Kpad / corr_f32_tile_k());
+            }
+            if (P->dec) {
+                const int fpc = sep_filters_per_cta(g.joint != 0);
+                sep_tiles += ((gl.Wo + sep_tile_x() - 1) / sep_tile_x()) * ((gl.Ho + sep_tile_y() - 1) / sep_tile_y()) *
+                             (g.joint ? (g.K + fpc - 1) / fpc : g.K);
+            }
+        }
+        P->g_tiles[gi] = tiles;
+        P->g_sep_tiles[gi] = sep_tiles;
+    }
+    P->dt_off = jb.take(sizeof(DtJob) * std::max<size_t>(1, P->dts.size()));
+    P->asm_off = jb.take(sizeof(AsmJob) * std::max<size_t>(1, P->asms.size()));
+    P->blob_bytes = align256(jb.off);
+    P->arena_bytes = P->blob_off + P->blob_bytes;
+    for (const DtPlan &p : P->dts) {
+        P->x_warps += (p.Hs + 31) / 32;
+        P->y_warps += (p.X + 31) / 32;
+        P->max_W = std::max(P->max_W, p.Ws);
+        P->max_H = std::max(P->max_H, p.Hs);
+    }
+    return P;
+}
+
+// Write every job table of the plan into the arena's host blob (device pointers into this arena).
+tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Arena &A)
+{
+    char *base = A.dev;
+    char *hb = A.host;
+    std::memset(hb, 0, P.blob_bytes);
+    const_cast<Plan &>(P).patches.clear();
+    std::vector<std::pair<size_t, int>> patches;
+    if (P.bf) {
+        ConvJob *cj = reinterpret_cast<ConvJob *>(hb + P.conv_off);
+        long long begin = 0;
+        for (int j = 0; j < P.L; ++j) {
+            cj[j].src = pyr->levels[j].data;
+            patches.push_back({P.conv_off + sizeof(ConvJob) * j + offsetof(ConvJob, src), j});
+            cj[j].dst = reinterpret_cast<uint16_t *>(base + P.bf_off[j]);
+            cj[j].cells = (long long)P.sizes[j].first * P.sizes[j].second;
+            cj[j].begin = begin;
+            begin += 4 * cj[j].cells;
+        }
+    }
+    for (size_t gi = 0; gi < m.groups.size(); ++gi) {
+        const Group &g = m.groups[gi];
+        int begin = 0, sep_begin = 0;
+        for (size_t i = 0; i < P.glv[gi].size(); ++i) {
+            const GroupLevel &gl = P.glv[gi][i];
+            const int H = P.sizes[gl.j].first, W = P.sizes[gl.j].second;
+            float *out = reinterpret_cast<float *>(base + gl.out_off);
+            if (P.bf) {
+                TcJob &t = reinterpret_cast<TcJob *>(hb + P.g_jobs_off[gi])[i];
+                if (!encode_level_tmap(&t.tmap, reinterpret_cast<const uint16_t *>(base + P.bf_off[gl.j]),
+                                       (long long)H * W))
+                    return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+                t.out = P.dec ? reinterpret_cast<float *>(base + gl.z_off) : out;
+                t.H = H; t.W = W;
+                t.Ho = P.dec ? H : gl.Ho;
+                t.Wo = P.dec ? W : gl.Wo;
+                t.begin = begin;
+                const int Npad = P.dec ? g.Rpad_tc : g.Npad_tc;
+                const long long span = P.dec ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
+                begin += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad);
+            } else if (P.dec) {
+                ZJob &z = reinterpret_cast<ZJob *>(hb + P.g_jobs_off[gi])[i];
+                z.feat = pyr->levels[gl.j].data;
+                patches.push_back({P.g_jobs_off[gi] + sizeof(ZJob) * i + offsetof(ZJob, feat), gl.j});
+                z.Z = reinterpret_cast<float *>(base + gl.z_off);
+                z.cells = H * W;
+                z.begin = begin;
+                begin += ((z.cells + zproj_simt_cells_per_tile() - 1) / zproj_simt_cells_per_tile()) *
+                         ((g.R + zproj_simt_r_chunk() - 1) / zproj_simt_r_chunk());
+            } else {
+                CorrJob &c = reinterpret_cast<CorrJob *>(hb + P.g_jobs_off[gi])[i];
+                c.feat = pyr->levels[gl.j].data;
+                patches.push_back({P.g_jobs_off[gi] + sizeof(CorrJob) * i + offsetof(CorrJob, feat), gl.j});
+                c.out = out;
+                c.H = H; c.W = W; c.Ho = gl.Ho; c.Wo = gl.Wo;
+                c.tiles_x = (gl.Wo + corr_f32_tile_x() - 1) / corr_f32_tile_x();
+                c.tiles_y = (gl.Ho + corr_f32_tile_y() - 1) / corr_f32_tile_y();
+                c.begin = begin;
+                begin += c.tiles_x * c.tiles_y * (g.Kpad / corr_f32_tile_k());
+            }
+            if (P.dec) {
+                SepJob &sp = reinterpret_cast<SepJob *>(hb + P.g_sep_off[gi])[i];
+                sp.Z = reinterpret_cast<const float *>(base + gl.z_off);
+                sp.out = out;
+                sp.H = H; sp.W = W; sp.Ho = gl.Ho; sp.Wo = gl.Wo;
+                sp.tiles_x = (gl.Wo + sep_tile_x() - 1) / sep_tile_x();
+                sp.tiles_y = (gl.Ho + sep_tile_y() - 1) / sep_tile_y();
+                sp.begin = sep_begin;
+                const int fpc = sep_filters_per_cta(g.joint != 0);
+                sep_begin += sp.tiles_x * sp.tiles_y * (g.joint ? (g.K + fpc - 1) / fpc : g.K);
+            }
+        }
+    }
+    DtJob *dj = reinterpret_cast<DtJob *>(hb + P.dt_off);
+    int xw = 0, yw = 0;
+    for (size_t i = 0; i < P.dts.size(); ++i) {
+        const DtPlan &p = P.dts[i];
+        DtJob &d = dj[i];
+        d.S = reinterpret_cast<const float *>(base + p.s_off);
+        d.H = p.Hs; d.W = p.Ws;
+        d.lx = p.d[0]; d.qx = p.d[1]; d.ly = p.d[2]; d.qy = p.d[3];
+        d.x_off = p.vx; d.x_step = 2; d.nx = p.X;
+        d.y_off = p.vy; d.y_step = 2; d.ny = p.Y;
+        d.V = reinterpret_cast<float *>(base + p.v_off);
+        d.IV = reinterpret_cast<int32_t *>(base + p.iv_off);
+        d.D = reinterpret_cast<float *>(base + p.d_off);
+        d.A = reinterpret_cast<int32_t *>(base + p.a_off);
+        d.xbegin = xw; d.ybegin = yw;
+        xw += (p.Hs + 31) / 32;
+        yw += (p.X + 31) / 32;
+    }
+    AsmJob *aj = reinterpret_cast<AsmJob *>(hb + P.asm_off);
+    long long pos = 0;
+    for (size_t i = 0; i < P.asms.size(); ++i) {
+        const AsmPlan &p = P.asms[i];
+        AsmJob &a = aj[i];
+        a.root = reinterpret_cast<const float *>(base + p.root_off);
+        a.root_W = p.root_W;
+        a.Y = p.Y; a.X = p.X; a.bias = p.bias; a.n_parts = (int)p.dt.size();
+        a.comp = p.c; a.level = p.j;
+        a.out = reinterpret_cast<float *>(base + p.out_off);
+        for (size_t k = 0; k < p.dt.size(); ++k) {
+            a.D[k] = reinterpret_cast<const float *>(base + P.dts[p.dt[k]].d_off);
+            a.A[k] = reinterpret_cast<const int32_t *>(base + P.dts[p.dt[k]].a_off);
+        }
+        a.begin = pos;
+        pos += (long long)p.Y * p.X;
+    }
+    const_cast<Plan &>(P).patches = patches;
+    A.levels.assign(pyr->n_levels, nullptr);
+    for (int j = 0; j < pyr->n_levels; ++j) A.levels[j] = pyr->levels[j].data;
+    return TDPM_OK;
+}
+
+cudaEvent_t prof_event(tdpm_ctx *ctx)
+{
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Bracket one stage with CUDA events on its stream when the context profiles (no-op otherwise).
+struct Prof {
+    tdpm_ctx *ctx;
+    cudaStream_t s;
+    const char *name;
+    cudaEvent_t a = nullptr;
+    Prof(tdpm_ctx *c, cudaStream_t st, const char *n) : ctx(c), s(st), name(n)
+    {
+        if (ctx->prof && (a = prof_event(ctx))) cudaEventRecord(a, s);
+    }
+    void end()
+    {
+        if (!a) return;
+        cudaEvent_t b = prof_event(ctx);
+        if (b) {
+            cudaEventRecord(b, s);
+            ctx->pending.push_back(Pending{name, a, b});
+        } else {
+            ctx->event_pool.push_back(a);
+        }
+        a = nullptr;
+    }
+};
+
+void prof_collect(tdpm_ctx *ctx)
+{
+    for (Pending &p : ctx->pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(p.b);
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        size_t i = 0;
+        while (i < ctx->stages.size() && ctx->stages[i].first != p.name) ++i;
+        if (i == ctx->stages.size()) ctx->stages.push_back({p.name, {0.0, 0}});
+        ctx->stages[i].second.first += ms;
+        ctx->stages[i].second.second += 1;
+        ctx->event_pool.push_back(p.a);
+        ctx->event_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+}
+
+// Every stage of the plan on stream s.
+cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A, cudaStream_t s)
+{
+    char *dblob = A.dev + P.blob_off;
+    cudaError_t e = cudaMemcpyAsync(dblob, A.host, P.blob_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (P.bf) {
+        Prof pr(ctx, s, "to_bf16");
+        e = launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(dblob + P.conv_off), P.L, P.conv_items, s);
+        if (e != cudaSuccess) return e;
+        pr.end();
+    }
+    for (size_t gi = 0; gi < m.groups.size(); ++gi) {
+        const Group &g = m.groups[gi];
+        const int nj = (int)P.glv[gi].size();
+        if (!nj) continue;
+        const char *jobs = dblob + P.g_jobs_off[gi];
+        if (P.bf) {
+            Prof pr(ctx, s, P.dec ? "zproj_tc" : "corr_tc");
+            if (P.dec)
+                e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_C_tc, g.R, g.Rpad_tc, 1,
+                                   1, ctx->d_err, s);
+            else
+                e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_filt_tc, g.K,
+                                   g.Npad_tc, g.h, g.w, ctx->d_err, s);
+            if (e != cudaSuccess) return e;
+            pr.end();
+        } else if (P.dec) {
+            Prof pr(ctx, s, "zproj_f32");
+            e = launch_zproj_simt(reinterpret_cast<const ZJob *>(jobs), nj, P.g_tiles[gi], g.d_Ct[0], g.R, s);
+            if (e != cudaSuccess) return e;
+            pr.end();
+        } else {
+            Prof pr(ctx, s, "corr_f32");
+            e = launch_corr_f32(reinterpret_cast<const CorrJob *>(jobs), nj, P.g_tiles[gi], g.d_filt_t, g.K, g.Kpad,
+                                g.h, g.w, s);
+            if (e != cudaSuccess) return e;
+            pr.end();
+        }
+        if (P.dec) {
+            const int p = P.bf ? 1 : 0;
+            Prof pr(ctx, s, "sep");
+            e = launch_sep(reinterpret_cast<const SepJob *>(dblob + P.g_sep_off[gi]), nj, P.g_sep_tiles[gi], g.d_A[p],
+                           g.d_B[p], g.d_lam[p], g.d_rank_off, g.K, g.R, g.h, g.w, g.joint != 0, s);
+            if (e != cudaSuccess) return e;
+            pr.end();
+        }
+    }
+    {
+        Prof pr(ctx, s, "dt");
+        e = launch_dt(reinterpret_cast<const DtJob *>(dblob + P.dt_off), (int)P.dts.size(), P.x_warps, P.y_warps,
+                      P.max_W, P.max_H, s);
+        if (e != cudaSuccess) return e;
+        pr.end();
+    }
+    {
+        Prof pr(ctx, s, "assemble");
+        e = launch_assemble(reinterpret_cast<const AsmJob *>(dblob + P.asm_off), (int)P.asms.size(), P.total, s);
+        if (e != cudaSuccess) return e;
+        pr.end();
+    }
+    return cudaSuccess;
+}
+
+tdpm_status arena_get(tdpm_ctx *ctx, const Plan &P, Arena &out)
+{
+    const size_t bytes = P.arena_bytes, host_bytes = P.blob_bytes;
+    for (size_t i = 0; i < ctx->free_arenas.size(); ++i)
+        if (ctx->free_arenas[i].plan_uid == P.uid) {
+            out = ctx->free_arenas[i];
+            ctx->free_arenas.erase(ctx->free_arenas.begin() + i);
+            return TDPM_OK;
+        }
+    for (size_t i = 0; i < ctx->free_arenas.size(); ++i) {
+        Arena &a = ctx->free_arenas[i];
+        if (a.bytes >= bytes && a.bytes <= bytes + bytes / 4 + (1 << 20) && a.host_bytes >= host_bytes) {
+            out = a;
+            ctx->free_arenas.erase(ctx->free_arenas.begin() + i);
+            out.plan_uid = 0;
+            if (out.graph) {
+                cudaGraphExecDestroy(out.graph);
+                out.graph = nullptr;
+            }
+            out.uses = 0;
+            return TDPM_OK;
+        }
+    }
+    while (ctx->budget && ctx->used + bytes > ctx->budget && !ctx->free_arenas.empty()) {
+        arena_free(ctx, ctx->free_arenas.back());
+        ctx->free_arenas.pop_back();
+    }
+    if (ctx->budget && ctx->used + bytes > ctx->budget)
+        return fail(TDPM_ERR_OOM, "scores need " + std::to_string(bytes) + " bytes; budget " +
+                                      std::to_string(ctx->budget) + ", in use " + std::to_string(ctx->used));
+    Arena a;
+    cudaError_t e = cudaMalloc(&a.dev, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TDPM_ERR_OOM, std::string("cudaMalloc arena: ") + cudaGetErrorString(e));
+    }
+    e = cudaMallocHost(&a.host, host_bytes);
+    if (e != cudaSuccess) {
+        cudaFree(a.dev);
+        return fail(TDPM_ERR_OOM, std::string("cudaMallocHost staging: ") + cudaGetErrorString(e));
+    }
+    a.bytes = bytes;
+    a.host_bytes = host_bytes;
+    ctx->used += bytes;
+    out = a;
+    return TDPM_OK;
+}
+
+void arena_put(tdpm_ctx *ctx, Arena &a)
+{
+    if (!a.dev) return;
+    ctx->free_arenas.push_back(a);
+    a = Arena{};
+    while (ctx->free_arenas.size() > 8) {
+        arena_free(ctx, ctx->free_arenas.front());
+        ctx->free_arenas.erase(ctx->free_arenas.begin());
+    }
+}
+
+Scores *get_scores(tdpm_ctx *ctx, int id)
+{
+    auto it = ctx->scores.find(id);
+    return it == ctx->scores.end() ? nullptr : it->second.get();
+}
+
+// Read and clear the device error flag (bounded waits that expired); call after the stream has been synchronised.
+tdpm_status check_device_flag(tdpm_ctx *ctx)
+{
+    int v = 0;
+    CUDA_TRY(cudaMemcpy(&v, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return fail(TDPM_ERR_TIMEOUT, "a bounded device wait expired; results of the last scoring are invalid");
+    }
+    return TDPM_OK;
+}
+
+}  // namespace
+
+void arena_free(tdpm_ctx *ctx, Arena &a)
+{
+    if (a.graph) cudaGraphExecDestroy(a.graph);
+    if (a.dev) cudaFree(a.dev);
+    if (a.host) cudaFreeHost(a.host);
+    ctx->used -= std::min(ctx->used, a.bytes);
+    a = Arena{};
+}
+
+void free_scores(tdpm_ctx *ctx, Scores &s)
+{
+    if (s.done) {
+        cudaEventSynchronize(s.done);
+        cudaEventDestroy(s.done);
+        s.done = nullptr;
+    }
+    if (s.d_records) {
+        cudaFree(s.d_records);
+        ctx->used -= std::min(ctx->used, s.rec_cap * sizeof(tdpm_detection));
+        s.d_records = nullptr;
+    }
+    arena_put(ctx, s.arena);
+}
+
+void drop_plans_of_model(tdpm_ctx *ctx, int model_id)
+{
+    for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
+        if (it->second->model_id == model_id) {
+            for (Arena &a : ctx->free_arenas)
+                if (a.plan_uid == it->second->uid) {
+                    a.plan_uid = 0;
+                    if (a.graph) cudaGraphExecDestroy(a.graph);
+                    a.graph = nullptr;
+                }
+            it = ctx->plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+}  // namespace tdpm
+
+using namespace tdpm;
+
+extern "C" {
+
+tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyr, int32_t form,
+                                      int32_t precision, void *stream, int32_t *scores_id)
+{
+    clear_error();
+    if (!ctx || !pyr || !scores_id) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (form != TDPM_FORM_FULL && form != TDPM_FORM_DECOMPOSED) return fail(TDPM_ERR_ARG, "bad form");
+    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16) return fail(TDPM_ERR_ARG, "unsupported precision");
+    if (pyr->n_levels <= 0 || !pyr->levels) return fail(TDPM_ERR_ARG, "empty pyramid");
+    if (pyr->n_levels > 4096) return fail(TDPM_ERR_ARG, "too many levels");
+    if (pyr->lambda < 1 || pyr->lambda > pyr->n_levels) return fail(TDPM_ERR_ARG, "lambda out of range");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    tdpm_status st = set_device(ctx);
+    if (st) return st;
+    Model *m = get_model(ctx, model_id);
+    if (!m) return fail(TDPM_ERR_STATE, "unknown model id");
+    if (form == TDPM_FORM_DECOMPOSED && !m->decomposed)
+        return fail(TDPM_ERR_STATE, "decomposed form requested before tdpm_decompose");
+    for (int j = 0; j < pyr->n_levels; ++j) {
+        const tdpm_level &lv = pyr->levels[j];
+        if (lv.H <= 0 || lv.W <= 0 || !lv.data) return fail(TDPM_ERR_ARG, "level with non-positive size or NULL data");
+        if (lv.H > 4096 || lv.W > 4096) return fail(TDPM_ERR_ARG, "level side above 4096 cells");
+        if (reinterpret_cast<uintptr_t>(lv.data) % 16) return fail(TDPM_ERR_ARG, "level data not 16-byte aligned");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const std::string key = plan_key(model_id, *m, form, precision, pyr);
+    std::shared_ptr<Plan> plan;
+    auto pit = ctx->plans.find(key);
+    if (pit != ctx->plans.end()) {
+        plan = pit->second;
+    } else {
+        plan = make_plan(*m, model_id, pyr, form, precision);
+        if (plan->max_W > 800 || plan->max_H > 800)
+            return fail(TDPM_ERR_ARG, "part score maps wider or taller than 800 cells are not supported");
+        ctx->plans[key] = plan;
+    }
+    auto sc = std::make_unique<Scores>();
+    sc->model_id = model_id;
+    sc->plan = plan;
+    if ((st = arena_get(ctx, *plan, sc->arena))) return st;
+    Arena &A = sc->arena;
+    if (A.plan_uid != plan->uid) {
+        if (A.graph) {
+            cudaGraphExecDestroy(A.graph);
+            A.graph = nullptr;
+        }
+        A.uses = 0;
+        if ((st = fill_blob(*plan, *m, pyr, A))) {
+            arena_put(ctx, A);
+            return st;
+        }
+        A.plan_uid = plan->uid;
+    } else {
+        bool same = (int)A.levels.size() == pyr->n_levels;
+        for (int j = 0; same && j < pyr->n_levels; ++j) same = A.levels[j] == pyr->levels[j].data;
+        if (!same) {
+            for (const auto &pt : plan->patches)
+                *reinterpret_cast<const float **>(A.host + pt.first) = pyr->levels[pt.second].data;
+            A.levels.assign(pyr->n_levels, nullptr);
+            for (int j = 0; j < pyr->n_levels; ++j) A.levels[j] = pyr->levels[j].data;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    const bool graphs = ctx->use_graphs && !ctx->prof;
+    if (graphs && !A.graph && A.uses >= 1) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t eq = enqueue(ctx, *plan, *m, A, ctx->cap_stream);
+            e = cudaStreamEndCapture(ctx->cap_stream, &g);
+            if (eq != cudaSuccess) e = eq;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&A.graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            A.graph = nullptr;
+            e = cudaSuccess;  // fall back to direct launches below
+        }
+    }
+    if (graphs && A.graph) e = cudaGraphLaunch(A.graph, s);
+    else e = enqueue(ctx, *plan, *m, A, s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sc->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(sc->done, s);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        if (sc->done) cudaEventDestroy(sc->done);
+        A.plan_uid = 0;
+        arena_put(ctx, A);
+        return fail(TDPM_ERR_CUDA, std::string("enqueue: ") + cudaGetErrorString(e));
+    }
+    A.uses++;
+    const int id = ctx->next_id++;
+    ctx->scores[id] = std::move(sc);
+    *scores_id = id;
+    return TDPM_OK;
+}
+
+tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detection *out, size_t capacity,
+                        size_t *n_out, void *stream)
+{
+    clear_error();
+    if (!ctx || !n_out || (capacity > 0 && !out)) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (std::isnan(tau)) return fail(TDPM_ERR_ARG, "tau is NaN");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    tdpm_status st = set_device(ctx);
+    if (st) return st;
+    Scores *sc = get_scores(ctx, scores_id);
+    if (!sc) return fail(TDPM_ERR_STATE, "unknown scores id");
+    const Plan &P = *sc->plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t want = std::min<size_t>(capacity, (size_t)P.total);
+    if (want > sc->rec_cap) {
+        if (sc->d_records) {
+            cudaFree(sc->d_records);
+            ctx->used -= std::min(ctx->used, sc->rec_cap * sizeof(tdpm_detection));
+            sc->d_records = nullptr;
+            sc->rec_cap = 0;
+        }
+        if (ctx->budget && ctx->used + want * sizeof(tdpm_detection) > ctx->budget)
+            return fail(TDPM_ERR_OOM, "detection buffer exceeds the memory budget");
+        CUDA_TRY(cudaMalloc(&sc->d_records, want * sizeof(tdpm_detection)));
+        sc->rec_cap = want;
+        ctx->used += want * sizeof(tdpm_detection);
+    }
+    char *base = sc->arena.dev;
+    CUDA_TRY(cudaStreamWaitEvent(s, sc->done, 0));
+    Prof pr(ctx, s, "detect");
+    CUDA_TRY(launch_detect(reinterpret_cast<const AsmJob *>(base + P.blob_off + P.asm_off), (int)P.asms.size(), P.total,
+                           tau, reinterpret_cast<int *>(base + P.counts_off), reinterpret_cast<int *>(base + P.offsets_off),
+                           P.n_det_blocks, sc->d_records, (long long)want,
+                           reinterpret_cast<long long *>(base + P.total_off), s));
+    pr.end();
+    long long total = 0;
+    CUDA_TRY(cudaMemcpyAsync(&total, base + P.total_off, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if ((st = check_device_flag(ctx))) return st;
+    const size_t n = std::min<size_t>((size_t)total, want);
+    if (n) CUDA_TRY(cudaMemcpy(out, sc->d_records, n * sizeof(tdpm_detection), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaEventRecord(sc->done, s));
+    *n_out = (size_t)total;
+    if ((size_t)total > capacity)
+        return fail(TDPM_ERR_CAPACITY, "detections exceed capacity: " + std::to_string(total));
+    return TDPM_OK;
+}
+
+tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_t index_a, int32_t index_b,
+                          void *out_host, size_t capacity_bytes, int32_t *rows, int32_t *cols, void *stream)
+{
+    clear_error();
+    if (!ctx || !rows || !cols) return fail(TDPM_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    tdpm_status st = set_device(ctx);
+    if (st) return st;
+    Scores *sc = get_scores(ctx, scores_id);
+    if (!sc) return fail(TDPM_ERR_STATE, "unknown scores id");
+    const Plan &P = *sc->plan;
+    const std::map<std::pair<int, int>, MapRef> *mp = nullptr;
+    switch (kind) {
+    case TDPM_MAP_FILTER_SCORE: mp = &P.filter_maps; break;
+    case TDPM_MAP_FINAL_SCORE: mp = &P.final_maps; break;
+    case TDPM_MAP_PART_DT: mp = &P.dt_maps; break;
+    case TDPM_MAP_PART_ARG: mp = &P.arg_maps; break;
+    default: return fail(TDPM_ERR_ARG, "bad map kind");
+    }
+    auto it = mp->find({index_a, index_b});
+    *rows = 0;
+    *cols = 0;
+    if (it == mp->end()) return TDPM_OK;
+    *rows = it->second.rows;
+    *cols = it->second.cols;
+    const size_t bytes = (size_t)it->second.rows * it->second.cols * 4;
+    if (bytes > capacity_bytes || !out_host)
+        return fail(TDPM_ERR_CAPACITY, "map needs " + std::to_string(bytes) + " bytes");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaStreamWaitEvent(s, sc->done, 0));
+    CUDA_TRY(cudaMemcpyAsync(out_host, sc->arena.dev + it->second.off, bytes, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return check_device_flag(ctx);
+}
+
+tdpm_status tdpm_release(tdpm_ctx *ctx, int32_t scores_id)
+{
+    clear_error();
+    if (!ctx) return fail(TDPM_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    tdpm_status st = set_device(ctx);
+    if (st) return st;
+    auto it = ctx->scores.find(scores_id);
+    if (it == ctx->scores.end()) return fail(TDPM_ERR_STATE, "unknown scores id");
+    free_scores(ctx, *it->second);
+    ctx->scores.erase(it);
+    return TDPM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ instrumentation
+uint64_t tdpm_kernel_launches(void) { return g_launches.load(); }
+
+tdpm_status tdpm_profile_enable(tdpm_ctx *ctx, int32_t enable)
+{
+    clear_error();
+    if (!ctx) return fail(TDPM_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->prof = enable != 0;
+    return TDPM_OK;
+}
+
+tdpm_status tdpm_profile_read(tdpm_ctx *ctx, int32_t index, char *name, size_t name_cap, double *total_ms,
+                              int64_t *launches, int32_t *n_stages)
+{
+    clear_error();
+    if (!ctx) return fail(TDPM_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    tdpm_status st = set_device(ctx);
+    if (st) return st;
+    prof_collect(ctx);
+    if (n_stages) *n_stages = (int)ctx->stages.size();
+    if (index < 0 || index >= (int)ctx->stages.size()) return TDPM_OK;
+    const auto &sg = ctx->stages[index];
+    if (name && name_cap) {
+        std::strncpy(name, sg.first.c_str(), name_cap - 1);
+        name[name_cap - 1] = 0;
+    }
+    if (total_ms) *total_ms = sg.second.first;
+    if (launches) *launches = sg.second.second;
+    return TDPM_OK;
+}
+
+tdpm_status tdpm_profile_reset(tdpm_ctx *ctx)
+{
+    clear_error();
+    if (!ctx) return fail(TDPM_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    prof_collect(ctx);
+    ctx->stages.clear();
+    return TDPM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------ stateless ops
+size_t tdpm_dt_scratch_bytes(int32_t H, int32_t nx)
+{
+    if (H <= 0 || nx <= 0) return 256;
+    return align256(sizeof(DtJob)) + align256(sizeof(float) * (size_t)H * nx) + align256(sizeof(int32_t) * (size_t)H * nx);
+}
+
+tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int32_t x_off, int32_t x_step, int32_t nx,
+                    int32_t y_off, int32_t y_step, int32_t ny, float *D, int32_t *arg, void *scratch, void *stream)
+{
+    clear_error();
+    if (!S || !d || !D || !arg || !scratch) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (H <= 0 || W <= 0 || H > 800 || W > 800) return fail(TDPM_ERR_ARG, "map sides must be in [1, 800]");
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(d[k])) return fail(TDPM_ERR_ARG, "non-finite deformation coefficient");
+    if (!(d[1] > 0.f) || !(d[3] > 0.f)) return fail(TDPM_ERR_ARG, "quadratic coefficients must be > 0");
+    if (nx <= 0 || ny <= 0 || x_step <= 0 || y_step <= 0 || x_off < 0 || y_off < 0 ||
+        (long long)x_off + (long long)x_step * (nx - 1) >= W || (long long)y_off + (long long)y_step * (ny - 1) >= H)
+        return fail(TDPM_ERR_ARG, "sampled positions outside the map");
+    DtJob J{};
+    char *sb = reinterpret_cast<char *>(scratch);
+    J.S = S; J.H = H; J.W = W;
+    J.lx = d[0]; J.qx = d[1]; J.ly = d[2]; J.qy = d[3];
+    J.x_off = x_off; J.x_step = x_step; J.nx = nx;
+    J.y_off = y_off; J.y_step = y_step; J.ny = ny;
+    J.V = reinterpret_cast<float *>(sb + align256(sizeof(DtJob)));
+    J.IV = reinterpret_cast<int32_t *>(sb + align256(sizeof(DtJob)) + align256(sizeof(float) * (size_t)H * nx));
+    J.D = D; J.A = arg;
+    J.xbegin = 0; J.ybegin = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(sb, &J, sizeof(DtJob), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(launch_dt(reinterpret_cast<const DtJob *>(sb), 1, (H + 31) / 32, (nx + 31) / 32, W, H, s));
+    return TDPM_OK;
+}
+
+tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float *filt_host, int32_t K, int32_t h,
+                           int32_t w, int32_t precision, float *out, void *stream)
+{
+    clear_error();
+    if (!feat || !filt_host || !out) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (H <= 0 || W <= 0 || K <= 0 || h <= 0 || w <= 0 || h > 16 || w > 16 || H > 4096 || W > 4096 || K > 4096)
+        return fail(TDPM_ERR_ARG, "bad sizes");
+    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16) return fail(TDPM_ERR_ARG, "unsupported precision");
+    if (reinterpret_cast<uintptr_t>(feat) % 16) return fail(TDPM_ERR_ARG, "feat not 16-byte aligned");
+    const int Ho = H - h + 1, Wo = W - w + 1;
+    if (Ho <= 0 || Wo <= 0) return TDPM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int taps = h * w;
+    std::vector<char> tmp;
+    void *dmem = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (precision == TDPM_PREC_FP32) {
+        const int Kpad = (K + corr_f32_tile_k() - 1) / corr_f32_tile_k() * corr_f32_tile_k();
+        std::vector<float> ft((size_t)taps * FD * Kpad, 0.f);
+        for (int k = 0; k < K; ++k)
+            for (int t = 0; t < taps; ++t)
+                for (int c = 0; c < FD; ++c) ft[((size_t)t * FD + c) * Kpad + k] = filt_host[((size_t)k * taps + t) * FD + c];
+        CorrJob J{};
+        J.feat = feat; J.out = out; J.H = H; J.W = W; J.Ho = Ho; J.Wo = Wo;
+        J.tiles_x = (Wo + corr_f32_tile_x() - 1) / corr_f32_tile_x();
+        J.tiles_y = (Ho + corr_f32_tile_y() - 1) / corr_f32_tile_y();
+        J.begin = 0;
+        const int tiles = J.tiles_x * J.tiles_y * (Kpad / corr_f32_tile_k());
+        const size_t fbytes = align256(sizeof(float) * ft.size());
+        CUDA_TRY(cudaMalloc(&dmem, fbytes + sizeof(CorrJob)));
+        char *db = reinterpret_cast<char *>(dmem);
+        e = cudaMemcpyAsync(db, ft.data(), sizeof(float) * ft.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(db + fbytes, &J, sizeof(J), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = launch_corr_f32(reinterpret_cast<const CorrJob *>(db + fbytes), 1, tiles, reinterpret_cast<float *>(db),
+                                K, Kpad, h, w, s);
+    } else {
+        const int Npad = corr_tc_pad(K);
+        std::vector<uint16_t> fb((size_t)taps * 4 * Npad * 8, 0);
+        for (int k = 0; k < K; ++k)
+            for (int t = 0; t < taps; ++t)
+                for (int c = 0; c < FD; ++c)
+                    fb[(((size_t)t * 4 + c / 8) * Npad + k) * 8 + (c % 8)] = bf16_bits(filt_host[((size_t)k * taps + t) * FD + c]);
+        const long long cells = (long long)H * W;
+        const size_t fbytes = align256(sizeof(uint16_t) * fb.size());
+        const size_t pbytes = align256(sizeof(uint16_t) * (size_t)cells * FD);
+        CUDA_TRY(cudaMalloc(&dmem, fbytes + pbytes + align256(sizeof(ConvJob)) + sizeof(TcJob)));
+        char *db = reinterpret_cast<char *>(dmem);
+        uint16_t *planar = reinterpret_cast<uint16_t *>(db + fbytes);
+        ConvJob cj{feat, planar, cells, 0};
+        TcJob tj{};
+        if (!encode_level_tmap(&tj.tmap, planar, cells)) {
+            cudaFree(dmem);
+            return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        }
+        tj.out = out; tj.H = H; tj.W = W; tj.Ho = Ho; tj.Wo = Wo; tj.begin = 0;
+        const long long span = (long long)(Ho - 1) * W + Wo;
+        const int tiles = (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad);
+        char *cjd = db + fbytes + pbytes, *tjd = cjd + align256(sizeof(ConvJob));
+        e = cudaMemcpyAsync(db, fb.data(), sizeof(uint16_t) * fb.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cjd, &cj, sizeof(cj), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tjd, &tj, sizeof(tj), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(cjd), 1, 4 * cells, s);
+        if (e == cudaSuccess) {
+            int *d_err = reinterpret_cast<int *>(tjd + offsetof(TcJob, pad));
+            e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+            if (e == cudaSuccess)
+                e = launch_corr_tc(reinterpret_cast<const TcJob *>(tjd), 1, tiles, reinterpret_cast<uint16_t *>(db), K,
+                                   Npad, h, w, d_err, s);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dmem);
+    if (e != cudaSuccess) return fail(TDPM_ERR_CUDA, std::string("correlate: ") + cudaGetErrorString(e));
+    return TDPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+"""GPU parity of the tcgen05 tensor-core path (BF16 operands, FP32 accumulation) against the FP64 oracle.
+
+Two references: the oracle on BF16-rounded operands, which the kernel must match to FP32 summation-order error
+(every BF16 x BF16 product is exact in FP32; a wrong operand layout or descriptor shows up at once), and the oracle
+on the original FP32 operands, the stated 1e-2 bar for BF16 arithmetic.
+"""
+import numpy as np
+import pytest
+
+from helpers import agreement, det_keys, device_pyramid, rel_err
+from oracle import oracle as orc
+from paper_1707_03268_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def T(torch):
+    from paper_1707_03268_gb300 import tdpm
+    return tdpm
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    c = T.tdpm_create(0)
+    yield c
+    T.tdpm_destroy(c)
+
+
+def bf16(a, torch):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).bfloat16().float().numpy()
+
+
+@pytest.mark.parametrize("H,W,h,w,K", [(13, 29, 6, 6, 3), (30, 40, 6, 11, 1), (60, 80, 6, 6, 48), (9, 17, 5, 11, 70),
+                                       (40, 16, 7, 7, 65), (11, 5, 11, 5, 2), (1, 300, 1, 1, 260), (50, 37, 1, 1, 384),
+                                       (23, 45, 6, 6, 257)])
+def test_correlate_bf16_tensor_cores(torch, T, H, W, h, w, K):
+    rng = np.random.default_rng(H * 1000 + W * 10 + K + 7)
+    feat = rng.uniform(0, 0.2, size=(H, W, 32)).astype(np.float32)
+    filt = rng.normal(0, 0.05, size=(K, h, w, 32)).astype(np.float32)
+    out = torch.full((K, H - h + 1, W - w + 1), float("nan"), device="cuda")
+    T.tdpm_correlate(torch.from_numpy(feat).cuda(), filt, out, precision=T.PREC_BF16)
+    got = out.cpu().numpy()
+    assert np.isfinite(got).all()
+    fr, kr = bf16(feat, torch), bf16(filt, torch)
+    for k in range(K):
+        assert rel_err(got[k], orc.correlate(fr, kr[k])) <= 2e-5, k
+        assert rel_err(got[k], orc.correlate(feat, filt[k])) <= 1e-2, k
+
+
+def _bf16_model(model, torch):
+    comps = []
+    for c in model.components:
+        parts = [synth.Part(filt=bf16(p.filt, torch), anchor=p.anchor, deform=p.deform) for p in c.parts]
+        comps.append(synth.Component(root=bf16(c.root, torch), parts=parts, bias=c.bias))
+    return synth.Model(comps)
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c2"])
+def test_full_bf16_end_to_end(torch, T, ctx, cfg):
+    wl = synth.config_c1() if cfg == "c1" else synth.config_c2()
+    pyr = wl.pyramids[0]
+    mid = T.tdpm_load_model(ctx, wl.model)
+    sid = T.tdpm_build_pyramid_scores(ctx, mid, device_pyramid(pyr, torch), T.FORM_FULL, T.PREC_BF16)
+    rounded = synth.Pyramid([bf16(l, torch) for l in pyr.levels], pyr.lam)
+    ref_r = orc.score_pyramid(_bf16_model(wl.model, torch), rounded)
+    ref = orc.score_pyramid(wl.model, pyr)
+    for mr, m in zip(ref_r, ref):
+        got = T.tdpm_get_maps(ctx, sid, T.MAP_FINAL_SCORE, m["component"], m["level"])
+        assert rel_err(got, mr["score"]) <= 2e-5
+        assert rel_err(got, m["score"]) <= 1e-2
+    tau = float(np.percentile(orc.all_scores(ref_r), 99))
+    dets = T.tdpm_detect(ctx, sid, tau)
+    assert agreement(det_keys(dets), det_keys(orc.detect(ref_r, tau))) >= 0.995
+    T.tdpm_release(ctx, sid)
+
+
+def test_decomposed_bf16_channel_stage_on_tensor_cores(torch, T, ctx):
+    """Decomposed BF16 scores (tensor-core channel stage, FP32 separable passes) against the oracle rebuilt from the
+    library's factors: within 1e-2 of the FP64 result."""
+    wl = synth.config_c1()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    T.tdpm_decompose(ctx, mid, 8, T.DECOMP_PER_FILTER, max_iters=100, seed=3)
+    n_f, n_g = T.tdpm_model_info(ctx, mid)
+    filters = [None] * n_f
+    for g in range(n_g):
+        info = T.tdpm_group_info(ctx, mid, g)
+        A, B, C, Lam = T.tdpm_get_factors(ctx, mid, g)
+        F = orc.joint_reconstruct(Lam, A, B, C)
+        for k, fid in enumerate(info["filter_ids"]):
+            filters[fid] = F[k]
+    sid = T.tdpm_build_pyramid_scores(ctx, mid, device_pyramid(wl.pyramids[0], torch), T.FORM_DECOMPOSED,
+                                      T.PREC_BF16)
+    ref = orc.score_pyramid(wl.model, wl.pyramids[0], filters=filters)
+    for m in ref:
+        got = T.tdpm_get_maps(ctx, sid, T.MAP_FINAL_SCORE, m["component"], m["level"])
+        assert rel_err(got, m["score"]) <= 1e-2
+    T.tdpm_release(ctx, sid)
+
+
+def test_graph_replay_matches_direct_launches(torch, T, ctx):
+    """The third build of the same plan replays a captured CUDA graph; its maps must equal the first build's."""
+    wl = synth.config_c2()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    dp = device_pyramid(wl.pyramids[0], torch)
+    maps = []
+    for it in range(3):
+        sid = T.tdpm_build_pyramid_scores(ctx, mid, dp, T.FORM_FULL, T.PREC_BF16)
+        maps.append([T.tdpm_get_maps(ctx, sid, T.MAP_FINAL_SCORE, c, j)
+                     for c in range(len(wl.model.components)) for j in (12, 20, 30)])
+        T.tdpm_release(ctx, sid)
+    for a, b in zip(maps[0], maps[2]):
+        np.testing.assert_array_equal(a, b)
