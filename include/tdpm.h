@@ -199,7 +199,7 @@ tdpm_status tdpm_release(tdpm_ctx *ctx, int32_t scores_id);
  *   D[i][k] = max_{qy,qx} S[qy][qx] - d . (qx - px, (qx - px)^2, qy - py, (qy - py)^2),
  *   px = x_off + x_step*k (k < nx), py = y_off + y_step*i (i < ny), both inside the map;
  *   arg[i][k] = (qy << 16) | qx, the lexicographically smallest maximiser.
- * S: device [H][W] FP32 (H, W <= 32767); D: device [ny][nx] FP32; arg: device [ny][nx] int32; scratch: device
+ * S: device [H][W] FP32 (1 <= H, W <= 800); D: device [ny][nx] FP32; arg: device [ny][nx] int32; scratch: device
  * buffer of at least tdpm_dt_scratch_bytes(H, nx) bytes (intermediate x-pass result), owned by the caller.
  * Errors: ERR_ARG (d[1] or d[3] <= 0, sampled positions outside the map, NULL pointers). */
 size_t tdpm_dt_scratch_bytes(int32_t H, int32_t nx);

@@ -147,6 +147,83 @@ double residual(const double *T, const Shape &S, const std::vector<std::vector<d
     return std::sqrt(e2);
 }
 
+// Eigenvectors of a small symmetric matrix (cyclic Jacobi rotations), columns sorted by decreasing eigenvalue.
+void sym_eig(std::vector<double> A, int n, std::vector<double> &vecs)
+{
+    vecs.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) vecs[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (off < 1e-30) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                const double theta = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = vecs[(size_t)k * n + p], vkq = vecs[(size_t)k * n + q];
+                    vecs[(size_t)k * n + p] = c * vkp - s * vkq;
+                    vecs[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return A[(size_t)a * n + a] > A[(size_t)b * n + b]; });
+    std::vector<double> sorted((size_t)n * n);
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j) sorted[(size_t)k * n + j] = vecs[(size_t)k * n + order[j]];
+    vecs.swap(sorted);
+}
+
+// Starting factors: for modes of at most 64 rows the leading eigenvectors of T_(m) T_(m)^T (the higher-order SVD
+// subspace), Gaussian columns beyond the mode's size and for larger modes.
+void init_factors(const double *T, const Shape &S, int R, uint64_t &st, std::vector<std::vector<double>> &U)
+{
+    const int N = (int)S.dims.size();
+    for (int m = 0; m < N; ++m) {
+        const int n = S.dims[m];
+        U[m].resize((size_t)n * R);
+        for (double &v : U[m]) v = normal01(st);
+        if (n > 64) continue;
+        // Gram matrix of the mode-m unfolding
+        std::vector<double> G((size_t)n * n, 0.0);
+        size_t inner = 1;
+        for (int k = m + 1; k < N; ++k) inner *= (size_t)S.dims[k];
+        const size_t outer = S.size / (inner * n);
+        for (size_t o = 0; o < outer; ++o)
+            for (int a = 0; a < n; ++a) {
+                const double *ra = T + (o * n + a) * inner;
+                for (int b = a; b < n; ++b) {
+                    const double *rb = T + (o * n + b) * inner;
+                    double v = 0.0;
+                    for (size_t i = 0; i < inner; ++i) v += ra[i] * rb[i];
+                    G[(size_t)a * n + b] += v;
+                }
+            }
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < a; ++b) G[(size_t)a * n + b] = G[(size_t)b * n + a];
+        std::vector<double> V;
+        sym_eig(G, n, V);
+        for (int r = 0; r < std::min(R, n); ++r)
+            for (int i = 0; i < n; ++i) U[m][(size_t)i * R + r] = V[(size_t)i * n + r];
+    }
+}
+
 }  // namespace
 
 CpResult cp_als(const double *T, const std::vector<int> &dims, int R, int max_iters, double tol, uint64_t seed)
@@ -156,10 +233,7 @@ CpResult cp_als(const double *T, const std::vector<int> &dims, int R, int max_it
     CpResult res;
     res.U.resize(N);
     uint64_t st = seed * 0x2545F4914F6CDD1Dull + 0x1234567ull;
-    for (int m = 0; m < N; ++m) {
-        res.U[m].resize((size_t)dims[m] * R);
-        for (double &v : res.U[m]) v = normal01(st);
-    }
+    init_factors(T, S, R, st, res.U);
     double normT = 0.0;
     for (size_t i = 0; i < S.size; ++i) normT += T[i] * T[i];
     normT = std::sqrt(normT);

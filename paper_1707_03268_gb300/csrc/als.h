@@ -14,7 +14,8 @@ struct CpResult {
     double rel_error = 0.0;                // ||T - CP||_F / ||T||_F after the last cycle
 };
 
-// Rank-R CP of a dense tensor T (row-major, last mode fastest) by ALS from a seeded Gaussian start.
+// Rank-R CP of a dense tensor T (row-major, last mode fastest) by ALS, started from the leading eigenvectors of each
+// small mode unfolding (Gaussian columns beyond them, seeded).
 CpResult cp_als(const double *T, const std::vector<int> &dims, int R, int max_iters, double tol, uint64_t seed);
 
 double frob(const double *T, size_t n);

@@ -1,83 +1,26 @@
 // Step 2: generalised distance transform with argmax (Sec. 2 argmax equation),
-//   D[p] = max_q f[q] - (lin*(q-p) + quad*(q-p)^2), smallest maximising q,
+//   D[p] = max_q f[q] - (lin*(q-p) + quad*(q-p)^2),  the smallest maximising q,
 // run as an x pass over every row of a part score map and a y pass over every sampled column of its result.
 //
-// One thread owns one line and builds the upper envelope of the parabolas q -> f[q] - cost(q - p) in increasing q.
-// Because quad > 0, candidate r > q beats q (strictly) exactly for p above one threshold, so each envelope entry stores
-// the first integer p where it starts to win. That breakpoint comes from the closed-form intersection and is then
-// corrected by direct comparison of the two candidates' values at the neighbouring integers, so the envelope makes
-// the same decisions as a brute-force scan that keeps the first strict maximum. Entries live in shared memory in a
-// [entry][lane] layout (one 32-bit word per lane per row: conflict-free whatever entry each lane touches).
+// One warp owns one line: it stages the line in shared memory and reduces its maximum M. Each lane then takes output
+// positions p and scans the candidates q in increasing order, keeping the first strict maximum, exactly like the
+// brute-force definition. The scan is restricted to the window where the deformation cost is at most
+// (M - f[p]) + margin: any q outside it has f[q] - cost <= M - cost < f[p] - margin, so it can never beat the
+// candidate q = p (whose value is f[p] exactly). The margin covers FP32 rounding of the evaluated values, so the
+// window never changes the result of the full scan, in exact or in FP32 arithmetic; it only skips hopeless
+// candidates (for the default deformation costs the window spans a few to a few tens of cells).
 //
-// x pass: a warp owns 32 consecutive rows; 32x32 blocks of the map are staged through shared memory so the global
-// reads and writes stay coalesced. y pass: a warp owns 32 consecutive sampled columns; its reads of V are coalesced.
+// x pass: line = row y of S (length W); outputs at p = x_off + x_step*k, written transposed: V[k][y], IV[k][y].
+// y pass: line = row k of V (length H, contiguous); outputs at p = y_off + y_step*i: D[i][k], A[i][k] =
+//         (qy << 16) | IV[k][qy].
 #include "internal.h"
 
 namespace tdpm {
 namespace {
 
-struct Line {
-    float lin, quad;
-    int n;
-};
+constexpr int DT_WARPS = 8;
 
-__device__ __forceinline__ float dt_cost(float lin, float quad, int d)
-{
-    const float fd = (float)d;
-    return fmaf(quad, fd * fd, lin * fd);
-}
-
-// candidate r (value fr) strictly beats q (value fq) at p
-__device__ __forceinline__ bool dt_beats(const Line &L, int r, float fr, int q, float fq, int p)
-{
-    return (fr - dt_cost(L.lin, L.quad, r - p)) > (fq - dt_cost(L.lin, L.quad, q - p));
-}
-
-// first integer p in [0, n] at which r > q strictly beats q (n: never inside the line)
-__device__ __forceinline__ int dt_break(const Line &L, int q, float fq, int r, float fr)
-{
-    const float num = (fq - fr) + L.lin * (float)(r - q) + L.quad * (float)(r * r - q * q);
-    const float den = 2.f * L.quad * (float)(r - q);
-    const float s = num / den;
-    int p;
-    if (!(s < (float)L.n)) p = L.n;  // also catches NaN
-    else if (s < 0.f) p = 0;
-    else p = (int)floorf(s) + 1;
-    if (p > L.n) p = L.n;
-    for (int it = 0; it < 2 && p > 0 && dt_beats(L, r, fr, q, fq, p - 1); ++it) --p;
-    for (int it = 0; it < 2 && p < L.n && !dt_beats(L, r, fr, q, fq, p); ++it) ++p;
-    return p;
-}
-
-// envelope storage: ENVP[k*32+lane] = v | (z << 16); ENVF[k*32+lane] = f[v]
-struct Env {
-    int *P;
-    float *F;
-    int lane;
-    int top;
-    __device__ __forceinline__ int v(int k) const { return P[k * 32 + lane] & 0xffff; }
-    __device__ __forceinline__ int z(int k) const { return P[k * 32 + lane] >> 16; }
-    __device__ __forceinline__ float f(int k) const { return F[k * 32 + lane]; }
-    __device__ __forceinline__ void push(int q, int zq, float fq)
-    {
-        ++top;
-        P[top * 32 + lane] = q | (zq << 16);
-        F[top * 32 + lane] = fq;
-    }
-    __device__ __forceinline__ void insert(const Line &L, int q, float fq)
-    {
-        int s = 0;
-        while (top >= 0) {
-            s = dt_break(L, v(top), f(top), q, fq);
-            if (s <= z(top)) --top; else break;
-        }
-        if (top < 0) push(q, 0, fq);
-        else if (s < L.n) push(q, s, fq);
-    }
-};
-
-template <class Job>
-__device__ __forceinline__ int find_begin(const Job *jobs, int n, int idx, bool xpass)
+__device__ __forceinline__ int find_line_job(const DtJob *jobs, int n, int idx, bool xpass)
 {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -88,99 +31,86 @@ __device__ __forceinline__ int find_begin(const Job *jobs, int n, int idx, bool 
     return lo;
 }
 
-__global__ void __launch_bounds__(32) dt_x_kernel(const DtJob *__restrict__ jobs, int n_jobs, int nmax)
+// Candidate window [lo, hi] of output p for a line of length n with maximum mx.
+__device__ __forceinline__ void dt_window(float lin, float quad, float mx, float fp, int p, int n, int &lo, int &hi)
 {
-    extern __shared__ __align__(16) int dsm[];
-    int *envp = dsm;
-    float *envf = reinterpret_cast<float *>(dsm + nmax * 32);
-    float *tile = reinterpret_cast<float *>(dsm + 2 * nmax * 32);   // [32][33]
-    int *tilei = dsm + 2 * nmax * 32 + 32 * 33;                      // [32][33]
-    const int lane = threadIdx.x;
-    const int gw = blockIdx.x;
-    const DtJob J = jobs[find_begin(jobs, n_jobs, gw, true)];
-    const int row0 = (gw - J.xbegin) * 32, row = row0 + lane;
-    const bool active = row < J.H;
-    const Line L{J.lx, J.qx, J.W};
-    Env E{envp, envf, lane, -1};
-
-    for (int c0 = 0; c0 < J.W; c0 += 32) {
-        const int col = c0 + lane;
-        for (int i = 0; i < 32; ++i) {
-            const int r = row0 + i;
-            tile[lane * 33 + i] = (r < J.H && col < J.W) ? __ldg(J.S + (size_t)r * J.W + col) : 0.f;
-        }
-        __syncwarp();
-        const int cend = min(32, J.W - c0);
-        if (active)
-            for (int j = 0; j < cend; ++j) E.insert(L, c0 + j, tile[j * 33 + lane]);
-        __syncwarp();
-    }
-
-    int kk = 0;
-    for (int k0 = 0; k0 < J.nx; k0 += 32) {
-        const int kend = min(32, J.nx - k0);
-        if (active) {
-            for (int j = 0; j < kend; ++j) {
-                const int p = J.x_off + J.x_step * (k0 + j);
-                while (kk < E.top && E.z(kk + 1) <= p) ++kk;
-                const int q = E.v(kk);
-                tile[j * 33 + lane] = E.f(kk) - dt_cost(L.lin, L.quad, q - p);
-                tilei[j * 33 + lane] = q;
-            }
-        }
-        __syncwarp();
-        const int k = k0 + lane;
-        for (int i = 0; i < 32; ++i) {
-            const int r = row0 + i;
-            if (r < J.H && lane < kend) {
-                J.V[(size_t)r * J.nx + k] = tile[lane * 33 + i];
-                J.IV[(size_t)r * J.nx + k] = tilei[lane * 33 + i];
-            }
-        }
-        __syncwarp();
-    }
+    const float T = (mx - fp) + 1e-5f * (1.f + fabsf(mx) + fabsf(fp));
+    const float s = sqrtf(fmaf(4.f * quad, T, lin * lin));
+    const float inv = 0.5f / quad;
+    const float dlo = (-lin - s) * inv, dhi = (-lin + s) * inv;
+    lo = (dlo > -(float)n) ? p + (int)floorf(dlo) - 1 : 0;
+    hi = (dhi < (float)n) ? p + (int)ceilf(dhi) + 1 : n - 1;
+    lo = max(lo, 0);
+    hi = min(hi, n - 1);
 }
 
-__global__ void __launch_bounds__(32) dt_y_kernel(const DtJob *__restrict__ jobs, int n_jobs, int nmax)
+template <bool XPASS>
+__global__ void __launch_bounds__(DT_WARPS * 32) dt_line_kernel(const DtJob *__restrict__ jobs, int n_jobs,
+                                                                int total_lines, int nmax)
 {
-    extern __shared__ __align__(16) int dsm[];
-    int *envp = dsm;
-    float *envf = reinterpret_cast<float *>(dsm + nmax * 32);
-    const int lane = threadIdx.x;
-    const int gw = blockIdx.x;
-    const DtJob J = jobs[find_begin(jobs, n_jobs, gw, false)];
-    const int k = (gw - J.ybegin) * 32 + lane;
-    if (k >= J.nx) return;
-    const Line L{J.ly, J.qy, J.H};
-    Env E{envp, envf, lane, -1};
-    for (int q = 0; q < J.H; ++q) E.insert(L, q, __ldg(J.V + (size_t)q * J.nx + k));
-    int kk = 0;
-    for (int i = 0; i < J.ny; ++i) {
-        const int p = J.y_off + J.y_step * i;
-        while (kk < E.top && E.z(kk + 1) <= p) ++kk;
-        const int q = E.v(kk);
-        J.D[(size_t)i * J.nx + k] = E.f(kk) - dt_cost(L.lin, L.quad, q - p);
-        J.A[(size_t)i * J.nx + k] = (q << 16) | J.IV[(size_t)q * J.nx + k];
+    extern __shared__ float lines[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gl = blockIdx.x * DT_WARPS + warp;
+    if (gl >= total_lines) return;
+    const DtJob &J = jobs[find_line_job(jobs, n_jobs, gl, XPASS)];
+    const int line = gl - (XPASS ? J.xbegin : J.ybegin);
+    const int n = XPASS ? J.W : J.H;
+    const float *in = XPASS ? J.S + (size_t)line * J.W : J.V + (size_t)line * J.H;
+    const float lin = XPASS ? J.lx : J.ly, quad = XPASS ? J.qx : J.qy;
+    const int off = XPASS ? J.x_off : J.y_off, step = XPASS ? J.x_step : J.y_step, m = XPASS ? J.nx : J.ny;
+    float *L = lines + (size_t)warp * nmax;
+
+    float mx = -INFINITY;
+    for (int q = lane; q < n; q += 32) {
+        const float v = __ldg(in + q);
+        L[q] = v;
+        mx = fmaxf(mx, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncwarp();
+
+    for (int i = lane; i < m; i += 32) {
+        const int p = off + step * i;
+        int lo, hi;
+        dt_window(lin, quad, mx, L[p], p, n, lo, hi);
+        float best = -INFINITY;
+        int arg = lo;
+        for (int q = lo; q <= hi; ++q) {
+            const float d = (float)(q - p);
+            const float v = L[q] - fmaf(quad, d * d, lin * d);
+            if (v > best) {
+                best = v;
+                arg = q;
+            }
+        }
+        if (XPASS) {
+            J.V[(size_t)i * J.H + line] = best;
+            J.IV[(size_t)i * J.H + line] = arg;
+        } else {
+            J.D[(size_t)i * J.nx + line] = best;
+            J.A[(size_t)i * J.nx + line] = (arg << 16) | J.IV[(size_t)line * J.H + arg];
+        }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_warps, int y_warps, int max_W, int max_H, cudaStream_t s)
+cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_lines, int y_lines, int max_W, int max_H, cudaStream_t s)
 {
     if (n_jobs <= 0) return cudaSuccess;
-    const size_t smem_x = sizeof(int) * (2 * (size_t)max_W * 32 + 2 * 32 * 33);
-    const size_t smem_y = sizeof(int) * (2 * (size_t)max_H * 32);
-    if (smem_x > 220 * 1024 || smem_y > 220 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(dt_x_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x);
+    if (max_W > 800 || max_H > 800) return cudaErrorInvalidValue;
+    const size_t smem_x = sizeof(float) * DT_WARPS * (size_t)max_W;
+    const size_t smem_y = sizeof(float) * DT_WARPS * (size_t)max_H;
+    note_launches((x_lines > 0) + (y_lines > 0));
+    if (x_lines > 0)
+        dt_line_kernel<true><<<(x_lines + DT_WARPS - 1) / DT_WARPS, DT_WARPS * 32, smem_x, s>>>(d_jobs, n_jobs, x_lines,
+                                                                                                max_W);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(dt_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y);
-    if (e != cudaSuccess) return e;
-    note_launches((x_warps > 0) + (y_warps > 0));
-    if (x_warps > 0) dt_x_kernel<<<x_warps, 32, smem_x, s>>>(d_jobs, n_jobs, max_W);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (y_warps > 0) dt_y_kernel<<<y_warps, 32, smem_y, s>>>(d_jobs, n_jobs, max_H);
+    if (y_lines > 0)
+        dt_line_kernel<false><<<(y_lines + DT_WARPS - 1) / DT_WARPS, DT_WARPS * 32, smem_y, s>>>(d_jobs, n_jobs,
+                                                                                                 y_lines, max_H);
     return cudaGetLastError();
 }
 

@@ -67,12 +67,12 @@ struct DtJob {
     float lx, qx, ly, qy;     // d0 (dx), d1 (dx^2), d2 (dy), d3 (dy^2)
     int x_off, x_step, nx;    // sampled columns
     int y_off, y_step, ny;    // sampled rows
-    float *V;                 // x-pass values  [H][nx]
-    int32_t *IV;              // x-pass argmax  [H][nx]
+    float *V;                 // x-pass values, transposed  [nx][H]
+    int32_t *IV;              // x-pass argmax, transposed  [nx][H]
     float *D;                 // result         [ny][nx]
     int32_t *A;               // (qy << 16) | qx [ny][nx]
-    int xbegin;               // first warp of this job in the x pass (warps of 32 rows)
-    int ybegin;               // first warp of this job in the y pass (warps of 32 sampled columns)
+    int xbegin;               // first line of this job in the x pass (one line per row)
+    int ybegin;               // first line of this job in the y pass (one line per sampled column)
 };
 
 // Step 3: one (component, root level) pair.
@@ -126,8 +126,8 @@ int sep_tile_x();
 int sep_tile_y();
 int sep_filters_per_cta(bool joint);
 
-// K5/K6: distance transform passes.
-cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_warps, int y_warps, int max_W, int max_H, cudaStream_t s);
+// K5/K6: distance transform passes (x_lines = sum of map rows, y_lines = sum of sampled columns; sides <= 800).
+cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_lines, int y_lines, int max_W, int max_H, cudaStream_t s);
 
 // K7: assembly (shift and sum), then detection count / scan / write.
 cudaError_t launch_assemble(const AsmJob *d_jobs, int n_jobs, long long total, cudaStream_t s);

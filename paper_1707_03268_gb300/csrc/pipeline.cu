@@ -214,8 +214,8 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     P->blob_bytes = align256(jb.off);
     P->arena_bytes = P->blob_off + P->blob_bytes;
     for (const DtPlan &p : P->dts) {
-        P->x_warps += (p.Hs + 31) / 32;
-        P->y_warps += (p.X + 31) / 32;
+        P->x_warps += p.Hs;
+        P->y_warps += p.X;
         P->max_W = std::max(P->max_W, p.Ws);
         P->max_H = std::max(P->max_H, p.Hs);
     }
@@ -310,8 +310,8 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Ar
         d.D = reinterpret_cast<float *>(base + p.d_off);
         d.A = reinterpret_cast<int32_t *>(base + p.a_off);
         d.xbegin = xw; d.ybegin = yw;
-        xw += (p.Hs + 31) / 32;
-        yw += (p.X + 31) / 32;
+        xw += p.Hs;
+        yw += p.X;
     }
     AsmJob *aj = reinterpret_cast<AsmJob *>(hb + P.asm_off);
     long long pos = 0;
@@ -847,7 +847,7 @@ tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int3
     J.xbegin = 0; J.ybegin = 0;
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaMemcpyAsync(sb, &J, sizeof(DtJob), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(launch_dt(reinterpret_cast<const DtJob *>(sb), 1, (H + 31) / 32, (nx + 31) / 32, W, H, s));
+    CUDA_TRY(launch_dt(reinterpret_cast<const DtJob *>(sb), 1, H, nx, W, H, s));
     return TDPM_OK;
 }
 
