@@ -263,7 +263,7 @@ cudaError_t launch_corr_f32(const CorrJob *d_jobs, int n_jobs, int total_tiles, 
     if (total_tiles <= 0) return cudaSuccess;
     const int plane = (CT_TY + h - 1) * (CT_TX + w - 1);
     const size_t smem = sizeof(float) * (((FD * plane + 3) & ~3) + CT_TAPS * FD * CT_TK);
-    cudaError_t e = cudaFuncSetAttribute(corr_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(corr_f32_kernel), 1);
     if (e != cudaSuccess) return e;
     note_launches(1);
     corr_f32_kernel<<<total_tiles, CT_THREADS, smem, s>>>(d_jobs, n_jobs, filt_t, K, Kpad, h, w);

@@ -294,8 +294,8 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, con
     size_t smem = corr_tc_smem_bytes(NT);
     const size_t floor_bytes = 233472 / (size_t)(max_ctas + 1);
     if (smem < floor_bytes) smem = floor_bytes;
-    if (smem > 232448) smem = 232448;
-    cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > (size_t)kMaxDynamicSmem) smem = kMaxDynamicSmem;
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(corr_tc_kernel), 0);
     if (e != cudaSuccess) return e;
     note_launches(1);
     corr_tc_kernel<<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, K, Npad, NT, n_tiles_n, h, w, cols,

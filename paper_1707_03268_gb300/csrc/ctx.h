@@ -56,9 +56,8 @@ struct Group {
     std::vector<double> A, B, C, Lam;
     std::vector<int> rank_off;           // per-filter mode: filter k owns terms [rank_off[k], rank_off[k+1])
     std::vector<double> rel_err;         // per filter
-    // device copies: [0] FP32, [1] BF16-rounded values held in FP32
-    float *d_A[2] = {nullptr, nullptr}, *d_B[2] = {nullptr, nullptr}, *d_Ct[2] = {nullptr, nullptr},
-          *d_lam[2] = {nullptr, nullptr};
+    // FP32 device copies (the 1-D passes run in FP32 for every precision)
+    float *d_A = nullptr, *d_B = nullptr, *d_Ct = nullptr, *d_lam = nullptr;
     int *d_rank_off = nullptr;
     int Rpad_tc = 0;
     uint16_t *d_C_tc = nullptr;          // [1][4][Rpad_tc][8] BF16: the channel factor as a 1x1 "filter bank"

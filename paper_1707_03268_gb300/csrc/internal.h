@@ -94,6 +94,11 @@ struct AsmJob {
 // returns the launch error (cudaSuccess when the launch was accepted).
 void note_launches(int n);
 
+// Raise a kernel's dynamic shared memory limit to the per-block maximum, once per device. Launches still request only
+// what they use; a fixed limit keeps captured CUDA graphs valid whatever order their launches were recorded in.
+cudaError_t allow_max_dynamic_smem(const void *func, int slot);
+constexpr int kMaxDynamicSmem = 232448;
+
 // K8: FP32 SIMT direct correlation. filt_t: [h*w*32][Kpad] (filter index fastest), Kpad a multiple of 64.
 cudaError_t launch_corr_f32(const CorrJob *d_jobs, int n_jobs, int total_tiles, const float *filt_t, int K, int Kpad,
                             int h, int w, cudaStream_t s);

@@ -41,10 +41,8 @@ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 void Group::free_factors()
 {
-    for (int p = 0; p < 2; ++p) {
-        cudaFree(d_A[p]); cudaFree(d_B[p]); cudaFree(d_Ct[p]); cudaFree(d_lam[p]);
-        d_A[p] = d_B[p] = d_Ct[p] = d_lam[p] = nullptr;
-    }
+    cudaFree(d_A); cudaFree(d_B); cudaFree(d_Ct); cudaFree(d_lam);
+    d_A = d_B = d_Ct = d_lam = nullptr;
     cudaFree(d_rank_off);
     cudaFree(d_C_tc);
     d_rank_off = nullptr;
@@ -85,30 +83,26 @@ tdpm_status upload_tc_bank(uint16_t **dst, int taps, int Npad, int n_rows,
     return upload(dst, b);
 }
 
-// Device copies of a group's factors: FP32 and BF16-rounded copies for the SIMT kernels, and the channel factor C
-// as a BF16 1x1 bank for the tensor-core channel stage.
+// Device copies of a group's factors: FP32 for the SIMT kernels (channel stage of the FP32 path, 1-D passes and
+// recombination of every path), and the channel factor C as a BF16 1x1 bank for the tensor-core channel stage.
 tdpm_status upload_factors(Group &g)
 {
     g.free_factors();
     const int R = g.R, K = (int)g.fids.size();
-    for (int p = 0; p < 2; ++p) {
-        auto cvt = [p](double v) { return p ? bf16_round((float)v) : (float)v; };
-        std::vector<float> A(g.A.size()), B(g.B.size()), Ct((size_t)R * FD), lam;
-        for (size_t i = 0; i < A.size(); ++i) A[i] = cvt(g.A[i]);
-        for (size_t i = 0; i < B.size(); ++i) B[i] = cvt(g.B[i]);
+    {
+        std::vector<float> A(g.A.begin(), g.A.end()), B(g.B.begin(), g.B.end()), Ct((size_t)R * FD), lam;
         for (int r = 0; r < R; ++r)
-            for (int c = 0; c < FD; ++c) Ct[(size_t)r * FD + c] = cvt(g.C[(size_t)c * R + r]);
+            for (int c = 0; c < FD; ++c) Ct[(size_t)r * FD + c] = (float)g.C[(size_t)c * R + r];
         if (g.joint) {
-            lam.resize((size_t)K * R);
-            for (size_t i = 0; i < lam.size(); ++i) lam[i] = cvt(g.Lam[i]);
+            lam.assign(g.Lam.begin(), g.Lam.end());
         } else {
             lam.assign(R, 0.f);
             for (int k = 0; k < K; ++k)
-                for (int r = g.rank_off[k]; r < g.rank_off[k + 1]; ++r) lam[r] = cvt(g.Lam[(size_t)k * R + r]);
+                for (int r = g.rank_off[k]; r < g.rank_off[k + 1]; ++r) lam[r] = (float)g.Lam[(size_t)k * R + r];
         }
         tdpm_status st;
-        if ((st = upload(&g.d_A[p], A)) || (st = upload(&g.d_B[p], B)) || (st = upload(&g.d_Ct[p], Ct)) ||
-            (st = upload(&g.d_lam[p], lam)))
+        if ((st = upload(&g.d_A, A)) || (st = upload(&g.d_B, B)) || (st = upload(&g.d_Ct, Ct)) ||
+            (st = upload(&g.d_lam, lam)))
             return st;
     }
     std::vector<int> ro = g.rank_off;

@@ -38,6 +38,20 @@ struct Bump {
 
 void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
+cudaError_t allow_max_dynamic_smem(const void *func, int slot)
+{
+    static std::atomic<bool> done[8][64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (slot < 0 || slot >= 8 || dev < 0 || dev >= 64)
+        return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynamicSmem);
+    if (done[slot][dev].load(std::memory_order_acquire)) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynamicSmem);
+    if (e == cudaSuccess) done[slot][dev].store(true, std::memory_order_release);
+    return e;
+}
+
 struct GroupLevel {
     int j;
     size_t out_off, z_off;
@@ -418,7 +432,7 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
             pr.end();
         } else if (P.dec) {
             Prof pr(ctx, s, "zproj_f32");
-            e = launch_zproj_simt(reinterpret_cast<const ZJob *>(jobs), nj, P.g_tiles[gi], g.d_Ct[0], g.R, s);
+            e = launch_zproj_simt(reinterpret_cast<const ZJob *>(jobs), nj, P.g_tiles[gi], g.d_Ct, g.R, s);
             if (e != cudaSuccess) return e;
             pr.end();
         } else {
@@ -429,10 +443,9 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
             pr.end();
         }
         if (P.dec) {
-            const int p = P.bf ? 1 : 0;
             Prof pr(ctx, s, "sep");
-            e = launch_sep(reinterpret_cast<const SepJob *>(dblob + P.g_sep_off[gi]), nj, P.g_sep_tiles[gi], g.d_A[p],
-                           g.d_B[p], g.d_lam[p], g.d_rank_off, g.K, g.R, g.h, g.w, g.joint != 0, s);
+            e = launch_sep(reinterpret_cast<const SepJob *>(dblob + P.g_sep_off[gi]), nj, P.g_sep_tiles[gi], g.d_A,
+                           g.d_B, g.d_lam, g.d_rank_off, g.K, g.R, g.h, g.w, g.joint != 0, s);
             if (e != cudaSuccess) return e;
             pr.end();
         }

@@ -10,8 +10,9 @@ stand in for them with the same shapes and value ranges:
 * features: 32 channels per cell, i.i.d. U[0, 0.2) (0.2 is the HOG truncation value);
 * pyramid: DPM-style, ``lam`` levels per octave; the first ``lam`` levels form the 2x octave (cell size sbin/2) that
   part filters are evaluated on, the remaining levels are at cell size ``sbin`` and hold root positions;
-* filters: h x w x 32; "iid" draws N(0, 0.05) entries, "dpm" draws a filter with a decaying CP spectrum (trained DPM
-  filters are close to low rank, Sec. 5: rank 6-11 matches full accuracy) plus an i.i.d. residual;
+* filters: h x w x 32; "iid" draws N(0, 0.05) entries, "dpm" draws a filter with a smooth, geometrically decaying CP
+  spectrum (trained DPM filters are close to low rank: Sec. 5 finds ranks 6-11 within a small percentage of rank 21,
+  which almost matches the full filters);
 * deformation coefficients (d1, d2, d3, d4) of (dx, dx^2, dy, dy^2), each U[0.001, 0.1];
 * part anchors in part-level cells relative to twice the root position, drawn so every anchored part filter lies
   inside the root's 2x footprint.
@@ -110,25 +111,25 @@ def make_pyramid(rng: np.random.Generator, sizes: Sequence[Tuple[int, int]], lam
 # --------------------------------------------------------------------------------------------------------------------
 # filters and models
 # --------------------------------------------------------------------------------------------------------------------
-def make_filter(rng: np.random.Generator, h: int, w: int, kind: str = "iid", planted_rank: int = 6,
-                decay: float = 0.6, residual: float = 0.01) -> np.ndarray:
-    """One h x w x 32 filter with entry RMS ~ FILTER_STD.
+def make_filter(rng: np.random.Generator, h: int, w: int, kind: str = "iid", n_terms: int = 36,
+                decay: float = 0.7) -> np.ndarray:
+    """One h x w x 32 filter with entry RMS FILTER_STD.
 
-    kind "iid": i.i.d. N(0, FILTER_STD). kind "dpm": sum of ``planted_rank`` outer products of random unit vectors with
-    weights decay^r, rescaled to RMS FILTER_STD, plus i.i.d. noise of relative size ``residual``.
+    kind "iid": i.i.d. N(0, FILTER_STD). kind "dpm": a smooth CP spectrum, the sum of ``n_terms`` outer products of
+    random unit vectors with weights decay^r, rescaled to RMS FILTER_STD (a rank-R truncation leaves roughly decay^R
+    of the filter's norm).
     """
     if kind == "iid":
         return rng.normal(0.0, FILTER_STD, size=(h, w, FEAT_DIM)).astype(np.float32)
     if kind != "dpm":
         raise ValueError(kind)
     F = np.zeros((h, w, FEAT_DIM))
-    for r in range(planted_rank):
+    for r in range(n_terms):
         a = rng.standard_normal(h); a /= np.linalg.norm(a)
         b = rng.standard_normal(w); b /= np.linalg.norm(b)
         c = rng.standard_normal(FEAT_DIM); c /= np.linalg.norm(c)
         F += (decay ** r) * a[:, None, None] * b[None, :, None] * c[None, None, :]
     F *= FILTER_STD / np.sqrt(np.mean(F * F))
-    F += rng.normal(0.0, FILTER_STD * residual, size=F.shape)
     return F.astype(np.float32)
 
 
