@@ -206,6 +206,23 @@ size_t tdpm_dt_scratch_bytes(int32_t H, int32_t nx);
 tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int32_t x_off, int32_t x_step, int32_t nx,
                     int32_t y_off, int32_t y_step, int32_t ny, float *D, int32_t *arg, void *scratch, void *stream);
 
+/* Allocation-free variant of tdpm_dt. The paper has no counterpart; this entry point exists for callers that must not
+ * allocate device memory: code that runs while a stream is being captured into a CUDA graph (allocation calls are
+ * not captured), latency-critical loops that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+ * imply, and applications whose device memory is owned entirely by another allocator.
+ *   - Same arguments, layouts and results as tdpm_dt, without the scratch buffer: the x-pass intermediate lives in a
+ *     fixed 4 MiB device array inside the library, which every GPU that loads the library holds until the process
+ *     exits. H * nx may not exceed tdpm_dt_noalloc_max_elements() (524,224): larger sizes return TDPM_ERR_ARG.
+ *   - The first call on a device looks up that array's device address (with the device current); make that first
+ *     call before any stream capture starts.
+ *   - Every call on a device shares the one array and overwrites it: calls whose work overlaps on the GPU (other
+ *     streams, or other threads) race and corrupt each other's results. Serialise them, e.g. on one stream.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+size_t tdpm_dt_noalloc_max_elements(void);
+tdpm_status tdpm_dt_noalloc(const float *S, int32_t H, int32_t W, const float d[4], int32_t x_off, int32_t x_step,
+                            int32_t nx, int32_t y_off, int32_t y_step, int32_t ny, float *D, int32_t *arg,
+                            void *stream);
+
 /* Correlation of K filters of one shape with one feature level (step 1, Sec. 2), on device buffers:
  *   out[k][y][x] = sum_{dy<h,dx<w,c<32} filt[k][dy][dx][c] * feat[y+dy][x+dx][c], y < H-h+1, x < W-w+1.
  * feat: device NHWC FP32; filt: HOST [K][h][w][32] FP32 (uploaded per call); out: device [K][H-h+1][W-w+1] FP32.

@@ -97,6 +97,9 @@ SIGNATURES = {
     "tdpm_dt": (_c_i32, [_VP, _c_i32, _c_i32, _c_f32p, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _VP, _VP, _VP,
                          _VP]),
     "tdpm_correlate": (_c_i32, [_VP, _c_i32, _c_i32, _c_f32p, _c_i32, _c_i32, _c_i32, _c_i32, _VP, _VP]),
+    "tdpm_dt_noalloc_max_elements": (ctypes.c_size_t, []),
+    "tdpm_dt_noalloc": (_c_i32, [_VP, _c_i32, _c_i32, _c_f32p, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _VP,
+                                 _VP, _VP]),
     "tdpm_kernel_launches": (ctypes.c_uint64, []),
     "tdpm_profile_enable": (_c_i32, [_VP, _c_i32]),
     "tdpm_profile_read": (_c_i32, [_VP, _c_i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
@@ -301,6 +304,19 @@ def tdpm_dt(S, d: Sequence[float], x_off: int, x_step: int, nx: int, y_off: int,
     dd = (ctypes.c_float * 4)(*[float(v) for v in d])
     _check(lib().tdpm_dt(_ptr(S), H, W, dd, x_off, x_step, nx, y_off, y_step, ny, _ptr(D), _ptr(arg), _ptr(scratch),
                          _stream_ptr(stream)))
+
+
+def tdpm_dt_noalloc_max_elements() -> int:
+    return int(lib().tdpm_dt_noalloc_max_elements())
+
+
+def tdpm_dt_noalloc(S, d: Sequence[float], x_off: int, x_step: int, nx: int, y_off: int, y_step: int, ny: int, D,
+                    arg, stream=None) -> None:
+    """tdpm_dt without a caller scratch buffer: the library's fixed device scratch is used (no device allocation)."""
+    H, W = int(S.shape[0]), int(S.shape[1])
+    dd = (ctypes.c_float * 4)(*[float(v) for v in d])
+    _check(lib().tdpm_dt_noalloc(_ptr(S), H, W, dd, x_off, x_step, nx, y_off, y_step, ny, _ptr(D), _ptr(arg),
+                                 _stream_ptr(stream)))
 
 
 def tdpm_correlate(feat, filters: np.ndarray, out, precision: int = PREC_FP32, stream=None) -> None:
