@@ -3,11 +3,17 @@
 
 Workload (default): one 500x375 image as a 36-level HOG-shaped pyramid (10 levels per octave, sbin 8; 88,330 cells,
 uniform [0, 0.2)), scored by a 6-component DPM-shaped class model (roots 5x11, 7x7, 11x5 and their mirrors, 8 parts of
-6x6 each, 54 filters). A step is one whole pass of the path over that image: correlation (decomposed BF16 by default),
-both distance-transform passes, assembly, threshold and the copy of the detections to the host.
+6x6 each, 54 filters). A step is one whole pass of the path over that image: correlation (decomposed, rank 8 per
+filter, on BF16 tensor cores by default), both distance-transform passes, assembly, threshold and the copy of the
+detections to the host.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--form decomposed|full] [--precision bf16|fp32] [--rank R]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form decomposed|full] [--precision bf16x3|bf16|fp32]
+                  [--rank R] [--mode per_filter|joint]
   python bench.py --impl reference    # the FP64 CPU oracle on the same workload and metric
+
+Reported beside the headline: the full form in FP32 (the GPU baseline the decomposed form must beat) and in the same
+precision, detection agreement with the FP64 oracle on the same factors (parity), and a rank sweep of the detection
+agreement of the decomposed form with the full FP32 form (the accuracy the decomposition gives up).
 
 Under torchrun every rank scores its own replica of the image (images are independent: no data-path collective); the
 barrier and the max-over-ranks timing use the process group.
@@ -22,7 +28,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -34,7 +39,8 @@ from paper_1707_03268_gb300 import synth  # noqa: E402
 
 METRIC = "images/sec and p50/p99 latency, decomposed BF16 vs full FP32, at >=99.5% agreement"
 L2_BYTES = 129 * 1024 * 1024
-RANK_LADDER = (4, 6, 8, 12, 16, 20, 24, 28, 32)
+RANK_SWEEP = (4, 8, 16, 24, 32, 36)
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 3}
 
 
 def parse():
@@ -44,13 +50,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tdpm", choices=["tdpm", "reference"])
     ap.add_argument("--form", default="decomposed", choices=["decomposed", "full"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
-    ap.add_argument("--rank", type=int, default=0,
-                    help="CP rank of the decomposed form; 0 = the smallest rank of RANK_LADDER whose detections agree "
-                         ">= 99.5%% with the full FP32 form")
+    ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
+    ap.add_argument("--rank", type=int, default=8, help="CP rank per filter (per_filter) or per shape group (joint)")
     ap.add_argument("--mode", default="per_filter", choices=["per_filter", "joint"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-compare", action="store_true", help="skip the full FP32 comparison run")
+    ap.add_argument("--no-compare", action="store_true", help="skip the full-form comparison runs")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the rank sweep")
     return ap.parse_args()
 
 
@@ -110,7 +115,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------------------ roofline model
 def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
-    """Algorithmic DRAM bytes (and flops) per stage for one image: every input read once, every output written once."""
+    """Algorithmic DRAM bytes and flops per stage for one image: every input read once, every output written once."""
     sizes = pyr.sizes
     lam = pyr.lam
     L = len(sizes)
@@ -119,13 +124,13 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
         groups.setdefault((0,) + comp.root.shape[:2], []).append(comp.root)
         for p in comp.parts:
             groups.setdefault((1,) + p.filt.shape[:2], []).append(p.filt)
-    bf = precision == "bf16"
-    fb = 2 if bf else 4
-    corr = "corr_tc" if bf else "corr_f32"
-    zproj = "zproj_tc" if bf else "zproj_f32"
+    tc = precision in ("bf16", "bf16x3")
+    fb = {"fp32": 4, "bf16": 2, "bf16x3": 4}[precision]  # feature bytes per channel read by the correlation
+    corr = "corr_tc" if tc else "corr_f32"
+    zproj = "zproj_tc" if tc else "zproj_f32"
     out = {corr: [0, 0], zproj: [0, 0], "sep": [0, 0], "dt": [0, 0], "assemble": [0, 0], "to_bf16": [0, 0]}
-    if bf:
-        out["to_bf16"][0] = sum(H * W * 32 * (4 + 2) for (H, W) in sizes)
+    if tc:
+        out["to_bf16"][0] = sum(H * W * 32 * (4 + fb) for (H, W) in sizes)
     for (role, h, w), fl in groups.items():
         K = len(fl)
         R = (rank * K if not joint else rank) if rank < h * w else h * w * K
@@ -188,10 +193,9 @@ def stage_roofline(name, ms_per_image, launches_per_image, model, peaks, sm_mhz)
     src_hbm = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
     b, f = model[name]["bytes"], model[name]["flops"]
     s = ms_per_image / 1e3
-    t_hbm = b / (hbm * 1e9)
-    cand = [("hbm", t_hbm)]
+    cand = [("hbm", b / (hbm * 1e9))]
+    tp = float(peaks.get("bf16_tflops", 1900.0))
     if name in TENSOR_STAGES:
-        tp = float(peaks.get("bf16_tflops", 1900.0))
         cand.append(("tensor", f / (tp * 1e12)))
     elif name in ALU_STAGES:
         cand.append(("alu", f / (fp32_alu_peak_tflops(sm_mhz) * 1e12)))
@@ -201,7 +205,6 @@ def stage_roofline(name, ms_per_image, launches_per_image, model, peaks, sm_mhz)
     if bound == "hbm":
         out.update(achieved=b / s / 1e9, peak=hbm, unit="GB/s", peak_source=src_hbm)
     elif bound == "tensor":
-        tp = float(peaks.get("bf16_tflops", 1900.0))
         out.update(achieved=f / s / 1e12, peak=tp, unit="TFLOP/s",
                    peak_source="MEASURED_PEAKS.json bf16_tflops burst (of measured)" if "bf16_tflops" in peaks
                    else "fallback 1900 TFLOP/s")
@@ -213,24 +216,22 @@ def stage_roofline(name, ms_per_image, launches_per_image, model, peaks, sm_mhz)
     return out
 
 
-# ------------------------------------------------------------------------------------------------ reference arm
+# ------------------------------------------------------------------------------------------------ oracle legs
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, same workload and metric (rank 0 of N only)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import oracle as orc
-    from paper_1707_03268_gb300 import synth as sy
 
-    wl = sy.config_c2()
+    wl = synth.config_c2()
     pyr = wl.pyramids[0]
     n_comp = len(wl.model.components)
 
     def one_step(i):
         # one component of the model over the whole pyramid: 1/6 of an image
-        c = i % n_comp
-        sub = sy.Model([wl.model.components[c]])
-        scored = orc.score_pyramid(sub, pyr)
-        orc.detect(scored, load_tau())
+        sub = synth.Model([wl.model.components[i % n_comp]])
+        orc.detect(orc.score_pyramid(sub, pyr), load_tau())
 
     for i in range(args.warmup):
         one_step(i)
@@ -238,8 +239,7 @@ def run_reference(args):
     for i in range(args.steps):
         one_step(i)
     dt = time.perf_counter() - t0
-    images = args.steps / n_comp
-    v = images / dt
+    v = (args.steps / n_comp) / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "images/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -252,20 +252,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_oracle(wl, budget_s: float = 15.0):
-    """The FP64 oracle as it stands, on this host's cores: whole-image full-form scoring, repeated within a budget."""
+def cpu_baseline_oracle(wl, filters, gpu_keys, tau, budget_s: float = 15.0):
+    """The FP64 oracle as it stands, on this host's cores: the same whole image with the same filters (rebuilt from
+    the library's FP64 factors for the decomposed form), repeated within a time budget. Its detections also give the
+    parity agreement of the GPU's detections."""
     from oracle import oracle as orc
     pyr = wl.pyramids[0]
     n = 0
     t0 = time.perf_counter()
+    dets = None
     while True:
-        orc.detect(orc.score_pyramid(wl.model, pyr), load_tau())
+        dets = orc.detect(orc.score_pyramid(wl.model, pyr, filters=filters), tau)
         n += 1
         if time.perf_counter() - t0 >= budget_s or n >= 20:
             break
     dt = time.perf_counter() - t0
+    ok = set(d[:4] for d in dets)
     return {"value": n / dt, "unit": "images/s", "cores": orc.num_threads(), "kind": "oracle",
-            "sample": f"{n} whole 500x375 images (36 levels, 54 filters), full form, FP64"}
+            "sample": f"{n} whole 500x375 images (36 levels, 54 filters), FP64, same filters as the GPU run",
+            "parity_agreement_with_gpu": len(ok & gpu_keys) / max(1, len(ok | gpu_keys)),
+            "oracle_detections": len(ok)}
+
+
+def factor_filters(tdpm, ctx, mid):
+    """Filters rebuilt in FP64 from the library's exported factors, model order (for the oracle leg)."""
+    from oracle import oracle as orc
+    n_f, n_g = tdpm.tdpm_model_info(ctx, mid)
+    out = [None] * n_f
+    for g in range(n_g):
+        info = tdpm.tdpm_group_info(ctx, mid, g)
+        A, B, C, Lam = tdpm.tdpm_get_factors(ctx, mid, g)
+        F = orc.joint_reconstruct(Lam, A, B, C)
+        for k, fid in enumerate(info["filter_ids"]):
+            out[fid] = F[k]
+    return out
 
 
 # ------------------------------------------------------------------------------------------------ main arm
@@ -286,8 +306,9 @@ def main():
         dist.init_process_group("nccl")
 
     form = tdpm.FORM_DECOMPOSED if args.form == "decomposed" else tdpm.FORM_FULL
-    prec = tdpm.PREC_BF16 if args.precision == "bf16" else tdpm.PREC_FP32
+    prec = PRECISIONS[args.precision]
     joint = args.mode == "joint"
+    dmode = tdpm.DECOMP_JOINT if joint else tdpm.DECOMP_PER_FILTER
     wl = synth.config_c2()
     pyr = wl.pyramids[0]
     tau = load_tau()
@@ -300,8 +321,8 @@ def main():
     cap = 1 << 16
     det_buf = np.zeros(cap, dtype=tdpm.DETECTION_DTYPE)
 
-    def step(model_id, f, p):
-        sid = tdpm.tdpm_build_pyramid_scores(ctx, model_id, dp, f, p, stream)
+    def step(f, p):
+        sid = tdpm.tdpm_build_pyramid_scores(ctx, mid, dp, f, p, stream)
         dets = tdpm.tdpm_detect(ctx, sid, tau, capacity=cap, stream=stream, out=det_buf)
         tdpm.tdpm_release(ctx, sid)
         return dets
@@ -309,30 +330,9 @@ def main():
     def keys(d):
         return set(zip(d["component"].tolist(), d["level"].tolist(), d["y"].tolist(), d["x"].tolist()))
 
-    rep = None
-    rank_sweep = None
-    chosen_rank = args.rank
-    if form == tdpm.FORM_DECOMPOSED:
-        dmode = tdpm.DECOMP_JOINT if joint else tdpm.DECOMP_PER_FILTER
-        if args.rank > 0:
-            rep = tdpm.tdpm_decompose(ctx, mid, args.rank, dmode, max_iters=500, seed=1)
-        else:
-            # smallest rank whose detections agree >= 99.5% with the full FP32 form (the metric's condition)
-            ref_keys = keys(step(mid, tdpm.FORM_FULL, tdpm.PREC_FP32))
-            rank_sweep = {}
-            for r in RANK_LADDER:
-                rep = tdpm.tdpm_decompose(ctx, mid, r, dmode, max_iters=500, seed=1)
-                a = keys(step(mid, form, prec))
-                rank_sweep[r] = {"agreement": len(a & ref_keys) / max(1, len(a | ref_keys)),
-                                 "max_rel_error": rep["max_rel_error"], "mean_rel_error": rep["mean_rel_error"],
-                                 "gain_formula_1": rep["gain"]}
-                chosen_rank = r
-                if rank_sweep[r]["agreement"] >= 0.995:
-                    break
-
-    def timed(model_id, f, p, steps, warmup, prof=False):
+    def timed(f, p, steps, warmup, prof=False):
         for _ in range(warmup):
-            step(model_id, f, p)
+            step(f, p)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -345,11 +345,10 @@ def main():
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        n_det = 0
         for i in range(steps):
-            flush.zero_()  # inputs are smaller than L2: evict them between steps (outside the events)
+            flush.zero_()  # the pyramid is smaller than L2: evict it between steps (outside the events)
             ev[i][0].record(stream)
-            n_det = len(step(model_id, f, p))
+            step(f, p)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -366,35 +365,41 @@ def main():
             t = torch.tensor([total_ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = float(t.item())
-        return {"ms": ms, "total_ms": total_ms, "wall_s": wall, "launches": launches, "n_det": n_det,
-                "stages": stages}
+        return {"ms": ms, "total_ms": total_ms, "wall_s": wall, "launches": launches, "stages": stages}
 
-    # ---- headline run (decomposed BF16 by default)
+    def rate(run):
+        return len(run["ms"]) * world / (run["total_ms"] / 1e3)
+
+    rep = None
+    if form == tdpm.FORM_DECOMPOSED:
+        rep = tdpm.tdpm_decompose(ctx, mid, args.rank, dmode, max_iters=500, seed=1)
+
+    # ---- headline run
     clocks = ClockSampler(local)
     clocks.start()
-    main_run = timed(mid, form, prec, args.steps, args.warmup)
+    main_run = timed(form, prec, args.steps, args.warmup)
     clk = clocks.stop()
-    value = args.steps * world / (main_run["total_ms"] / 1e3)
+    value = rate(main_run)
     ms_sorted = sorted(main_run["ms"])
     p50 = ms_sorted[len(ms_sorted) // 2]
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]
+    head_keys = keys(step(form, prec))
 
     # ---- per-stage device time (same workload, CUDA events around each stage on its stream)
-    prof_run = timed(mid, form, prec, max(10, args.steps // 2), 1, prof=True)
+    prof_run = timed(form, prec, max(10, args.steps // 4), 1, prof=True)
     stages = prof_run["stages"]
-    model = stage_bytes(wl, pyr, args.form, args.precision, chosen_rank, joint)
-    dom_name, (dom_ms, dom_n) = max(stages.items(), key=lambda kv: kv[1][0])
-    roofline = None
+    n_prof = len(prof_run["ms"])
+    model = stage_bytes(wl, pyr, args.form, args.precision, args.rank, joint)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             peaks = json.load(f)
     except Exception:
         pass
-    steps_prof = prof_run_steps(prof_run)
     sm_mhz = (clk or {}).get("sm_mhz") or 1920.0
-    rooflines = {name: stage_roofline(name, ms / steps_prof, n / steps_prof, model, peaks, sm_mhz)
+    rooflines = {name: stage_roofline(name, ms / n_prof, n / n_prof, model, peaks, sm_mhz)
                  for name, (ms, n) in stages.items() if name in model}
+    dom_name = max(stages.items(), key=lambda kv: kv[1][0])[0]
     roofline = rooflines.get(dom_name)
 
     # ---- end to end through the public API: pyramid H2D from pinned host memory, detections D2H
@@ -404,14 +409,13 @@ def main():
     def e2e_step():
         for hl, dl in zip(host_levels, levels):
             dl.copy_(hl, non_blocking=True)
-        return step(mid, form, prec)
+        return step(form, prec)
 
     for _ in range(args.warmup):
         e2e_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    t0 = time.perf_counter()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -428,49 +432,63 @@ def main():
     e2e = {"value": args.steps * world / (e2e_ms / 1e3), "unit": "images/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": n_det * tdpm.DETECTION_DTYPE.itemsize + 8}
 
-    # ---- comparison: full FP32 on the same image, and detection agreement with it
+    # ---- full-form comparison runs on the same image
     compare = None
     if not args.no_compare:
-        full_run = timed(mid, tdpm.FORM_FULL, tdpm.PREC_FP32, max(10, args.steps // 2), 2)
-        d_main = step(mid, form, prec).copy()
-        d_full = step(mid, tdpm.FORM_FULL, tdpm.PREC_FP32).copy()
-        ka = set(zip(d_main["component"], d_main["level"], d_main["y"], d_main["x"]))
-        kb = set(zip(d_full["component"], d_full["level"], d_full["y"], d_full["x"]))
-        agree = len(ka & kb) / max(1, len(ka | kb))
-        full_ms = sorted(full_run["ms"])
-        compare = {"full_fp32_images_per_s": len(full_ms) / (sum(full_ms) / 1e3),
-                   "full_fp32_p50_ms": full_ms[len(full_ms) // 2],
-                   "agreement_vs_full_fp32": agree, "detections": len(ka), "detections_full_fp32": len(kb)}
+        n_cmp = max(10, args.steps // 4)
+        full32 = timed(tdpm.FORM_FULL, tdpm.PREC_FP32, n_cmp, 2)
+        full_keys = keys(step(tdpm.FORM_FULL, tdpm.PREC_FP32))
+        compare = {"full_fp32_images_per_s": rate(full32), "full_fp32_p50_ms": sorted(full32["ms"])[n_cmp // 2],
+                   "speedup_vs_full_fp32": value / rate(full32),
+                   "agreement_with_full_fp32": len(head_keys & full_keys) / max(1, len(head_keys | full_keys)),
+                   "detections": len(head_keys), "detections_full_fp32": len(full_keys)}
+        if prec != tdpm.PREC_FP32 or form != tdpm.FORM_FULL:
+            fullp = timed(tdpm.FORM_FULL, prec, n_cmp, 2)
+            compare[f"full_{args.precision}_images_per_s"] = rate(fullp)
 
+    # ---- oracle leg: CPU baseline and parity of the headline detections (same factors)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_oracle(wl)
+        filters = factor_filters(tdpm, ctx, mid) if form == tdpm.FORM_DECOMPOSED else None
+        cpu = cpu_baseline_oracle(wl, filters, head_keys, tau)
+
+    # ---- accuracy given up by the decomposition: agreement with the full FP32 form per rank
+    sweep = None
+    if form == tdpm.FORM_DECOMPOSED and not args.no_sweep and compare is not None:
+        sweep = {}
+        for r in RANK_SWEEP:
+            rr = tdpm.tdpm_decompose(ctx, mid, r, dmode, max_iters=500, seed=1)
+            a = keys(step(form, prec))
+            run = timed(form, prec, 50, 2)
+            sweep[r] = {"agreement_with_full_fp32": len(a & full_keys) / max(1, len(a | full_keys)),
+                        "images_per_s": rate(run), "max_rel_error": rr["max_rel_error"],
+                        "mean_rel_error": rr["mean_rel_error"], "gain_formula_1": rr["gain"]}
 
     line = {"metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main_run["total_ms"] / args.steps, "p50_ms": p50, "p99_ms": p99,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if prec == tdpm.PREC_BF16 else "f32", "data": "synthetic",
+            "dtype": args.precision if prec != tdpm.PREC_FP32 else "f32", "data": "synthetic",
             "config": {"workload": wl.name, "image": "500x375", "levels": len(pyr.levels),
                        "components": len(wl.model.components), "filters": len(wl.model.filters()),
                        "form": args.form, "precision": args.precision,
-                       "rank": chosen_rank if form == tdpm.FORM_DECOMPOSED else None,
+                       "precision_note": {"bf16x3": "BF16 tensor cores, operands split hi+lo (3 MMAs per product), "
+                                                    "FP32 accumulation",
+                                          "bf16": "BF16 tensor cores, FP32 accumulation",
+                                          "fp32": "FP32 ALUs"}[args.precision],
+                       "rank": args.rank if form == tdpm.FORM_DECOMPOSED else None,
                        "decomposition": args.mode if form == tdpm.FORM_DECOMPOSED else None,
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}"},
-            "gpu_launches": main_run["launches"], "stages_ms_per_image": {k: v[0] / prof_run_steps(prof_run)
-                                                                          for k, v in stages.items()},
+            "gpu_launches": main_run["launches"],
+            "stages_ms_per_image": {k: v[0] / n_prof for k, v in stages.items()},
             "roofline": roofline, "rooflines": rooflines, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
-            "compare": compare,
-            "decomposition_report": rep, "rank_sweep": rank_sweep, "wall_s_timed": main_run["wall_s"]}
+            "compare": compare, "decomposition_report": rep, "rank_sweep": sweep,
+            "wall_s_timed": main_run["wall_s"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     tdpm.tdpm_destroy(ctx)
     if world > 1:
         dist.destroy_process_group()
-
-
-def prof_run_steps(run) -> int:
-    return len(run["ms"])
 
 
 if __name__ == "__main__":

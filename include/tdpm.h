@@ -53,10 +53,16 @@ typedef int32_t tdpm_status;
 #define TDPM_FORM_FULL 0
 #define TDPM_FORM_DECOMPOSED 1
 
-/* arithmetic of the correlation: operands in FP32, BF16 or FP8 e4m3 (per-tensor scale); FP32 accumulation always */
+/* arithmetic of the correlation, FP32 accumulation always:
+ *   FP32     FP32 operands on the FP32 ALUs;
+ *   BF16     BF16 operands on the tensor cores (features and tensor-core factors rounded to BF16);
+ *   FP8      reserved (not implemented: returns TDPM_ERR_ARG);
+ *   BF16X3   split BF16 on the tensor cores: every operand x = hi + lo with hi = bf16(x), lo = bf16(x - hi), and each
+ *            product is formed as hi*hi + hi*lo + lo*hi (relative error about 2^-16, three MMAs per product). */
 #define TDPM_PREC_FP32 0
 #define TDPM_PREC_BF16 1
 #define TDPM_PREC_FP8 2
+#define TDPM_PREC_BF16X3 3
 
 /* decomposition mode: one CP per filter (Sec. 4, per-filter rank R) or one CP per stacked shape group with shared
  * factors a_r, b_r, c_r and per-filter weights Lambda[k][r] */

@@ -145,110 +145,114 @@ __global__ void __launch_bounds__(ZP_CELLS) zproj_kernel(const ZJob *__restrict_
 }
 
 // ------------------------------------------------------------------------------------------------------------ K3/K4
-// A warp owns 32 consecutive columns x SP_ROWS rows of output positions for FC filters (CTA = 4 warps stacked along
-// y, 32 x 32 positions). For every rank-1 term r of the filter chunk each lane loads the column strips
-// Z_r[y0 .. y0+SP_ROWS+h-2][x] and [x+32] into registers, runs the y pass with a_r in registers (sliding window),
-// exchanges the SP_ROWS x 64 intermediate row through shared memory, runs the x pass with b_r, and adds
-// Lambda[k][r] * U_r to each filter's accumulators. No block-wide barrier is needed.
-constexpr int SP_ROWS = 8, SP_WARPS = 4, SP_FC_JOINT = 8, SP_MAXW = 16;
+// CTA tile: SQ_T x SQ_T output positions of one filter (per-filter mode) or of SQ_FC_JOINT filters (joint mode).
+// For every rank-1 term r of those filters the CTA copies the Z_r halo ((SQ_T+h-1) x (SQ_T+w-1) cells) into shared
+// memory with cp.async (zero fill outside the map), double-buffered so term r+1 is in flight while term r is
+// processed: the y pass with a_r writes a SQ_T x (SQ_T+w-1) intermediate to shared memory, the x pass with b_r gives
+// U_r at each thread's 4 positions, and Lambda[k][r] * U_r is added to each filter's accumulators.
+constexpr int SQ_T = 32, SQ_THREADS = 256, SQ_MAXHW = 16, SQ_HALO = SQ_T + SQ_MAXHW - 1, SQ_FC_JOINT = 8;
+constexpr int SQ_ROWS_PER_THREAD = SQ_T * SQ_T / SQ_THREADS;  // 4
 
-template <int FC, int HH>
-__global__ void __launch_bounds__(SP_WARPS * 32) sep_kernel(const SepJob *__restrict__ jobs, int n_jobs,
-                                                            const float *__restrict__ A, const float *__restrict__ B,
-                                                            const float *__restrict__ lam,
-                                                            const int *__restrict__ rank_off, int K, int R, int h,
-                                                            int w)
+__device__ __forceinline__ void cp_async_f32(float *dst, const float *src, bool pred)
 {
-    __shared__ float tsm[SP_WARPS][SP_ROWS][64 + 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const int n = pred ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int FC>
+__global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restrict__ jobs, int n_jobs,
+                                                         const float *__restrict__ A, const float *__restrict__ B,
+                                                         const float *__restrict__ lam,
+                                                         const int *__restrict__ rank_off, int K, int R, int h, int w)
+{
+    __shared__ float zs[2][SQ_HALO][SQ_HALO + 1];
+    __shared__ float ts[SQ_T][SQ_HALO + 1];
+    __shared__ float coef[2][2 * SQ_MAXHW + FC];
+
+    const int tid = threadIdx.x;
     const int ji = find_job(jobs, n_jobs, blockIdx.x);
     const SepJob J = jobs[ji];
     int local = blockIdx.x - J.begin;
     const int f_chunks = (FC == 1) ? K : (K + FC - 1) / FC;
     const int fc = local % f_chunks;
     local /= f_chunks;
-    const int x0 = (local % J.tiles_x) * 32, y0 = (local / J.tiles_x) * (SP_ROWS * SP_WARPS) + warp * SP_ROWS;
-    if (y0 >= J.Ho) return;
+    const int x0 = (local % J.tiles_x) * SQ_T, y0 = (local / J.tiles_x) * SQ_T;
     const int k0 = fc * FC;
     int r_begin = 0, r_end = R;
     if (FC == 1) { r_begin = rank_off[k0]; r_end = rank_off[k0 + 1]; }
-    const int x = x0 + lane;
+    const int HY = SQ_T + h - 1, HX = SQ_T + w - 1;
     const size_t plane = (size_t)J.H * J.W;
-    const bool inA = x < J.W, inB = x + 32 < J.W;
-    float acc[FC][SP_ROWS];
+
+    auto load_term = [&](int r, int buf) {
+        const float *Zr = J.Z + (size_t)r * plane;
+        for (int i = tid; i < HY * HX; i += SQ_THREADS) {
+            const int yy = i / HX, xx = i - yy * HX;
+            const int gy = y0 + yy, gx = x0 + xx;
+            const bool in = gy < J.H && gx < J.W;
+            cp_async_f32(&zs[buf][yy][xx], in ? Zr + (size_t)gy * J.W + gx : Zr, in);
+        }
+        if (tid < h) coef[buf][tid] = __ldg(A + (size_t)tid * R + r);
+        else if (tid < h + w) coef[buf][tid] = __ldg(B + (size_t)(tid - h) * R + r);
+        else if (tid < h + w + FC) {
+            const int f = tid - h - w;
+            coef[buf][tid] = (FC == 1) ? __ldg(lam + r) : ((k0 + f < K) ? __ldg(lam + (size_t)(k0 + f) * R + r) : 0.f);
+        }
+        cp_async_commit();
+    };
+
+    const int tx = tid % SQ_T, ty = tid / SQ_T;  // each thread: column tx, rows ty*4 .. ty*4+3
+    float acc[FC][SQ_ROWS_PER_THREAD];
 #pragma unroll
     for (int f = 0; f < FC; ++f)
 #pragma unroll
-        for (int i = 0; i < SP_ROWS; ++i) acc[f][i] = 0.f;
-    float (*ts)[64 + 1] = tsm[warp];
+        for (int j = 0; j < SQ_ROWS_PER_THREAD; ++j) acc[f][j] = 0.f;
 
+    if (r_begin < r_end) load_term(r_begin, 0);
     for (int r = r_begin; r < r_end; ++r) {
-        const float *Zr = J.Z + (size_t)r * plane;
-        float a[HH];
-#pragma unroll
-        for (int dy = 0; dy < HH; ++dy) a[dy] = (dy < h) ? __ldg(A + dy * R + r) : 0.f;
-        float zA[SP_ROWS + HH - 1], zB[SP_ROWS + HH - 1];
-#pragma unroll
-        for (int i = 0; i < SP_ROWS + HH - 1; ++i) {
-            const int yy = y0 + i;
-            const bool ry = yy < J.H;
-            zA[i] = (ry && inA) ? __ldg(Zr + (size_t)yy * J.W + x) : 0.f;
-            zB[i] = (ry && inB) ? __ldg(Zr + (size_t)yy * J.W + x + 32) : 0.f;
+        const int buf = (r - r_begin) & 1;
+        if (r + 1 < r_end) {
+            load_term(r + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
-#pragma unroll
-        for (int i = 0; i < SP_ROWS; ++i) {
-            float tA = 0.f, tB = 0.f;
-#pragma unroll
-            for (int dy = 0; dy < HH; ++dy) {
-                tA = fmaf(a[dy], zA[i + dy], tA);
-                tB = fmaf(a[dy], zB[i + dy], tB);
-            }
-            ts[i][lane] = tA;
-            ts[i][lane + 32] = tB;
+        __syncthreads();
+        const float *a = coef[buf], *b = coef[buf] + h, *lf = coef[buf] + h + w;
+        for (int i = tid; i < SQ_T * HX; i += SQ_THREADS) {
+            const int yy = i / HX, xx = i - yy * HX;
+            float t = 0.f;
+            for (int dy = 0; dy < h; ++dy) t = fmaf(a[dy], zs[buf][yy + dy][xx], t);
+            ts[yy][xx] = t;
         }
-        __syncwarp();
-        float lf[FC];
+        __syncthreads();
 #pragma unroll
-        for (int f = 0; f < FC; ++f)
-            lf[f] = (FC == 1) ? __ldg(lam + r) : ((k0 + f < K) ? __ldg(lam + (size_t)(k0 + f) * R + r) : 0.f);
-        float bw[SP_MAXW];
-#pragma unroll
-        for (int dx = 0; dx < SP_MAXW; ++dx) bw[dx] = (dx < w) ? __ldg(B + dx * R + r) : 0.f;
-#pragma unroll
-        for (int i = 0; i < SP_ROWS; ++i) {
+        for (int j = 0; j < SQ_ROWS_PER_THREAD; ++j) {
+            const int yy = ty * SQ_ROWS_PER_THREAD + j;
             float u = 0.f;
+            for (int dx = 0; dx < w; ++dx) u = fmaf(b[dx], ts[yy][tx + dx], u);
 #pragma unroll
-            for (int dx = 0; dx < SP_MAXW; ++dx)
-                if (dx < w) u = fmaf(bw[dx], ts[i][lane + dx], u);
-#pragma unroll
-            for (int f = 0; f < FC; ++f) acc[f][i] = fmaf(lf[f], u, acc[f][i]);
+            for (int f = 0; f < FC; ++f) acc[f][j] = fmaf(lf[f], u, acc[f][j]);
         }
-        __syncwarp();
+        __syncthreads();
     }
+    const int x = x0 + tx;
     if (x >= J.Wo) return;
 #pragma unroll
     for (int f = 0; f < FC; ++f) {
         if (k0 + f >= K) break;
         float *o = J.out + (size_t)(k0 + f) * J.Ho * J.Wo + x;
 #pragma unroll
-        for (int i = 0; i < SP_ROWS; ++i)
-            if (y0 + i < J.Ho) o[(size_t)(y0 + i) * J.Wo] = acc[f][i];
+        for (int j = 0; j < SQ_ROWS_PER_THREAD; ++j) {
+            const int y = y0 + ty * SQ_ROWS_PER_THREAD + j;
+            if (y < J.Ho) o[(size_t)y * J.Wo] = acc[f][j];
+        }
     }
-}
-
-template <int FC>
-cudaError_t launch_sep_fc(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
-                          const float *lam, const int *rank_off, int K, int R, int h, int w, cudaStream_t s)
-{
-    const dim3 grid(total_tiles), block(SP_WARPS * 32);
-    switch (h) {
-    case 5: sep_kernel<FC, 5><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
-    case 6: sep_kernel<FC, 6><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
-    case 7: sep_kernel<FC, 7><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
-    case 11: sep_kernel<FC, 11><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
-    default: sep_kernel<FC, 16><<<grid, block, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w); break;
-    }
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -281,18 +285,21 @@ cudaError_t launch_zproj_simt(const ZJob *d_jobs, int n_jobs, int total_tiles, c
     return cudaGetLastError();
 }
 
-int sep_tile_x() { return 32; }
-int sep_tile_y() { return SP_ROWS * SP_WARPS; }
-int sep_filters_per_cta(bool joint) { return joint ? SP_FC_JOINT : 1; }
+int sep_tile_x() { return SQ_T; }
+int sep_tile_y() { return SQ_T; }
+int sep_filters_per_cta(bool joint) { return joint ? SQ_FC_JOINT : 1; }
 
 cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
                        const float *lam, const int *rank_off, int K, int R, int h, int w, bool joint, cudaStream_t s)
 {
     if (total_tiles <= 0) return cudaSuccess;
-    if (h < 1 || h > 16 || w < 1 || w > SP_MAXW) return cudaErrorInvalidValue;
+    if (h < 1 || h > SQ_MAXHW || w < 1 || w > SQ_MAXHW) return cudaErrorInvalidValue;
     note_launches(1);
-    if (joint) return launch_sep_fc<SP_FC_JOINT>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
-    return launch_sep_fc<1>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
+    if (joint)
+        sep_kernel<SQ_FC_JOINT><<<total_tiles, SQ_THREADS, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w);
+    else
+        sep_kernel<1><<<total_tiles, SQ_THREADS, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w);
+    return cudaGetLastError();
 }
 
 }  // namespace tdpm

@@ -136,16 +136,22 @@ __device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
     return lo;
 }
 
-// grid: one CTA per (job, M tile, N tile); filt: [taps][4][Npad][8] BF16; NT = N tile width (multiple of 16, <= 256)
+// grid: one CTA per (job, M tile, N tile); filt: [taps][4][Npad][8] BF16; NT = N tile width (multiple of 16, <= 256).
+// SPLIT: operands come as hi and lo BF16 parts (filt_lo, the job's tmap_lo) and every K step issues three MMAs,
+// hi*hi + hi*lo + lo*hi, into the same FP32 accumulator.
+template <bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__restrict__ jobs, int n_jobs,
-                                                                const uint16_t *__restrict__ filt, int K, int Npad,
+                                                                const uint16_t *__restrict__ filt,
+                                                                const uint16_t *__restrict__ filt_lo, int K, int Npad,
                                                                 int NT, int n_tiles_n, int h, int w, uint32_t tmem_cols,
                                                                 int *err)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
-    const uint32_t b_stage_bytes = (uint32_t)NT * 64;
+    constexpr uint32_t NPART = SPLIT ? 2 : 1;
+    const uint32_t b_part_bytes = (uint32_t)NT * 64;
+    const uint32_t a_stage_bytes = NPART * A_STAGE_BYTES, b_stage_bytes = NPART * b_part_bytes;
     uint8_t *a_smem = sm;
-    uint8_t *b_smem = sm + TC_STAGES * A_STAGE_BYTES;
+    uint8_t *b_smem = sm + TC_STAGES * a_stage_bytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + TC_STAGES * b_stage_bytes);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * TC_STAGES + 1);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES), done = smem_u32(bars + 2 * TC_STAGES);
@@ -184,12 +190,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
             const int s = t % TC_STAGES;
             if (t >= TC_STAGES) mbar_wait(empty0 + 8 * s, ((t / TC_STAGES) - 1) & 1, err);
             const uint32_t full = full0 + 8 * s;
-            mbar_expect_tx(full, A_STAGE_BYTES + b_stage_bytes);
+            mbar_expect_tx(full, a_stage_bytes + b_stage_bytes);
             const int dy = t / w, dx = t - dy * w;
-            tma_load_3d(smem_u32(a_smem + s * A_STAGE_BYTES), &J->tmap, 0, p0 + dy * W + dx, 0, full);
+            const uint32_t adst = smem_u32(a_smem + s * a_stage_bytes);
+            tma_load_3d(adst, &J->tmap, 0, p0 + dy * W + dx, 0, full);
+            if (SPLIT) tma_load_3d(adst + A_STAGE_BYTES, &J->tmap_lo, 0, p0 + dy * W + dx, 0, full);
             const uint32_t bdst = smem_u32(b_smem + s * b_stage_bytes);
-            for (int kc = 0; kc < 4; ++kc)
-                bulk_load(bdst + kc * NT * 16, filt + (((size_t)t * 4 + kc) * Npad + n0) * 8, (uint32_t)NT * 16, full);
+            for (int kc = 0; kc < 4; ++kc) {
+                const size_t off = (((size_t)t * 4 + kc) * Npad + n0) * 8;
+                bulk_load(bdst + kc * NT * 16, filt + off, (uint32_t)NT * 16, full);
+                if (SPLIT) bulk_load(bdst + b_part_bytes + kc * NT * 16, filt_lo + off, (uint32_t)NT * 16, full);
+            }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: two K=16 steps per tap (channel chunks {0,1} and {2,3})
@@ -198,13 +209,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
             const int s = t % TC_STAGES;
             mbar_wait(full0 + 8 * s, (t / TC_STAGES) & 1, err);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_base = smem_u32(a_smem + s * A_STAGE_BYTES);
+            const uint32_t a_base = smem_u32(a_smem + s * a_stage_bytes);
             const uint32_t b_base = smem_u32(b_smem + s * b_stage_bytes);
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks) {
                 const uint64_t ad = smem_desc(a_base + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
                 const uint64_t bd = smem_desc(b_base + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
                 mma_bf16(tmem, ad, bd, idesc, (t | ks) != 0);
+                if (SPLIT) {
+                    const uint64_t ad_lo = smem_desc(a_base + A_STAGE_BYTES + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
+                    const uint64_t bd_lo = smem_desc(b_base + b_part_bytes + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
+                    mma_bf16(tmem, ad, bd_lo, idesc, 1u);
+                    mma_bf16(tmem, ad_lo, bd, idesc, 1u);
+                }
             }
             mma_commit(empty0 + 8 * s);
         }
@@ -254,14 +271,19 @@ __global__ void to_bf16_planar_kernel(const ConvJob *__restrict__ jobs, int n_jo
     const float4 a = __ldg(reinterpret_cast<const float4 *>(J.src + cell * FD + kc * 8));
     const float4 b = __ldg(reinterpret_cast<const float4 *>(J.src + cell * FD + kc * 8 + 4));
     const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    uint32_t wv[4];
+    uint32_t wv[4], wl[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const __nv_bfloat16 lo16 = __float2bfloat16_rn(v[2 * j]), hi16 = __float2bfloat16_rn(v[2 * j + 1]);
-        wv[j] = (uint32_t)(*reinterpret_cast<const uint16_t *>(&lo16)) |
-                ((uint32_t)(*reinterpret_cast<const uint16_t *>(&hi16)) << 16);
+        const __nv_bfloat16 e0 = __float2bfloat16_rn(v[2 * j]), e1 = __float2bfloat16_rn(v[2 * j + 1]);
+        wv[j] = (uint32_t)__bfloat16_as_ushort(e0) | ((uint32_t)__bfloat16_as_ushort(e1) << 16);
+        // residuals (exact in FP32) rounded to BF16: the lo part of the split operand
+        const __nv_bfloat16 r0 = __float2bfloat16_rn(v[2 * j] - __bfloat162float(e0));
+        const __nv_bfloat16 r1 = __float2bfloat16_rn(v[2 * j + 1] - __bfloat162float(e1));
+        wl[j] = (uint32_t)__bfloat16_as_ushort(r0) | ((uint32_t)__bfloat16_as_ushort(r1) << 16);
     }
-    *reinterpret_cast<uint4 *>(J.dst + ((size_t)kc * J.cells + cell) * 8) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    const size_t o = ((size_t)kc * J.cells + cell) * 8;
+    *reinterpret_cast<uint4 *>(J.dst + o) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    if (J.dst_lo) *reinterpret_cast<uint4 *>(J.dst_lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
 }
 
 }  // namespace
@@ -278,12 +300,17 @@ int corr_tc_pad(int K)
     return nt * n_tiles;
 }
 
-size_t corr_tc_smem_bytes(int NT) { return TC_STAGES * (A_STAGE_BYTES + (size_t)NT * 64) + 8 * (2 * TC_STAGES + 1) + 16; }
+size_t corr_tc_smem_bytes(int NT, bool split)
+{
+    const size_t parts = split ? 2 : 1;
+    return TC_STAGES * parts * (A_STAGE_BYTES + (size_t)NT * 64) + 8 * (2 * TC_STAGES + 1) + 16;
+}
 
-cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc, int K, int Npad,
-                           int h, int w, int *d_err, cudaStream_t s)
+cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc,
+                           const uint16_t *filt_tc_lo, int K, int Npad, int h, int w, int *d_err, cudaStream_t s)
 {
     if (total_tiles <= 0) return cudaSuccess;
+    const bool split = filt_tc_lo != nullptr;
     const int n_tiles_n = (Npad + 255) / 256;
     const int NT = Npad / n_tiles_n;
     if (NT % 16 != 0 || NT < 16 || NT > 256 || NT * n_tiles_n != Npad) return cudaErrorInvalidValue;
@@ -291,15 +318,21 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, con
     while (cols < (uint32_t)NT) cols <<= 1;
     // keep residency within TMEM: at most 512 / cols CTAs per SM, enforced through the shared memory request
     const int max_ctas = 512 / (int)cols;
-    size_t smem = corr_tc_smem_bytes(NT);
+    size_t smem = corr_tc_smem_bytes(NT, split);
     const size_t floor_bytes = 233472 / (size_t)(max_ctas + 1);
     if (smem < floor_bytes) smem = floor_bytes;
-    if (smem > (size_t)kMaxDynamicSmem) smem = kMaxDynamicSmem;
-    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(corr_tc_kernel), 0);
+    if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
+    const void *fn = split ? reinterpret_cast<const void *>(corr_tc_kernel<true>)
+                           : reinterpret_cast<const void *>(corr_tc_kernel<false>);
+    cudaError_t e = allow_max_dynamic_smem(fn, split ? 2 : 0);
     if (e != cudaSuccess) return e;
     note_launches(1);
-    corr_tc_kernel<<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, K, Npad, NT, n_tiles_n, h, w, cols,
-                                                         d_err);
+    if (split)
+        corr_tc_kernel<true><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, filt_tc_lo, K, Npad, NT,
+                                                                   n_tiles_n, h, w, cols, d_err);
+    else
+        corr_tc_kernel<false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, nullptr, K, Npad, NT,
+                                                                    n_tiles_n, h, w, cols, d_err);
     return cudaGetLastError();
 }
 

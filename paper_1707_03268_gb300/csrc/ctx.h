@@ -50,7 +50,8 @@ struct Group {
     int Kpad = 0;                        // FP32 SIMT layout padding (multiple of 64)
     float *d_filt_t = nullptr;           // [h*w*32][Kpad] FP32
     int Npad_tc = 0;                     // tensor-core layout padding
-    uint16_t *d_filt_tc = nullptr;       // [h*w][4][Npad_tc][8] BF16
+    uint16_t *d_filt_tc = nullptr;       // [h*w][4][Npad_tc][8] BF16 (hi part: bf16(x))
+    uint16_t *d_filt_tc_lo = nullptr;    // lo part bf16(x - bf16(x)), same layout (split-BF16 precision)
     // decomposition, FP64 master copies
     int R = 0, joint = 0;
     std::vector<double> A, B, C, Lam;
@@ -61,6 +62,7 @@ struct Group {
     int *d_rank_off = nullptr;
     int Rpad_tc = 0;
     uint16_t *d_C_tc = nullptr;          // [1][4][Rpad_tc][8] BF16: the channel factor as a 1x1 "filter bank"
+    uint16_t *d_C_tc_lo = nullptr;       // its lo part
 
     void free_factors();
     void free_all();

@@ -72,16 +72,28 @@ __global__ void __launch_bounds__(DT_WARPS * 32) dt_line_kernel(const DtJob *__r
 
     for (int i = lane; i < m; i += 32) {
         const int p = off + step * i;
-        int lo, hi;
-        dt_window(lin, quad, mx, L[p], p, n, lo, hi);
-        float best = -INFINITY;
-        int arg = lo;
-        for (int q = lo; q <= hi; ++q) {
-            const float d = (float)(q - p);
-            const float v = L[q] - fmaf(quad, d * d, lin * d);
-            if (v > best) {
-                best = v;
-                arg = q;
+        // start from q = p and walk outwards; every improvement of the best value shrinks the window
+        float best = L[p];
+        int arg = p, lo, hi;
+        dt_window(lin, quad, mx, best, p, n, lo, hi);
+        for (int d = 1; p - d >= lo || p + d <= hi; ++d) {
+            const float fd = (float)d;
+            if (p - d >= lo) {
+                // smallest index seen so far: it also wins a tie
+                const float v = L[p - d] - fmaf(quad, fd * fd, -lin * fd);
+                if (v >= best) {
+                    best = v;
+                    arg = p - d;
+                    dt_window(lin, quad, mx, best, p, n, lo, hi);
+                }
+            }
+            if (p + d <= hi) {
+                const float v = L[p + d] - fmaf(quad, fd * fd, lin * fd);
+                if (v > best) {
+                    best = v;
+                    arg = p + d;
+                    dt_window(lin, quad, mx, best, p, n, lo, hi);
+                }
             }
         }
         if (XPASS) {

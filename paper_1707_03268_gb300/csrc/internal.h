@@ -28,7 +28,8 @@ struct CorrJob {
 // Step 1 on tensor cores (full form, or the channel stage of the decomposed form with a 1x1 tap): one (group,
 // level) pair. The tensor map describes the level's BF16 planar copy [4][H*W][8].
 struct alignas(64) TcJob {
-    CUtensorMap tmap;
+    CUtensorMap tmap;         // BF16 (hi part) planar copy of the level
+    CUtensorMap tmap_lo;      // lo part (split-BF16 precision only)
     float *out;               // [N][Ho][Wo] (channel stage: [R][H][W])
     int H, W, Ho, Wo;
     int begin;                // first linear CTA index (M tiles x N tiles)
@@ -55,7 +56,8 @@ struct SepJob {
 // FP32 NHWC level -> BF16 planar [4][cells][8].
 struct ConvJob {
     const float *src;
-    uint16_t *dst;
+    uint16_t *dst;            // bf16(x)
+    uint16_t *dst_lo;         // bf16(x - bf16(x)), or null
     long long cells;
     long long begin;          // first (cell, chunk) item of this job
 };
@@ -107,9 +109,10 @@ int corr_f32_tile_y();
 int corr_f32_tile_k();
 
 // K1: tcgen05 BF16 implicit-GEMM correlation. filt_tc: [h*w][4][Npad][8] BF16, Npad = n_tiles * NT, NT <= 256 and a
-// multiple of 16 (corr_tc_pad). d_err: device flag raised when a bounded wait expires.
-cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc, int K, int Npad,
-                           int h, int w, int *d_err, cudaStream_t s);
+// multiple of 16 (corr_tc_pad). filt_tc_lo non-null selects split-BF16 operands (lo parts of the filters; the jobs'
+// tmap_lo must describe the lo parts of the features). d_err: device flag raised when a bounded wait expires.
+cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc,
+                           const uint16_t *filt_tc_lo, int K, int Npad, int h, int w, int *d_err, cudaStream_t s);
 int corr_tc_tile_m();
 int corr_tc_pad(int K);            // padded N for K filters
 int corr_tc_n_tiles(int Npad);     // N tiles of one launch

@@ -45,8 +45,9 @@ void Group::free_factors()
     d_A = d_B = d_Ct = d_lam = nullptr;
     cudaFree(d_rank_off);
     cudaFree(d_C_tc);
+    cudaFree(d_C_tc_lo);
     d_rank_off = nullptr;
-    d_C_tc = nullptr;
+    d_C_tc = d_C_tc_lo = nullptr;
 }
 
 void Group::free_all()
@@ -54,8 +55,9 @@ void Group::free_all()
     free_factors();
     cudaFree(d_filt_t);
     cudaFree(d_filt_tc);
+    cudaFree(d_filt_tc_lo);
     d_filt_t = nullptr;
-    d_filt_tc = nullptr;
+    d_filt_tc = d_filt_tc_lo = nullptr;
 }
 
 tdpm_status set_device(tdpm_ctx *ctx)
@@ -72,15 +74,22 @@ Model *get_model(tdpm_ctx *ctx, int id)
 
 namespace {
 
-// Tensor-core filter bank: [taps][4 channel chunks][Npad][8] BF16, zero rows for n >= n_rows.
-tdpm_status upload_tc_bank(uint16_t **dst, int taps, int Npad, int n_rows,
+// Tensor-core filter banks: [taps][4 channel chunks][Npad][8] BF16, zero rows for n >= n_rows; the hi part bf16(x)
+// and the lo part bf16(x - bf16(x)) of the split-BF16 operands.
+tdpm_status upload_tc_bank(uint16_t **dst_hi, uint16_t **dst_lo, int taps, int Npad, int n_rows,
                            const std::function<float(int, int, int)> &value)
 {
-    std::vector<uint16_t> b((size_t)taps * 4 * Npad * 8, 0);
+    std::vector<uint16_t> hi((size_t)taps * 4 * Npad * 8, 0), lo(hi.size(), 0);
     for (int t = 0; t < taps; ++t)
         for (int n = 0; n < n_rows; ++n)
-            for (int c = 0; c < FD; ++c) b[(((size_t)t * 4 + c / 8) * Npad + n) * 8 + (c % 8)] = bf16_bits(value(t, n, c));
-    return upload(dst, b);
+            for (int c = 0; c < FD; ++c) {
+                const float x = value(t, n, c);
+                const size_t i = (((size_t)t * 4 + c / 8) * Npad + n) * 8 + (c % 8);
+                hi[i] = bf16_bits(x);
+                lo[i] = bf16_bits(x - bf16_round(x));
+            }
+    tdpm_status st = upload(dst_hi, hi);
+    return st ? st : upload(dst_lo, lo);
 }
 
 // Device copies of a group's factors: FP32 for the SIMT kernels (channel stage of the FP32 path, 1-D passes and
@@ -110,7 +119,8 @@ tdpm_status upload_factors(Group &g)
     tdpm_status st = upload(&g.d_rank_off, ro);
     if (st) return st;
     g.Rpad_tc = corr_tc_pad(R);
-    return upload_tc_bank(&g.d_C_tc, 1, g.Rpad_tc, R, [&](int, int r, int c) { return (float)g.C[(size_t)c * R + r]; });
+    return upload_tc_bank(&g.d_C_tc, &g.d_C_tc_lo, 1, g.Rpad_tc, R,
+                          [&](int, int r, int c) { return (float)g.C[(size_t)c * R + r]; });
 }
 
 }  // namespace
@@ -254,7 +264,7 @@ tdpm_status tdpm_load_model(tdpm_ctx *ctx, const tdpm_model_desc *desc, int32_t 
         }
         g.Npad_tc = corr_tc_pad(g.K);
         if ((st = upload(&g.d_filt_t, ft)) ||
-            (st = upload_tc_bank(&g.d_filt_tc, taps, g.Npad_tc, g.K, [&](int t, int k, int c) {
+            (st = upload_tc_bank(&g.d_filt_tc, &g.d_filt_tc_lo, taps, g.Npad_tc, g.K, [&](int t, int k, int c) {
                  return m->filters[g.fids[k]].data[(size_t)t * FD + c];
              }))) {
             for (Group &gg : m->groups) gg.free_all();

@@ -74,10 +74,10 @@ struct AsmPlan {
 struct Plan {
     uint64_t uid = 0;
     int model_id = 0, form = 0, precision = 0, L = 0, lam = 0;
-    bool bf = false, dec = false;
+    bool bf = false, split = false, dec = false;
     std::vector<std::pair<int, int>> sizes;
     size_t arena_bytes = 0, blob_off = 0, blob_bytes = 0;
-    std::vector<size_t> bf_off;
+    std::vector<size_t> bf_off, bf_lo_off;  // BF16 planar copies of the levels (hi part, lo part)
     std::vector<std::vector<GroupLevel>> glv;
     std::vector<DtPlan> dts;
     std::vector<AsmPlan> asms;
@@ -112,7 +112,8 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     P->uid = g_plan_uid.fetch_add(1);
     P->model_id = model_id; P->form = form; P->precision = prec;
     P->L = pyr->n_levels; P->lam = pyr->lambda;
-    P->bf = prec == TDPM_PREC_BF16;
+    P->bf = prec == TDPM_PREC_BF16 || prec == TDPM_PREC_BF16X3;
+    P->split = prec == TDPM_PREC_BF16X3;
     P->dec = form == TDPM_FORM_DECOMPOSED;
     const int L = P->L, lam = P->lam;
     for (int j = 0; j < L; ++j) P->sizes.push_back({pyr->levels[j].H, pyr->levels[j].W});
@@ -120,6 +121,11 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     if (P->bf) {
         P->bf_off.resize(L);
         for (int j = 0; j < L; ++j) P->bf_off[j] = bump.take(sizeof(uint16_t) * (size_t)P->sizes[j].first * P->sizes[j].second * FD);
+        if (P->split) {
+            P->bf_lo_off.resize(L);
+            for (int j = 0; j < L; ++j)
+                P->bf_lo_off[j] = bump.take(sizeof(uint16_t) * (size_t)P->sizes[j].first * P->sizes[j].second * FD);
+        }
     }
     P->glv.resize(m.groups.size());
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
@@ -251,6 +257,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Ar
             cj[j].src = pyr->levels[j].data;
             patches.push_back({P.conv_off + sizeof(ConvJob) * j + offsetof(ConvJob, src), j});
             cj[j].dst = reinterpret_cast<uint16_t *>(base + P.bf_off[j]);
+            cj[j].dst_lo = P.split ? reinterpret_cast<uint16_t *>(base + P.bf_lo_off[j]) : nullptr;
             cj[j].cells = (long long)P.sizes[j].first * P.sizes[j].second;
             cj[j].begin = begin;
             begin += 4 * cj[j].cells;
@@ -267,6 +274,9 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Ar
                 TcJob &t = reinterpret_cast<TcJob *>(hb + P.g_jobs_off[gi])[i];
                 if (!encode_level_tmap(&t.tmap, reinterpret_cast<const uint16_t *>(base + P.bf_off[gl.j]),
                                        (long long)H * W))
+                    return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+                if (P.split && !encode_level_tmap(&t.tmap_lo, reinterpret_cast<const uint16_t *>(base + P.bf_lo_off[gl.j]),
+                                                  (long long)H * W))
                     return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
                 t.out = P.dec ? reinterpret_cast<float *>(base + gl.z_off) : out;
                 t.H = H; t.W = W;
@@ -423,10 +433,12 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         if (P.bf) {
             Prof pr(ctx, s, P.dec ? "zproj_tc" : "corr_tc");
             if (P.dec)
-                e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_C_tc, g.R, g.Rpad_tc, 1,
+                e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_C_tc,
+                                   P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, 1,
                                    1, ctx->d_err, s);
             else
-                e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_filt_tc, g.K,
+                e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_filt_tc,
+                                   P.split ? g.d_filt_tc_lo : nullptr, g.K,
                                    g.Npad_tc, g.h, g.w, ctx->d_err, s);
             if (e != cudaSuccess) return e;
             pr.end();
@@ -598,7 +610,8 @@ tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdp
     clear_error();
     if (!ctx || !pyr || !scores_id) return fail(TDPM_ERR_ARG, "NULL argument");
     if (form != TDPM_FORM_FULL && form != TDPM_FORM_DECOMPOSED) return fail(TDPM_ERR_ARG, "bad form");
-    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16) return fail(TDPM_ERR_ARG, "unsupported precision");
+    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16 && precision != TDPM_PREC_BF16X3)
+        return fail(TDPM_ERR_ARG, "unsupported precision (FP8 is not implemented)");
     if (pyr->n_levels <= 0 || !pyr->levels) return fail(TDPM_ERR_ARG, "empty pyramid");
     if (pyr->n_levels > 4096) return fail(TDPM_ERR_ARG, "too many levels");
     if (pyr->lambda < 1 || pyr->lambda > pyr->n_levels) return fail(TDPM_ERR_ARG, "lambda out of range");
@@ -871,7 +884,8 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
     if (!feat || !filt_host || !out) return fail(TDPM_ERR_ARG, "NULL argument");
     if (H <= 0 || W <= 0 || K <= 0 || h <= 0 || w <= 0 || h > 16 || w > 16 || H > 4096 || W > 4096 || K > 4096)
         return fail(TDPM_ERR_ARG, "bad sizes");
-    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16) return fail(TDPM_ERR_ARG, "unsupported precision");
+    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16 && precision != TDPM_PREC_BF16X3)
+        return fail(TDPM_ERR_ARG, "unsupported precision");
     if (reinterpret_cast<uintptr_t>(feat) % 16) return fail(TDPM_ERR_ARG, "feat not 16-byte aligned");
     const int Ho = H - h + 1, Wo = W - w + 1;
     if (Ho <= 0 || Wo <= 0) return TDPM_OK;
@@ -901,39 +915,48 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
             e = launch_corr_f32(reinterpret_cast<const CorrJob *>(db + fbytes), 1, tiles, reinterpret_cast<float *>(db),
                                 K, Kpad, h, w, s);
     } else {
+        // tensor cores: BF16 filter bank(s) and planar BF16 copies of the level; split precision adds the lo parts
+        const bool split = precision == TDPM_PREC_BF16X3;
         const int Npad = corr_tc_pad(K);
-        std::vector<uint16_t> fb((size_t)taps * 4 * Npad * 8, 0);
+        std::vector<uint16_t> fb((size_t)taps * 4 * Npad * 8, 0), fl(fb.size(), 0);
         for (int k = 0; k < K; ++k)
             for (int t = 0; t < taps; ++t)
-                for (int c = 0; c < FD; ++c)
-                    fb[(((size_t)t * 4 + c / 8) * Npad + k) * 8 + (c % 8)] = bf16_bits(filt_host[((size_t)k * taps + t) * FD + c]);
+                for (int c = 0; c < FD; ++c) {
+                    const float x = filt_host[((size_t)k * taps + t) * FD + c];
+                    const size_t i = (((size_t)t * 4 + c / 8) * Npad + k) * 8 + (c % 8);
+                    fb[i] = bf16_bits(x);
+                    fl[i] = bf16_bits(x - bf16_round(x));
+                }
         const long long cells = (long long)H * W;
         const size_t fbytes = align256(sizeof(uint16_t) * fb.size());
         const size_t pbytes = align256(sizeof(uint16_t) * (size_t)cells * FD);
-        CUDA_TRY(cudaMalloc(&dmem, fbytes + pbytes + align256(sizeof(ConvJob)) + sizeof(TcJob)));
+        const size_t parts = split ? 2 : 1;
+        CUDA_TRY(cudaMalloc(&dmem, parts * (fbytes + pbytes) + align256(sizeof(ConvJob)) + sizeof(TcJob) + 256));
         char *db = reinterpret_cast<char *>(dmem);
-        uint16_t *planar = reinterpret_cast<uint16_t *>(db + fbytes);
-        ConvJob cj{feat, planar, cells, 0};
+        uint16_t *bank = reinterpret_cast<uint16_t *>(db);
+        uint16_t *bank_lo = split ? reinterpret_cast<uint16_t *>(db + fbytes) : nullptr;
+        uint16_t *planar = reinterpret_cast<uint16_t *>(db + parts * fbytes);
+        uint16_t *planar_lo = split ? reinterpret_cast<uint16_t *>(db + parts * fbytes + pbytes) : nullptr;
+        char *cjd = db + parts * (fbytes + pbytes), *tjd = cjd + align256(sizeof(ConvJob));
+        int *d_err = reinterpret_cast<int *>(tjd + align256(sizeof(TcJob)));
+        ConvJob cj{feat, planar, planar_lo, cells, 0};
         TcJob tj{};
-        if (!encode_level_tmap(&tj.tmap, planar, cells)) {
+        if (!encode_level_tmap(&tj.tmap, planar, cells) || (split && !encode_level_tmap(&tj.tmap_lo, planar_lo, cells))) {
             cudaFree(dmem);
             return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         }
         tj.out = out; tj.H = H; tj.W = W; tj.Ho = Ho; tj.Wo = Wo; tj.begin = 0;
         const long long span = (long long)(Ho - 1) * W + Wo;
         const int tiles = (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad);
-        char *cjd = db + fbytes + pbytes, *tjd = cjd + align256(sizeof(ConvJob));
-        e = cudaMemcpyAsync(db, fb.data(), sizeof(uint16_t) * fb.size(), cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(bank, fb.data(), sizeof(uint16_t) * fb.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && split)
+            e = cudaMemcpyAsync(bank_lo, fl.data(), sizeof(uint16_t) * fl.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(cjd, &cj, sizeof(cj), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tjd, &tj, sizeof(tj), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
         if (e == cudaSuccess) e = launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(cjd), 1, 4 * cells, s);
-        if (e == cudaSuccess) {
-            int *d_err = reinterpret_cast<int *>(tjd + offsetof(TcJob, pad));
-            e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
-            if (e == cudaSuccess)
-                e = launch_corr_tc(reinterpret_cast<const TcJob *>(tjd), 1, tiles, reinterpret_cast<uint16_t *>(db), K,
-                                   Npad, h, w, d_err, s);
-        }
+        if (e == cudaSuccess)
+            e = launch_corr_tc(reinterpret_cast<const TcJob *>(tjd), 1, tiles, bank, bank_lo, K, Npad, h, w, d_err, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(dmem);

@@ -19,7 +19,7 @@ MAX_PARTS = 16
 
 OK, ERR_ARG, ERR_SHAPE, ERR_OOM, ERR_CAPACITY, ERR_TIMEOUT, ERR_CUDA, ERR_STATE, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7, -8
 FORM_FULL, FORM_DECOMPOSED = 0, 1
-PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3
 DECOMP_PER_FILTER, DECOMP_JOINT = 0, 1
 MAP_FILTER_SCORE, MAP_FINAL_SCORE, MAP_PART_DT, MAP_PART_ARG = 0, 1, 2, 3
 

@@ -132,3 +132,39 @@ def test_graph_replay_matches_direct_launches(torch, T, ctx):
         T.tdpm_release(ctx, sid)
     for a, b in zip(maps[0], maps[2]):
         np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------------------------------------------------------- split-BF16 precision
+@pytest.mark.parametrize("H,W,h,w,K", [(13, 29, 6, 6, 3), (60, 80, 6, 6, 48), (9, 17, 5, 11, 70), (50, 37, 1, 1, 384),
+                                       (23, 45, 6, 6, 257)])
+def test_correlate_split_bf16_matches_fp32_oracle(torch, T, H, W, h, w, K):
+    """hi*hi + hi*lo + lo*hi on BF16 tensor cores: relative error ~2^-16, so the unrounded FP64 result is matched to
+    1e-4 of the largest score (plain BF16 misses it by ~1e-3)."""
+    rng = np.random.default_rng(H * 1000 + W * 10 + K + 11)
+    feat = rng.uniform(0, 0.2, size=(H, W, 32)).astype(np.float32)
+    filt = rng.normal(0, 0.05, size=(K, h, w, 32)).astype(np.float32)
+    out = torch.full((K, H - h + 1, W - w + 1), float("nan"), device="cuda")
+    T.tdpm_correlate(torch.from_numpy(feat).cuda(), filt, out, precision=T.PREC_BF16X3)
+    got = out.cpu().numpy()
+    for k in range(K):
+        assert rel_err(got[k], orc.correlate(feat, filt[k])) <= 1e-4, k
+
+
+@pytest.mark.parametrize("form", ["full", "decomposed"])
+def test_split_bf16_end_to_end_agrees_with_oracle(torch, T, ctx, form):
+    wl = synth.config_c2()
+    pyr = wl.pyramids[0]
+    mid = T.tdpm_load_model(ctx, wl.model)
+    filters = None
+    if form == "decomposed":
+        T.tdpm_decompose(ctx, mid, 8, T.DECOMP_PER_FILTER, max_iters=150, seed=1)
+        filters = _factor_filters(T, ctx, mid, torch)
+    f = T.FORM_FULL if form == "full" else T.FORM_DECOMPOSED
+    sid = T.tdpm_build_pyramid_scores(ctx, mid, device_pyramid(pyr, torch), f, T.PREC_BF16X3)
+    ref = orc.score_pyramid(wl.model, pyr, filters=filters)
+    for m in ref:
+        got = T.tdpm_get_maps(ctx, sid, T.MAP_FINAL_SCORE, m["component"], m["level"])
+        assert rel_err(got, m["score"]) <= 1e-4
+    tau = float(np.percentile(orc.all_scores(ref), 99))
+    assert agreement(det_keys(T.tdpm_detect(ctx, sid, tau)), det_keys(orc.detect(ref, tau))) >= 0.995
+    T.tdpm_release(ctx, sid)
