@@ -189,13 +189,16 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
     const int HY = SQ_T + h - 1, HX = SQ_T + w - 1;
     const size_t plane = (size_t)J.H * J.W;
 
+    const int tx = tid % SQ_T, ty = tid / SQ_T;  // 32 x 8 thread grid: a warp covers one row segment
     auto load_term = [&](int r, int buf) {
         const float *Zr = J.Z + (size_t)r * plane;
-        for (int i = tid; i < HY * HX; i += SQ_THREADS) {
-            const int yy = i / HX, xx = i - yy * HX;
-            const int gy = y0 + yy, gx = x0 + xx;
-            const bool in = gy < J.H && gx < J.W;
-            cp_async_f32(&zs[buf][yy][xx], in ? Zr + (size_t)gy * J.W + gx : Zr, in);
+        for (int yy = ty; yy < HY; yy += SQ_THREADS / SQ_T) {
+            const int gy = y0 + yy;
+            for (int xx = tx; xx < HX; xx += SQ_T) {
+                const int gx = x0 + xx;
+                const bool in = gy < J.H && gx < J.W;
+                cp_async_f32(&zs[buf][yy][xx], in ? Zr + (size_t)gy * J.W + gx : Zr, in);
+            }
         }
         if (tid < h) coef[buf][tid] = __ldg(A + (size_t)tid * R + r);
         else if (tid < h + w) coef[buf][tid] = __ldg(B + (size_t)(tid - h) * R + r);
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
         cp_async_commit();
     };
 
-    const int tx = tid % SQ_T, ty = tid / SQ_T;  // each thread: column tx, rows ty*4 .. ty*4+3
+    // x pass: each thread owns column tx, rows ty*4 .. ty*4+3
     float acc[FC][SQ_ROWS_PER_THREAD];
 #pragma unroll
     for (int f = 0; f < FC; ++f)
@@ -224,12 +227,12 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
         }
         __syncthreads();
         const float *a = coef[buf], *b = coef[buf] + h, *lf = coef[buf] + h + w;
-        for (int i = tid; i < SQ_T * HX; i += SQ_THREADS) {
-            const int yy = i / HX, xx = i - yy * HX;
-            float t = 0.f;
-            for (int dy = 0; dy < h; ++dy) t = fmaf(a[dy], zs[buf][yy + dy][xx], t);
-            ts[yy][xx] = t;
-        }
+        for (int yy = ty; yy < SQ_T; yy += SQ_THREADS / SQ_T)
+            for (int xx = tx; xx < HX; xx += SQ_T) {
+                float t = 0.f;
+                for (int dy = 0; dy < h; ++dy) t = fmaf(a[dy], zs[buf][yy + dy][xx], t);
+                ts[yy][xx] = t;
+            }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < SQ_ROWS_PER_THREAD; ++j) {

@@ -144,17 +144,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
                                                                 const uint16_t *__restrict__ filt,
                                                                 const uint16_t *__restrict__ filt_lo, int K, int Npad,
                                                                 int NT, int n_tiles_n, int h, int w, uint32_t tmem_cols,
-                                                                int *err)
+                                                                int stages, int *err)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     constexpr uint32_t NPART = SPLIT ? 2 : 1;
     const uint32_t b_part_bytes = (uint32_t)NT * 64;
     const uint32_t a_stage_bytes = NPART * A_STAGE_BYTES, b_stage_bytes = NPART * b_part_bytes;
     uint8_t *a_smem = sm;
-    uint8_t *b_smem = sm + TC_STAGES * a_stage_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + TC_STAGES * b_stage_bytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * TC_STAGES + 1);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES), done = smem_u32(bars + 2 * TC_STAGES);
+    uint8_t *b_smem = sm + stages * a_stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + stages * b_stage_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + stages), done = smem_u32(bars + 2 * stages);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ji = find_job(jobs, n_jobs, blockIdx.x);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
     const int taps = h * w;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < stages; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
@@ -187,8 +187,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
     if (warp == 0 && lane == 0) {
         // producer: one A box and four B chunk copies per tap
         for (int t = 0; t < taps; ++t) {
-            const int s = t % TC_STAGES;
-            if (t >= TC_STAGES) mbar_wait(empty0 + 8 * s, ((t / TC_STAGES) - 1) & 1, err);
+            const int s = t % stages;
+            if (t >= stages) mbar_wait(empty0 + 8 * s, ((t / stages) - 1) & 1, err);
             const uint32_t full = full0 + 8 * s;
             mbar_expect_tx(full, a_stage_bytes + b_stage_bytes);
             const int dy = t / w, dx = t - dy * w;
@@ -206,8 +206,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
         // MMA issuer: two K=16 steps per tap (channel chunks {0,1} and {2,3})
         const uint32_t idesc = instr_desc(TC_M, NT);
         for (int t = 0; t < taps; ++t) {
-            const int s = t % TC_STAGES;
-            mbar_wait(full0 + 8 * s, (t / TC_STAGES) & 1, err);
+            const int s = t % stages;
+            mbar_wait(full0 + 8 * s, (t / stages) & 1, err);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_base = smem_u32(a_smem + s * a_stage_bytes);
             const uint32_t b_base = smem_u32(b_smem + s * b_stage_bytes);
@@ -290,20 +290,29 @@ __global__ void to_bf16_planar_kernel(const ConvJob *__restrict__ jobs, int n_jo
 
 int corr_tc_tile_m() { return TC_M; }
 
-int corr_tc_n_tiles(int Npad) { return (Npad + 255) / 256; }
+// Largest N tile: 256 for multi-tap correlations (more MMA work per staged byte); 128 for the single-tap channel
+// stage, which is bound by its output writes and gains from more CTAs per SM (TMEM holds 512 columns).
+int corr_tc_max_nt(int taps) { return taps > 1 ? 256 : 128; }
 
-int corr_tc_pad(int K)
+int corr_tc_n_tiles(int Npad, int taps)
 {
-    const int n_tiles = (K + 255) / 256;
+    const int mx = corr_tc_max_nt(taps);
+    return (Npad + mx - 1) / mx;
+}
+
+int corr_tc_pad(int K, int taps)
+{
+    const int mx = corr_tc_max_nt(taps);
+    const int n_tiles = (K + mx - 1) / mx;
     int nt = (K + n_tiles - 1) / n_tiles;
     nt = (nt + 15) / 16 * 16;
     return nt * n_tiles;
 }
 
-size_t corr_tc_smem_bytes(int NT, bool split)
+size_t corr_tc_smem_bytes(int NT, bool split, int stages)
 {
     const size_t parts = split ? 2 : 1;
-    return TC_STAGES * parts * (A_STAGE_BYTES + (size_t)NT * 64) + 8 * (2 * TC_STAGES + 1) + 16;
+    return stages * parts * (A_STAGE_BYTES + (size_t)NT * 64) + 8 * (2 * stages + 1) + 16;
 }
 
 cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc,
@@ -311,14 +320,15 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, con
 {
     if (total_tiles <= 0) return cudaSuccess;
     const bool split = filt_tc_lo != nullptr;
-    const int n_tiles_n = (Npad + 255) / 256;
+    const int n_tiles_n = corr_tc_n_tiles(Npad, h * w);
     const int NT = Npad / n_tiles_n;
+    const int stages = h * w < TC_STAGES ? h * w : TC_STAGES;
     if (NT % 16 != 0 || NT < 16 || NT > 256 || NT * n_tiles_n != Npad) return cudaErrorInvalidValue;
     uint32_t cols = 32;
     while (cols < (uint32_t)NT) cols <<= 1;
     // keep residency within TMEM: at most 512 / cols CTAs per SM, enforced through the shared memory request
     const int max_ctas = 512 / (int)cols;
-    size_t smem = corr_tc_smem_bytes(NT, split);
+    size_t smem = corr_tc_smem_bytes(NT, split, stages);
     const size_t floor_bytes = 233472 / (size_t)(max_ctas + 1);
     if (smem < floor_bytes) smem = floor_bytes;
     if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
@@ -329,10 +339,10 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, con
     note_launches(1);
     if (split)
         corr_tc_kernel<true><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, filt_tc_lo, K, Npad, NT,
-                                                                   n_tiles_n, h, w, cols, d_err);
+                                                                   n_tiles_n, h, w, cols, stages, d_err);
     else
         corr_tc_kernel<false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, nullptr, K, Npad, NT,
-                                                                    n_tiles_n, h, w, cols, d_err);
+                                                                    n_tiles_n, h, w, cols, stages, d_err);
     return cudaGetLastError();
 }
 

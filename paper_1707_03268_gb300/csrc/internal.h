@@ -114,8 +114,8 @@ int corr_f32_tile_k();
 cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc,
                            const uint16_t *filt_tc_lo, int K, int Npad, int h, int w, int *d_err, cudaStream_t s);
 int corr_tc_tile_m();
-int corr_tc_pad(int K);            // padded N for K filters
-int corr_tc_n_tiles(int Npad);     // N tiles of one launch
+int corr_tc_pad(int K, int taps);          // padded N for K filters of h*w = taps
+int corr_tc_n_tiles(int Npad, int taps);   // N tiles of one launch
 bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells);
 
 // FP32 NHWC -> BF16 planar for many levels in one launch (total = sum of 4 * cells).

@@ -118,7 +118,7 @@ tdpm_status upload_factors(Group &g)
     if (ro.empty()) ro.assign(K + 1, 0);
     tdpm_status st = upload(&g.d_rank_off, ro);
     if (st) return st;
-    g.Rpad_tc = corr_tc_pad(R);
+    g.Rpad_tc = corr_tc_pad(R, 1);
     return upload_tc_bank(&g.d_C_tc, &g.d_C_tc_lo, 1, g.Rpad_tc, R,
                           [&](int, int r, int c) { return (float)g.C[(size_t)c * R + r]; });
 }
@@ -262,7 +262,7 @@ tdpm_status tdpm_load_model(tdpm_ctx *ctx, const tdpm_model_desc *desc, int32_t 
             for (int t = 0; t < taps; ++t)
                 for (int c = 0; c < FD; ++c) ft[((size_t)t * FD + c) * g.Kpad + k] = F.data[(size_t)t * FD + c];
         }
-        g.Npad_tc = corr_tc_pad(g.K);
+        g.Npad_tc = corr_tc_pad(g.K, g.h * g.w);
         if ((st = upload(&g.d_filt_t, ft)) ||
             (st = upload_tc_bank(&g.d_filt_tc, &g.d_filt_tc_lo, taps, g.Npad_tc, g.K, [&](int t, int k, int c) {
                  return m->filters[g.fids[k]].data[(size_t)t * FD + c];

@@ -212,7 +212,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
             if (P->bf) {
                 const int Npad = P->dec ? g.Rpad_tc : g.Npad_tc;
                 const long long span = P->dec ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
-                tiles += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad);
+                tiles += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad, P->dec ? 1 : g.h * g.w);
             } else if (P->dec) {
                 tiles += ((H * W + zproj_simt_cells_per_tile() - 1) / zproj_simt_cells_per_tile()) *
                          ((g.R + zproj_simt_r_chunk() - 1) / zproj_simt_r_chunk());
@@ -285,7 +285,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Ar
                 t.begin = begin;
                 const int Npad = P.dec ? g.Rpad_tc : g.Npad_tc;
                 const long long span = P.dec ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
-                begin += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad);
+                begin += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad, P.dec ? 1 : g.h * g.w);
             } else if (P.dec) {
                 ZJob &z = reinterpret_cast<ZJob *>(hb + P.g_jobs_off[gi])[i];
                 z.feat = pyr->levels[gl.j].data;
@@ -917,7 +917,7 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
     } else {
         // tensor cores: BF16 filter bank(s) and planar BF16 copies of the level; split precision adds the lo parts
         const bool split = precision == TDPM_PREC_BF16X3;
-        const int Npad = corr_tc_pad(K);
+        const int Npad = corr_tc_pad(K, taps);
         std::vector<uint16_t> fb((size_t)taps * 4 * Npad * 8, 0), fl(fb.size(), 0);
         for (int k = 0; k < K; ++k)
             for (int t = 0; t < taps; ++t)
@@ -947,7 +947,7 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
         }
         tj.out = out; tj.H = H; tj.W = W; tj.Ho = Ho; tj.Wo = Wo; tj.begin = 0;
         const long long span = (long long)(Ho - 1) * W + Wo;
-        const int tiles = (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad);
+        const int tiles = (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad, taps);
         e = cudaMemcpyAsync(bank, fb.data(), sizeof(uint16_t) * fb.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && split)
             e = cudaMemcpyAsync(bank_lo, fl.data(), sizeof(uint16_t) * fl.size(), cudaMemcpyHostToDevice, s);
