@@ -148,10 +148,11 @@ __global__ void __launch_bounds__(ZP_CELLS) zproj_kernel(const ZJob *__restrict_
 // CTA tile: SQ_T x SQ_T output positions of one filter (per-filter mode) or of SQ_FC_JOINT filters (joint mode).
 // For every rank-1 term r of those filters the CTA copies the Z_r halo ((SQ_T+h-1) x (SQ_T+w-1) cells) into shared
 // memory with cp.async (zero fill outside the map), double-buffered so term r+1 is in flight while term r is
-// processed: the y pass with a_r writes a SQ_T x (SQ_T+w-1) intermediate to shared memory, the x pass with b_r gives
-// U_r at each thread's 4 positions, and Lambda[k][r] * U_r is added to each filter's accumulators.
+// processed. y pass: each work item forms 4 rows of one column of T = a_r o_y Z_r from h+3 loads; x pass: each
+// thread forms U_r = b_r o_x T at 4 consecutive columns of one row from w+3 loads, then adds Lambda[k][r] * U_r to
+// each filter's accumulators. HH / WW are the filter sides when known at compile time (0: runtime sides).
 constexpr int SQ_T = 32, SQ_THREADS = 256, SQ_MAXHW = 16, SQ_HALO = SQ_T + SQ_MAXHW - 1, SQ_FC_JOINT = 8;
-constexpr int SQ_ROWS_PER_THREAD = SQ_T * SQ_T / SQ_THREADS;  // 4
+constexpr int SQ_TS_STRIDE = 65;  // == 1 (mod 32): the x pass's 4 rows x 8 column groups per warp hit distinct banks
 
 __device__ __forceinline__ void cp_async_f32(float *dst, const float *src, bool pred)
 {
@@ -165,14 +166,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int FC>
+template <int FC, int HH, int WW>
 __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restrict__ jobs, int n_jobs,
                                                          const float *__restrict__ A, const float *__restrict__ B,
                                                          const float *__restrict__ lam,
-                                                         const int *__restrict__ rank_off, int K, int R, int h, int w)
+                                                         const int *__restrict__ rank_off, int K, int R, int h_rt,
+                                                         int w_rt)
 {
+    constexpr int MH = HH ? HH : SQ_MAXHW, MW = WW ? WW : SQ_MAXHW;
+    const int h = HH ? HH : h_rt, w = WW ? WW : w_rt;
     __shared__ float zs[2][SQ_HALO][SQ_HALO + 1];
-    __shared__ float ts[SQ_T][SQ_HALO + 1];
+    __shared__ float ts[SQ_T][SQ_TS_STRIDE];
     __shared__ float coef[2][2 * SQ_MAXHW + FC];
 
     const int tid = threadIdx.x;
@@ -188,13 +192,13 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
     if (FC == 1) { r_begin = rank_off[k0]; r_end = rank_off[k0 + 1]; }
     const int HY = SQ_T + h - 1, HX = SQ_T + w - 1;
     const size_t plane = (size_t)J.H * J.W;
+    const int lx = tid % SQ_T, ly = tid / SQ_T;  // 32 x 8 layout for the copies
 
-    const int tx = tid % SQ_T, ty = tid / SQ_T;  // 32 x 8 thread grid: a warp covers one row segment
     auto load_term = [&](int r, int buf) {
         const float *Zr = J.Z + (size_t)r * plane;
-        for (int yy = ty; yy < HY; yy += SQ_THREADS / SQ_T) {
+        for (int yy = ly; yy < HY; yy += SQ_THREADS / SQ_T) {
             const int gy = y0 + yy;
-            for (int xx = tx; xx < HX; xx += SQ_T) {
+            for (int xx = lx; xx < HX; xx += SQ_T) {
                 const int gx = x0 + xx;
                 const bool in = gy < J.H && gx < J.W;
                 cp_async_f32(&zs[buf][yy][xx], in ? Zr + (size_t)gy * J.W + gx : Zr, in);
@@ -209,12 +213,13 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
         cp_async_commit();
     };
 
-    // x pass: each thread owns column tx, rows ty*4 .. ty*4+3
-    float acc[FC][SQ_ROWS_PER_THREAD];
+    // x pass ownership: row xr, columns xc .. xc+3
+    const int xr = tid / 8, xc = (tid % 8) * 4;
+    float acc[FC][4];
 #pragma unroll
     for (int f = 0; f < FC; ++f)
 #pragma unroll
-        for (int j = 0; j < SQ_ROWS_PER_THREAD; ++j) acc[f][j] = 0.f;
+        for (int j = 0; j < 4; ++j) acc[f][j] = 0.f;
 
     if (r_begin < r_end) load_term(r_begin, 0);
     for (int r = r_begin; r < r_end; ++r) {
@@ -227,35 +232,65 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
         }
         __syncthreads();
         const float *a = coef[buf], *b = coef[buf] + h, *lf = coef[buf] + h + w;
-        for (int yy = ty; yy < SQ_T; yy += SQ_THREADS / SQ_T)
-            for (int xx = tx; xx < HX; xx += SQ_T) {
+        // y pass: items (column xx, row group g of 4 rows)
+        for (int item = tid; item < HX * (SQ_T / 4); item += SQ_THREADS) {
+            const int g = item / HX, xx = item - g * HX, y = g * 4;
+            float z[4 + MH - 1];
+#pragma unroll
+            for (int k = 0; k < 4 + MH - 1; ++k)
+                if (HH || k < 4 + h - 1) z[k] = zs[buf][y + k][xx];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
                 float t = 0.f;
-                for (int dy = 0; dy < h; ++dy) t = fmaf(a[dy], zs[buf][yy + dy][xx], t);
-                ts[yy][xx] = t;
+#pragma unroll
+                for (int dy = 0; dy < MH; ++dy)
+                    if (HH || dy < h) t = fmaf(a[dy], z[j + dy], t);
+                ts[y + j][xx] = t;
             }
+        }
         __syncthreads();
+        {
+            float tv[4 + MW - 1];
 #pragma unroll
-        for (int j = 0; j < SQ_ROWS_PER_THREAD; ++j) {
-            const int yy = ty * SQ_ROWS_PER_THREAD + j;
-            float u = 0.f;
-            for (int dx = 0; dx < w; ++dx) u = fmaf(b[dx], ts[yy][tx + dx], u);
+            for (int k = 0; k < 4 + MW - 1; ++k)
+                if (WW || k < 4 + w - 1) tv[k] = ts[xr][xc + k];
 #pragma unroll
-            for (int f = 0; f < FC; ++f) acc[f][j] = fmaf(lf[f], u, acc[f][j]);
+            for (int j = 0; j < 4; ++j) {
+                float u = 0.f;
+#pragma unroll
+                for (int dx = 0; dx < MW; ++dx)
+                    if (WW || dx < w) u = fmaf(b[dx], tv[j + dx], u);
+#pragma unroll
+                for (int f = 0; f < FC; ++f) acc[f][j] = fmaf(lf[f], u, acc[f][j]);
+            }
         }
         __syncthreads();
     }
-    const int x = x0 + tx;
-    if (x >= J.Wo) return;
+    const int y = y0 + xr;
+    if (y >= J.Ho) return;
 #pragma unroll
     for (int f = 0; f < FC; ++f) {
         if (k0 + f >= K) break;
-        float *o = J.out + (size_t)(k0 + f) * J.Ho * J.Wo + x;
+        float *o = J.out + ((size_t)(k0 + f) * J.Ho + y) * J.Wo;
 #pragma unroll
-        for (int j = 0; j < SQ_ROWS_PER_THREAD; ++j) {
-            const int y = y0 + ty * SQ_ROWS_PER_THREAD + j;
-            if (y < J.Ho) o[(size_t)y * J.Wo] = acc[f][j];
-        }
+        for (int j = 0; j < 4; ++j)
+            if (x0 + xc + j < J.Wo) o[x0 + xc + j] = acc[f][j];
     }
+}
+
+template <int FC>
+cudaError_t launch_sep_fc(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
+                          const float *lam, const int *rank_off, int K, int R, int h, int w, cudaStream_t s)
+{
+#define TDPM_SEP(HH, WW) \
+    sep_kernel<FC, HH, WW><<<total_tiles, SQ_THREADS, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w)
+    if (h == 6 && w == 6) TDPM_SEP(6, 6);
+    else if (h == 5 && w == 11) TDPM_SEP(5, 11);
+    else if (h == 7 && w == 7) TDPM_SEP(7, 7);
+    else if (h == 11 && w == 5) TDPM_SEP(11, 5);
+    else TDPM_SEP(0, 0);
+#undef TDPM_SEP
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -298,11 +333,8 @@ cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, int total_tiles, const 
     if (total_tiles <= 0) return cudaSuccess;
     if (h < 1 || h > SQ_MAXHW || w < 1 || w > SQ_MAXHW) return cudaErrorInvalidValue;
     note_launches(1);
-    if (joint)
-        sep_kernel<SQ_FC_JOINT><<<total_tiles, SQ_THREADS, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w);
-    else
-        sep_kernel<1><<<total_tiles, SQ_THREADS, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w);
-    return cudaGetLastError();
+    if (joint) return launch_sep_fc<SQ_FC_JOINT>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
+    return launch_sep_fc<1>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
 }
 
 }  // namespace tdpm
