@@ -109,6 +109,7 @@ typedef struct {
 
 /* ---------------------------------------------------------------- detections (Algorithm 1 result set D) */
 typedef struct {
+    int32_t image;                  /* index of the pyramid in the batch (0 for tdpm_build_pyramid_scores) */
     int32_t component, level, y, x; /* root placement (top-left cell) */
     float score;                    /* s = f0.phi(p0) + sum_i (f_i.phi(p_i) - d_i.psi(p_i, p0)) + bias */
     int32_t n_parts;
@@ -178,8 +179,14 @@ tdpm_status tdpm_load_factors(tdpm_ctx *ctx, int32_t model_id, const char *path)
 tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyr, int32_t form,
                                       int32_t precision, void *stream, int32_t *scores_id);
 
-/* Step 4: every scored position with s >= tau, ordered by (component, level, y, x), copied to the host array `out`
- * (capacity records). Blocks until `stream` has finished. *n_out = number of detections, even when it exceeds
+/* Steps 1-3 for a batch of pyramids (images of any sizes) in one scores set: every stage is one launch over all
+ * levels of all images, and repeated batches of the same shapes replay one captured CUDA graph. Detections carry the
+ * image index. Same errors as tdpm_build_pyramid_scores; ERR_ARG for n_images < 1. */
+tdpm_status tdpm_build_batch_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                                    int32_t form, int32_t precision, void *stream, int32_t *scores_id);
+
+/* Step 4: every scored position with s >= tau, ordered by (image, component, level, y, x), copied to the host array
+ * `out` (capacity records). Blocks until `stream` has finished. *n_out = number of detections, even when it exceeds
  * capacity (then ERR_CAPACITY and the first `capacity` records are written). */
 tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detection *out, size_t capacity,
                         size_t *n_out, void *stream);
@@ -191,10 +198,12 @@ tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detect
                                    anchored positions [Y][X] FP32 */
 #define TDPM_MAP_PART_ARG 3     /* same indices: argmax (part_y << 16) | part_x, int32 [Y][X] */
 
-/* Copy one map of a scores set to host memory (blocks on `stream`). rows/cols receive its size; a map that was not
- * computed (filter does not fit, empty domain) has 0 rows. Errors: ERR_CAPACITY (bytes too small), ERR_STATE. */
-tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_t index_a, int32_t index_b,
-                          void *out_host, size_t capacity_bytes, int32_t *rows, int32_t *cols, void *stream);
+/* Copy one map of image `image` of a scores set to host memory (blocks on `stream`). rows/cols receive its size; a map
+ * that was not computed (filter does not fit, empty domain) has 0 rows. Errors: ERR_CAPACITY (bytes too small),
+ * ERR_STATE, ERR_ARG (image out of range). */
+tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_t image, int32_t index_a,
+                          int32_t index_b, void *out_host, size_t capacity_bytes, int32_t *rows, int32_t *cols,
+                          void *stream);
 
 /* Free a scores set. */
 tdpm_status tdpm_release(tdpm_ctx *ctx, int32_t scores_id);

@@ -3,7 +3,7 @@
 //
 // assemble_kernel  s[y][x] = root[y][x] + bias + sum_i D_i[y][x]  (D_i already sampled at 2y+vy, 2x+vx)
 // detect kernels   deterministic stream compaction: per-block counts, one scan, per-block ordered writes, so the
-//                  records come out ordered by (component, level, y, x) with no sort and no float atomics.
+//                  records come out ordered by (image, component, level, y, x) with no sort and no float atomics.
 #include "internal.h"
 
 namespace tdpm {
@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(DET_THREADS) detect_write_kernel(const AsmJob 
     const AsmJob &J = jobs[ji];
     const int local = (int)(idx - J.begin);
     tdpm_detection d;
+    d.image = J.image;
     d.component = J.comp;
     d.level = J.level;
     d.y = local / J.X;

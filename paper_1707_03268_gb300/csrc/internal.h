@@ -84,7 +84,7 @@ struct AsmJob {
     int Y, X;                 // scored root positions
     float bias;
     int n_parts;
-    int comp, level;
+    int image, comp, level;   // level index within its image
     float *out;               // [Y][X]
     const float *D[MAXP];     // [Y][X] each
     const int32_t *A[MAXP];   // [Y][X] each

@@ -65,7 +65,7 @@ struct DtPlan {
 };
 
 struct AsmPlan {
-    int c, j, Y, X, root_W;
+    int image, c, j, Y, X, root_W;
     float bias;
     size_t out_off, root_off;
     std::vector<int> dt;
@@ -73,7 +73,9 @@ struct AsmPlan {
 
 struct Plan {
     uint64_t uid = 0;
-    int model_id = 0, form = 0, precision = 0, L = 0, lam = 0;
+    int model_id = 0, form = 0, precision = 0, L = 0;  // L: levels of all images (flat index)
+    int n_images = 0;
+    std::vector<int> img_base, img_L, img_lam;         // per image: first flat level, level count, lambda
     bool bf = false, split = false, dec = false;
     std::vector<std::pair<int, int>> sizes;
     size_t arena_bytes = 0, blob_off = 0, blob_bytes = 0;
@@ -97,26 +99,36 @@ struct Plan {
 
 namespace {
 
-std::string plan_key(int model_id, const Model &m, int form, int prec, const tdpm_pyramid *pyr)
+std::string plan_key(int model_id, const Model &m, int form, int prec, const tdpm_pyramid *pyrs, int n)
 {
     std::string k = std::to_string(model_id) + ":" + std::to_string(m.version) + ":" + std::to_string(form) + ":" +
-                    std::to_string(prec) + ":" + std::to_string(pyr->lambda);
-    for (int j = 0; j < pyr->n_levels; ++j)
-        k += ":" + std::to_string(pyr->levels[j].H) + "x" + std::to_string(pyr->levels[j].W);
+                    std::to_string(prec) + ":" + std::to_string(n);
+    for (int i = 0; i < n; ++i) {
+        k += "|" + std::to_string(pyrs[i].lambda);
+        for (int j = 0; j < pyrs[i].n_levels; ++j)
+            k += ":" + std::to_string(pyrs[i].levels[j].H) + "x" + std::to_string(pyrs[i].levels[j].W);
+    }
     return k;
 }
 
-std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid *pyr, int form, int prec)
+std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid *pyrs, int n_images, int form,
+                                int prec)
 {
     auto P = std::make_shared<Plan>();
     P->uid = g_plan_uid.fetch_add(1);
     P->model_id = model_id; P->form = form; P->precision = prec;
-    P->L = pyr->n_levels; P->lam = pyr->lambda;
+    P->n_images = n_images;
+    for (int i = 0; i < n_images; ++i) {
+        P->img_base.push_back((int)P->sizes.size());
+        P->img_L.push_back(pyrs[i].n_levels);
+        P->img_lam.push_back(pyrs[i].lambda);
+        for (int j = 0; j < pyrs[i].n_levels; ++j) P->sizes.push_back({pyrs[i].levels[j].H, pyrs[i].levels[j].W});
+    }
+    P->L = (int)P->sizes.size();
     P->bf = prec == TDPM_PREC_BF16 || prec == TDPM_PREC_BF16X3;
     P->split = prec == TDPM_PREC_BF16X3;
     P->dec = form == TDPM_FORM_DECOMPOSED;
-    const int L = P->L, lam = P->lam;
-    for (int j = 0; j < L; ++j) P->sizes.push_back({pyr->levels[j].H, pyr->levels[j].W});
+    const int L = P->L;
     Bump bump;
     if (P->bf) {
         P->bf_off.resize(L);
@@ -130,23 +142,29 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     P->glv.resize(m.groups.size());
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
         const Group &g = m.groups[gi];
-        const int j0 = g.role == 0 ? lam : 0, j1 = g.role == 0 ? L : L - lam;
-        for (int j = j0; j < j1; ++j) {
-            const int H = P->sizes[j].first, W = P->sizes[j].second;
-            const int Ho = H - g.h + 1, Wo = W - g.w + 1;
-            if (Ho <= 0 || Wo <= 0) continue;
-            GroupLevel gl{j, 0, 0, Ho, Wo};
-            gl.out_off = bump.take(sizeof(float) * (size_t)g.K * Ho * Wo);
-            if (P->dec) gl.z_off = bump.take(sizeof(float) * (size_t)g.R * H * W);
-            P->glv[gi].push_back(gl);
-            for (int k = 0; k < g.K; ++k)
-                P->filter_maps[{g.fids[k], j}] = MapRef{gl.out_off + sizeof(float) * (size_t)k * Ho * Wo, Ho, Wo};
+        for (int im = 0; im < n_images; ++im) {
+            // roots score levels [lambda, L) of each image, parts levels [0, L - lambda)
+            const int base = P->img_base[im], lam = P->img_lam[im], Li = P->img_L[im];
+            const int j0 = base + (g.role == 0 ? lam : 0), j1 = base + (g.role == 0 ? Li : Li - lam);
+            for (int j = j0; j < j1; ++j) {
+                const int H = P->sizes[j].first, W = P->sizes[j].second;
+                const int Ho = H - g.h + 1, Wo = W - g.w + 1;
+                if (Ho <= 0 || Wo <= 0) continue;
+                GroupLevel gl{j, 0, 0, Ho, Wo};
+                gl.out_off = bump.take(sizeof(float) * (size_t)g.K * Ho * Wo);
+                if (P->dec) gl.z_off = bump.take(sizeof(float) * (size_t)g.R * H * W);
+                P->glv[gi].push_back(gl);
+                for (int k = 0; k < g.K; ++k)
+                    P->filter_maps[{g.fids[k], j}] = MapRef{gl.out_off + sizeof(float) * (size_t)k * Ho * Wo, Ho, Wo};
+            }
         }
     }
+    for (int im = 0; im < n_images; ++im)
     for (size_t c = 0; c < m.comps.size(); ++c) {
         const CompH &C = m.comps[c];
         const FilterH &Rf = m.filters[C.root_fid];
-        for (int j = lam; j < L; ++j) {
+        const int base = P->img_base[im], lam = P->img_lam[im], Li = P->img_L[im];
+        for (int j = base + lam; j < base + Li; ++j) {
             const int l = j - lam;
             // root positions where the root and every anchored part placement fit
             int Y = P->sizes[j].first - Rf.h + 1, X = P->sizes[j].second - Rf.w + 1;
@@ -159,7 +177,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
             }
             if (Y <= 0 || X <= 0) continue;
             AsmPlan ap;
-            ap.c = (int)c; ap.j = j; ap.Y = Y; ap.X = X; ap.bias = C.bias;
+            ap.image = im; ap.c = (int)c; ap.j = j; ap.Y = Y; ap.X = X; ap.bias = C.bias;
             const MapRef &Rm = P->filter_maps.at({C.root_fid, j});
             ap.root_off = Rm.off;
             ap.root_W = Rm.cols;
@@ -243,7 +261,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
 }
 
 // Write every job table of the plan into the arena's host blob (device pointers into this arena).
-tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Arena &A)
+tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdpm_level *> &lv, Arena &A)
 {
     char *base = A.dev;
     char *hb = A.host;
@@ -254,7 +272,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Ar
         ConvJob *cj = reinterpret_cast<ConvJob *>(hb + P.conv_off);
         long long begin = 0;
         for (int j = 0; j < P.L; ++j) {
-            cj[j].src = pyr->levels[j].data;
+            cj[j].src = lv[j]->data;
             patches.push_back({P.conv_off + sizeof(ConvJob) * j + offsetof(ConvJob, src), j});
             cj[j].dst = reinterpret_cast<uint16_t *>(base + P.bf_off[j]);
             cj[j].dst_lo = P.split ? reinterpret_cast<uint16_t *>(base + P.bf_lo_off[j]) : nullptr;
@@ -288,7 +306,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Ar
                 begin += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad, P.dec ? 1 : g.h * g.w);
             } else if (P.dec) {
                 ZJob &z = reinterpret_cast<ZJob *>(hb + P.g_jobs_off[gi])[i];
-                z.feat = pyr->levels[gl.j].data;
+                z.feat = lv[gl.j]->data;
                 patches.push_back({P.g_jobs_off[gi] + sizeof(ZJob) * i + offsetof(ZJob, feat), gl.j});
                 z.Z = reinterpret_cast<float *>(base + gl.z_off);
                 z.cells = H * W;
@@ -297,7 +315,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Ar
                          ((g.R + zproj_simt_r_chunk() - 1) / zproj_simt_r_chunk());
             } else {
                 CorrJob &c = reinterpret_cast<CorrJob *>(hb + P.g_jobs_off[gi])[i];
-                c.feat = pyr->levels[gl.j].data;
+                c.feat = lv[gl.j]->data;
                 patches.push_back({P.g_jobs_off[gi] + sizeof(CorrJob) * i + offsetof(CorrJob, feat), gl.j});
                 c.out = out;
                 c.H = H; c.W = W; c.Ho = gl.Ho; c.Wo = gl.Wo;
@@ -345,7 +363,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Ar
         a.root = reinterpret_cast<const float *>(base + p.root_off);
         a.root_W = p.root_W;
         a.Y = p.Y; a.X = p.X; a.bias = p.bias; a.n_parts = (int)p.dt.size();
-        a.comp = p.c; a.level = p.j;
+        a.image = p.image; a.comp = p.c; a.level = p.j - P.img_base[p.image];
         a.out = reinterpret_cast<float *>(base + p.out_off);
         for (size_t k = 0; k < p.dt.size(); ++k) {
             a.D[k] = reinterpret_cast<const float *>(base + P.dts[p.dt[k]].d_off);
@@ -355,8 +373,8 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const tdpm_pyramid *pyr, Ar
         pos += (long long)p.Y * p.X;
     }
     const_cast<Plan &>(P).patches = patches;
-    A.levels.assign(pyr->n_levels, nullptr);
-    for (int j = 0; j < pyr->n_levels; ++j) A.levels[j] = pyr->levels[j].data;
+    A.levels.assign(lv.size(), nullptr);
+    for (size_t j = 0; j < lv.size(); ++j) A.levels[j] = lv[j]->data;
     return TDPM_OK;
 }
 
@@ -604,17 +622,29 @@ using namespace tdpm;
 
 extern "C" {
 
-tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyr, int32_t form,
-                                      int32_t precision, void *stream, int32_t *scores_id)
+tdpm_status tdpm_build_batch_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                                    int32_t form, int32_t precision, void *stream, int32_t *scores_id)
 {
     clear_error();
-    if (!ctx || !pyr || !scores_id) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (!ctx || !pyrs || !scores_id) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (n_images < 1 || n_images > 4096) return fail(TDPM_ERR_ARG, "n_images must be in [1, 4096]");
     if (form != TDPM_FORM_FULL && form != TDPM_FORM_DECOMPOSED) return fail(TDPM_ERR_ARG, "bad form");
     if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16 && precision != TDPM_PREC_BF16X3)
         return fail(TDPM_ERR_ARG, "unsupported precision (FP8 is not implemented)");
-    if (pyr->n_levels <= 0 || !pyr->levels) return fail(TDPM_ERR_ARG, "empty pyramid");
-    if (pyr->n_levels > 4096) return fail(TDPM_ERR_ARG, "too many levels");
-    if (pyr->lambda < 1 || pyr->lambda > pyr->n_levels) return fail(TDPM_ERR_ARG, "lambda out of range");
+    std::vector<const tdpm_level *> lv;
+    for (int i = 0; i < n_images; ++i) {
+        const tdpm_pyramid &py = pyrs[i];
+        if (py.n_levels <= 0 || !py.levels) return fail(TDPM_ERR_ARG, "empty pyramid");
+        if (py.n_levels > 4096) return fail(TDPM_ERR_ARG, "too many levels");
+        if (py.lambda < 1 || py.lambda > py.n_levels) return fail(TDPM_ERR_ARG, "lambda out of range");
+        for (int j = 0; j < py.n_levels; ++j) {
+            const tdpm_level &l = py.levels[j];
+            if (l.H <= 0 || l.W <= 0 || !l.data) return fail(TDPM_ERR_ARG, "level with non-positive size or NULL data");
+            if (l.H > 4096 || l.W > 4096) return fail(TDPM_ERR_ARG, "level side above 4096 cells");
+            if (reinterpret_cast<uintptr_t>(l.data) % 16) return fail(TDPM_ERR_ARG, "level data not 16-byte aligned");
+            lv.push_back(&l);
+        }
+    }
     std::lock_guard<std::mutex> lk(ctx->mu);
     tdpm_status st = set_device(ctx);
     if (st) return st;
@@ -622,22 +652,17 @@ tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdp
     if (!m) return fail(TDPM_ERR_STATE, "unknown model id");
     if (form == TDPM_FORM_DECOMPOSED && !m->decomposed)
         return fail(TDPM_ERR_STATE, "decomposed form requested before tdpm_decompose");
-    for (int j = 0; j < pyr->n_levels; ++j) {
-        const tdpm_level &lv = pyr->levels[j];
-        if (lv.H <= 0 || lv.W <= 0 || !lv.data) return fail(TDPM_ERR_ARG, "level with non-positive size or NULL data");
-        if (lv.H > 4096 || lv.W > 4096) return fail(TDPM_ERR_ARG, "level side above 4096 cells");
-        if (reinterpret_cast<uintptr_t>(lv.data) % 16) return fail(TDPM_ERR_ARG, "level data not 16-byte aligned");
-    }
     cudaStream_t s = (cudaStream_t)stream;
-    const std::string key = plan_key(model_id, *m, form, precision, pyr);
+    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images);
     std::shared_ptr<Plan> plan;
     auto pit = ctx->plans.find(key);
     if (pit != ctx->plans.end()) {
         plan = pit->second;
     } else {
-        plan = make_plan(*m, model_id, pyr, form, precision);
+        plan = make_plan(*m, model_id, pyrs, n_images, form, precision);
         if (plan->max_W > 800 || plan->max_H > 800)
             return fail(TDPM_ERR_ARG, "part score maps wider or taller than 800 cells are not supported");
+        if (ctx->plans.size() > 256) ctx->plans.clear();
         ctx->plans[key] = plan;
     }
     auto sc = std::make_unique<Scores>();
@@ -651,19 +676,19 @@ tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdp
             A.graph = nullptr;
         }
         A.uses = 0;
-        if ((st = fill_blob(*plan, *m, pyr, A))) {
+        if ((st = fill_blob(*plan, *m, lv, A))) {
             arena_put(ctx, A);
             return st;
         }
         A.plan_uid = plan->uid;
     } else {
-        bool same = (int)A.levels.size() == pyr->n_levels;
-        for (int j = 0; same && j < pyr->n_levels; ++j) same = A.levels[j] == pyr->levels[j].data;
+        bool same = A.levels.size() == lv.size();
+        for (size_t j = 0; same && j < lv.size(); ++j) same = A.levels[j] == lv[j]->data;
         if (!same) {
             for (const auto &pt : plan->patches)
-                *reinterpret_cast<const float **>(A.host + pt.first) = pyr->levels[pt.second].data;
-            A.levels.assign(pyr->n_levels, nullptr);
-            for (int j = 0; j < pyr->n_levels; ++j) A.levels[j] = pyr->levels[j].data;
+                *reinterpret_cast<const float **>(A.host + pt.first) = lv[pt.second]->data;
+            A.levels.assign(lv.size(), nullptr);
+            for (size_t j = 0; j < lv.size(); ++j) A.levels[j] = lv[j]->data;
         }
     }
     cudaError_t e = cudaSuccess;
@@ -700,6 +725,12 @@ tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdp
     ctx->scores[id] = std::move(sc);
     *scores_id = id;
     return TDPM_OK;
+}
+
+tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyr, int32_t form,
+                                      int32_t precision, void *stream, int32_t *scores_id)
+{
+    return tdpm_build_batch_scores(ctx, model_id, pyr, 1, form, precision, stream, scores_id);
 }
 
 tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detection *out, size_t capacity,
@@ -750,8 +781,9 @@ tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detect
     return TDPM_OK;
 }
 
-tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_t index_a, int32_t index_b,
-                          void *out_host, size_t capacity_bytes, int32_t *rows, int32_t *cols, void *stream)
+tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_t image, int32_t index_a,
+                          int32_t index_b, void *out_host, size_t capacity_bytes, int32_t *rows, int32_t *cols,
+                          void *stream)
 {
     clear_error();
     if (!ctx || !rows || !cols) return fail(TDPM_ERR_ARG, "NULL argument");
@@ -769,7 +801,9 @@ tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_
     case TDPM_MAP_PART_ARG: mp = &P.arg_maps; break;
     default: return fail(TDPM_ERR_ARG, "bad map kind");
     }
-    auto it = mp->find({index_a, index_b});
+    if (image < 0 || image >= P.n_images) return fail(TDPM_ERR_ARG, "image out of range");
+    if (index_b < 0 || index_b >= P.img_L[image]) return fail(TDPM_ERR_ARG, "level out of range");
+    auto it = mp->find({index_a, P.img_base[image] + index_b});
     *rows = 0;
     *cols = 0;
     if (it == mp->end()) return TDPM_OK;

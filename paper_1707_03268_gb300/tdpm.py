@@ -58,7 +58,7 @@ class PyramidDesc(ctypes.Structure):
 
 
 class Detection(ctypes.Structure):
-    _fields_ = [("component", _c_i32), ("level", _c_i32), ("y", _c_i32), ("x", _c_i32), ("score", ctypes.c_float),
+    _fields_ = [("image", _c_i32), ("component", _c_i32), ("level", _c_i32), ("y", _c_i32), ("x", _c_i32), ("score", ctypes.c_float),
                 ("n_parts", _c_i32), ("part_y", _c_i32 * MAX_PARTS), ("part_x", _c_i32 * MAX_PARTS)]
 
 
@@ -67,7 +67,7 @@ class DecompReport(ctypes.Structure):
                 ("max_rel_error", ctypes.c_double), ("mean_rel_error", ctypes.c_double), ("gain", ctypes.c_double)]
 
 
-DETECTION_DTYPE = np.dtype([("component", np.int32), ("level", np.int32), ("y", np.int32), ("x", np.int32),
+DETECTION_DTYPE = np.dtype([("image", np.int32), ("component", np.int32), ("level", np.int32), ("y", np.int32), ("x", np.int32),
                             ("score", np.float32), ("n_parts", np.int32), ("part_y", np.int32, MAX_PARTS),
                             ("part_x", np.int32, MAX_PARTS)])
 assert DETECTION_DTYPE.itemsize == ctypes.sizeof(Detection)
@@ -90,8 +90,10 @@ SIGNATURES = {
     "tdpm_build_pyramid_scores": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _c_i32, _VP,
                                            ctypes.POINTER(_c_i32)]),
     "tdpm_detect": (_c_i32, [_VP, _c_i32, ctypes.c_float, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _VP]),
-    "tdpm_get_maps": (_c_i32, [_VP, _c_i32, _c_i32, _c_i32, _c_i32, _VP, ctypes.c_size_t, ctypes.POINTER(_c_i32),
-                               ctypes.POINTER(_c_i32), _VP]),
+    "tdpm_build_batch_scores": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _c_i32, _c_i32, _VP,
+                                         ctypes.POINTER(_c_i32)]),
+    "tdpm_get_maps": (_c_i32, [_VP, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _VP, ctypes.c_size_t,
+                               ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i32), _VP]),
     "tdpm_release": (_c_i32, [_VP, _c_i32]),
     "tdpm_dt_scratch_bytes": (ctypes.c_size_t, [_c_i32, _c_i32]),
     "tdpm_dt": (_c_i32, [_VP, _c_i32, _c_i32, _c_f32p, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _VP, _VP, _VP,
@@ -261,6 +263,16 @@ def tdpm_build_pyramid_scores(ctx: int, model_id: int, pyramid: DevicePyramid, f
     return sid.value
 
 
+def tdpm_build_batch_scores(ctx: int, model_id: int, pyramids: Sequence[DevicePyramid], form: int = FORM_FULL,
+                            precision: int = PREC_FP32, stream=None) -> int:
+    """Score a batch of pyramids in one scores set (detections carry the image index)."""
+    arr = (PyramidDesc * len(pyramids))(*[p.desc for p in pyramids])
+    sid = _c_i32()
+    _check(lib().tdpm_build_batch_scores(ctx, model_id, arr, len(pyramids), int(form), int(precision),
+                                         _stream_ptr(stream), ctypes.byref(sid)))
+    return sid.value
+
+
 def tdpm_detect(ctx: int, scores_id: int, tau: float, capacity: int = 1 << 20, stream=None,
                 out: Optional[np.ndarray] = None) -> np.ndarray:
     """Detections with score >= tau as a structured array (DETECTION_DTYPE), ordered by (component, level, y, x).
@@ -274,16 +286,18 @@ def tdpm_detect(ctx: int, scores_id: int, tau: float, capacity: int = 1 << 20, s
     return out[: n.value]
 
 
-def tdpm_get_maps(ctx: int, scores_id: int, kind: int, index_a: int, index_b: int, stream=None) -> np.ndarray:
+def tdpm_get_maps(ctx: int, scores_id: int, kind: int, index_a: int, index_b: int, stream=None,
+                  image: int = 0) -> np.ndarray:
+    """Map (kind, index_a, level index_b) of image `image` of a scores set."""
     rows, cols = _c_i32(), _c_i32()
-    st = lib().tdpm_get_maps(ctx, scores_id, kind, index_a, index_b, None, 0, ctypes.byref(rows), ctypes.byref(cols),
-                             _stream_ptr(stream))
-    if rows.value == 0:
-        return np.zeros((0, 0), dtype=np.int32 if kind == MAP_PART_ARG else np.float32)
+    st = lib().tdpm_get_maps(ctx, scores_id, kind, image, index_a, index_b, None, 0, ctypes.byref(rows),
+                             ctypes.byref(cols), _stream_ptr(stream))
     if st not in (OK, ERR_CAPACITY):
         _check(st)
+    if rows.value == 0:
+        return np.zeros((0, 0), dtype=np.int32 if kind == MAP_PART_ARG else np.float32)
     out = np.zeros((rows.value, cols.value), dtype=np.int32 if kind == MAP_PART_ARG else np.float32)
-    _check(lib().tdpm_get_maps(ctx, scores_id, kind, index_a, index_b, out.ctypes.data, out.nbytes,
+    _check(lib().tdpm_get_maps(ctx, scores_id, kind, image, index_a, index_b, out.ctypes.data, out.nbytes,
                                ctypes.byref(rows), ctypes.byref(cols), _stream_ptr(stream)))
     return out
 

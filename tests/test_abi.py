@@ -25,7 +25,7 @@ def lib_path():
 def test_header_declares_the_pipeline_calls():
     syms = declared_symbols()
     for name in ["tdpm_create", "tdpm_destroy", "tdpm_load_model", "tdpm_decompose", "tdpm_build_pyramid_scores",
-                 "tdpm_detect", "tdpm_get_maps", "tdpm_get_factors", "tdpm_save_factors", "tdpm_load_factors",
+                 "tdpm_detect", "tdpm_get_maps", "tdpm_build_batch_scores", "tdpm_get_factors", "tdpm_save_factors", "tdpm_load_factors",
                  "tdpm_release", "tdpm_dt", "tdpm_correlate", "tdpm_last_error"]:
         assert name in syms
 
@@ -45,8 +45,8 @@ def test_binding_covers_every_declared_symbol(lib_path):
 
 def test_struct_layouts_match_header_sizes(lib_path):
     from paper_1707_03268_gb300 import tdpm
-    # tdpm_detection: 6 int32/float fields + 2 x 16 int32
-    assert ctypes.sizeof(tdpm.Detection) == 4 * (6 + 2 * 16)
+    # tdpm_detection: 7 int32/float fields + 2 x 16 int32
+    assert ctypes.sizeof(tdpm.Detection) == 4 * (7 + 2 * 16)
     assert ctypes.sizeof(tdpm.Part) == 16 + 8 + 16
 
 
