@@ -151,6 +151,8 @@ __global__ void __launch_bounds__(ZP_CELLS) zproj_kernel(const ZJob *__restrict_
 // processed. y pass: each work item forms 4 rows of one column of T = a_r o_y Z_r from h+3 loads; x pass: each
 // thread forms U_r = b_r o_x T at 4 consecutive columns of one row from w+3 loads, then adds Lambda[k][r] * U_r to
 // each filter's accumulators. HH / WW are the filter sides when known at compile time (0: runtime sides).
+// TERMS: the CTA owns 8 consecutive terms instead of 8 filters; its "weights" are the unit vectors, so the
+// accumulators hold U_r exactly, and they are stored as BF16 planar (16 bytes per cell: the 8 terms' values).
 constexpr int SQ_T = 32, SQ_THREADS = 256, SQ_MAXHW = 16, SQ_HALO = SQ_T + SQ_MAXHW - 1, SQ_FC_JOINT = 8;
 constexpr int SQ_TS_STRIDE = 65;  // == 1 (mod 32): the x pass's 4 rows x 8 column groups per warp hit distinct banks
 
@@ -166,7 +168,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int FC, int HH, int WW>
+template <int FC, int HH, int WW, bool TERMS>
 __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restrict__ jobs, int n_jobs,
                                                          const float *__restrict__ A, const float *__restrict__ B,
                                                          const float *__restrict__ lam,
@@ -190,6 +192,7 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
     const int k0 = fc * FC;
     int r_begin = 0, r_end = R;
     if (FC == 1) { r_begin = rank_off[k0]; r_end = rank_off[k0 + 1]; }
+    if (TERMS) { r_begin = min(k0, R); r_end = min(k0 + FC, R); }
     const int HY = SQ_T + h - 1, HX = SQ_T + w - 1;
     const size_t plane = (size_t)J.H * J.W;
     const int lx = tid % SQ_T, ly = tid / SQ_T;  // 32 x 8 layout for the copies
@@ -208,7 +211,11 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
         else if (tid < h + w) coef[buf][tid] = __ldg(B + (size_t)(tid - h) * R + r);
         else if (tid < h + w + FC) {
             const int f = tid - h - w;
-            coef[buf][tid] = (FC == 1) ? __ldg(lam + r) : ((k0 + f < K) ? __ldg(lam + (size_t)(k0 + f) * R + r) : 0.f);
+            if (TERMS)
+                coef[buf][tid] = (f == r - k0) ? 1.f : 0.f;
+            else
+                coef[buf][tid] =
+                    (FC == 1) ? __ldg(lam + r) : ((k0 + f < K) ? __ldg(lam + (size_t)(k0 + f) * R + r) : 0.f);
         }
         cp_async_commit();
     };
@@ -268,6 +275,28 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
     }
     const int y = y0 + xr;
     if (y >= J.Ho) return;
+    if (TERMS) {
+        static_assert(!TERMS || FC == 8, "one planar chunk of 8 terms per CTA");
+        const size_t cells = (size_t)J.Ho * J.Wo;
+        const size_t row = ((size_t)fc * cells + (size_t)y * J.Wo) * 8;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = x0 + xc + j;
+            if (x >= J.Wo) break;
+            uint32_t hv[4], lv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(acc[2 * q][j]), h1 = __float2bfloat16_rn(acc[2 * q + 1][j]);
+                hv[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(acc[2 * q][j] - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(acc[2 * q + 1][j] - __bfloat162float(h1));
+                lv[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            *reinterpret_cast<uint4 *>(J.U + row + (size_t)x * 8) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+            if (J.U_lo) *reinterpret_cast<uint4 *>(J.U_lo + row + (size_t)x * 8) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+        }
+        return;
+    }
 #pragma unroll
     for (int f = 0; f < FC; ++f) {
         if (k0 + f >= K) break;
@@ -278,12 +307,12 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
     }
 }
 
-template <int FC>
+template <int FC, bool TERMS>
 cudaError_t launch_sep_fc(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
                           const float *lam, const int *rank_off, int K, int R, int h, int w, cudaStream_t s)
 {
 #define TDPM_SEP(HH, WW) \
-    sep_kernel<FC, HH, WW><<<total_tiles, SQ_THREADS, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w)
+    sep_kernel<FC, HH, WW, TERMS><<<total_tiles, SQ_THREADS, 0, s>>>(d_jobs, n_jobs, A, B, lam, rank_off, K, R, h, w)
     if (h == 6 && w == 6) TDPM_SEP(6, 6);
     else if (h == 5 && w == 11) TDPM_SEP(5, 11);
     else if (h == 7 && w == 7) TDPM_SEP(7, 7);
@@ -325,16 +354,20 @@ cudaError_t launch_zproj_simt(const ZJob *d_jobs, int n_jobs, int total_tiles, c
 
 int sep_tile_x() { return SQ_T; }
 int sep_tile_y() { return SQ_T; }
-int sep_filters_per_cta(bool joint) { return joint ? SQ_FC_JOINT : 1; }
+int sep_filters_per_cta(int mode) { return mode == SEP_PER_FILTER ? 1 : SQ_FC_JOINT; }
 
 cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
-                       const float *lam, const int *rank_off, int K, int R, int h, int w, bool joint, cudaStream_t s)
+                       const float *lam, const int *rank_off, int K, int R, int h, int w, int mode, cudaStream_t s)
 {
     if (total_tiles <= 0) return cudaSuccess;
     if (h < 1 || h > SQ_MAXHW || w < 1 || w > SQ_MAXHW) return cudaErrorInvalidValue;
+    if (mode == SEP_TERMS && (K % SQ_FC_JOINT != 0 || K < R)) return cudaErrorInvalidValue;
     note_launches(1);
-    if (joint) return launch_sep_fc<SQ_FC_JOINT>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
-    return launch_sep_fc<1>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
+    if (mode == SEP_TERMS)
+        return launch_sep_fc<SQ_FC_JOINT, true>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
+    if (mode == SEP_JOINT)
+        return launch_sep_fc<SQ_FC_JOINT, false>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
+    return launch_sep_fc<1, false>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
 }
 
 }  // namespace tdpm

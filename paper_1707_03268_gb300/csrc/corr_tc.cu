@@ -1,10 +1,12 @@
 // Step 1 on the 5th-generation tensor cores (tcgen05, sm_103a): BF16 operands, FP32 accumulation in TMEM.
 //
-// One kernel serves two contractions of the path:
+// One kernel serves three contractions of the path:
 //   * full correlation (Sec. 2 score equation): S[k][y][x] = sum_{dy,dx,c} F_k[dy][dx][c] phi[y+dy][x+dx][c], an
 //     implicit GEMM with M = positions, N = filters, K = taps x 32 channels, walked tap by tap;
 //   * the channel stage of the decomposed form (Sec. 4, correlation with c_r): Z[r][cell] = sum_c C[c][r] phi[cell][c],
-//     the same kernel with a single 1x1 tap and N = rank-1 terms.
+//     the same kernel with a single 1x1 tap and N = rank-1 terms;
+//   * the recombination of the jointly decomposed form: S[k][pos] = sum_r Lambda[k][r] U_r[pos], a 1x1 tap over
+//     cb blocks of 32 "channels" (the terms r), N = filters.
 //
 // Positions are flattened over the full level width (p = y*W + x, so a 128-row M tile is one contiguous run of cells
 // and rows with x >= W-w+1 are computed and dropped). Features are stored as BF16 in a channel-chunk-planar layout
@@ -136,15 +138,16 @@ __device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
     return lo;
 }
 
-// grid: one CTA per (job, M tile, N tile); filt: [taps][4][Npad][8] BF16; NT = N tile width (multiple of 16, <= 256).
+// grid: one CTA per (job, M tile, N tile); filt: [h*w*cb][4][Npad][8] BF16 (tap-major, then channel block);
+// NT = N tile width (multiple of 16, <= 256); the input has 32*cb channels in 4*cb planar chunks.
 // SPLIT: operands come as hi and lo BF16 parts (filt_lo, the job's tmap_lo) and every K step issues three MMAs,
 // hi*hi + hi*lo + lo*hi, into the same FP32 accumulator.
 template <bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__restrict__ jobs, int n_jobs,
                                                                 const uint16_t *__restrict__ filt,
                                                                 const uint16_t *__restrict__ filt_lo, int K, int Npad,
-                                                                int NT, int n_tiles_n, int h, int w, uint32_t tmem_cols,
-                                                                int stages, int *err)
+                                                                int NT, int n_tiles_n, int h, int w, int cb,
+                                                                uint32_t tmem_cols, int stages, int *err)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     constexpr uint32_t NPART = SPLIT ? 2 : 1;
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
     const int nt = local % n_tiles_n, mt = local / n_tiles_n;
     const int p0 = mt * TC_M, n0 = nt * NT;
     const int W = J->W, Ho = J->Ho, Wo = J->Wo;
-    const int taps = h * w;
+    const int taps = h * w * cb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -191,10 +194,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
             if (t >= stages) mbar_wait(empty0 + 8 * s, ((t / stages) - 1) & 1, err);
             const uint32_t full = full0 + 8 * s;
             mbar_expect_tx(full, a_stage_bytes + b_stage_bytes);
-            const int dy = t / w, dx = t - dy * w;
+            const int ts = t / cb, blk = t - ts * cb;
+            const int dy = ts / w, dx = ts - dy * w;
             const uint32_t adst = smem_u32(a_smem + s * a_stage_bytes);
-            tma_load_3d(adst, &J->tmap, 0, p0 + dy * W + dx, 0, full);
-            if (SPLIT) tma_load_3d(adst + A_STAGE_BYTES, &J->tmap_lo, 0, p0 + dy * W + dx, 0, full);
+            tma_load_3d(adst, &J->tmap, 0, p0 + dy * W + dx, 4 * blk, full);
+            if (SPLIT) tma_load_3d(adst + A_STAGE_BYTES, &J->tmap_lo, 0, p0 + dy * W + dx, 4 * blk, full);
             const uint32_t bdst = smem_u32(b_smem + s * b_stage_bytes);
             for (int kc = 0; kc < 4; ++kc) {
                 const size_t off = (((size_t)t * 4 + kc) * Npad + n0) * 8;
@@ -316,13 +320,16 @@ size_t corr_tc_smem_bytes(int NT, bool split, int stages)
 }
 
 cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc,
-                           const uint16_t *filt_tc_lo, int K, int Npad, int h, int w, int *d_err, cudaStream_t s)
+                           const uint16_t *filt_tc_lo, int K, int Npad, int h, int w, int cb, int *d_err,
+                           cudaStream_t s)
 {
     if (total_tiles <= 0) return cudaSuccess;
+    if (cb < 1) return cudaErrorInvalidValue;
     const bool split = filt_tc_lo != nullptr;
-    const int n_tiles_n = corr_tc_n_tiles(Npad, h * w);
+    const int taps = h * w * cb;
+    const int n_tiles_n = corr_tc_n_tiles(Npad, taps);
     const int NT = Npad / n_tiles_n;
-    const int stages = h * w < TC_STAGES ? h * w : TC_STAGES;
+    const int stages = taps < TC_STAGES ? taps : TC_STAGES;
     if (NT % 16 != 0 || NT < 16 || NT > 256 || NT * n_tiles_n != Npad) return cudaErrorInvalidValue;
     uint32_t cols = 32;
     while (cols < (uint32_t)NT) cols <<= 1;
@@ -339,10 +346,10 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, con
     note_launches(1);
     if (split)
         corr_tc_kernel<true><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, filt_tc_lo, K, Npad, NT,
-                                                                   n_tiles_n, h, w, cols, stages, d_err);
+                                                                   n_tiles_n, h, w, cb, cols, stages, d_err);
     else
         corr_tc_kernel<false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, nullptr, K, Npad, NT,
-                                                                    n_tiles_n, h, w, cols, stages, d_err);
+                                                                    n_tiles_n, h, w, cb, cols, stages, d_err);
     return cudaGetLastError();
 }
 
@@ -354,12 +361,12 @@ cudaError_t launch_to_bf16_planar(const ConvJob *d_jobs, int n_jobs, long long t
     return cudaGetLastError();
 }
 
-// Tensor map over one BF16 planar level: dims {8 channels, cells, 4 chunks}, box {8, 128, 4}, zero fill outside.
+// Tensor map over one BF16 planar array: dims {8 channels, cells, chunks}, box {8, 128, 4}, zero fill outside.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells)
+bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks)
 {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -371,7 +378,8 @@ bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells
             return false;
         fn = reinterpret_cast<EncodeTiledFn>(p);
     }
-    const cuuint64_t dims[3] = {8, (cuuint64_t)cells, 4};
+    if (chunks < 4 || chunks % 4) return false;
+    const cuuint64_t dims[3] = {8, (cuuint64_t)cells, (cuuint64_t)chunks};
     const cuuint64_t strides[2] = {16, (cuuint64_t)cells * 16};
     const cuuint32_t box[3] = {8, (cuuint32_t)TC_M, 4};
     const cuuint32_t estr[3] = {1, 1, 1};

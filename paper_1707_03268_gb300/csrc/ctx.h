@@ -63,6 +63,11 @@ struct Group {
     int Rpad_tc = 0;
     uint16_t *d_C_tc = nullptr;          // [1][4][Rpad_tc][8] BF16: the channel factor as a 1x1 "filter bank"
     uint16_t *d_C_tc_lo = nullptr;       // its lo part
+    // joint mode on tensor cores: per-term maps U_r are recombined by S = Lambda U as a GEMM over Upad terms
+    int Upad = 0;                        // R rounded up to a multiple of 32 (zero terms beyond R)
+    int Npad_lam = 0;
+    uint16_t *d_lam_tc = nullptr;        // [Upad/32][4][Npad_lam][8] BF16: Lambda as a bank of K "filters"
+    uint16_t *d_lam_tc_lo = nullptr;     // its lo part
 
     void free_factors();
     void free_all();

@@ -44,10 +44,11 @@ struct ZJob {
     int begin;                // first linear tile index
 };
 
-// Step 1, decomposed form, separable passes + recombination.
+// Step 1, decomposed form, separable passes + recombination (or, in the per-term mode, the per-term maps U_r).
 struct SepJob {
     const float *Z;           // [R][H][W]
     float *out;               // [K][Ho][Wo]
+    uint16_t *U, *U_lo;       // per-term mode: U_r as BF16 planar [Upad/8][Ho*Wo][8] (hi part, lo part or null)
     int H, W, Ho, Wo;
     int tiles_x, tiles_y;
     int begin;
@@ -108,15 +109,18 @@ int corr_f32_tile_x();
 int corr_f32_tile_y();
 int corr_f32_tile_k();
 
-// K1: tcgen05 BF16 implicit-GEMM correlation. filt_tc: [h*w][4][Npad][8] BF16, Npad = n_tiles * NT, NT <= 256 and a
-// multiple of 16 (corr_tc_pad). filt_tc_lo non-null selects split-BF16 operands (lo parts of the filters; the jobs'
-// tmap_lo must describe the lo parts of the features). d_err: device flag raised when a bounded wait expires.
+// K1: tcgen05 BF16 implicit-GEMM correlation. filt_tc: [h*w*cb][4][Npad][8] BF16, Npad = n_tiles * NT, NT <= 256 and
+// a multiple of 16 (corr_tc_pad). The input has 32*cb channels (cb = 1 for HOG features; cb = terms / 32 for the
+// recombination of per-term maps). filt_tc_lo non-null selects split-BF16 operands (lo parts of the filters; the
+// jobs' tmap_lo must describe the lo parts of the input). d_err: device flag raised when a bounded wait expires.
 cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc,
-                           const uint16_t *filt_tc_lo, int K, int Npad, int h, int w, int *d_err, cudaStream_t s);
+                           const uint16_t *filt_tc_lo, int K, int Npad, int h, int w, int cb, int *d_err,
+                           cudaStream_t s);
 int corr_tc_tile_m();
-int corr_tc_pad(int K, int taps);          // padded N for K filters of h*w = taps
+int corr_tc_pad(int K, int taps);          // padded N for K filters over `taps` K blocks (h*w*cb)
 int corr_tc_n_tiles(int Npad, int taps);   // N tiles of one launch
-bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells);
+// Tensor map of a BF16 planar array [chunks][cells][8] (chunks a multiple of 4), box {8, 128, 4}.
+bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks = 4);
 
 // FP32 NHWC -> BF16 planar for many levels in one launch (total = sum of 4 * cells).
 cudaError_t launch_to_bf16_planar(const ConvJob *d_jobs, int n_jobs, long long total, cudaStream_t s);
@@ -126,13 +130,16 @@ cudaError_t launch_zproj_simt(const ZJob *d_jobs, int n_jobs, int total_tiles, c
 int zproj_simt_cells_per_tile();
 int zproj_simt_r_chunk();
 
-// K3+K4: separable passes along y (a_r) and x (b_r) + recombination. A: [h][R], B: [w][R]; per-filter mode: lam[R]
-// per-term weights, filter k owns terms [rank_off[k], rank_off[k+1]); joint mode: lam = Lambda [K][R].
+// K3+K4: separable passes along y (a_r) and x (b_r) + recombination. A: [h][R], B: [w][R].
+//   SEP_PER_FILTER: lam[R] per-term weights, filter k owns terms [rank_off[k], rank_off[k+1]);
+//   SEP_JOINT:      lam = Lambda [K][R], every filter sums all R terms;
+//   SEP_TERMS:      no recombination: U_r for r < K (= Upad, a multiple of 8) written as BF16 planar (zero for r >= R).
+enum SepMode { SEP_PER_FILTER = 0, SEP_JOINT = 1, SEP_TERMS = 2 };
 cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
-                       const float *lam, const int *rank_off, int K, int R, int h, int w, bool joint, cudaStream_t s);
+                       const float *lam, const int *rank_off, int K, int R, int h, int w, int mode, cudaStream_t s);
 int sep_tile_x();
 int sep_tile_y();
-int sep_filters_per_cta(bool joint);
+int sep_filters_per_cta(int mode);   // filters (or terms) one CTA produces
 
 // K5/K6: distance transform passes (x_lines = sum of map rows, y_lines = sum of sampled columns; sides <= 800).
 cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_lines, int y_lines, int max_W, int max_H, cudaStream_t s);

@@ -46,8 +46,12 @@ void Group::free_factors()
     cudaFree(d_rank_off);
     cudaFree(d_C_tc);
     cudaFree(d_C_tc_lo);
+    cudaFree(d_lam_tc);
+    cudaFree(d_lam_tc_lo);
     d_rank_off = nullptr;
     d_C_tc = d_C_tc_lo = nullptr;
+    d_lam_tc = d_lam_tc_lo = nullptr;
+    Upad = Npad_lam = 0;
 }
 
 void Group::free_all()
@@ -92,8 +96,9 @@ tdpm_status upload_tc_bank(uint16_t **dst_hi, uint16_t **dst_lo, int taps, int N
     return st ? st : upload(dst_lo, lo);
 }
 
-// Device copies of a group's factors: FP32 for the SIMT kernels (channel stage of the FP32 path, 1-D passes and
-// recombination of every path), and the channel factor C as a BF16 1x1 bank for the tensor-core channel stage.
+// Device copies of a group's factors: FP32 for the SIMT kernels (channel stage of the FP32 path, 1-D passes of every
+// path, recombination of the FP32 path), the channel factor C as a BF16 1x1 bank for the tensor-core channel stage
+// and, in joint mode, Lambda as a BF16 bank over Upad/32 blocks of terms for the tensor-core recombination.
 tdpm_status upload_factors(Group &g)
 {
     g.free_factors();
@@ -119,8 +124,16 @@ tdpm_status upload_factors(Group &g)
     tdpm_status st = upload(&g.d_rank_off, ro);
     if (st) return st;
     g.Rpad_tc = corr_tc_pad(R, 1);
-    return upload_tc_bank(&g.d_C_tc, &g.d_C_tc_lo, 1, g.Rpad_tc, R,
-                          [&](int, int r, int c) { return (float)g.C[(size_t)c * R + r]; });
+    st = upload_tc_bank(&g.d_C_tc, &g.d_C_tc_lo, 1, g.Rpad_tc, R,
+                        [&](int, int r, int c) { return (float)g.C[(size_t)c * R + r]; });
+    if (st || !g.joint) return st;
+    g.Upad = (R + 31) / 32 * 32;
+    const int cb = g.Upad / 32;
+    g.Npad_lam = corr_tc_pad(K, cb);
+    return upload_tc_bank(&g.d_lam_tc, &g.d_lam_tc_lo, cb, g.Npad_lam, K, [&](int t, int k, int c) {
+        const int r = t * FD + c;
+        return r < R ? (float)g.Lam[(size_t)k * R + r] : 0.f;
+    });
 }
 
 }  // namespace

@@ -56,6 +56,7 @@ struct GroupLevel {
     int j;
     size_t out_off, z_off;
     int Ho, Wo;
+    size_t u_off = 0, u_lo_off = 0;  // joint form on tensor cores: per-term maps U_r, BF16 planar hi / lo
 };
 
 struct DtPlan {
@@ -90,11 +91,16 @@ struct Plan {
     // job tables, offsets inside the blob
     size_t conv_off = 0;
     long long conv_items = 0;
-    std::vector<size_t> g_jobs_off, g_sep_off;
-    std::vector<int> g_tiles, g_sep_tiles;
+    std::vector<size_t> g_jobs_off, g_sep_off, g_rec_off;
+    std::vector<int> g_tiles, g_sep_tiles, g_rec_tiles;
     size_t dt_off = 0, asm_off = 0;
     int x_warps = 0, y_warps = 0, max_W = 1, max_H = 1;
     std::vector<std::pair<size_t, int>> patches;  // blob offsets of caller level pointers
+
+    // joint decomposition with tensor-core operands: the separable stage writes U_r and Lambda U runs as a GEMM
+    bool rec_tc(const Group &g) const { return bf && dec && g.joint; }
+    int sep_mode(const Group &g) const { return rec_tc(g) ? SEP_TERMS : (g.joint ? SEP_JOINT : SEP_PER_FILTER); }
+    int sep_k(const Group &g) const { return rec_tc(g) ? g.Upad : g.K; }
 };
 
 namespace {
@@ -153,6 +159,10 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
                 GroupLevel gl{j, 0, 0, Ho, Wo};
                 gl.out_off = bump.take(sizeof(float) * (size_t)g.K * Ho * Wo);
                 if (P->dec) gl.z_off = bump.take(sizeof(float) * (size_t)g.R * H * W);
+                if (P->rec_tc(g)) {
+                    gl.u_off = bump.take(sizeof(uint16_t) * (size_t)g.Upad * Ho * Wo);
+                    if (P->split) gl.u_lo_off = bump.take(sizeof(uint16_t) * (size_t)g.Upad * Ho * Wo);
+                }
                 P->glv[gi].push_back(gl);
                 for (int k = 0; k < g.K; ++k)
                     P->filter_maps[{g.fids[k], j}] = MapRef{gl.out_off + sizeof(float) * (size_t)k * Ho * Wo, Ho, Wo};
@@ -218,13 +228,15 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     }
     const size_t ng = m.groups.size();
     P->g_jobs_off.assign(ng, 0); P->g_sep_off.assign(ng, 0); P->g_tiles.assign(ng, 0); P->g_sep_tiles.assign(ng, 0);
+    P->g_rec_off.assign(ng, 0); P->g_rec_tiles.assign(ng, 0);
     for (size_t gi = 0; gi < ng; ++gi) {
         const Group &g = m.groups[gi];
         const size_t nj = std::max<size_t>(1, P->glv[gi].size());
         const size_t job_bytes = P->bf ? sizeof(TcJob) : (P->dec ? sizeof(ZJob) : sizeof(CorrJob));
         P->g_jobs_off[gi] = jb.take(job_bytes * nj);
         if (P->dec) P->g_sep_off[gi] = jb.take(sizeof(SepJob) * nj);
-        int tiles = 0, sep_tiles = 0;
+        if (P->rec_tc(g)) P->g_rec_off[gi] = jb.take(sizeof(TcJob) * nj);
+        int tiles = 0, sep_tiles = 0, rec_tiles = 0;
         for (const GroupLevel &gl : P->glv[gi]) {
             const int H = P->sizes[gl.j].first, W = P->sizes[gl.j].second;
             if (P->bf) {
@@ -239,13 +251,17 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
                          ((gl.Ho + corr_f32_tile_y() - 1) / corr_f32_tile_y()) * (g.Kpad / corr_f32_tile_k());
             }
             if (P->dec) {
-                const int fpc = sep_filters_per_cta(g.joint != 0);
+                const int fpc = sep_filters_per_cta(P->sep_mode(g)), kk = P->sep_k(g);
                 sep_tiles += ((gl.Wo + sep_tile_x() - 1) / sep_tile_x()) * ((gl.Ho + sep_tile_y() - 1) / sep_tile_y()) *
-                             (g.joint ? (g.K + fpc - 1) / fpc : g.K);
+                             ((kk + fpc - 1) / fpc);
             }
+            if (P->rec_tc(g))
+                rec_tiles += (int)(((long long)gl.Ho * gl.Wo + corr_tc_tile_m() - 1) / corr_tc_tile_m()) *
+                             corr_tc_n_tiles(g.Npad_lam, g.Upad / FD);
         }
         P->g_tiles[gi] = tiles;
         P->g_sep_tiles[gi] = sep_tiles;
+        P->g_rec_tiles[gi] = rec_tiles;
     }
     P->dt_off = jb.take(sizeof(DtJob) * std::max<size_t>(1, P->dts.size()));
     P->asm_off = jb.take(sizeof(AsmJob) * std::max<size_t>(1, P->asms.size()));
@@ -283,7 +299,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
     }
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
         const Group &g = m.groups[gi];
-        int begin = 0, sep_begin = 0;
+        int begin = 0, sep_begin = 0, rec_begin = 0;
         for (size_t i = 0; i < P.glv[gi].size(); ++i) {
             const GroupLevel &gl = P.glv[gi][i];
             const int H = P.sizes[gl.j].first, W = P.sizes[gl.j].second;
@@ -328,12 +344,29 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
                 SepJob &sp = reinterpret_cast<SepJob *>(hb + P.g_sep_off[gi])[i];
                 sp.Z = reinterpret_cast<const float *>(base + gl.z_off);
                 sp.out = out;
+                sp.U = P.rec_tc(g) ? reinterpret_cast<uint16_t *>(base + gl.u_off) : nullptr;
+                sp.U_lo = P.rec_tc(g) && P.split ? reinterpret_cast<uint16_t *>(base + gl.u_lo_off) : nullptr;
                 sp.H = H; sp.W = W; sp.Ho = gl.Ho; sp.Wo = gl.Wo;
                 sp.tiles_x = (gl.Wo + sep_tile_x() - 1) / sep_tile_x();
                 sp.tiles_y = (gl.Ho + sep_tile_y() - 1) / sep_tile_y();
                 sp.begin = sep_begin;
-                const int fpc = sep_filters_per_cta(g.joint != 0);
-                sep_begin += sp.tiles_x * sp.tiles_y * (g.joint ? (g.K + fpc - 1) / fpc : g.K);
+                const int fpc = sep_filters_per_cta(P.sep_mode(g)), kk = P.sep_k(g);
+                sep_begin += sp.tiles_x * sp.tiles_y * ((kk + fpc - 1) / fpc);
+            }
+            if (P.rec_tc(g)) {
+                // recombination S_k = sum_r Lambda[k][r] U_r: a 1x1 tap over the Ho x Wo grid with Upad input terms
+                TcJob &t = reinterpret_cast<TcJob *>(hb + P.g_rec_off[gi])[i];
+                const long long cells = (long long)gl.Ho * gl.Wo;
+                if (!encode_level_tmap(&t.tmap, reinterpret_cast<const uint16_t *>(base + gl.u_off), cells, g.Upad / 8))
+                    return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+                if (P.split && !encode_level_tmap(&t.tmap_lo, reinterpret_cast<const uint16_t *>(base + gl.u_lo_off),
+                                                  cells, g.Upad / 8))
+                    return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+                t.out = out;
+                t.H = gl.Ho; t.W = gl.Wo; t.Ho = gl.Ho; t.Wo = gl.Wo;
+                t.begin = rec_begin;
+                rec_begin += (int)((cells + corr_tc_tile_m() - 1) / corr_tc_tile_m()) *
+                             corr_tc_n_tiles(g.Npad_lam, g.Upad / FD);
             }
         }
     }
@@ -452,12 +485,10 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
             Prof pr(ctx, s, P.dec ? "zproj_tc" : "corr_tc");
             if (P.dec)
                 e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_C_tc,
-                                   P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, 1,
-                                   1, ctx->d_err, s);
+                                   P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, 1, 1, 1, ctx->d_err, s);
             else
                 e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_filt_tc,
-                                   P.split ? g.d_filt_tc_lo : nullptr, g.K,
-                                   g.Npad_tc, g.h, g.w, ctx->d_err, s);
+                                   P.split ? g.d_filt_tc_lo : nullptr, g.K, g.Npad_tc, g.h, g.w, 1, ctx->d_err, s);
             if (e != cudaSuccess) return e;
             pr.end();
         } else if (P.dec) {
@@ -475,7 +506,15 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         if (P.dec) {
             Prof pr(ctx, s, "sep");
             e = launch_sep(reinterpret_cast<const SepJob *>(dblob + P.g_sep_off[gi]), nj, P.g_sep_tiles[gi], g.d_A,
-                           g.d_B, g.d_lam, g.d_rank_off, g.K, g.R, g.h, g.w, g.joint != 0, s);
+                           g.d_B, g.d_lam, g.d_rank_off, P.sep_k(g), g.R, g.h, g.w, P.sep_mode(g), s);
+            if (e != cudaSuccess) return e;
+            pr.end();
+        }
+        if (P.rec_tc(g)) {
+            Prof pr(ctx, s, "recomb_tc");
+            e = launch_corr_tc(reinterpret_cast<const TcJob *>(dblob + P.g_rec_off[gi]), nj, P.g_rec_tiles[gi],
+                               g.d_lam_tc, P.split ? g.d_lam_tc_lo : nullptr, g.K, g.Npad_lam, 1, 1, g.Upad / FD,
+                               ctx->d_err, s);
             if (e != cudaSuccess) return e;
             pr.end();
         }
@@ -990,7 +1029,7 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
         if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
         if (e == cudaSuccess) e = launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(cjd), 1, 4 * cells, s);
         if (e == cudaSuccess)
-            e = launch_corr_tc(reinterpret_cast<const TcJob *>(tjd), 1, tiles, bank, bank_lo, K, Npad, h, w, d_err, s);
+            e = launch_corr_tc(reinterpret_cast<const TcJob *>(tjd), 1, tiles, bank, bank_lo, K, Npad, h, w, 1, d_err, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(dmem);
