@@ -39,7 +39,7 @@ from paper_1707_03268_gb300 import synth  # noqa: E402
 
 METRIC = "images/sec and p50/p99 latency, decomposed BF16 vs full FP32, at >=99.5% agreement"
 L2_BYTES = 129 * 1024 * 1024
-RANK_SWEEP = (4, 8, 16, 24, 32, 36)
+RANK_SWEEP = {"per_filter": (4, 8, 16, 24, 32, 36), "joint": (16, 32, 64, 128, 256)}
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 3}
 
 
@@ -128,12 +128,17 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
     fb = {"fp32": 4, "bf16": 2, "bf16x3": 4}[precision]  # feature bytes per channel read by the correlation
     corr = "corr_tc" if tc else "corr_f32"
     zproj = "zproj_tc" if tc else "zproj_f32"
-    out = {corr: [0, 0], zproj: [0, 0], "sep": [0, 0], "dt": [0, 0], "assemble": [0, 0], "to_bf16": [0, 0]}
+    out = {corr: [0, 0], zproj: [0, 0], "sep": [0, 0], "recomb_tc": [0, 0], "dt": [0, 0], "assemble": [0, 0],
+           "to_bf16": [0, 0]}
+    ub = 4 if precision == "bf16x3" else 2  # bytes per U_r value on the joint tensor-core path (hi + lo parts)
     if tc:
         out["to_bf16"][0] = sum(H * W * 32 * (4 + fb) for (H, W) in sizes)
     for (role, h, w), fl in groups.items():
         K = len(fl)
-        R = (rank * K if not joint else rank) if rank < h * w else h * w * K
+        if joint:
+            R = min(rank, h * w * 32)       # the joint form is exact from h*w*32 shared terms on
+        else:
+            R = K * min(rank, h * w)        # per filter: exact from h*w terms (the slices) on
         js = range(lam, L) if role == 0 else range(0, L - lam)
         for j in js:
             H, W = sizes[j]
@@ -146,9 +151,16 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
             else:
                 out[zproj][0] += H * W * 32 * fb + R * H * W * 4
                 out[zproj][1] += 2 * 32 * R * H * W
-                out["sep"][0] += R * H * W * 4 + K * Ho * Wo * 4
-                per_filter_terms = R if joint else R // K
-                out["sep"][1] += 2 * K * Ho * Wo * per_filter_terms * (h + w + 1)
+                if joint and tc:
+                    # separable passes write U_r; Lambda U runs on tensor cores
+                    out["sep"][0] += R * H * W * 4 + R * Ho * Wo * ub
+                    out["sep"][1] += 2 * R * Ho * Wo * (h + w)
+                    out["recomb_tc"][0] += R * Ho * Wo * ub + K * Ho * Wo * 4
+                    out["recomb_tc"][1] += 2 * K * R * Ho * Wo
+                else:
+                    out["sep"][0] += R * H * W * 4 + K * Ho * Wo * 4
+                    per_filter_terms = R if joint else R // K
+                    out["sep"][1] += 2 * K * Ho * Wo * per_filter_terms * (h + w + 1)
     for comp in wl.model.components:
         h0, w0 = comp.root.shape[:2]
         for j in range(lam, L):
@@ -182,7 +194,7 @@ def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-TENSOR_STAGES = ("corr_tc", "zproj_tc")
+TENSOR_STAGES = ("corr_tc", "zproj_tc", "recomb_tc")
 ALU_STAGES = ("corr_f32", "zproj_f32", "sep")
 
 
@@ -456,7 +468,7 @@ def main():
     sweep = None
     if form == tdpm.FORM_DECOMPOSED and not args.no_sweep and compare is not None:
         sweep = {}
-        for r in RANK_SWEEP:
+        for r in RANK_SWEEP[args.mode]:
             rr = tdpm.tdpm_decompose(ctx, mid, r, dmode, max_iters=500, seed=1)
             a = keys(step(form, prec))
             run = timed(form, prec, 50, 2)

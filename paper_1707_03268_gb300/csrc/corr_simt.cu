@@ -307,6 +307,97 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
     }
 }
 
+// Per-filter mode, warp form (no shared memory, no block barrier). A warp owns one filter k and a block of SW_ROWS
+// output rows x (32 - (w-1)) output columns. Lane l owns column x0 + l: for each term it loads the block's
+// SW_ROWS + h - 1 values of Z_r in that column at once (independent loads), forms T_r = a_r o_y Z_r row by row from
+// registers, takes T_r at columns x .. x+w-1 from lanes l .. l+w-1 by shuffles for the x pass, and accumulates
+// lambda_r U_r in registers across the filter's terms. The loads of term r+1 are issued before term r is computed,
+// so one memory latency is hidden behind each term's arithmetic. The multiply-add order (dy ascending, then dx
+// ascending, then the terms) is that of sep_kernel, so both give identical results.
+constexpr int SW_ROWS = 16, SW_WARPS = 8;
+
+template <int HH, int WW>
+struct SepTerm {
+    float a[HH], b[WW], l;
+    float z[SW_ROWS + HH - 1];
+};
+
+template <int HH, int WW>
+__global__ void __launch_bounds__(SW_WARPS * 32, 2) sep_warp_kernel(const SepJob *__restrict__ jobs, int n_jobs,
+                                                                 long long total, const float *__restrict__ A,
+                                                                 const float *__restrict__ B,
+                                                                 const float *__restrict__ lam,
+                                                                 const int *__restrict__ rank_off, int K, int R)
+{
+    constexpr int SW = 32 - (WW - 1);  // output columns per warp
+    constexpr int NZ = SW_ROWS + HH - 1;
+    const int lane = threadIdx.x & 31;
+    const long long task = (long long)blockIdx.x * SW_WARPS + (threadIdx.x >> 5);
+    if (task >= total) return;
+    const SepJob &J = jobs[find_job(jobs, n_jobs, task)];
+    long long local = task - J.begin;
+    const int k = (int)(local % K);
+    local /= K;
+    const int sx = (int)(local % J.tiles_x), sy = (int)(local / J.tiles_x);
+    const int x0 = sx * SW, y0 = sy * SW_ROWS;
+    const int x = x0 + lane;
+    const int W = J.W;
+    const size_t plane = (size_t)J.H * W;
+    // Rows: output row y < Ho reads Z rows y .. y+h-1 <= H-1, so no row is out of range. Columns: a lane past the
+    // last column reads column W-1 instead; its T only reaches outputs at x >= Wo, which are not written.
+    const int xc = x < W ? x : W - 1;
+    const int n_out = min(SW_ROWS, J.Ho - y0), n_in = n_out + HH - 1;  // output rows, Z rows of the block
+    const float *zbase = J.Z + (size_t)y0 * W + xc;
+    float acc[SW_ROWS];
+#pragma unroll
+    for (int i = 0; i < SW_ROWS; ++i) acc[i] = 0.f;
+
+    auto load = [&](SepTerm<HH, WW> &t, int r) {
+#pragma unroll
+        for (int i = 0; i < HH; ++i) t.a[i] = __ldg(A + (size_t)i * R + r);
+#pragma unroll
+        for (int i = 0; i < WW; ++i) t.b[i] = __ldg(B + (size_t)i * R + r);
+        t.l = __ldg(lam + r);
+        const float *zp = zbase + (size_t)r * plane;
+        // an opaque copy of the row stride: the row offsets are recomputed per term, not held live across the loop
+        int ws = W;
+        asm volatile("" : "+r"(ws));
+#pragma unroll
+        for (int i = 0; i < NZ; ++i) t.z[i] = __ldg(zp + min(i, n_in - 1) * ws);  // rows past the block: repeats
+    };
+    auto run = [&](const SepTerm<HH, WW> &t) {
+#pragma unroll
+        for (int i = 0; i < SW_ROWS; ++i) {
+            if (i < n_out) {  // warp-uniform
+                float tv = 0.f;
+#pragma unroll
+                for (int dy = 0; dy < HH; ++dy) tv = fmaf(t.a[dy], t.z[i + dy], tv);
+                float u = 0.f;
+#pragma unroll
+                for (int dx = 0; dx < WW; ++dx) u = fmaf(t.b[dx], dx ? __shfl_down_sync(0xffffffffu, tv, dx) : tv, u);
+                acc[i] = fmaf(t.l, u, acc[i]);
+            }
+        }
+    };
+
+    const int r_begin = rank_off[k], r_end = rank_off[k + 1];
+    SepTerm<HH, WW> t0, t1;
+    if (r_begin < r_end) load(t0, r_begin);
+    for (int r = r_begin; r < r_end; r += 2) {
+        if (r + 1 < r_end) load(t1, r + 1);
+        run(t0);
+        if (r + 1 < r_end) {
+            if (r + 2 < r_end) load(t0, r + 2);
+            run(t1);
+        }
+    }
+    if (lane >= SW || x >= J.Wo) return;
+    float *o = J.out + (size_t)k * J.Ho * J.Wo + x;
+#pragma unroll
+    for (int i = 0; i < SW_ROWS; ++i)
+        if (i < n_out) o[(size_t)(y0 + i) * J.Wo] = acc[i];
+}
+
 template <int FC, bool TERMS>
 cudaError_t launch_sep_fc(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
                           const float *lam, const int *rank_off, int K, int R, int h, int w, cudaStream_t s)
@@ -352,17 +443,48 @@ cudaError_t launch_zproj_simt(const ZJob *d_jobs, int n_jobs, int total_tiles, c
     return cudaGetLastError();
 }
 
-int sep_tile_x() { return SQ_T; }
-int sep_tile_y() { return SQ_T; }
-int sep_filters_per_cta(int mode) { return mode == SEP_PER_FILTER ? 1 : SQ_FC_JOINT; }
+// The filter shapes with a compiled warp form of the per-filter mode.
+bool sep_warp_shape(int h, int w)
+{
+    return (h == 6 && w == 6) || (h == 5 && w == 11) || (h == 7 && w == 7) || (h == 11 && w == 5);
+}
 
-cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
+bool sep_uses_warp_form(int mode, int h, int w) { return mode == SEP_PER_FILTER && sep_warp_shape(h, w); }
+
+long long sep_job_items(int mode, int h, int w, int Ho, int Wo, int K, int *tiles_x, int *tiles_y)
+{
+    if (sep_uses_warp_form(mode, h, w)) {
+        const int sw = 32 - (w - 1);
+        *tiles_x = (Wo + sw - 1) / sw;
+        *tiles_y = (Ho + SW_ROWS - 1) / SW_ROWS;
+        return (long long)*tiles_x * *tiles_y * K;
+    }
+    *tiles_x = (Wo + SQ_T - 1) / SQ_T;
+    *tiles_y = (Ho + SQ_T - 1) / SQ_T;
+    const int fpc = mode == SEP_PER_FILTER ? 1 : SQ_FC_JOINT;
+    return (long long)*tiles_x * *tiles_y * ((K + fpc - 1) / fpc);
+}
+
+cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, long long total_items, const float *A, const float *B,
                        const float *lam, const int *rank_off, int K, int R, int h, int w, int mode, cudaStream_t s)
 {
-    if (total_tiles <= 0) return cudaSuccess;
+    if (total_items <= 0) return cudaSuccess;
     if (h < 1 || h > SQ_MAXHW || w < 1 || w > SQ_MAXHW) return cudaErrorInvalidValue;
     if (mode == SEP_TERMS && (K % SQ_FC_JOINT != 0 || K < R)) return cudaErrorInvalidValue;
     note_launches(1);
+    if (sep_uses_warp_form(mode, h, w)) {
+        const unsigned blocks = (unsigned)((total_items + SW_WARPS - 1) / SW_WARPS);
+#define TDPM_SEPW(HH, WW)                                                                                       \
+    sep_warp_kernel<HH, WW><<<blocks, SW_WARPS * 32, 0, s>>>(d_jobs, n_jobs, total_items, A, B, lam, rank_off, K, R)
+        if (h == 6 && w == 6) TDPM_SEPW(6, 6);
+        else if (h == 5 && w == 11) TDPM_SEPW(5, 11);
+        else if (h == 7 && w == 7) TDPM_SEPW(7, 7);
+        else TDPM_SEPW(11, 5);
+#undef TDPM_SEPW
+        return cudaGetLastError();
+    }
+    if (total_items > 0x7fffffffll) return cudaErrorInvalidValue;
+    const int total_tiles = (int)total_items;
     if (mode == SEP_TERMS)
         return launch_sep_fc<SQ_FC_JOINT, true>(d_jobs, n_jobs, total_tiles, A, B, lam, rank_off, K, R, h, w, s);
     if (mode == SEP_JOINT)

@@ -118,6 +118,8 @@ struct Pending {
 
 }  // namespace tdpm
 
+constexpr int kSideStreams = 4;
+
 struct tdpm_ctx {
     int device = 0;
     size_t budget = 0, used = 0;
@@ -128,6 +130,11 @@ struct tdpm_ctx {
     std::map<std::string, std::shared_ptr<tdpm::Plan>> plans;
     std::vector<tdpm::Arena> free_arenas;
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    // the shape groups' correlation chains are independent: they run on side streams forked from (and joined back
+    // into) the caller's stream, as parallel branches of a captured graph
+    std::vector<cudaStream_t> side;
+    cudaEvent_t fork_ev = nullptr;
+    std::vector<cudaEvent_t> join_ev;
     int *d_err = nullptr;                // raised by bounded device waits
     int *h_err = nullptr;                // pinned mirror
     bool use_graphs = true;

@@ -51,7 +51,7 @@ struct SepJob {
     uint16_t *U, *U_lo;       // per-term mode: U_r as BF16 planar [Upad/8][Ho*Wo][8] (hi part, lo part or null)
     int H, W, Ho, Wo;
     int tiles_x, tiles_y;
-    int begin;
+    long long begin;          // first work item of this job
 };
 
 // FP32 NHWC level -> BF16 planar [4][cells][8].
@@ -135,11 +135,11 @@ int zproj_simt_r_chunk();
 //   SEP_JOINT:      lam = Lambda [K][R], every filter sums all R terms;
 //   SEP_TERMS:      no recombination: U_r for r < K (= Upad, a multiple of 8) written as BF16 planar (zero for r >= R).
 enum SepMode { SEP_PER_FILTER = 0, SEP_JOINT = 1, SEP_TERMS = 2 };
-cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, int total_tiles, const float *A, const float *B,
+cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, long long total_items, const float *A, const float *B,
                        const float *lam, const int *rank_off, int K, int R, int h, int w, int mode, cudaStream_t s);
-int sep_tile_x();
-int sep_tile_y();
-int sep_filters_per_cta(int mode);   // filters (or terms) one CTA produces
+// Work items of one level job of launch_sep (K filters, or Upad terms in SEP_TERMS mode): sets the job's tiles_x and
+// tiles_y; the jobs' begin fields are the running sums of these counts.
+long long sep_job_items(int mode, int h, int w, int Ho, int Wo, int K, int *tiles_x, int *tiles_y);
 
 // K5/K6: distance transform passes (x_lines = sum of map rows, y_lines = sum of sampled columns; sides <= 800).
 cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_lines, int y_lines, int max_W, int max_H, cudaStream_t s);

@@ -166,11 +166,23 @@ tdpm_status tdpm_create(tdpm_ctx **out, int32_t device, size_t mem_budget_bytes)
     c->device = device;
     c->budget = mem_budget_bytes;
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
+    for (int i = 0; i < kSideStreams && e == cudaSuccess; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) c->side.push_back(st);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) c->join_ev.push_back(ev);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
     if (e != cudaSuccess) {
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+        for (cudaStream_t st : c->side) cudaStreamDestroy(st);
+        for (cudaEvent_t ev : c->join_ev) cudaEventDestroy(ev);
+        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
         cudaFree(c->d_err);
         delete c;
         return fail(TDPM_ERR_CUDA, std::string("context setup: ") + cudaGetErrorString(e));
@@ -202,6 +214,9 @@ void tdpm_destroy(tdpm_ctx *ctx)
         }
         for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
         cudaStreamDestroy(ctx->cap_stream);
+        for (cudaStream_t st : ctx->side) cudaStreamDestroy(st);
+        for (cudaEvent_t ev : ctx->join_ev) cudaEventDestroy(ev);
+        cudaEventDestroy(ctx->fork_ev);
         cudaFree(ctx->d_err);
         cudaFreeHost(ctx->h_err);
     }

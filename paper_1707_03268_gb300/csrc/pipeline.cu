@@ -92,7 +92,8 @@ struct Plan {
     size_t conv_off = 0;
     long long conv_items = 0;
     std::vector<size_t> g_jobs_off, g_sep_off, g_rec_off;
-    std::vector<int> g_tiles, g_sep_tiles, g_rec_tiles;
+    std::vector<int> g_tiles, g_rec_tiles;
+    std::vector<long long> g_sep_tiles;
     size_t dt_off = 0, asm_off = 0;
     int x_warps = 0, y_warps = 0, max_W = 1, max_H = 1;
     std::vector<std::pair<size_t, int>> patches;  // blob offsets of caller level pointers
@@ -236,7 +237,8 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         P->g_jobs_off[gi] = jb.take(job_bytes * nj);
         if (P->dec) P->g_sep_off[gi] = jb.take(sizeof(SepJob) * nj);
         if (P->rec_tc(g)) P->g_rec_off[gi] = jb.take(sizeof(TcJob) * nj);
-        int tiles = 0, sep_tiles = 0, rec_tiles = 0;
+        int tiles = 0, rec_tiles = 0;
+        long long sep_tiles = 0;
         for (const GroupLevel &gl : P->glv[gi]) {
             const int H = P->sizes[gl.j].first, W = P->sizes[gl.j].second;
             if (P->bf) {
@@ -251,9 +253,8 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
                          ((gl.Ho + corr_f32_tile_y() - 1) / corr_f32_tile_y()) * (g.Kpad / corr_f32_tile_k());
             }
             if (P->dec) {
-                const int fpc = sep_filters_per_cta(P->sep_mode(g)), kk = P->sep_k(g);
-                sep_tiles += ((gl.Wo + sep_tile_x() - 1) / sep_tile_x()) * ((gl.Ho + sep_tile_y() - 1) / sep_tile_y()) *
-                             ((kk + fpc - 1) / fpc);
+                int tx, ty;
+                sep_tiles += sep_job_items(P->sep_mode(g), g.h, g.w, gl.Ho, gl.Wo, P->sep_k(g), &tx, &ty);
             }
             if (P->rec_tc(g))
                 rec_tiles += (int)(((long long)gl.Ho * gl.Wo + corr_tc_tile_m() - 1) / corr_tc_tile_m()) *
@@ -299,7 +300,8 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
     }
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
         const Group &g = m.groups[gi];
-        int begin = 0, sep_begin = 0, rec_begin = 0;
+        int begin = 0, rec_begin = 0;
+        long long sep_begin = 0;
         for (size_t i = 0; i < P.glv[gi].size(); ++i) {
             const GroupLevel &gl = P.glv[gi][i];
             const int H = P.sizes[gl.j].first, W = P.sizes[gl.j].second;
@@ -347,11 +349,8 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
                 sp.U = P.rec_tc(g) ? reinterpret_cast<uint16_t *>(base + gl.u_off) : nullptr;
                 sp.U_lo = P.rec_tc(g) && P.split ? reinterpret_cast<uint16_t *>(base + gl.u_lo_off) : nullptr;
                 sp.H = H; sp.W = W; sp.Ho = gl.Ho; sp.Wo = gl.Wo;
-                sp.tiles_x = (gl.Wo + sep_tile_x() - 1) / sep_tile_x();
-                sp.tiles_y = (gl.Ho + sep_tile_y() - 1) / sep_tile_y();
                 sp.begin = sep_begin;
-                const int fpc = sep_filters_per_cta(P.sep_mode(g)), kk = P.sep_k(g);
-                sep_begin += sp.tiles_x * sp.tiles_y * ((kk + fpc - 1) / fpc);
+                sep_begin += sep_job_items(P.sep_mode(g), g.h, g.w, gl.Ho, gl.Wo, P.sep_k(g), &sp.tiles_x, &sp.tiles_y);
             }
             if (P.rec_tc(g)) {
                 // recombination S_k = sum_r Lambda[k][r] U_r: a 1x1 tap over the Ho x Wo grid with Upad input terms
@@ -476,47 +475,76 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         if (e != cudaSuccess) return e;
         pr.end();
     }
-    for (size_t gi = 0; gi < m.groups.size(); ++gi) {
+    // step 1 for one shape group, on stream gs
+    auto run_group = [&](size_t gi, cudaStream_t gs) -> cudaError_t {
         const Group &g = m.groups[gi];
         const int nj = (int)P.glv[gi].size();
-        if (!nj) continue;
+        cudaError_t e = cudaSuccess;
         const char *jobs = dblob + P.g_jobs_off[gi];
         if (P.bf) {
-            Prof pr(ctx, s, P.dec ? "zproj_tc" : "corr_tc");
+            Prof pr(ctx, gs, P.dec ? "zproj_tc" : "corr_tc");
             if (P.dec)
                 e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_C_tc,
-                                   P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, 1, 1, 1, ctx->d_err, s);
+                                   P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, 1, 1, 1, ctx->d_err, gs);
             else
                 e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_filt_tc,
-                                   P.split ? g.d_filt_tc_lo : nullptr, g.K, g.Npad_tc, g.h, g.w, 1, ctx->d_err, s);
+                                   P.split ? g.d_filt_tc_lo : nullptr, g.K, g.Npad_tc, g.h, g.w, 1, ctx->d_err, gs);
             if (e != cudaSuccess) return e;
             pr.end();
         } else if (P.dec) {
-            Prof pr(ctx, s, "zproj_f32");
-            e = launch_zproj_simt(reinterpret_cast<const ZJob *>(jobs), nj, P.g_tiles[gi], g.d_Ct, g.R, s);
+            Prof pr(ctx, gs, "zproj_f32");
+            e = launch_zproj_simt(reinterpret_cast<const ZJob *>(jobs), nj, P.g_tiles[gi], g.d_Ct, g.R, gs);
             if (e != cudaSuccess) return e;
             pr.end();
         } else {
-            Prof pr(ctx, s, "corr_f32");
+            Prof pr(ctx, gs, "corr_f32");
             e = launch_corr_f32(reinterpret_cast<const CorrJob *>(jobs), nj, P.g_tiles[gi], g.d_filt_t, g.K, g.Kpad,
-                                g.h, g.w, s);
+                                g.h, g.w, gs);
             if (e != cudaSuccess) return e;
             pr.end();
         }
         if (P.dec) {
-            Prof pr(ctx, s, "sep");
+            Prof pr(ctx, gs, "sep");
             e = launch_sep(reinterpret_cast<const SepJob *>(dblob + P.g_sep_off[gi]), nj, P.g_sep_tiles[gi], g.d_A,
-                           g.d_B, g.d_lam, g.d_rank_off, P.sep_k(g), g.R, g.h, g.w, P.sep_mode(g), s);
+                           g.d_B, g.d_lam, g.d_rank_off, P.sep_k(g), g.R, g.h, g.w, P.sep_mode(g), gs);
             if (e != cudaSuccess) return e;
             pr.end();
         }
         if (P.rec_tc(g)) {
-            Prof pr(ctx, s, "recomb_tc");
+            Prof pr(ctx, gs, "recomb_tc");
             e = launch_corr_tc(reinterpret_cast<const TcJob *>(dblob + P.g_rec_off[gi]), nj, P.g_rec_tiles[gi],
                                g.d_lam_tc, P.split ? g.d_lam_tc_lo : nullptr, g.K, g.Npad_lam, 1, 1, g.Upad / FD,
-                               ctx->d_err, s);
+                               ctx->d_err, gs);
             if (e != cudaSuccess) return e;
             pr.end();
+        }
+        return cudaSuccess;
+    };
+    std::vector<size_t> busy;
+    for (size_t gi = 0; gi < m.groups.size(); ++gi)
+        if (!P.glv[gi].empty()) busy.push_back(gi);
+    if (ctx->prof || busy.size() < 2 || ctx->side.empty()) {
+        // serial on the caller's stream (always when profiling, so that every stage is timed on its own)
+        for (size_t gi : busy)
+            if ((e = run_group(gi, s)) != cudaSuccess) return e;
+    } else {
+        // fork: every side stream waits for the work already on s; the group with the most jobs stays on s
+        if ((e = cudaEventRecord(ctx->fork_ev, s)) != cudaSuccess) return e;
+        const size_t ns = std::min(ctx->side.size(), busy.size() - 1);
+        for (size_t i = 0; i < ns; ++i)
+            if ((e = cudaStreamWaitEvent(ctx->side[i], ctx->fork_ev, 0)) != cudaSuccess) return e;
+        size_t big = 0;
+        for (size_t i = 1; i < busy.size(); ++i)
+            if (P.g_tiles[busy[i]] > P.g_tiles[busy[big]]) big = i;
+        size_t next = 0;
+        for (size_t i = 0; i < busy.size(); ++i) {
+            cudaStream_t gs = i == big ? s : ctx->side[(next++) % ns];
+            if ((e = run_group(busy[i], gs)) != cudaSuccess) return e;
+        }
+        // join
+        for (size_t i = 0; i < ns; ++i) {
+            if ((e = cudaEventRecord(ctx->join_ev[i], ctx->side[i])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, ctx->join_ev[i], 0)) != cudaSuccess) return e;
         }
     }
     {

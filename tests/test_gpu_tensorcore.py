@@ -226,3 +226,33 @@ def test_split_bf16_end_to_end_agrees_with_oracle(torch, T, ctx, form):
     tau = float(np.percentile(orc.all_scores(ref), 99))
     assert agreement(det_keys(T.tdpm_detect(ctx, sid, tau)), det_keys(orc.detect(ref, tau))) >= 0.995
     T.tdpm_release(ctx, sid)
+
+
+@pytest.mark.parametrize("form,prec", [("decomposed", "bf16x3"), ("full", "bf16"), ("decomposed", "fp32")])
+def test_concurrent_group_streams_match_serial(torch, T, ctx, form, prec):
+    """The shape groups' chains run on forked side streams (and as parallel graph branches from the second build
+    on); with profiling on they run serially on the caller's stream. All three give identical maps."""
+    wl = synth.config_c2()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    f = T.FORM_DECOMPOSED if form == "decomposed" else T.FORM_FULL
+    p = {"bf16x3": T.PREC_BF16X3, "bf16": T.PREC_BF16, "fp32": T.PREC_FP32}[prec]
+    if f == T.FORM_DECOMPOSED:
+        T.tdpm_decompose(ctx, mid, 8, T.DECOMP_PER_FILTER, max_iters=60, seed=1)
+    dp = device_pyramid(wl.pyramids[0], torch)
+    n_f, _ = T.tdpm_model_info(ctx, mid)
+
+    def maps():
+        sid = T.tdpm_build_pyramid_scores(ctx, mid, dp, f, p)
+        out = [T.tdpm_get_maps(ctx, sid, T.MAP_FILTER_SCORE, fid, j) for fid in range(n_f) for j in (3, 12, 24)]
+        out += [T.tdpm_get_maps(ctx, sid, T.MAP_FINAL_SCORE, c, j) for c in range(len(wl.model.components))
+                for j in (10, 20, 30)]
+        T.tdpm_release(ctx, sid)
+        return out
+
+    forked, replayed = maps(), maps()
+    T.tdpm_profile_enable(ctx, True)
+    serial = maps()
+    T.tdpm_profile_enable(ctx, False)
+    for a, b, c in zip(forked, replayed, serial):
+        np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(a, c)
