@@ -110,6 +110,7 @@ typedef struct {
 /* ---------------------------------------------------------------- detections (Algorithm 1 result set D) */
 typedef struct {
     int32_t image;                  /* index of the pyramid in the batch (0 for tdpm_build_pyramid_scores) */
+    int32_t model;                  /* id of the model that scored it */
     int32_t component, level, y, x; /* root placement (top-left cell) */
     float score;                    /* s = f0.phi(p0) + sum_i (f_i.phi(p_i) - d_i.psi(p_i, p0)) + bias */
     int32_t n_parts;
@@ -198,6 +199,11 @@ tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detect
                                    anchored positions [Y][X] FP32 */
 #define TDPM_MAP_PART_ARG 3     /* same indices: argmax (part_y << 16) | part_x, int32 [Y][X] */
 
+/* Device bytes tdpm_build_batch_scores would hold for this batch (the scores set's arena, rounded up to the size the
+ * library allocates), without launching anything. Same argument rules; errors as tdpm_build_batch_scores. */
+tdpm_status tdpm_scores_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                              int32_t form, int32_t precision, size_t *bytes);
+
 /* Copy one map of image `image` of a scores set to host memory (blocks on `stream`). rows/cols receive its size; a map
  * that was not computed (filter does not fit, empty domain) has 0 rows. Errors: ERR_CAPACITY (bytes too small),
  * ERR_STATE, ERR_ARG (image out of range). */
@@ -251,8 +257,9 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
 uint64_t tdpm_kernel_launches(void);
 
 /* When enabled, every stage the context enqueues is bracketed by CUDA events recorded on the stage's own stream, and
- * the device time is accumulated per stage name ("corr_f32", "zproj", "sep", "dt_x", "dt_y", "assemble", "detect",
- * ...). Disabled by default. */
+ * the device time is accumulated per stage name ("to_bf16", "corr_tc", "corr_f32", "zproj_tc", "zproj_f32", "sep",
+ * "recomb_tc", "dt", "assemble", "detect"). While enabled, the shape groups' correlation chains run one after another
+ * on the caller's stream instead of concurrently, so that each stage is timed alone. Disabled by default. */
 tdpm_status tdpm_profile_enable(tdpm_ctx *ctx, int32_t enable);
 
 /* Stage `index` of the accumulated profile (waits for the recorded events): its name (NUL-terminated, truncated to
@@ -263,6 +270,63 @@ tdpm_status tdpm_profile_read(tdpm_ctx *ctx, int32_t index, char *name, size_t n
 
 /* Clear the accumulated profile. */
 tdpm_status tdpm_profile_reset(tdpm_ctx *ctx);
+
+/* ================================================================================ serving (continuous batching) */
+/* Not in the paper: a request loop around the scoring path. A server thread owned by the context takes submitted
+ * requests (an image pyramid already on the device plus the class models to score it with), groups the pending ones
+ * that use the same (model, form, precision) into one multi-image batch (tdpm_build_batch_scores), and keeps up to
+ * max_inflight batches on the device at once, each on its own stream: requests that arrive while others run are
+ * launched as soon as a slot and the memory budget allow, and the detections of one batch are read back while the
+ * next is already running. A batch's device footprint is its arena (every map and intermediate of its plan); the
+ * batches in flight together stay within mem_budget_bytes. A request scored alone and in a mix gives the same
+ * detections: every stage computes each image's positions with the same arithmetic whatever else is in the batch. */
+#define TDPM_MAX_REQUEST_MODELS 64
+
+typedef struct {
+    int32_t max_batch_images; /* images in one batch (1..4096) */
+    int32_t max_inflight;     /* batches on the device at once (1..4) */
+    int32_t max_wait_us;      /* with nothing in flight, how long to wait for more requests before launching (>= 0) */
+    size_t mem_budget_bytes;  /* device bytes the batches in flight may hold together (0 = no limit) */
+} tdpm_server_config;
+
+typedef struct {
+    const tdpm_pyramid *pyramid; /* device levels (same rules as tdpm_build_pyramid_scores); the caller keeps them
+                                    alive and unchanged until the request's result has been polled */
+    const int32_t *model_ids;    /* the class models to score the image with: 1..TDPM_MAX_REQUEST_MODELS ids */
+    int32_t n_models;
+    int32_t form, precision;     /* as for tdpm_build_pyramid_scores */
+    float tau;                   /* detection threshold (Algorithm 1, step 16) */
+} tdpm_request;
+
+typedef struct {
+    int32_t status;          /* TDPM_OK, or the error that ended one of the request's batches */
+    int32_t batch_images;    /* images in the largest batch the request was scored in */
+    uint64_t t_submit_ns;    /* steady clock: tdpm_submit accepted it */
+    uint64_t t_start_ns;     /* its first batch was launched */
+    uint64_t t_done_ns;      /* its last detections were read back */
+    uint64_t n_detections;   /* detections over all of its models */
+} tdpm_result_info;
+
+/* Start the context's server thread. Errors: ERR_ARG (config out of range), ERR_STATE (already running). */
+tdpm_status tdpm_server_start(tdpm_ctx *ctx, const tdpm_server_config *cfg);
+
+/* Finish every submitted request, then stop and join the server thread (results stay pollable). No-op when not
+ * running. tdpm_destroy calls it. */
+tdpm_status tdpm_server_stop(tdpm_ctx *ctx);
+
+/* Queue a request; *ticket identifies its result. The request is copied (the pyramid's level array and the model id
+ * list may be reused at once; the device data they point to may not). Errors: ERR_ARG (invalid request),
+ * ERR_STATE (server not running). A model id that is not loaded fails the request later, with ERR_STATE. */
+tdpm_status tdpm_submit(tdpm_ctx *ctx, const tdpm_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a request to finish. Returns ERR_TIMEOUT if it has not. When it has: the
+ * detections of every model, ordered by (model as listed in the request, component, level, y, x), with image = 0 and
+ * model = the model id, are copied to out (up to capacity records; *n_out = their number). The result is then
+ * released, unless it did not fit (ERR_CAPACITY: poll again with a larger buffer). *info (optional) receives the
+ * request's status and timestamps. A request that failed returns its error status, with *n_out = 0 (no records),
+ * its info filled and the result released. Errors: ERR_STATE (unknown or already released ticket). */
+tdpm_status tdpm_poll(tdpm_ctx *ctx, uint64_t ticket, int32_t timeout_ms, tdpm_detection *out, size_t capacity,
+                      size_t *n_out, tdpm_result_info *info);
 
 #ifdef __cplusplus
 }

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(DET_THREADS) detect_write_kernel(const AsmJob 
                                                                    long long total, float tau,
                                                                    const int *__restrict__ offsets,
                                                                    tdpm_detection *__restrict__ out,
-                                                                   long long capacity)
+                                                                   long long capacity, int model)
 {
     __shared__ int warp_counts[DET_THREADS / 32];
     const long long idx = (long long)blockIdx.x * DET_THREADS + threadIdx.x;
@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(DET_THREADS) detect_write_kernel(const AsmJob 
     const int local = (int)(idx - J.begin);
     tdpm_detection d;
     d.image = J.image;
+    d.model = model;
     d.component = J.comp;
     d.level = J.level;
     d.y = local / J.X;
@@ -140,13 +141,14 @@ cudaError_t launch_assemble(const AsmJob *d_jobs, int n_jobs, long long total, c
 
 cudaError_t launch_detect(const AsmJob *d_jobs, int n_jobs, long long total, float tau, int *d_block_counts,
                           int *d_block_offsets, int n_blocks, tdpm_detection *d_out, long long capacity,
-                          long long *d_total, cudaStream_t s)
+                          long long *d_total, int model, cudaStream_t s)
 {
     if (total <= 0 || n_blocks <= 0) return cudaMemsetAsync(d_total, 0, sizeof(long long), s);
     note_launches(3);
     detect_count_kernel<<<n_blocks, DET_THREADS, 0, s>>>(d_jobs, n_jobs, total, tau, d_block_counts);
     detect_scan_kernel<<<1, 1024, 0, s>>>(d_block_counts, d_block_offsets, n_blocks, d_total);
-    detect_write_kernel<<<n_blocks, DET_THREADS, 0, s>>>(d_jobs, n_jobs, total, tau, d_block_offsets, d_out, capacity);
+    detect_write_kernel<<<n_blocks, DET_THREADS, 0, s>>>(d_jobs, n_jobs, total, tau, d_block_offsets, d_out, capacity,
+                                                        model);
     return cudaGetLastError();
 }
 

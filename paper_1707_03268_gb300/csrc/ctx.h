@@ -120,6 +120,10 @@ struct Pending {
 
 constexpr int kSideStreams = 4;
 
+namespace tdpm {
+struct Server;  // serve.cpp
+}
+
 struct tdpm_ctx {
     int device = 0;
     size_t budget = 0, used = 0;
@@ -135,6 +139,7 @@ struct tdpm_ctx {
     std::vector<cudaStream_t> side;
     cudaEvent_t fork_ev = nullptr;
     std::vector<cudaEvent_t> join_ev;
+    tdpm::Server *server = nullptr;      // the serving loop, when started
     int *d_err = nullptr;                // raised by bounded device waits
     int *h_err = nullptr;                // pinned mirror
     bool use_graphs = true;
@@ -152,6 +157,11 @@ Model *get_model(tdpm_ctx *ctx, int id);
 void free_scores(tdpm_ctx *ctx, Scores &s);
 void arena_free(tdpm_ctx *ctx, Arena &a);
 void drop_plans_of_model(tdpm_ctx *ctx, int model_id);
+// Device bytes of the arena a batch needs (makes, or finds, and caches its plan).
+tdpm_status batch_arena_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                              int32_t form, int32_t precision, size_t *bytes);
+// Stop the server thread (finishing its requests) and free it; the caller must not hold ctx->mu.
+void server_free(tdpm_ctx *ctx);
 
 template <class T>
 tdpm_status upload(T **dst, const std::vector<T> &src)

@@ -148,7 +148,7 @@ cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_lines, int y_lines,
 cudaError_t launch_assemble(const AsmJob *d_jobs, int n_jobs, long long total, cudaStream_t s);
 cudaError_t launch_detect(const AsmJob *d_jobs, int n_jobs, long long total, float tau, int *d_block_counts,
                           int *d_block_offsets, int n_blocks, tdpm_detection *d_out, long long capacity,
-                          long long *d_total, cudaStream_t s);
+                          long long *d_total, int model, cudaStream_t s);
 int detect_positions_per_block();
 
 }  // namespace tdpm

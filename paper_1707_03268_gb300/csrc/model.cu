@@ -197,6 +197,7 @@ tdpm_status tdpm_create(tdpm_ctx **out, int32_t device, size_t mem_budget_bytes)
 void tdpm_destroy(tdpm_ctx *ctx)
 {
     if (!ctx) return;
+    server_free(ctx);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         cudaSetDevice(ctx->device);

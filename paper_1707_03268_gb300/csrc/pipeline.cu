@@ -563,6 +563,17 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
     return cudaSuccess;
 }
 
+// Arena sizes are rounded up to one of four sizes per octave, so that plans of similar size (a server's batches of
+// different images) reuse each other's arenas instead of allocating: cudaMalloc and cudaFree can stall the device.
+size_t arena_bucket(size_t bytes)
+{
+    if (bytes <= (1u << 20)) return 1u << 20;
+    int e = 0;
+    while ((bytes >> e) > 7) ++e;          // bytes >> e in [4, 7]
+    const size_t unit = (size_t)1 << e;    // a quarter of the octave's base size
+    return (bytes + unit - 1) / unit * unit;
+}
+
 tdpm_status arena_get(tdpm_ctx *ctx, const Plan &P, Arena &out)
 {
     const size_t bytes = P.arena_bytes, host_bytes = P.blob_bytes;
@@ -574,7 +585,7 @@ tdpm_status arena_get(tdpm_ctx *ctx, const Plan &P, Arena &out)
         }
     for (size_t i = 0; i < ctx->free_arenas.size(); ++i) {
         Arena &a = ctx->free_arenas[i];
-        if (a.bytes >= bytes && a.bytes <= bytes + bytes / 4 + (1 << 20) && a.host_bytes >= host_bytes) {
+        if (a.bytes >= bytes && a.bytes <= arena_bucket(bytes) + arena_bucket(bytes) / 4 && a.host_bytes >= host_bytes) {
             out = a;
             ctx->free_arenas.erase(ctx->free_arenas.begin() + i);
             out.plan_uid = 0;
@@ -586,27 +597,30 @@ tdpm_status arena_get(tdpm_ctx *ctx, const Plan &P, Arena &out)
             return TDPM_OK;
         }
     }
-    while (ctx->budget && ctx->used + bytes > ctx->budget && !ctx->free_arenas.empty()) {
+    size_t alloc = arena_bucket(bytes);
+    if (ctx->budget && alloc > ctx->budget) alloc = bytes;
+    while (ctx->budget && ctx->used + alloc > ctx->budget && !ctx->free_arenas.empty()) {
         arena_free(ctx, ctx->free_arenas.back());
         ctx->free_arenas.pop_back();
     }
-    if (ctx->budget && ctx->used + bytes > ctx->budget)
-        return fail(TDPM_ERR_OOM, "scores need " + std::to_string(bytes) + " bytes; budget " +
+    if (ctx->budget && ctx->used + alloc > ctx->budget)
+        return fail(TDPM_ERR_OOM, "scores need " + std::to_string(alloc) + " bytes; budget " +
                                       std::to_string(ctx->budget) + ", in use " + std::to_string(ctx->used));
     Arena a;
-    cudaError_t e = cudaMalloc(&a.dev, bytes);
+    cudaError_t e = cudaMalloc(&a.dev, alloc);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(TDPM_ERR_OOM, std::string("cudaMalloc arena: ") + cudaGetErrorString(e));
     }
-    e = cudaMallocHost(&a.host, host_bytes);
+    const size_t host_alloc = arena_bucket(host_bytes);
+    e = cudaMallocHost(&a.host, host_alloc);
     if (e != cudaSuccess) {
         cudaFree(a.dev);
         return fail(TDPM_ERR_OOM, std::string("cudaMallocHost staging: ") + cudaGetErrorString(e));
     }
-    a.bytes = bytes;
-    a.host_bytes = host_bytes;
-    ctx->used += bytes;
+    a.bytes = alloc;
+    a.host_bytes = host_alloc;
+    ctx->used += alloc;
     out = a;
     return TDPM_OK;
 }
@@ -681,6 +695,27 @@ void drop_plans_of_model(tdpm_ctx *ctx, int model_id)
             ++it;
         }
     }
+}
+
+// Device bytes of the arena a batch needs, as allocated (its plan is made, or found, and cached). Used by the server's
+// admission and by tdpm_scores_bytes.
+tdpm_status batch_arena_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                              int32_t form, int32_t precision, size_t *bytes)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Model *m = get_model(ctx, model_id);
+    if (!m) return fail(TDPM_ERR_STATE, "unknown model id");
+    if (form == TDPM_FORM_DECOMPOSED && !m->decomposed)
+        return fail(TDPM_ERR_STATE, "decomposed form requested before tdpm_decompose");
+    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images);
+    auto pit = ctx->plans.find(key);
+    if (pit == ctx->plans.end()) {
+        auto plan = make_plan(*m, model_id, pyrs, n_images, form, precision);
+        if (ctx->plans.size() > 256) ctx->plans.clear();
+        pit = ctx->plans.emplace(key, plan).first;
+    }
+    *bytes = arena_bucket(pit->second->arena_bytes);  // what arena_get allocates for it
+    return TDPM_OK;
 }
 
 }  // namespace tdpm
@@ -794,6 +829,26 @@ tdpm_status tdpm_build_batch_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_
     return TDPM_OK;
 }
 
+tdpm_status tdpm_scores_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                              int32_t form, int32_t precision, size_t *bytes)
+{
+    clear_error();
+    if (!ctx || !pyrs || !bytes) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (n_images < 1 || n_images > 4096) return fail(TDPM_ERR_ARG, "n_images must be in [1, 4096]");
+    if (form != TDPM_FORM_FULL && form != TDPM_FORM_DECOMPOSED) return fail(TDPM_ERR_ARG, "bad form");
+    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16 && precision != TDPM_PREC_BF16X3)
+        return fail(TDPM_ERR_ARG, "unsupported precision");
+    for (int i = 0; i < n_images; ++i) {
+        const tdpm_pyramid &py = pyrs[i];
+        if (py.n_levels <= 0 || py.n_levels > 4096 || !py.levels) return fail(TDPM_ERR_ARG, "empty pyramid");
+        if (py.lambda < 1 || py.lambda > py.n_levels) return fail(TDPM_ERR_ARG, "lambda out of range");
+        for (int j = 0; j < py.n_levels; ++j)
+            if (py.levels[j].H <= 0 || py.levels[j].W <= 0 || py.levels[j].H > 4096 || py.levels[j].W > 4096)
+                return fail(TDPM_ERR_ARG, "level with a bad size");
+    }
+    return batch_arena_bytes(ctx, model_id, pyrs, n_images, form, precision, bytes);
+}
+
 tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyr, int32_t form,
                                       int32_t precision, void *stream, int32_t *scores_id)
 {
@@ -833,7 +888,7 @@ tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detect
     CUDA_TRY(launch_detect(reinterpret_cast<const AsmJob *>(base + P.blob_off + P.asm_off), (int)P.asms.size(), P.total,
                            tau, reinterpret_cast<int *>(base + P.counts_off), reinterpret_cast<int *>(base + P.offsets_off),
                            P.n_det_blocks, sc->d_records, (long long)want,
-                           reinterpret_cast<long long *>(base + P.total_off), s));
+                           reinterpret_cast<long long *>(base + P.total_off), sc->model_id, s));
     pr.end();
     long long total = 0;
     CUDA_TRY(cudaMemcpyAsync(&total, base + P.total_off, sizeof(long long), cudaMemcpyDeviceToHost, s));

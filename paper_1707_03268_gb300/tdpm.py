@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import List, Optional, Sequence, Tuple
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -58,8 +58,24 @@ class PyramidDesc(ctypes.Structure):
 
 
 class Detection(ctypes.Structure):
-    _fields_ = [("image", _c_i32), ("component", _c_i32), ("level", _c_i32), ("y", _c_i32), ("x", _c_i32), ("score", ctypes.c_float),
-                ("n_parts", _c_i32), ("part_y", _c_i32 * MAX_PARTS), ("part_x", _c_i32 * MAX_PARTS)]
+    _fields_ = [("image", _c_i32), ("model", _c_i32), ("component", _c_i32), ("level", _c_i32), ("y", _c_i32),
+                ("x", _c_i32), ("score", ctypes.c_float), ("n_parts", _c_i32), ("part_y", _c_i32 * MAX_PARTS),
+                ("part_x", _c_i32 * MAX_PARTS)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("pyramid", ctypes.POINTER(PyramidDesc)), ("model_ids", ctypes.POINTER(_c_i32)), ("n_models", _c_i32),
+                ("form", _c_i32), ("precision", _c_i32), ("tau", ctypes.c_float)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch_images", _c_i32), ("max_inflight", _c_i32), ("max_wait_us", _c_i32),
+                ("mem_budget_bytes", ctypes.c_size_t)]
+
+
+class ResultInfo(ctypes.Structure):
+    _fields_ = [("status", _c_i32), ("batch_images", _c_i32), ("t_submit_ns", ctypes.c_uint64),
+                ("t_start_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64), ("n_detections", ctypes.c_uint64)]
 
 
 class DecompReport(ctypes.Structure):
@@ -67,9 +83,9 @@ class DecompReport(ctypes.Structure):
                 ("max_rel_error", ctypes.c_double), ("mean_rel_error", ctypes.c_double), ("gain", ctypes.c_double)]
 
 
-DETECTION_DTYPE = np.dtype([("image", np.int32), ("component", np.int32), ("level", np.int32), ("y", np.int32), ("x", np.int32),
-                            ("score", np.float32), ("n_parts", np.int32), ("part_y", np.int32, MAX_PARTS),
-                            ("part_x", np.int32, MAX_PARTS)])
+DETECTION_DTYPE = np.dtype([("image", np.int32), ("model", np.int32), ("component", np.int32), ("level", np.int32),
+                            ("y", np.int32), ("x", np.int32), ("score", np.float32), ("n_parts", np.int32),
+                            ("part_y", np.int32, MAX_PARTS), ("part_x", np.int32, MAX_PARTS)])
 assert DETECTION_DTYPE.itemsize == ctypes.sizeof(Detection)
 
 # every symbol include/tdpm.h declares, with (restype, argtypes)
@@ -92,6 +108,13 @@ SIGNATURES = {
     "tdpm_detect": (_c_i32, [_VP, _c_i32, ctypes.c_float, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _VP]),
     "tdpm_build_batch_scores": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _c_i32, _c_i32, _VP,
                                          ctypes.POINTER(_c_i32)]),
+    "tdpm_scores_bytes": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _c_i32, _c_i32,
+                                   ctypes.POINTER(ctypes.c_size_t)]),
+    "tdpm_server_start": (_c_i32, [_VP, ctypes.POINTER(ServerConfig)]),
+    "tdpm_server_stop": (_c_i32, [_VP]),
+    "tdpm_submit": (_c_i32, [_VP, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "tdpm_poll": (_c_i32, [_VP, ctypes.c_uint64, _c_i32, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                           ctypes.POINTER(ResultInfo)]),
     "tdpm_get_maps": (_c_i32, [_VP, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _VP, ctypes.c_size_t,
                                ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i32), _VP]),
     "tdpm_release": (_c_i32, [_VP, _c_i32]),
@@ -284,6 +307,60 @@ def tdpm_detect(ctx: int, scores_id: int, tau: float, capacity: int = 1 << 20, s
                            ctypes.byref(n), _stream_ptr(stream))
     _check(st)
     return out[: n.value]
+
+
+def tdpm_scores_bytes(ctx: int, model_id: int, pyramids: Sequence[DevicePyramid], form: int = FORM_FULL,
+                      precision: int = PREC_FP32) -> int:
+    """Device bytes a batch of these pyramids would hold (nothing is launched)."""
+    arr = (PyramidDesc * len(pyramids))(*[p.desc for p in pyramids])
+    b = ctypes.c_size_t()
+    _check(lib().tdpm_scores_bytes(ctx, model_id, arr, len(pyramids), int(form), int(precision), ctypes.byref(b)))
+    return b.value
+
+
+# --------------------------------------------------------------------------------------------------- serving
+_inflight_requests: Dict[Tuple[int, int], object] = {}  # (ctx, ticket) -> device pyramid kept alive until polled
+
+
+def tdpm_server_start(ctx: int, max_batch_images: int = 16, max_inflight: int = 2, max_wait_us: int = 200,
+                      mem_budget_bytes: int = 0) -> None:
+    cfg = ServerConfig(int(max_batch_images), int(max_inflight), int(max_wait_us), int(mem_budget_bytes))
+    _check(lib().tdpm_server_start(ctx, ctypes.byref(cfg)))
+
+
+def tdpm_server_stop(ctx: int) -> None:
+    _check(lib().tdpm_server_stop(ctx))
+
+
+def tdpm_submit(ctx: int, pyramid: DevicePyramid, model_ids: Sequence[int], form: int = FORM_FULL,
+                precision: int = PREC_FP32, tau: float = 0.0) -> int:
+    """Queue one request (an image pyramid on the device, scored with every model in model_ids); returns its ticket.
+    The pyramid's tensors are kept alive here until the result is polled."""
+    ids = (_c_i32 * len(model_ids))(*[int(m) for m in model_ids])
+    req = Request(ctypes.pointer(pyramid.desc), ids, len(model_ids), int(form), int(precision), float(tau))
+    t = ctypes.c_uint64()
+    _check(lib().tdpm_submit(ctx, ctypes.byref(req), ctypes.byref(t)))
+    _inflight_requests[(ctx, t.value)] = pyramid
+    return t.value
+
+
+def tdpm_poll(ctx: int, ticket: int, timeout_ms: int = -1, capacity: int = 4096) -> Tuple[np.ndarray, dict]:
+    """Wait for a request; returns (detections as DETECTION_DTYPE, info dict). Raises TdpmError(ERR_TIMEOUT) when it
+    is not finished within timeout_ms, or the request's own error status when it failed."""
+    info = ResultInfo()
+    n = ctypes.c_size_t()
+    while True:
+        out = np.zeros(max(1, capacity), dtype=DETECTION_DTYPE)
+        st = lib().tdpm_poll(ctx, int(ticket), int(timeout_ms), out.ctypes.data, int(capacity), ctypes.byref(n),
+                             ctypes.byref(info))
+        if st == ERR_CAPACITY:
+            capacity = int(n.value)
+            continue
+        break
+    if st != ERR_TIMEOUT:
+        _inflight_requests.pop((ctx, int(ticket)), None)
+    _check(st)
+    return out[: n.value], {f: getattr(info, f) for f, _ in ResultInfo._fields_}
 
 
 def tdpm_get_maps(ctx: int, scores_id: int, kind: int, index_a: int, index_b: int, stream=None,

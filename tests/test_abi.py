@@ -45,8 +45,8 @@ def test_binding_covers_every_declared_symbol(lib_path):
 
 def test_struct_layouts_match_header_sizes(lib_path):
     from paper_1707_03268_gb300 import tdpm
-    # tdpm_detection: 7 int32/float fields + 2 x 16 int32
-    assert ctypes.sizeof(tdpm.Detection) == 4 * (7 + 2 * 16)
+    # tdpm_detection: 8 int32/float fields + 2 x 16 int32
+    assert ctypes.sizeof(tdpm.Detection) == 4 * (8 + 2 * 16)
     assert ctypes.sizeof(tdpm.Part) == 16 + 8 + 16
 
 
@@ -66,3 +66,25 @@ def test_create_without_gpu_reports_error(lib_path):
 def test_oracle_library_loads():
     from oracle import oracle as orc
     assert orc.num_threads() >= 1
+
+
+def test_header_struct_sizes_match_the_binding(tmp_path):
+    """Compile the header with the host C compiler and compare every public struct's size with its ctypes mirror."""
+    import shutil
+    import subprocess
+    from paper_1707_03268_gb300 import tdpm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"tdpm_detection": tdpm.Detection, "tdpm_level": tdpm.Level, "tdpm_pyramid": tdpm.PyramidDesc,
+             "tdpm_part": tdpm.Part, "tdpm_decomp_report": tdpm.DecompReport, "tdpm_request": tdpm.Request,
+             "tdpm_server_config": tdpm.ServerConfig, "tdpm_result_info": tdpm.ResultInfo}
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "tdpm.h"\nint main(void){\n' +
+                   "".join(f'printf("{n} %zu\\n", sizeof({n}));\n' for n in pairs) + "return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {l.split()[0]: int(l.split()[1]) for l in out if l.strip()}
+    for name, cls in pairs.items():
+        assert got[name] == ctypes.sizeof(cls), name
