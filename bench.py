@@ -495,6 +495,7 @@ def main():
             "stages_ms_per_image": {k: v[0] / n_prof for k, v in stages.items()},
             "roofline": roofline, "rooflines": rooflines, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
             "compare": compare, "decomposition_report": rep, "rank_sweep": sweep,
+            "autotune": tdpm.tdpm_autotune_read(ctx),
             "wall_s_timed": main_run["wall_s"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

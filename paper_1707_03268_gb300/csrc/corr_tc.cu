@@ -19,6 +19,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace tdpm {
@@ -138,14 +140,15 @@ __device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
     return lo;
 }
 
-// grid: one CTA per (job, M tile, N tile); filt: [h*w*cb][4][Npad][8] BF16 (tap-major, then channel block);
-// NT = N tile width (multiple of 16, <= 256); the input has 32*cb channels in 4*cb planar chunks.
+// grid: one CTA per (M tile, N tile), M tiles numbered across the jobs (a job's begin is its first M tile), so the job
+// tables do not depend on the N tiling; filt: [h*w*cb][4][ld][8] BF16 (tap-major, then channel block, ld rows per
+// plane); NT = N tile width (multiple of 16, <= 256); the input has 32*cb channels in 4*cb planar chunks.
 // SPLIT: operands come as hi and lo BF16 parts (filt_lo, the job's tmap_lo) and every K step issues three MMAs,
 // hi*hi + hi*lo + lo*hi, into the same FP32 accumulator.
 template <bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__restrict__ jobs, int n_jobs,
                                                                 const uint16_t *__restrict__ filt,
-                                                                const uint16_t *__restrict__ filt_lo, int K, int Npad,
+                                                                const uint16_t *__restrict__ filt_lo, int K, int ld,
                                                                 int NT, int n_tiles_n, int h, int w, int cb,
                                                                 uint32_t tmem_cols, int stages, int *err)
 {
@@ -160,10 +163,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + stages), done = smem_u32(bars + 2 * stages);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ji = find_job(jobs, n_jobs, blockIdx.x);
+    const int nt = blockIdx.x % n_tiles_n, mg = blockIdx.x / n_tiles_n;
+    const int ji = find_job(jobs, n_jobs, mg);
     const TcJob *J = jobs + ji;
-    const int local = blockIdx.x - J->begin;
-    const int nt = local % n_tiles_n, mt = local / n_tiles_n;
+    const int mt = mg - J->begin;
     const int p0 = mt * TC_M, n0 = nt * NT;
     const int W = J->W, Ho = J->Ho, Wo = J->Wo;
     const int taps = h * w * cb;
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
             if (SPLIT) tma_load_3d(adst + A_STAGE_BYTES, &J->tmap_lo, 0, p0 + dy * W + dx, 4 * blk, full);
             const uint32_t bdst = smem_u32(b_smem + s * b_stage_bytes);
             for (int kc = 0; kc < 4; ++kc) {
-                const size_t off = (((size_t)t * 4 + kc) * Npad + n0) * 8;
+                const size_t off = (((size_t)t * 4 + kc) * ld + n0) * 8;
                 bulk_load(bdst + kc * NT * 16, filt + off, (uint32_t)NT * 16, full);
                 if (SPLIT) bulk_load(bdst + b_part_bytes + kc * NT * 16, filt_lo + off, (uint32_t)NT * 16, full);
             }
@@ -294,23 +297,41 @@ __global__ void to_bf16_planar_kernel(const ConvJob *__restrict__ jobs, int n_jo
 
 int corr_tc_tile_m() { return TC_M; }
 
-// Largest N tile: 256 for multi-tap correlations (more MMA work per staged byte); 128 for the single-tap channel
-// stage, which is bound by its output writes and gains from more CTAs per SM (TMEM holds 512 columns).
-int corr_tc_max_nt(int taps) { return taps > 1 ? 256 : 128; }
-
-int corr_tc_n_tiles(int Npad, int taps)
+// N tiling. A width cap mx gives the balanced tiling: n = ceil(K / mx) tiles of NT = ceil(K / n) rounded up to 16.
+int corr_tc_balanced_nt(int K, int mx)
 {
-    const int mx = corr_tc_max_nt(taps);
-    return (Npad + mx - 1) / mx;
+    const int n = (K + mx - 1) / mx;
+    const int nt = (K + n - 1) / n;
+    return (nt + 15) / 16 * 16;
 }
 
-int corr_tc_pad(int K, int taps)
+int corr_tc_n_tiles(int K, int NT) { return (K + NT - 1) / NT; }
+
+// Default without tuning: caps of 256 for multi-tap correlations (more MMA work per staged byte) and 128 for a single
+// tap (the channel stage, bound by its output writes, gains from more CTAs per SM; TMEM holds 512 columns).
+int corr_tc_default_nt(int K, int taps) { return corr_tc_balanced_nt(K, taps > 1 ? 256 : 128); }
+
+// The widths a tuner may choose from: the balanced tilings under caps 256, 128, 64 and 32 (duplicates dropped).
+int corr_tc_nt_candidates(int K, int *out)
 {
-    const int mx = corr_tc_max_nt(taps);
-    const int n_tiles = (K + mx - 1) / mx;
-    int nt = (K + n_tiles - 1) / n_tiles;
-    nt = (nt + 15) / 16 * 16;
-    return nt * n_tiles;
+    int n = 0;
+    for (int mx : {256, 128, 64, 32}) {
+        const int nt = corr_tc_balanced_nt(K, mx);
+        bool dup = false;
+        for (int i = 0; i < n; ++i) dup |= out[i] == nt;
+        if (!dup) out[n++] = nt;
+    }
+    return n;
+}
+
+// Rows a bank of K filters is padded to (zero rows beyond K): enough for every candidate tiling.
+int corr_tc_bank_rows(int K)
+{
+    int c[4];
+    const int n = corr_tc_nt_candidates(K, c);
+    int rows = (K + 15) / 16 * 16;
+    for (int i = 0; i < n; ++i) rows = std::max(rows, corr_tc_n_tiles(K, c[i]) * c[i]);
+    return rows;
 }
 
 size_t corr_tc_smem_bytes(int NT, bool split, int stages)
@@ -319,18 +340,20 @@ size_t corr_tc_smem_bytes(int NT, bool split, int stages)
     return stages * parts * (A_STAGE_BYTES + (size_t)NT * 64) + 8 * (2 * stages + 1) + 16;
 }
 
-cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc,
-                           const uint16_t *filt_tc_lo, int K, int Npad, int h, int w, int cb, int *d_err,
+cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const uint16_t *filt_tc,
+                           const uint16_t *filt_tc_lo, int K, int ld, int NT, int h, int w, int cb, int *d_err,
                            cudaStream_t s)
 {
-    if (total_tiles <= 0) return cudaSuccess;
+    if (m_tiles <= 0 || K <= 0) return cudaSuccess;
     if (cb < 1) return cudaErrorInvalidValue;
     const bool split = filt_tc_lo != nullptr;
     const int taps = h * w * cb;
-    const int n_tiles_n = corr_tc_n_tiles(Npad, taps);
-    const int NT = Npad / n_tiles_n;
+    const int n_tiles_n = corr_tc_n_tiles(K, NT);
     const int stages = taps < TC_STAGES ? taps : TC_STAGES;
-    if (NT % 16 != 0 || NT < 16 || NT > 256 || NT * n_tiles_n != Npad) return cudaErrorInvalidValue;
+    // every N tile's bulk copies stay inside the bank's ld rows
+    if (NT % 16 != 0 || NT < 16 || NT > 256 || n_tiles_n * NT > ld) return cudaErrorInvalidValue;
+    if ((long long)m_tiles * n_tiles_n > 0x7fffffffll) return cudaErrorInvalidValue;
+    const int total_tiles = m_tiles * n_tiles_n;
     uint32_t cols = 32;
     while (cols < (uint32_t)NT) cols <<= 1;
     // keep residency within TMEM: at most 512 / cols CTAs per SM, enforced through the shared memory request
@@ -345,10 +368,10 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, con
     if (e != cudaSuccess) return e;
     note_launches(1);
     if (split)
-        corr_tc_kernel<true><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, filt_tc_lo, K, Npad, NT,
+        corr_tc_kernel<true><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, filt_tc_lo, K, ld, NT,
                                                                    n_tiles_n, h, w, cb, cols, stages, d_err);
     else
-        corr_tc_kernel<false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, nullptr, K, Npad, NT,
+        corr_tc_kernel<false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, nullptr, K, ld, NT,
                                                                     n_tiles_n, h, w, cb, cols, stages, d_err);
     return cudaGetLastError();
 }

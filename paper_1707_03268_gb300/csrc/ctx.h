@@ -49,7 +49,7 @@ struct Group {
     std::vector<int> fids;
     int Kpad = 0;                        // FP32 SIMT layout padding (multiple of 64)
     float *d_filt_t = nullptr;           // [h*w*32][Kpad] FP32
-    int Npad_tc = 0;                     // tensor-core layout padding
+    int Npad_tc = 0;                     // tensor-core bank rows (K padded for every candidate N tiling)
     uint16_t *d_filt_tc = nullptr;       // [h*w][4][Npad_tc][8] BF16 (hi part: bf16(x))
     uint16_t *d_filt_tc_lo = nullptr;    // lo part bf16(x - bf16(x)), same layout (split-BF16 precision)
     // decomposition, FP64 master copies
@@ -60,12 +60,12 @@ struct Group {
     // FP32 device copies (the 1-D passes run in FP32 for every precision)
     float *d_A = nullptr, *d_B = nullptr, *d_Ct = nullptr, *d_lam = nullptr;
     int *d_rank_off = nullptr;
-    int Rpad_tc = 0;
+    int Rpad_tc = 0;                     // rows of the channel-factor bank
     uint16_t *d_C_tc = nullptr;          // [1][4][Rpad_tc][8] BF16: the channel factor as a 1x1 "filter bank"
     uint16_t *d_C_tc_lo = nullptr;       // its lo part
     // joint mode on tensor cores: per-term maps U_r are recombined by S = Lambda U as a GEMM over Upad terms
     int Upad = 0;                        // R rounded up to a multiple of 32 (zero terms beyond R)
-    int Npad_lam = 0;
+    int Npad_lam = 0;                    // rows of the Lambda bank
     uint16_t *d_lam_tc = nullptr;        // [Upad/32][4][Npad_lam][8] BF16: Lambda as a bank of K "filters"
     uint16_t *d_lam_tc_lo = nullptr;     // its lo part
 
@@ -143,6 +143,8 @@ struct tdpm_ctx {
     int *d_err = nullptr;                // raised by bounded device waits
     int *h_err = nullptr;                // pinned mirror
     bool use_graphs = true;
+    bool autotune = true;                // time the N tilings of a new plan's tensor-core launches (TDPM_AUTOTUNE=0: off)
+    std::map<std::string, int> tune_cache;  // shape class of a tensor-core launch -> chosen N tile width
     // profiling
     bool prof = false;
     std::vector<tdpm::Pending> pending;

@@ -32,7 +32,7 @@ struct alignas(64) TcJob {
     CUtensorMap tmap_lo;      // lo part (split-BF16 precision only)
     float *out;               // [N][Ho][Wo] (channel stage: [R][H][W])
     int H, W, Ho, Wo;
-    int begin;                // first linear CTA index (M tiles x N tiles)
+    int begin;                // first M tile of this job (M tiles numbered across the jobs of a launch)
     int pad[3];
 };
 
@@ -109,16 +109,19 @@ int corr_f32_tile_x();
 int corr_f32_tile_y();
 int corr_f32_tile_k();
 
-// K1: tcgen05 BF16 implicit-GEMM correlation. filt_tc: [h*w*cb][4][Npad][8] BF16, Npad = n_tiles * NT, NT <= 256 and
-// a multiple of 16 (corr_tc_pad). The input has 32*cb channels (cb = 1 for HOG features; cb = terms / 32 for the
+// K1: tcgen05 BF16 implicit-GEMM correlation over m_tiles M tiles (the jobs' begin fields number them) and
+// ceil(K / NT) N tiles of width NT (a multiple of 16, <= 256). filt_tc: [h*w*cb][4][ld][8] BF16 with ld >= the N tiles
+// times NT (corr_tc_bank_rows). The input has 32*cb channels (cb = 1 for HOG features; cb = terms / 32 for the
 // recombination of per-term maps). filt_tc_lo non-null selects split-BF16 operands (lo parts of the filters; the
 // jobs' tmap_lo must describe the lo parts of the input). d_err: device flag raised when a bounded wait expires.
-cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int total_tiles, const uint16_t *filt_tc,
-                           const uint16_t *filt_tc_lo, int K, int Npad, int h, int w, int cb, int *d_err,
+cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const uint16_t *filt_tc,
+                           const uint16_t *filt_tc_lo, int K, int ld, int NT, int h, int w, int cb, int *d_err,
                            cudaStream_t s);
 int corr_tc_tile_m();
-int corr_tc_pad(int K, int taps);          // padded N for K filters over `taps` K blocks (h*w*cb)
-int corr_tc_n_tiles(int Npad, int taps);   // N tiles of one launch
+int corr_tc_n_tiles(int K, int NT);
+int corr_tc_default_nt(int K, int taps);     // untuned N tile width for K filters over `taps` K blocks (h*w*cb)
+int corr_tc_nt_candidates(int K, int *out);  // up to 4 widths a tuner may choose; returns their number
+int corr_tc_bank_rows(int K);                // bank rows (ld) that fit every candidate width
 // Tensor map of a BF16 planar array [chunks][cells][8] (chunks a multiple of 4), box {8, 128, 4}.
 bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks = 4);
 

@@ -123,13 +123,13 @@ tdpm_status upload_factors(Group &g)
     if (ro.empty()) ro.assign(K + 1, 0);
     tdpm_status st = upload(&g.d_rank_off, ro);
     if (st) return st;
-    g.Rpad_tc = corr_tc_pad(R, 1);
+    g.Rpad_tc = corr_tc_bank_rows(R);
     st = upload_tc_bank(&g.d_C_tc, &g.d_C_tc_lo, 1, g.Rpad_tc, R,
                         [&](int, int r, int c) { return (float)g.C[(size_t)c * R + r]; });
     if (st || !g.joint) return st;
     g.Upad = (R + 31) / 32 * 32;
     const int cb = g.Upad / 32;
-    g.Npad_lam = corr_tc_pad(K, cb);
+    g.Npad_lam = corr_tc_bank_rows(K);
     return upload_tc_bank(&g.d_lam_tc, &g.d_lam_tc_lo, cb, g.Npad_lam, K, [&](int t, int k, int c) {
         const int r = t * FD + c;
         return r < R ? (float)g.Lam[(size_t)k * R + r] : 0.f;
@@ -190,6 +190,8 @@ tdpm_status tdpm_create(tdpm_ctx **out, int32_t device, size_t mem_budget_bytes)
     *c->h_err = 0;
     const char *g = std::getenv("TDPM_GRAPHS");
     c->use_graphs = !(g && g[0] == '0');
+    const char *at = std::getenv("TDPM_AUTOTUNE");
+    c->autotune = !(at && at[0] == '0');
     *out = c;
     return TDPM_OK;
 }
@@ -291,7 +293,7 @@ tdpm_status tdpm_load_model(tdpm_ctx *ctx, const tdpm_model_desc *desc, int32_t 
             for (int t = 0; t < taps; ++t)
                 for (int c = 0; c < FD; ++c) ft[((size_t)t * FD + c) * g.Kpad + k] = F.data[(size_t)t * FD + c];
         }
-        g.Npad_tc = corr_tc_pad(g.K, g.h * g.w);
+        g.Npad_tc = corr_tc_bank_rows(g.K);
         if ((st = upload(&g.d_filt_t, ft)) ||
             (st = upload_tc_bank(&g.d_filt_tc, &g.d_filt_tc_lo, taps, g.Npad_tc, g.K, [&](int t, int k, int c) {
                  return m->filters[g.fids[k]].data[(size_t)t * FD + c];

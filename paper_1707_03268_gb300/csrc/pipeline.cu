@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -92,7 +93,9 @@ struct Plan {
     size_t conv_off = 0;
     long long conv_items = 0;
     std::vector<size_t> g_jobs_off, g_sep_off, g_rec_off;
-    std::vector<int> g_tiles, g_rec_tiles;
+    std::vector<int> g_tiles, g_rec_tiles;  // tensor-core launches: M tiles (the N tiling is chosen at launch)
+    std::vector<int> g_nt, g_rec_nt;        // N tile widths of the group's tensor-core launches (tuned or default)
+    bool tuned = false;
     std::vector<long long> g_sep_tiles;
     size_t dt_off = 0, asm_off = 0;
     int x_warps = 0, y_warps = 0, max_W = 1, max_H = 1;
@@ -230,6 +233,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     const size_t ng = m.groups.size();
     P->g_jobs_off.assign(ng, 0); P->g_sep_off.assign(ng, 0); P->g_tiles.assign(ng, 0); P->g_sep_tiles.assign(ng, 0);
     P->g_rec_off.assign(ng, 0); P->g_rec_tiles.assign(ng, 0);
+    P->g_nt.assign(ng, 0); P->g_rec_nt.assign(ng, 0);
     for (size_t gi = 0; gi < ng; ++gi) {
         const Group &g = m.groups[gi];
         const size_t nj = std::max<size_t>(1, P->glv[gi].size());
@@ -242,9 +246,8 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         for (const GroupLevel &gl : P->glv[gi]) {
             const int H = P->sizes[gl.j].first, W = P->sizes[gl.j].second;
             if (P->bf) {
-                const int Npad = P->dec ? g.Rpad_tc : g.Npad_tc;
                 const long long span = P->dec ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
-                tiles += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad, P->dec ? 1 : g.h * g.w);
+                tiles += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m());
             } else if (P->dec) {
                 tiles += ((H * W + zproj_simt_cells_per_tile() - 1) / zproj_simt_cells_per_tile()) *
                          ((g.R + zproj_simt_r_chunk() - 1) / zproj_simt_r_chunk());
@@ -257,12 +260,13 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
                 sep_tiles += sep_job_items(P->sep_mode(g), g.h, g.w, gl.Ho, gl.Wo, P->sep_k(g), &tx, &ty);
             }
             if (P->rec_tc(g))
-                rec_tiles += (int)(((long long)gl.Ho * gl.Wo + corr_tc_tile_m() - 1) / corr_tc_tile_m()) *
-                             corr_tc_n_tiles(g.Npad_lam, g.Upad / FD);
+                rec_tiles += (int)(((long long)gl.Ho * gl.Wo + corr_tc_tile_m() - 1) / corr_tc_tile_m());
         }
         P->g_tiles[gi] = tiles;
         P->g_sep_tiles[gi] = sep_tiles;
         P->g_rec_tiles[gi] = rec_tiles;
+        P->g_nt[gi] = P->dec ? corr_tc_default_nt(g.R, 1) : corr_tc_default_nt(g.K, g.h * g.w);
+        P->g_rec_nt[gi] = P->rec_tc(g) ? corr_tc_default_nt(g.K, g.Upad / FD) : 0;
     }
     P->dt_off = jb.take(sizeof(DtJob) * std::max<size_t>(1, P->dts.size()));
     P->asm_off = jb.take(sizeof(AsmJob) * std::max<size_t>(1, P->asms.size()));
@@ -319,9 +323,8 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
                 t.Ho = P.dec ? H : gl.Ho;
                 t.Wo = P.dec ? W : gl.Wo;
                 t.begin = begin;
-                const int Npad = P.dec ? g.Rpad_tc : g.Npad_tc;
                 const long long span = P.dec ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
-                begin += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad, P.dec ? 1 : g.h * g.w);
+                begin += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m());
             } else if (P.dec) {
                 ZJob &z = reinterpret_cast<ZJob *>(hb + P.g_jobs_off[gi])[i];
                 z.feat = lv[gl.j]->data;
@@ -364,8 +367,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
                 t.out = out;
                 t.H = gl.Ho; t.W = gl.Wo; t.Ho = gl.Ho; t.Wo = gl.Wo;
                 t.begin = rec_begin;
-                rec_begin += (int)((cells + corr_tc_tile_m() - 1) / corr_tc_tile_m()) *
-                             corr_tc_n_tiles(g.Npad_lam, g.Upad / FD);
+                rec_begin += (int)((cells + corr_tc_tile_m() - 1) / corr_tc_tile_m());
             }
         }
     }
@@ -485,10 +487,12 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
             Prof pr(ctx, gs, P.dec ? "zproj_tc" : "corr_tc");
             if (P.dec)
                 e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_C_tc,
-                                   P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, 1, 1, 1, ctx->d_err, gs);
+                                   P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, P.g_nt[gi], 1, 1, 1, ctx->d_err,
+                                   gs);
             else
                 e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_filt_tc,
-                                   P.split ? g.d_filt_tc_lo : nullptr, g.K, g.Npad_tc, g.h, g.w, 1, ctx->d_err, gs);
+                                   P.split ? g.d_filt_tc_lo : nullptr, g.K, g.Npad_tc, P.g_nt[gi], g.h, g.w, 1,
+                                   ctx->d_err, gs);
             if (e != cudaSuccess) return e;
             pr.end();
         } else if (P.dec) {
@@ -513,8 +517,8 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         if (P.rec_tc(g)) {
             Prof pr(ctx, gs, "recomb_tc");
             e = launch_corr_tc(reinterpret_cast<const TcJob *>(dblob + P.g_rec_off[gi]), nj, P.g_rec_tiles[gi],
-                               g.d_lam_tc, P.split ? g.d_lam_tc_lo : nullptr, g.K, g.Npad_lam, 1, 1, g.Upad / FD,
-                               ctx->d_err, gs);
+                               g.d_lam_tc, P.split ? g.d_lam_tc_lo : nullptr, g.K, g.Npad_lam, P.g_rec_nt[gi], 1,
+                               1, g.Upad / FD, ctx->d_err, gs);
             if (e != cudaSuccess) return e;
             pr.end();
         }
@@ -561,6 +565,95 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         pr.end();
     }
     return cudaSuccess;
+}
+
+// Autotuner for the tensor-core launches (N tile width). A new plan's candidates are timed on its own inputs, on the
+// caller's stream, before its first real enqueue (whose launches then overwrite every output). The choice is cached in
+// the context per shape class: (launch kind, N, K blocks, split operands, M tiles rounded up to a power of two), so
+// later plans of the same class (other images, a server's batches) reuse it without timing.
+std::string tune_key(const char *kind, int N, int kblocks, bool split, int m_tiles)
+{
+    int b = 1;
+    while (b < m_tiles) b <<= 1;
+    return std::string(kind) + ":" + std::to_string(N) + ":" + std::to_string(kblocks) + ":" + (split ? "x3" : "x1") +
+           ":" + std::to_string(b);
+}
+
+cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, const Arena &A, cudaStream_t s)
+{
+    P.tuned = true;
+    if (!P.bf) return cudaSuccess;
+    char *dblob = A.dev + P.blob_off;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaError_t e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    bool staged = false;
+    // time one candidate: a warm-up launch, then three timed ones
+    auto time_ms = [&](const std::function<cudaError_t()> &launch, float *ms) -> cudaError_t {
+        cudaError_t r = launch();
+        if (r == cudaSuccess) r = cudaEventRecord(ev0, s);
+        for (int i = 0; i < 3 && r == cudaSuccess; ++i) r = launch();
+        if (r == cudaSuccess) r = cudaEventRecord(ev1, s);
+        if (r == cudaSuccess) r = cudaEventSynchronize(ev1);
+        if (r == cudaSuccess) r = cudaEventElapsedTime(ms, ev0, ev1);
+        return r;
+    };
+    auto choose = [&](const std::string &key, int N, const std::function<cudaError_t(int)> &launch_nt,
+                      int *chosen) -> cudaError_t {
+        auto it = ctx->tune_cache.find(key);
+        if (it != ctx->tune_cache.end()) {
+            *chosen = it->second;
+            return cudaSuccess;
+        }
+        if (!staged) {
+            staged = true;
+            cudaError_t r = cudaMemcpyAsync(dblob, A.host, P.blob_bytes, cudaMemcpyHostToDevice, s);
+            if (r == cudaSuccess)
+                r = launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(dblob + P.conv_off), P.L, P.conv_items, s);
+            if (r != cudaSuccess) return r;
+        }
+        int cand[4];
+        const int nc = corr_tc_nt_candidates(N, cand);
+        float best = 0.f;
+        for (int i = 0; i < nc; ++i) {
+            float ms = 0.f;
+            const cudaError_t r = time_ms([&] { return launch_nt(cand[i]); }, &ms);
+            if (r != cudaSuccess) return r;
+            if (i == 0 || ms < best) {
+                best = ms;
+                *chosen = cand[i];
+            }
+        }
+        ctx->tune_cache[key] = *chosen;
+        return cudaSuccess;
+    };
+    for (size_t gi = 0; gi < m.groups.size() && e == cudaSuccess; ++gi) {
+        const Group &g = m.groups[gi];
+        const int nj = (int)P.glv[gi].size();
+        if (!nj) continue;
+        const TcJob *jobs = reinterpret_cast<const TcJob *>(dblob + P.g_jobs_off[gi]);
+        if (P.dec) {
+            e = choose(tune_key("zproj", g.R, 1, P.split, P.g_tiles[gi]), g.R, [&](int nt) {
+                return launch_corr_tc(jobs, nj, P.g_tiles[gi], g.d_C_tc, P.split ? g.d_C_tc_lo : nullptr, g.R,
+                                      g.Rpad_tc, nt, 1, 1, 1, ctx->d_err, s);
+            }, &P.g_nt[gi]);
+        } else {
+            e = choose(tune_key("corr", g.K, g.h * g.w, P.split, P.g_tiles[gi]), g.K, [&](int nt) {
+                return launch_corr_tc(jobs, nj, P.g_tiles[gi], g.d_filt_tc, P.split ? g.d_filt_tc_lo : nullptr, g.K,
+                                      g.Npad_tc, nt, g.h, g.w, 1, ctx->d_err, s);
+            }, &P.g_nt[gi]);
+        }
+        if (e == cudaSuccess && P.rec_tc(g)) {
+            const TcJob *rj = reinterpret_cast<const TcJob *>(dblob + P.g_rec_off[gi]);
+            e = choose(tune_key("recomb", g.K, g.Upad / FD, P.split, P.g_rec_tiles[gi]), g.K, [&](int nt) {
+                return launch_corr_tc(rj, nj, P.g_rec_tiles[gi], g.d_lam_tc, P.split ? g.d_lam_tc_lo : nullptr, g.K,
+                                      g.Npad_lam, nt, 1, 1, g.Upad / FD, ctx->d_err, s);
+            }, &P.g_rec_nt[gi]);
+        }
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    return e;
 }
 
 // Arena sizes are rounded up to one of four sizes per octave, so that plans of similar size (a server's batches of
@@ -794,6 +887,15 @@ tdpm_status tdpm_build_batch_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_
         }
     }
     cudaError_t e = cudaSuccess;
+    if (!plan->tuned) {
+        if (ctx->autotune) e = autotune_plan(ctx, *plan, *m, A, s);
+        else plan->tuned = true;
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(s);
+            arena_put(ctx, A);
+            return fail(TDPM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        }
+    }
     const bool graphs = ctx->use_graphs && !ctx->prof;
     if (graphs && !A.graph && A.uses >= 1) {
         cudaGraph_t g = nullptr;
@@ -988,6 +1090,24 @@ tdpm_status tdpm_profile_read(tdpm_ctx *ctx, int32_t index, char *name, size_t n
     return TDPM_OK;
 }
 
+tdpm_status tdpm_autotune_read(tdpm_ctx *ctx, int32_t index, char *key, size_t key_cap, int32_t *tile_n,
+                               int32_t *n_entries)
+{
+    clear_error();
+    if (!ctx || !n_entries) return fail(TDPM_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *n_entries = (int32_t)ctx->tune_cache.size();
+    if (index < 0 || index >= *n_entries) return TDPM_OK;
+    auto it = ctx->tune_cache.begin();
+    std::advance(it, index);
+    if (key && key_cap) {
+        std::strncpy(key, it->first.c_str(), key_cap - 1);
+        key[key_cap - 1] = 0;
+    }
+    if (tile_n) *tile_n = it->second;
+    return TDPM_OK;
+}
+
 tdpm_status tdpm_profile_reset(tdpm_ctx *ctx)
 {
     clear_error();
@@ -1073,7 +1193,7 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
     } else {
         // tensor cores: BF16 filter bank(s) and planar BF16 copies of the level; split precision adds the lo parts
         const bool split = precision == TDPM_PREC_BF16X3;
-        const int Npad = corr_tc_pad(K, taps);
+        const int Npad = corr_tc_bank_rows(K), NT = corr_tc_default_nt(K, taps);
         std::vector<uint16_t> fb((size_t)taps * 4 * Npad * 8, 0), fl(fb.size(), 0);
         for (int k = 0; k < K; ++k)
             for (int t = 0; t < taps; ++t)
@@ -1103,7 +1223,7 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
         }
         tj.out = out; tj.H = H; tj.W = W; tj.Ho = Ho; tj.Wo = Wo; tj.begin = 0;
         const long long span = (long long)(Ho - 1) * W + Wo;
-        const int tiles = (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m()) * corr_tc_n_tiles(Npad, taps);
+        const int tiles = (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m());
         e = cudaMemcpyAsync(bank, fb.data(), sizeof(uint16_t) * fb.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && split)
             e = cudaMemcpyAsync(bank_lo, fl.data(), sizeof(uint16_t) * fl.size(), cudaMemcpyHostToDevice, s);
@@ -1112,7 +1232,8 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
         if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
         if (e == cudaSuccess) e = launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(cjd), 1, 4 * cells, s);
         if (e == cudaSuccess)
-            e = launch_corr_tc(reinterpret_cast<const TcJob *>(tjd), 1, tiles, bank, bank_lo, K, Npad, h, w, 1, d_err, s);
+            e = launch_corr_tc(reinterpret_cast<const TcJob *>(tjd), 1, tiles, bank, bank_lo, K, Npad, NT, h, w, 1,
+                               d_err, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(dmem);

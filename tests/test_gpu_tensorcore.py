@@ -256,3 +256,28 @@ def test_concurrent_group_streams_match_serial(torch, T, ctx, form, prec):
     for a, b, c in zip(forked, replayed, serial):
         np.testing.assert_array_equal(a, b)
         np.testing.assert_array_equal(a, c)
+
+
+@pytest.mark.parametrize("form", ["full", "decomposed"])
+def test_autotuned_tiling_matches_default_tiling(torch, T, form, monkeypatch):
+    """The autotuner only changes how the N dimension is tiled; every score is the same sum of the same products, so
+    the maps agree with the untuned tiling to FP32 rounding. Its choices are reported per shape class."""
+    wl = synth.config_c2()
+    f = T.FORM_FULL if form == "full" else T.FORM_DECOMPOSED
+    out = []
+    for tune in ("1", "0"):
+        monkeypatch.setenv("TDPM_AUTOTUNE", tune)
+        c = T.tdpm_create(0)
+        mid = T.tdpm_load_model(c, wl.model)
+        if f == T.FORM_DECOMPOSED:
+            T.tdpm_decompose(c, mid, 8, T.DECOMP_PER_FILTER, max_iters=60, seed=1)
+        sid = T.tdpm_build_pyramid_scores(c, mid, device_pyramid(wl.pyramids[0], torch), f, T.PREC_BF16X3)
+        out.append([T.tdpm_get_maps(c, sid, T.MAP_FINAL_SCORE, comp, j)
+                    for comp in range(len(wl.model.components)) for j in (10, 18, 30)])
+        choices = T.tdpm_autotune_read(c)
+        assert (len(choices) > 0) == (tune == "1")
+        for key, nt in choices.items():
+            assert nt % 16 == 0 and 16 <= nt <= 256, key
+        T.tdpm_destroy(c)
+    for a, b in zip(*out):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-6 * max(1.0, float(np.max(np.abs(b)))))
