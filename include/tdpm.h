@@ -186,6 +186,15 @@ tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdp
 tdpm_status tdpm_build_batch_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
                                     int32_t form, int32_t precision, void *stream, int32_t *scores_id);
 
+/* tdpm_build_batch_scores for a subset of the model's components per image (not in the paper: a bank of class models
+ * loaded as one model, each image scored for the classes it asks for). component_mask: host [n_images][components],
+ * nonzero = score that component on that image; NULL = all. Step 1 (the correlation) still covers every filter of
+ * the model, as one contraction; steps 2-4 run only for the selected components, and their results are those the
+ * full batch gives. */
+tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs,
+                                           int32_t n_images, const uint8_t *component_mask, int32_t form,
+                                           int32_t precision, void *stream, int32_t *scores_id);
+
 /* Step 4: every scored position with s >= tau, ordered by (image, component, level, y, x), copied to the host array
  * `out` (capacity records). Blocks until `stream` has finished. *n_out = number of detections, even when it exceeds
  * capacity (then ERR_CAPACITY and the first `capacity` records are written). */
@@ -304,6 +313,8 @@ typedef struct {
     int32_t n_models;
     int32_t form, precision;     /* as for tdpm_build_pyramid_scores */
     float tau;                   /* detection threshold (Algorithm 1, step 16) */
+    const int32_t *components;   /* optional: only these components of each listed model (distinct ids); NULL = all */
+    int32_t n_components;
 } tdpm_request;
 
 typedef struct {

@@ -161,7 +161,7 @@ void arena_free(tdpm_ctx *ctx, Arena &a);
 void drop_plans_of_model(tdpm_ctx *ctx, int model_id);
 // Device bytes of the arena a batch needs (makes, or finds, and caches its plan).
 tdpm_status batch_arena_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
-                              int32_t form, int32_t precision, size_t *bytes);
+                              const uint8_t *mask, int32_t form, int32_t precision, size_t *bytes);
 // Stop the server thread (finishing its requests) and free it; the caller must not hold ctx->mu.
 void server_free(tdpm_ctx *ctx);
 

@@ -109,7 +109,9 @@ struct Plan {
 
 namespace {
 
-std::string plan_key(int model_id, const Model &m, int form, int prec, const tdpm_pyramid *pyrs, int n)
+// mask: null (every component of every image) or [n][components], nonzero = score that component on that image
+std::string plan_key(int model_id, const Model &m, int form, int prec, const tdpm_pyramid *pyrs, int n,
+                     const uint8_t *mask)
 {
     std::string k = std::to_string(model_id) + ":" + std::to_string(m.version) + ":" + std::to_string(form) + ":" +
                     std::to_string(prec) + ":" + std::to_string(n);
@@ -117,12 +119,16 @@ std::string plan_key(int model_id, const Model &m, int form, int prec, const tdp
         k += "|" + std::to_string(pyrs[i].lambda);
         for (int j = 0; j < pyrs[i].n_levels; ++j)
             k += ":" + std::to_string(pyrs[i].levels[j].H) + "x" + std::to_string(pyrs[i].levels[j].W);
+        if (mask) {
+            k += "/";
+            for (size_t c = 0; c < m.comps.size(); ++c) k += mask[(size_t)i * m.comps.size() + c] ? '1' : '0';
+        }
     }
     return k;
 }
 
 std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid *pyrs, int n_images, int form,
-                                int prec)
+                                int prec, const uint8_t *mask)
 {
     auto P = std::make_shared<Plan>();
     P->uid = g_plan_uid.fetch_add(1);
@@ -175,6 +181,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     }
     for (int im = 0; im < n_images; ++im)
     for (size_t c = 0; c < m.comps.size(); ++c) {
+        if (mask && !mask[(size_t)im * m.comps.size() + c]) continue;  // component not asked for on this image
         const CompH &C = m.comps[c];
         const FilterH &Rf = m.filters[C.root_fid];
         const int base = P->img_base[im], lam = P->img_lam[im], Li = P->img_L[im];
@@ -793,17 +800,17 @@ void drop_plans_of_model(tdpm_ctx *ctx, int model_id)
 // Device bytes of the arena a batch needs, as allocated (its plan is made, or found, and cached). Used by the server's
 // admission and by tdpm_scores_bytes.
 tdpm_status batch_arena_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
-                              int32_t form, int32_t precision, size_t *bytes)
+                              const uint8_t *mask, int32_t form, int32_t precision, size_t *bytes)
 {
     std::lock_guard<std::mutex> lk(ctx->mu);
     Model *m = get_model(ctx, model_id);
     if (!m) return fail(TDPM_ERR_STATE, "unknown model id");
     if (form == TDPM_FORM_DECOMPOSED && !m->decomposed)
         return fail(TDPM_ERR_STATE, "decomposed form requested before tdpm_decompose");
-    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images);
+    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask);
     auto pit = ctx->plans.find(key);
     if (pit == ctx->plans.end()) {
-        auto plan = make_plan(*m, model_id, pyrs, n_images, form, precision);
+        auto plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask);
         if (ctx->plans.size() > 256) ctx->plans.clear();
         pit = ctx->plans.emplace(key, plan).first;
     }
@@ -820,6 +827,14 @@ extern "C" {
 tdpm_status tdpm_build_batch_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs, int32_t n_images,
                                     int32_t form, int32_t precision, void *stream, int32_t *scores_id)
 {
+    return tdpm_build_batch_scores_subset(ctx, model_id, pyrs, n_images, nullptr, form, precision, stream, scores_id);
+}
+
+tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyrs,
+                                           int32_t n_images, const uint8_t *component_mask, int32_t form,
+                                           int32_t precision, void *stream, int32_t *scores_id)
+{
+    const uint8_t *mask = component_mask;
     clear_error();
     if (!ctx || !pyrs || !scores_id) return fail(TDPM_ERR_ARG, "NULL argument");
     if (n_images < 1 || n_images > 4096) return fail(TDPM_ERR_ARG, "n_images must be in [1, 4096]");
@@ -848,13 +863,13 @@ tdpm_status tdpm_build_batch_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_
     if (form == TDPM_FORM_DECOMPOSED && !m->decomposed)
         return fail(TDPM_ERR_STATE, "decomposed form requested before tdpm_decompose");
     cudaStream_t s = (cudaStream_t)stream;
-    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images);
+    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask);
     std::shared_ptr<Plan> plan;
     auto pit = ctx->plans.find(key);
     if (pit != ctx->plans.end()) {
         plan = pit->second;
     } else {
-        plan = make_plan(*m, model_id, pyrs, n_images, form, precision);
+        plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask);
         if (plan->max_W > 800 || plan->max_H > 800)
             return fail(TDPM_ERR_ARG, "part score maps wider or taller than 800 cells are not supported");
         if (ctx->plans.size() > 256) ctx->plans.clear();
@@ -948,7 +963,7 @@ tdpm_status tdpm_scores_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyrami
             if (py.levels[j].H <= 0 || py.levels[j].W <= 0 || py.levels[j].H > 4096 || py.levels[j].W > 4096)
                 return fail(TDPM_ERR_ARG, "level with a bad size");
     }
-    return batch_arena_bytes(ctx, model_id, pyrs, n_images, form, precision, bytes);
+    return batch_arena_bytes(ctx, model_id, pyrs, n_images, nullptr, form, precision, bytes);
 }
 
 tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyr, int32_t form,

@@ -3,7 +3,7 @@
 // One server thread per context. Submitted requests are split into parts, one per (request, model); parts wait in a
 // FIFO queue. The thread repeatedly
 //   * forms a batch from the oldest part and every queued part with the same (model, form, precision), up to
-//     max_batch_images images;
+//     max_batch_images images (requests that ask for a subset of the model's components get a per-image mask);
 //   * admits it by device memory: the batch's arena size is known from its plan before anything is launched, and the
 //     batches in flight together stay within the budget (the oldest in-flight batch is finished first to make room;
 //     a batch that cannot fit even alone is halved, and a single image that cannot fit fails with ERR_OOM);
@@ -47,6 +47,7 @@ struct Request {
     std::vector<tdpm_level> levels;  // copy of the caller's level descriptors (device data stays the caller's)
     tdpm_pyramid pyr{};
     std::vector<int32_t> models;
+    std::vector<int32_t> components;  // empty: all
     int32_t form = 0, precision = 0;
     float tau = 0.f;
     uint64_t t_submit = 0, t_start = 0, t_done = 0;
@@ -186,8 +187,33 @@ void server_loop(tdpm_ctx *ctx, Server *S)
         b.precision = take.front().req->precision;
         std::vector<tdpm_pyramid> pyrs;
         for (const Part &p : take) pyrs.push_back(p.req->pyr);
-        tdpm_status st = batch_arena_bytes(ctx, b.model, pyrs.data(), (int32_t)pyrs.size(), b.form, b.precision,
-                                           &b.bytes);
+        // component mask of the batch ([image][component]); none when every image wants every component
+        std::vector<uint8_t> mask;
+        tdpm_status st = TDPM_OK;
+        bool subset = false;
+        for (const Part &p : take) subset |= !p.req->components.empty();
+        if (subset) {
+            size_t nc = 0;
+            {
+                std::lock_guard<std::mutex> lk(ctx->mu);
+                const Model *m = get_model(ctx, b.model);
+                nc = m ? m->comps.size() : 0;
+            }
+            mask.assign(take.size() * nc, 1);
+            for (size_t i = 0; i < take.size() && nc; ++i) {
+                const auto &cs = take[i].req->components;
+                if (cs.empty()) continue;
+                std::fill(mask.begin() + i * nc, mask.begin() + (i + 1) * nc, 0);
+                for (int32_t c : cs) {
+                    if (c < 0 || (size_t)c >= nc) st = TDPM_ERR_ARG;
+                    else mask[i * nc + c] = 1;
+                }
+            }
+            if (!nc) st = TDPM_ERR_STATE;
+        }
+        if (st == TDPM_OK)
+            st = batch_arena_bytes(ctx, b.model, pyrs.data(), (int32_t)pyrs.size(), subset ? mask.data() : nullptr,
+                                   b.form, b.precision, &b.bytes);
         if (st == TDPM_OK && budget && b.bytes > budget) {
             if (take.size() > 1) {
                 // too large even alone: run the first half now, put the second half back at the head of the queue
@@ -218,8 +244,9 @@ void server_loop(tdpm_ctx *ctx, Server *S)
             for (const Part &p : b.parts)
                 if (!p.req->t_start) p.req->t_start = t;
         }
-        st = tdpm_build_batch_scores(ctx, b.model, pyrs.data(), (int32_t)pyrs.size(), b.form, b.precision, b.stream,
-                                     &b.scores_id);
+        st = tdpm_build_batch_scores_subset(ctx, b.model, pyrs.data(), (int32_t)pyrs.size(),
+                                            subset ? mask.data() : nullptr, b.form, b.precision, b.stream,
+                                            &b.scores_id);
         if (st != TDPM_OK) {
             complete_parts(S, b, st, nullptr);
             continue;
@@ -314,11 +341,19 @@ tdpm_status tdpm_submit(tdpm_ctx *ctx, const tdpm_request *req, uint64_t *ticket
     for (int i = 0; i < req->n_models; ++i)
         for (int k = 0; k < i; ++k)
             if (req->model_ids[i] == req->model_ids[k]) return fail(TDPM_ERR_ARG, "model listed twice");
+    if (req->n_components < 0 || (req->n_components > 0 && !req->components))
+        return fail(TDPM_ERR_ARG, "bad component list");
+    for (int i = 0; i < req->n_components; ++i) {
+        if (req->components[i] < 0) return fail(TDPM_ERR_ARG, "negative component id");
+        for (int k = 0; k < i; ++k)
+            if (req->components[i] == req->components[k]) return fail(TDPM_ERR_ARG, "component listed twice");
+    }
     auto r = std::make_unique<Request>();
     r->levels.assign(py.levels, py.levels + py.n_levels);
     r->pyr = py;
     r->pyr.levels = r->levels.data();
     r->models.assign(req->model_ids, req->model_ids + req->n_models);
+    if (req->n_components > 0) r->components.assign(req->components, req->components + req->n_components);
     r->form = req->form;
     r->precision = req->precision;
     r->tau = req->tau;

@@ -65,7 +65,8 @@ class Detection(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("pyramid", ctypes.POINTER(PyramidDesc)), ("model_ids", ctypes.POINTER(_c_i32)), ("n_models", _c_i32),
-                ("form", _c_i32), ("precision", _c_i32), ("tau", ctypes.c_float)]
+                ("form", _c_i32), ("precision", _c_i32), ("tau", ctypes.c_float),
+                ("components", ctypes.POINTER(_c_i32)), ("n_components", _c_i32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -108,6 +109,8 @@ SIGNATURES = {
     "tdpm_detect": (_c_i32, [_VP, _c_i32, ctypes.c_float, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _VP]),
     "tdpm_build_batch_scores": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _c_i32, _c_i32, _VP,
                                          ctypes.POINTER(_c_i32)]),
+    "tdpm_build_batch_scores_subset": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _VP, _c_i32, _c_i32,
+                                                _VP, ctypes.POINTER(_c_i32)]),
     "tdpm_scores_bytes": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _c_i32, _c_i32,
                                    ctypes.POINTER(ctypes.c_size_t)]),
     "tdpm_server_start": (_c_i32, [_VP, ctypes.POINTER(ServerConfig)]),
@@ -311,6 +314,18 @@ def tdpm_detect(ctx: int, scores_id: int, tau: float, capacity: int = 1 << 20, s
     return out[: n.value]
 
 
+def tdpm_build_batch_scores_subset(ctx: int, model_id: int, pyramids: Sequence[DevicePyramid],
+                                   component_mask: np.ndarray, form: int = FORM_FULL, precision: int = PREC_FP32,
+                                   stream=None) -> int:
+    """tdpm_build_batch_scores for the components marked in component_mask ([images][components], nonzero = yes)."""
+    arr = (PyramidDesc * len(pyramids))(*[p.desc for p in pyramids])
+    mask = np.ascontiguousarray(component_mask, dtype=np.uint8)
+    sid = _c_i32()
+    _check(lib().tdpm_build_batch_scores_subset(ctx, model_id, arr, len(pyramids), mask.ctypes.data, int(form),
+                                                int(precision), _stream_ptr(stream), ctypes.byref(sid)))
+    return sid.value
+
+
 def tdpm_scores_bytes(ctx: int, model_id: int, pyramids: Sequence[DevicePyramid], form: int = FORM_FULL,
                       precision: int = PREC_FP32) -> int:
     """Device bytes a batch of these pyramids would hold (nothing is launched)."""
@@ -335,11 +350,13 @@ def tdpm_server_stop(ctx: int) -> None:
 
 
 def tdpm_submit(ctx: int, pyramid: DevicePyramid, model_ids: Sequence[int], form: int = FORM_FULL,
-                precision: int = PREC_FP32, tau: float = 0.0) -> int:
-    """Queue one request (an image pyramid on the device, scored with every model in model_ids); returns its ticket.
-    The pyramid's tensors are kept alive here until the result is polled."""
+                precision: int = PREC_FP32, tau: float = 0.0, components: Optional[Sequence[int]] = None) -> int:
+    """Queue one request (an image pyramid on the device, scored with every model in model_ids, optionally only for
+    some of their components); returns its ticket. The pyramid's tensors are kept alive here until it is polled."""
     ids = (_c_i32 * len(model_ids))(*[int(m) for m in model_ids])
-    req = Request(ctypes.pointer(pyramid.desc), ids, len(model_ids), int(form), int(precision), float(tau))
+    comps = (_c_i32 * len(components))(*[int(c) for c in components]) if components else None
+    req = Request(ctypes.pointer(pyramid.desc), ids, len(model_ids), int(form), int(precision), float(tau),
+                  comps, len(components) if components else 0)
     t = ctypes.c_uint64()
     _check(lib().tdpm_submit(ctx, ctypes.byref(req), ctypes.byref(t)))
     _inflight_requests[(ctx, t.value)] = pyramid

@@ -122,3 +122,37 @@ def test_batch_rejects_bad_image_index(torch, T, ctx):
     with pytest.raises(T.TdpmError):
         T.tdpm_build_batch_scores(ctx, mid, [], T.FORM_FULL, T.PREC_FP32)
     T.tdpm_release(ctx, sid)
+
+
+def test_component_subsets_equal_full_batch_filtered(torch, T, ctx):
+    """A batch scored for a subset of components per image gives, for those components, exactly the maps and
+    detections of the full batch; the others are not computed."""
+    wl = synth.config_c2()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    pyrs = _batch_images(seed=9)[:4]
+    dps = [device_pyramid(py, torch) for py in pyrs]
+    nc = len(wl.model.components)
+    mask = np.zeros((len(pyrs), nc), dtype=np.uint8)
+    mask[0, [0, 3]] = 1
+    mask[1, :] = 1
+    mask[2, [5]] = 1
+    mask[3, [1, 2, 4]] = 1
+    full = T.tdpm_build_batch_scores(ctx, mid, dps, T.FORM_FULL, T.PREC_BF16X3)
+    sub = T.tdpm_build_batch_scores_subset(ctx, mid, dps, mask, T.FORM_FULL, T.PREC_BF16X3)
+    tau = float(np.percentile(T.tdpm_detect(ctx, full, -np.inf)["score"], 95))
+    df, ds = T.tdpm_detect(ctx, full, tau), T.tdpm_detect(ctx, sub, tau)
+    keep = mask[df["image"], df["component"]].astype(bool)
+    assert keep.sum() == len(ds) > 0
+    for name in ("image", "component", "level", "y", "x", "score", "part_y", "part_x"):
+        np.testing.assert_array_equal(df[keep][name], ds[name])
+    for i, py in enumerate(pyrs):
+        for c in range(nc):
+            for j in range(py.lam, len(py.levels)):
+                a = T.tdpm_get_maps(ctx, full, T.MAP_FINAL_SCORE, c, j, image=i)
+                b = T.tdpm_get_maps(ctx, sub, T.MAP_FINAL_SCORE, c, j, image=i)
+                if mask[i, c]:
+                    np.testing.assert_array_equal(a, b)
+                else:
+                    assert b.size == 0
+    T.tdpm_release(ctx, full)
+    T.tdpm_release(ctx, sub)

@@ -160,3 +160,46 @@ def test_poll_timeout_then_result(T, setup):
     d, info = T.tdpm_poll(ctx, t, timeout_ms=20000)
     assert info["status"] == T.OK
     T.tdpm_server_stop(ctx)
+
+
+def test_class_subsets_of_a_bank(T, torch):
+    """Several classes loaded as one bank model; each request asks for some classes (component subsets). Alone, in
+    the mix and scored directly with the full bank (then filtered), the detections are the same."""
+    ctx = T.tdpm_create(0)
+    comps = []
+    for c in range(4):
+        comps += synth.make_dpm_class(np.random.default_rng(200 + c))
+    bank = T.tdpm_load_model(ctx, synth.Model(comps))
+    rng = np.random.default_rng(11)
+    pyrs = [device_pyramid(synth.make_pyramid(rng, synth.pyramid_sizes(h, w), synth.LAMBDA), torch)
+            for (h, w) in [(120, 160), (180, 240), (150, 150)]]
+    classes = [[0], [1, 3], [2], [0, 1, 2, 3], [3]]
+    reqs = []
+    for i, cl in enumerate(classes):
+        img = i % len(pyrs)
+        sid = T.tdpm_build_pyramid_scores(ctx, bank, pyrs[img], T.FORM_FULL, T.PREC_BF16X3)
+        allp = T.tdpm_detect(ctx, sid, -np.inf)
+        T.tdpm_release(ctx, sid)
+        cs = [6 * c + k for c in cl for k in range(6)]
+        tau = float(np.percentile(allp[np.isin(allp["component"], cs)]["score"], 96))
+        ref = allp[np.isin(allp["component"], cs) & (allp["score"] >= tau)]
+        reqs.append({"image": img, "components": cs, "tau": tau, "ref": ref})
+    T.tdpm_server_start(ctx, max_batch_images=8, max_inflight=2, max_wait_us=0)
+    alone = []
+    for r in reqs:
+        t = T.tdpm_submit(ctx, pyrs[r["image"]], [bank], T.FORM_FULL, T.PREC_BF16X3, r["tau"], r["components"])
+        alone.append(T.tdpm_poll(ctx, t)[0])
+    tickets = [T.tdpm_submit(ctx, pyrs[r["image"]], [bank], T.FORM_FULL, T.PREC_BF16X3, r["tau"], r["components"])
+               for r in reqs]
+    mixed = [T.tdpm_poll(ctx, t) for t in tickets]
+    bad = T.tdpm_submit(ctx, pyrs[0], [bank], T.FORM_FULL, T.PREC_BF16X3, 0.0, [999])  # no such component
+    with pytest.raises(T.TdpmError) as e:
+        T.tdpm_poll(ctx, bad)
+    assert e.value.status == T.ERR_ARG
+    T.tdpm_server_stop(ctx)
+    assert max(info["batch_images"] for _, info in mixed) > 1
+    for r, a, (m, info) in zip(reqs, alone, mixed):
+        assert len(r["ref"]) > 0
+        _same(a, r["ref"])
+        _same(m, r["ref"])
+    T.tdpm_destroy(ctx)
