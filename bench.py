@@ -10,6 +10,11 @@ detections to the host.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form decomposed|full] [--precision bf16x3|bf16|fp32]
                   [--rank R] [--mode per_filter|joint]
   python bench.py --impl reference    # the FP64 CPU oracle on the same workload and metric
+  python bench.py --workload c3|c4|c5 # the larger configurations (one JSON line each, same keys):
+      c3  a 20-class bank (120 components, 1080 filters) on one 1280x720 image (45 levels)
+      c4  the same bank on a batch of 64 images, W ~ U{320..1280}, H ~ U{240..720}, one batch call per step
+      c5  serving: Poisson arrivals (200 requests/s), sizes 640x480 / 1280x720 / 1920x1080, each request asking
+          for 1..20 classes of the bank; p50/p99 latency from submission to results
 
 Reported beside the headline: the full form in FP32 (the GPU baseline the decomposed form must beat) and in the same
 precision, detection agreement with the FP64 oracle on the same factors (parity), and a rank sweep of the detection
@@ -49,14 +54,24 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tdpm", choices=["tdpm", "reference"])
-    ap.add_argument("--form", default="decomposed", choices=["decomposed", "full"])
-    ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
-    ap.add_argument("--rank", type=int, default=8, help="CP rank per filter (per_filter) or per shape group (joint)")
-    ap.add_argument("--mode", default="per_filter", choices=["per_filter", "joint"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
+    ap.add_argument("--form", default=None, choices=["decomposed", "full"])
+    ap.add_argument("--precision", default=None, choices=sorted(PRECISIONS))
+    ap.add_argument("--rank", type=int, default=None, help="CP rank per filter (per_filter) or per shape group (joint)")
+    ap.add_argument("--mode", default=None, choices=["per_filter", "joint"])
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="c5: length of the arrival stream")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="c5: mean arrival rate (requests/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the full-form comparison runs")
     ap.add_argument("--no-sweep", action="store_true", help="skip the rank sweep")
-    return ap.parse_args()
+    args = ap.parse_args()
+    # per-workload defaults: the per-filter decomposition on the one-class model; the joint one on the class banks
+    dflt = {"c2": ("decomposed", "bf16x3", 8, "per_filter"), "c3": ("decomposed", "bf16", 32, "joint"),
+            "c4": ("decomposed", "bf16", 8, "joint"), "c5": ("decomposed", "bf16", 8, "joint")}[args.workload]
+    for k, v in zip(("form", "precision", "rank", "mode"), dflt):
+        if getattr(args, k) is None:
+            setattr(args, k, v)
+    return args
 
 
 def load_tau():
@@ -236,14 +251,15 @@ def run_reference(args):
         return
     from oracle import oracle as orc
 
-    wl = synth.config_c2()
+    wl = {"c2": synth.config_c2, "c3": synth.config_c3, "c4": synth.config_c3, "c5": synth.config_c3}[args.workload]()
     pyr = wl.pyramids[0]
     n_comp = len(wl.model.components)
+    tau = load_tau()
 
     def one_step(i):
-        # one component of the model over the whole pyramid: 1/6 of an image
+        # one component of the model over the whole pyramid: 1/n_comp of an image
         sub = synth.Model([wl.model.components[i % n_comp]])
-        orc.detect(orc.score_pyramid(sub, pyr), load_tau())
+        orc.detect(orc.score_pyramid(sub, pyr), tau)
 
     for i in range(args.warmup):
         one_step(i)
@@ -255,11 +271,11 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "images/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "form": "full (FP64 oracle)", "image": "500x375", "levels": len(pyr.levels),
+            "config": {"workload": wl.name, "form": "full (FP64 oracle)", "levels": len(pyr.levels),
                        "components": n_comp, "filters": len(wl.model.filters())},
             "cpu_baseline": {"value": v, "unit": "images/s", "cores": orc.num_threads(), "kind": "oracle",
-                             "sample": "each step scores one of the 6 components over the whole 36-level pyramid "
-                                       "(1/6 of an image)"},
+                             "sample": f"each step scores one of the {n_comp} components over the whole "
+                                       f"{len(pyr.levels)}-level pyramid (1/{n_comp} of an image)"},
             "e2e": {"value": v, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -300,11 +316,252 @@ def factor_filters(tdpm, ctx, mid):
     return out
 
 
+# ------------------------------------------------------------------------------------------------ class banks (c3, c4)
+def _timed_steps(torch, step, steps, warmup, flush, stream):
+    """Device time of each step (CUDA events on the launching stream), L2 flushed between steps outside the events."""
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    out = None
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        out = step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    return {"ms_sum": sum(ms), "p50": ms[len(ms) // 2], "p99": ms[min(len(ms) - 1, int(math.ceil(0.99 * len(ms))) - 1)],
+            "last": out}
+
+
+def _class_taus(dets, n_comp, comps_per_class=6, q=99.0):
+    """Per-class threshold: the q-th percentile of the class's scores over every scored position (from the full FP32
+    form, which matches the FP64 oracle to 1e-5 of the largest score)."""
+    taus = np.full(n_comp, np.inf, dtype=np.float64)
+    cls = dets["component"] // comps_per_class
+    for c in range(n_comp // comps_per_class):
+        sc = dets["score"][cls == c]
+        if len(sc):
+            taus[c * comps_per_class:(c + 1) * comps_per_class] = np.percentile(sc, q)
+    return taus
+
+
+def run_bank(args):
+    """c3 / c4: the 20-class bank on one 1280x720 image or on a batch of 64 images. Every variant is timed (one batch
+    call + detection readback per step); agreement of each with the full FP32 form under per-class thresholds; error
+    of sampled filter maps against the FP64 oracle."""
+    import torch
+    from paper_1707_03268_gb300 import tdpm
+    from oracle import oracle as orc
+
+    torch.cuda.set_device(0)
+    wl = synth.config_c3() if args.workload == "c3" else synth.config_c4()
+    n_comp = len(wl.model.components)
+    ctx = tdpm.tdpm_create(0)
+    mid = tdpm.tdpm_load_model(ctx, wl.model)
+    dps = [tdpm.DevicePyramid([torch.from_numpy(l).cuda() for l in p.levels], p.lam) for p in wl.pyramids]
+    cells = sum(l.shape[0] * l.shape[1] for p in wl.pyramids for l in p.levels)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    cap = 1 << 24
+    det_buf = np.zeros(cap, dtype=tdpm.DETECTION_DTYPE)
+    steps = max(3, min(args.steps, 20 if args.workload == "c3" else 5))
+    warmup = max(3, min(args.warmup, 3))
+
+    def detections(form, prec, taus):
+        sid = tdpm.tdpm_build_batch_scores(ctx, mid, dps, form, prec, stream)
+        d = tdpm.tdpm_detect_thresholds(ctx, sid, np.broadcast_to(taus, (len(dps), n_comp)), capacity=cap,
+                                        stream=stream, out=det_buf)
+        tdpm.tdpm_release(ctx, sid)
+        return d
+
+    def keys(d):
+        return set(zip(d["image"].tolist(), d["component"].tolist(), d["level"].tolist(), d["y"].tolist(),
+                       d["x"].tolist()))
+
+    # thresholds from the full FP32 form
+    sid = tdpm.tdpm_build_batch_scores(ctx, mid, dps[:1], tdpm.FORM_FULL, tdpm.PREC_FP32, stream)
+    allp = tdpm.tdpm_detect(ctx, sid, -np.inf, capacity=cap, stream=stream, out=det_buf).copy()
+    tdpm.tdpm_release(ctx, sid)
+    taus = _class_taus(allp, n_comp)
+    del allp
+
+    variants = [("full", "fp32", None, None), ("full", "bf16", None, None), ("full", "bf16x3", None, None)]
+    if args.workload == "c3":
+        variants += [("decomposed", "bf16", r, "joint") for r in (8, 32, 128)]
+        variants += [("decomposed", "bf16x3", 32, "joint"), ("decomposed", "bf16", 8, "per_filter")]
+    else:
+        variants += [("decomposed", "bf16", 8, "joint"), ("decomposed", "bf16x3", 8, "joint")]
+    head = (args.form, args.precision, args.rank if args.form == "decomposed" else None,
+            args.mode if args.form == "decomposed" else None)
+    if head not in variants:
+        variants.append(head)
+    rng = np.random.default_rng(0)
+    filters = wl.model.filters()
+    sample_maps = [(int(rng.integers(0, len(filters))), None) for _ in range(12)]
+    results = {}
+    ref_keys = None
+    for form_s, prec_s, r, mode in variants:
+        form = tdpm.FORM_FULL if form_s == "full" else tdpm.FORM_DECOMPOSED
+        prec = PRECISIONS[prec_s]
+        rep = None
+        if form == tdpm.FORM_DECOMPOSED:
+            t0 = time.perf_counter()
+            rep = tdpm.tdpm_decompose(ctx, mid, r, tdpm.DECOMP_JOINT if mode == "joint" else tdpm.DECOMP_PER_FILTER,
+                                      max_iters=30 if mode == "joint" else 100, seed=1)
+            rep["seconds"] = time.perf_counter() - t0
+        run = _timed_steps(torch, lambda: detections(form, prec, taus), steps, warmup, flush, stream)
+        k = keys(run["last"])
+        # one more step with every stage bracketed by events (shape groups serial on the stream)
+        tdpm.tdpm_profile_reset(ctx)
+        tdpm.tdpm_profile_enable(ctx, True)
+        detections(form, prec, taus)
+        tdpm.tdpm_profile_enable(ctx, False)
+        stages = {n: ms for n, (ms, _) in tdpm.tdpm_profile_read(ctx).items()}
+        if ref_keys is None:
+            ref_keys = k
+        label = f"{form_s}_{prec_s}" + (f"_{mode}_r{r}" if r else "")
+        # error of sampled filter maps (image 0) against the FP64 oracle: the exact filters, and for the decomposed
+        # form also the filters rebuilt from the library's factors (parity of the arithmetic, same factors)
+        sid = tdpm.tdpm_build_batch_scores(ctx, mid, dps[:1], form, prec, stream)
+        rebuilt = factor_filters(tdpm, ctx, mid) if form == tdpm.FORM_DECOMPOSED else None
+        err_exact, err_same = 0.0, 0.0
+        pyr0 = wl.pyramids[0]
+        for fid, _ in sample_maps:
+            f = filters[fid]
+            js = [j for j in range(len(pyr0.levels)) if pyr0.levels[j].shape[0] >= f.shape[0] and
+                  pyr0.levels[j].shape[1] >= f.shape[1]]
+            j = js[len(js) // 3]
+            got = tdpm.tdpm_get_maps(ctx, sid, tdpm.MAP_FILTER_SCORE, fid, j, image=0)
+            if got.size == 0:
+                continue
+            ref = orc.correlate(pyr0.levels[j], f)
+            err_exact = max(err_exact, float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30)))
+            if rebuilt is not None:
+                ref2 = orc.correlate(pyr0.levels[j], rebuilt[fid])
+                err_same = max(err_same, float(np.max(np.abs(got - ref2)) / max(np.max(np.abs(ref2)), 1e-30)))
+        tdpm.tdpm_release(ctx, sid)
+        n_img = len(dps)
+        results[label] = {"images_per_s": steps * n_img / (run["ms_sum"] / 1e3), "p50_ms_per_step": run["p50"],
+                          "p99_ms_per_step": run["p99"], "detections": len(k),
+                          "agreement_with_full_fp32": len(k & ref_keys) / max(1, len(k | ref_keys)),
+                          "max_rel_error_vs_fp64_exact_filters": err_exact,
+                          "max_rel_error_vs_fp64_same_factors": err_same if rebuilt is not None else None,
+                          "stages_ms_per_step": stages, "decomposition_report": rep}
+    hl = f"{head[0]}_{head[1]}" + (f"_{head[3]}_r{head[2]}" if head[2] else "")
+    h = results[hl]
+    line = {"metric": METRIC, "value": h["images_per_s"], "unit": "images/s", "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": None, "p50_ms": h["p50_ms_per_step"], "p99_ms": h["p99_ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision if args.precision != "fp32" else "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "images": len(dps), "cells": cells, "components": n_comp,
+                       "filters": len(filters), "form": head[0], "precision": head[1], "rank": head[2],
+                       "decomposition": head[3], "thresholds": "99th percentile of each class's scores (full FP32)",
+                       "l2": "flushed between timed steps (256 MB write outside the events)"},
+            "variants": results, "autotune": tdpm.tdpm_autotune_read(ctx)}
+    print(json.dumps(line), flush=True)
+    tdpm.tdpm_destroy(ctx)
+
+
+# ------------------------------------------------------------------------------------------------ serving (c5)
+def run_serve(args):
+    """c5: an open-loop Poisson stream of requests into the library's server; each request is one image (one of three
+    sizes, its pyramid already on the device) and a set of classes of the 20-class bank (a component subset of the
+    bank model). Latency = results ready - submission; throughput = requests completed / stream length."""
+    import threading
+    import torch
+    from paper_1707_03268_gb300 import tdpm
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(4)
+    comps = []
+    for _ in range(20):
+        comps.extend(synth.make_dpm_class(rng))
+    ctx = tdpm.tdpm_create(0)
+    bank = tdpm.tdpm_load_model(ctx, synth.Model(comps))
+    form = tdpm.FORM_FULL if args.form == "full" else tdpm.FORM_DECOMPOSED
+    prec = PRECISIONS[args.precision]
+    if form == tdpm.FORM_DECOMPOSED:
+        tdpm.tdpm_decompose(ctx, bank, args.rank, tdpm.DECOMP_JOINT if args.mode == "joint" else tdpm.DECOMP_PER_FILTER,
+                            max_iters=30, seed=1)
+    sizes = ((480, 640), (720, 1280), (1080, 1920))
+    pyrs = {hw: tdpm.DevicePyramid([torch.from_numpy(l).cuda()
+                                    for l in synth.make_pyramid(rng, synth.pyramid_sizes(*hw), synth.LAMBDA).levels],
+                                   synth.LAMBDA) for hw in sizes}
+    n_req = int(args.serve_seconds * args.serve_rate)
+    reqs = synth.serving_requests(seed=4, n=n_req, rate_hz=args.serve_rate, sizes=sizes)
+    n_warm = min(len(reqs) // 6, int(2000 * args.serve_rate / 200.0))
+    # one threshold for every class: the 99th percentile of the bank's scores on the 1280x720 image (full FP32)
+    sid = tdpm.tdpm_build_pyramid_scores(ctx, bank, pyrs[(720, 1280)], tdpm.FORM_FULL, tdpm.PREC_FP32)
+    tau = float(np.percentile(tdpm.tdpm_detect(ctx, sid, -np.inf, capacity=1 << 24)["score"], 99))
+    tdpm.tdpm_release(ctx, sid)
+    tdpm.tdpm_server_start(ctx, max_batch_images=16, max_inflight=3, max_wait_us=500, mem_budget_bytes=96 << 30)
+    # warm the plans and the tuner for each size with one request alone
+    for hw in sizes:
+        t = tdpm.tdpm_submit(ctx, pyrs[hw], [bank], form, prec, tau, list(range(6)))
+        tdpm.tdpm_poll(ctx, t)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            delay = r["t_arrival"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            cs = [6 * c + k for c in r["classes"] for k in range(6)]
+            tickets[i] = tdpm.tdpm_submit(ctx, pyrs[r["img_hw"]], [bank], form, prec, tau, cs)
+
+    th = threading.Thread(target=submitter)
+    clocks = ClockSampler(0)
+    clocks.start()
+    th.start()
+    lat, n_det, done_t = [], 0, []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.0002)
+        d, info = tdpm.tdpm_poll(ctx, tickets[i])
+        n_det += len(d)
+        lat.append((info["t_done_ns"] - info["t_submit_ns"]) / 1e6)
+        done_t.append(time.perf_counter() - t0)
+    th.join()
+    clk = clocks.stop()
+    wall = time.perf_counter() - t0
+    tdpm.tdpm_server_stop(ctx)
+    meas = sorted(lat[n_warm:])
+    span = done_t[-1] - done_t[n_warm - 1] if n_warm > 0 else done_t[-1]
+    thr = (len(reqs) - n_warm) / span
+    line = {"metric": "requests/s and p50/p99 latency under a Poisson stream (continuous batching)",
+            "value": thr, "unit": "images/s", "n_gpus": 1, "steps": len(reqs) - n_warm, "warmup": n_warm,
+            "ms_per_step": None, "p50_ms": meas[len(meas) // 2],
+            "p99_ms": meas[min(len(meas) - 1, int(math.ceil(0.99 * len(meas))) - 1)],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision if args.precision != "fp32" else "f32", "data": "synthetic",
+            "config": {"workload": f"c5_serving_{args.serve_rate:g}rps", "offered_rate": args.serve_rate,
+                       "requests": len(reqs), "warmup_requests_excluded": n_warm, "sizes": [f"{w}x{h}" for h, w in sizes],
+                       "classes_per_request": "U{1..20} distinct of a 20-class bank (component subsets of one model)",
+                       "form": args.form, "precision": args.precision,
+                       "rank": args.rank if form == tdpm.FORM_DECOMPOSED else None,
+                       "decomposition": args.mode if form == tdpm.FORM_DECOMPOSED else None,
+                       "server": {"max_batch_images": 16, "max_inflight": 3, "max_wait_us": 500},
+                       "tau": tau},
+            "latency_ms_mean": float(np.mean(meas)), "detections": n_det, "wall_s": wall, "clocks": clk,
+            "autotune": tdpm.tdpm_autotune_read(ctx)}
+    print(json.dumps(line), flush=True)
+    tdpm.tdpm_destroy(ctx)
+
+
 # ------------------------------------------------------------------------------------------------ main arm
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload in ("c3", "c4"):
+        run_bank(args)
+        return
+    if args.workload == "c5":
+        run_serve(args)
         return
     import torch
     import torch.distributed as dist

@@ -201,6 +201,11 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
 tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detection *out, size_t capacity,
                         size_t *n_out, void *stream);
 
+/* tdpm_detect with one threshold per (image, component): tau is a host array [n_images][components] (a class model's
+ * own threshold, a request's threshold). Same results and errors; ERR_ARG for a NaN threshold. */
+tdpm_status tdpm_detect_thresholds(tdpm_ctx *ctx, int32_t scores_id, const float *tau, tdpm_detection *out,
+                                   size_t capacity, size_t *n_out, void *stream);
+
 /* Map kinds for tdpm_get_maps */
 #define TDPM_MAP_FILTER_SCORE 0 /* index_a = filter id, index_b = level: correlation map [H-h+1][W-w+1] FP32 */
 #define TDPM_MAP_FINAL_SCORE 1  /* index_a = component, index_b = root level: score map [Y][X] FP32 */

@@ -35,14 +35,22 @@ __global__ void __launch_bounds__(AS_THREADS) assemble_kernel(const AsmJob *__re
     J.out[local] = s;
 }
 
+// threshold of job ji: job_tau[ji] when given (one per (image, component) of the scores set), else tau
+__device__ __forceinline__ float job_threshold(const float *job_tau, int ji, float tau)
+{
+    return job_tau ? job_tau[ji] : tau;
+}
+
 __global__ void __launch_bounds__(DET_THREADS) detect_count_kernel(const AsmJob *__restrict__ jobs, int n_jobs,
-                                                                   long long total, float tau, int *counts)
+                                                                   long long total, float tau,
+                                                                   const float *__restrict__ job_tau, int *counts)
 {
     const long long idx = (long long)blockIdx.x * DET_THREADS + threadIdx.x;
     bool hit = false;
     if (idx < total) {
-        const AsmJob &J = jobs[find_pos_job(jobs, n_jobs, idx)];
-        hit = J.out[idx - J.begin] >= tau;
+        const int ji = find_pos_job(jobs, n_jobs, idx);
+        const AsmJob &J = jobs[ji];
+        hit = J.out[idx - J.begin] >= job_threshold(job_tau, ji, tau);
     }
     const int c = __syncthreads_count(hit);
     if (threadIdx.x == 0) counts[blockIdx.x] = c;
@@ -86,6 +94,7 @@ __global__ void __launch_bounds__(1024) detect_scan_kernel(const int *counts, in
 
 __global__ void __launch_bounds__(DET_THREADS) detect_write_kernel(const AsmJob *__restrict__ jobs, int n_jobs,
                                                                    long long total, float tau,
+                                                                   const float *__restrict__ job_tau,
                                                                    const int *__restrict__ offsets,
                                                                    tdpm_detection *__restrict__ out,
                                                                    long long capacity, int model)
@@ -96,7 +105,7 @@ __global__ void __launch_bounds__(DET_THREADS) detect_write_kernel(const AsmJob 
     bool hit = false;
     if (idx < total) {
         ji = find_pos_job(jobs, n_jobs, idx);
-        hit = jobs[ji].out[idx - jobs[ji].begin] >= tau;
+        hit = jobs[ji].out[idx - jobs[ji].begin] >= job_threshold(job_tau, ji, tau);
     }
     const unsigned ballot = __ballot_sync(0xffffffffu, hit);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -139,16 +148,25 @@ cudaError_t launch_assemble(const AsmJob *d_jobs, int n_jobs, long long total, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_detect(const AsmJob *d_jobs, int n_jobs, long long total, float tau, int *d_block_counts,
-                          int *d_block_offsets, int n_blocks, tdpm_detection *d_out, long long capacity,
-                          long long *d_total, int model, cudaStream_t s)
+cudaError_t launch_detect_count(const AsmJob *d_jobs, int n_jobs, long long total, float tau, const float *d_job_tau,
+                                int *d_block_counts, int *d_block_offsets, int n_blocks, long long *d_total,
+                                cudaStream_t s)
 {
     if (total <= 0 || n_blocks <= 0) return cudaMemsetAsync(d_total, 0, sizeof(long long), s);
-    note_launches(3);
-    detect_count_kernel<<<n_blocks, DET_THREADS, 0, s>>>(d_jobs, n_jobs, total, tau, d_block_counts);
+    note_launches(2);
+    detect_count_kernel<<<n_blocks, DET_THREADS, 0, s>>>(d_jobs, n_jobs, total, tau, d_job_tau, d_block_counts);
     detect_scan_kernel<<<1, 1024, 0, s>>>(d_block_counts, d_block_offsets, n_blocks, d_total);
-    detect_write_kernel<<<n_blocks, DET_THREADS, 0, s>>>(d_jobs, n_jobs, total, tau, d_block_offsets, d_out, capacity,
-                                                        model);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_detect_write(const AsmJob *d_jobs, int n_jobs, long long total, float tau, const float *d_job_tau,
+                                const int *d_block_offsets, int n_blocks, tdpm_detection *d_out, long long capacity,
+                                int model, cudaStream_t s)
+{
+    if (total <= 0 || n_blocks <= 0) return cudaSuccess;
+    note_launches(1);
+    detect_write_kernel<<<n_blocks, DET_THREADS, 0, s>>>(d_jobs, n_jobs, total, tau, d_job_tau, d_block_offsets, d_out,
+                                                        capacity, model);
     return cudaGetLastError();
 }
 

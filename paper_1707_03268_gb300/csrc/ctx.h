@@ -106,8 +106,6 @@ struct Scores {
     int model_id = 0;
     std::shared_ptr<Plan> plan;
     Arena arena;
-    tdpm_detection *d_records = nullptr;
-    size_t rec_cap = 0;
     cudaEvent_t done = nullptr;
 };
 
@@ -140,6 +138,12 @@ struct tdpm_ctx {
     cudaEvent_t fork_ev = nullptr;
     std::vector<cudaEvent_t> join_ev;
     tdpm::Server *server = nullptr;      // the serving loop, when started
+    // device buffer the detection records are written to before their copy to the caller: one per context, grown on
+    // demand (tdpm_detect calls are serialised by the context lock and finish before they return)
+    tdpm_detection *d_records = nullptr;
+    size_t rec_cap = 0;
+    float *d_job_tau = nullptr;          // per-job thresholds of the current tdpm_detect_thresholds call
+    size_t tau_cap = 0;
     int *d_err = nullptr;                // raised by bounded device waits
     int *h_err = nullptr;                // pinned mirror
     bool use_graphs = true;

@@ -149,9 +149,14 @@ cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_lines, int y_lines,
 
 // K7: assembly (shift and sum), then detection count / scan / write.
 cudaError_t launch_assemble(const AsmJob *d_jobs, int n_jobs, long long total, cudaStream_t s);
-cudaError_t launch_detect(const AsmJob *d_jobs, int n_jobs, long long total, float tau, int *d_block_counts,
-                          int *d_block_offsets, int n_blocks, tdpm_detection *d_out, long long capacity,
-                          long long *d_total, int model, cudaStream_t s);
+// count per block + exclusive scan (total to *d_total), then the ordered write of the first `capacity` records
+// d_job_tau: null (every job uses tau) or one threshold per assembly job
+cudaError_t launch_detect_count(const AsmJob *d_jobs, int n_jobs, long long total, float tau, const float *d_job_tau,
+                                int *d_block_counts, int *d_block_offsets, int n_blocks, long long *d_total,
+                                cudaStream_t s);
+cudaError_t launch_detect_write(const AsmJob *d_jobs, int n_jobs, long long total, float tau, const float *d_job_tau,
+                                const int *d_block_offsets, int n_blocks, tdpm_detection *d_out, long long capacity,
+                                int model, cudaStream_t s);
 int detect_positions_per_block();
 
 }  // namespace tdpm

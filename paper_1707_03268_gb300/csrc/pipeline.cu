@@ -708,6 +708,13 @@ tdpm_status arena_get(tdpm_ctx *ctx, const Plan &P, Arena &out)
                                       std::to_string(ctx->budget) + ", in use " + std::to_string(ctx->used));
     Arena a;
     cudaError_t e = cudaMalloc(&a.dev, alloc);
+    while (e == cudaErrorMemoryAllocation && !ctx->free_arenas.empty()) {
+        // device memory exhausted: give back the cached arenas, oldest first, and try again
+        cudaGetLastError();
+        arena_free(ctx, ctx->free_arenas.front());
+        ctx->free_arenas.erase(ctx->free_arenas.begin());
+        e = cudaMalloc(&a.dev, alloc);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(TDPM_ERR_OOM, std::string("cudaMalloc arena: ") + cudaGetErrorString(e));
@@ -772,11 +779,6 @@ void free_scores(tdpm_ctx *ctx, Scores &s)
         cudaEventDestroy(s.done);
         s.done = nullptr;
     }
-    if (s.d_records) {
-        cudaFree(s.d_records);
-        ctx->used -= std::min(ctx->used, s.rec_cap * sizeof(tdpm_detection));
-        s.d_records = nullptr;
-    }
     arena_put(ctx, s.arena);
 }
 
@@ -815,6 +817,81 @@ tdpm_status batch_arena_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyrami
         pit = ctx->plans.emplace(key, plan).first;
     }
     *bytes = arena_bucket(pit->second->arena_bytes);  // what arena_get allocates for it
+    return TDPM_OK;
+}
+
+// Step 4 for tdpm_detect (one threshold) and tdpm_detect_thresholds (tau_table: host [images][components]).
+tdpm_status detect_impl(tdpm_ctx *ctx, int32_t scores_id, float tau, const float *tau_table, tdpm_detection *out,
+                        size_t capacity, size_t *n_out, void *stream)
+{
+    if (!ctx || !n_out || (capacity > 0 && !out)) return fail(TDPM_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    tdpm_status st = set_device(ctx);
+    if (st) return st;
+    Scores *sc = get_scores(ctx, scores_id);
+    if (!sc) return fail(TDPM_ERR_STATE, "unknown scores id");
+    const Plan &P = *sc->plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *base = sc->arena.dev;
+    const AsmJob *jobs = reinterpret_cast<const AsmJob *>(base + P.blob_off + P.asm_off);
+    int *counts = reinterpret_cast<int *>(base + P.counts_off), *offsets = reinterpret_cast<int *>(base + P.offsets_off);
+    long long *d_total = reinterpret_cast<long long *>(base + P.total_off);
+    CUDA_TRY(cudaStreamWaitEvent(s, sc->done, 0));
+    const float *d_job_tau = nullptr;
+    if (tau_table) {
+        // one threshold per assembly job, from the (image, component) table
+        const Model *m = get_model(ctx, sc->model_id);
+        if (!m) return fail(TDPM_ERR_STATE, "the scores' model was unloaded");
+        const size_t nc = m->comps.size();
+        std::vector<float> jt(std::max<size_t>(1, P.asms.size()));
+        for (size_t k = 0; k < P.asms.size(); ++k) {
+            jt[k] = tau_table[(size_t)P.asms[k].image * nc + P.asms[k].c];
+            if (std::isnan(jt[k])) return fail(TDPM_ERR_ARG, "a threshold is NaN");
+        }
+        if (jt.size() > ctx->tau_cap) {
+            if (ctx->d_job_tau) cudaFree(ctx->d_job_tau);
+            ctx->d_job_tau = nullptr;
+            ctx->tau_cap = 0;
+            CUDA_TRY(cudaMalloc(&ctx->d_job_tau, sizeof(float) * jt.size() * 2));
+            ctx->tau_cap = jt.size() * 2;
+        }
+        CUDA_TRY(cudaMemcpyAsync(ctx->d_job_tau, jt.data(), sizeof(float) * jt.size(), cudaMemcpyHostToDevice, s));
+        d_job_tau = ctx->d_job_tau;
+    }
+    // count and scan, read the count back, then write only the records that will be copied
+    Prof pr(ctx, s, "detect");
+    CUDA_TRY(launch_detect_count(jobs, (int)P.asms.size(), P.total, tau, d_job_tau, counts, offsets, P.n_det_blocks,
+                                 d_total, s));
+    long long total = 0;
+    CUDA_TRY(cudaMemcpyAsync(&total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if ((st = check_device_flag(ctx))) return st;
+    const size_t n = std::min<size_t>((size_t)total, capacity);
+    if (n > ctx->rec_cap) {
+        const size_t cap = std::max(n, ctx->rec_cap * 2);
+        if (ctx->d_records) {
+            cudaFree(ctx->d_records);
+            ctx->used -= std::min(ctx->used, ctx->rec_cap * sizeof(tdpm_detection));
+            ctx->d_records = nullptr;
+            ctx->rec_cap = 0;
+        }
+        if (ctx->budget && ctx->used + cap * sizeof(tdpm_detection) > ctx->budget)
+            return fail(TDPM_ERR_OOM, "detection buffer exceeds the memory budget");
+        CUDA_TRY(cudaMalloc(&ctx->d_records, cap * sizeof(tdpm_detection)));
+        ctx->rec_cap = cap;
+        ctx->used += cap * sizeof(tdpm_detection);
+    }
+    if (n) {
+        CUDA_TRY(launch_detect_write(jobs, (int)P.asms.size(), P.total, tau, d_job_tau, offsets, P.n_det_blocks,
+                                     ctx->d_records, (long long)n, sc->model_id, s));
+        CUDA_TRY(cudaMemcpyAsync(out, ctx->d_records, n * sizeof(tdpm_detection), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    pr.end();
+    CUDA_TRY(cudaEventRecord(sc->done, s));
+    *n_out = (size_t)total;
+    if ((size_t)total > capacity)
+        return fail(TDPM_ERR_CAPACITY, "detections exceed capacity: " + std::to_string(total));
     return TDPM_OK;
 }
 
@@ -976,48 +1053,16 @@ tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detect
                         size_t *n_out, void *stream)
 {
     clear_error();
-    if (!ctx || !n_out || (capacity > 0 && !out)) return fail(TDPM_ERR_ARG, "NULL argument");
     if (std::isnan(tau)) return fail(TDPM_ERR_ARG, "tau is NaN");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    tdpm_status st = set_device(ctx);
-    if (st) return st;
-    Scores *sc = get_scores(ctx, scores_id);
-    if (!sc) return fail(TDPM_ERR_STATE, "unknown scores id");
-    const Plan &P = *sc->plan;
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t want = std::min<size_t>(capacity, (size_t)P.total);
-    if (want > sc->rec_cap) {
-        if (sc->d_records) {
-            cudaFree(sc->d_records);
-            ctx->used -= std::min(ctx->used, sc->rec_cap * sizeof(tdpm_detection));
-            sc->d_records = nullptr;
-            sc->rec_cap = 0;
-        }
-        if (ctx->budget && ctx->used + want * sizeof(tdpm_detection) > ctx->budget)
-            return fail(TDPM_ERR_OOM, "detection buffer exceeds the memory budget");
-        CUDA_TRY(cudaMalloc(&sc->d_records, want * sizeof(tdpm_detection)));
-        sc->rec_cap = want;
-        ctx->used += want * sizeof(tdpm_detection);
-    }
-    char *base = sc->arena.dev;
-    CUDA_TRY(cudaStreamWaitEvent(s, sc->done, 0));
-    Prof pr(ctx, s, "detect");
-    CUDA_TRY(launch_detect(reinterpret_cast<const AsmJob *>(base + P.blob_off + P.asm_off), (int)P.asms.size(), P.total,
-                           tau, reinterpret_cast<int *>(base + P.counts_off), reinterpret_cast<int *>(base + P.offsets_off),
-                           P.n_det_blocks, sc->d_records, (long long)want,
-                           reinterpret_cast<long long *>(base + P.total_off), sc->model_id, s));
-    pr.end();
-    long long total = 0;
-    CUDA_TRY(cudaMemcpyAsync(&total, base + P.total_off, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if ((st = check_device_flag(ctx))) return st;
-    const size_t n = std::min<size_t>((size_t)total, want);
-    if (n) CUDA_TRY(cudaMemcpy(out, sc->d_records, n * sizeof(tdpm_detection), cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaEventRecord(sc->done, s));
-    *n_out = (size_t)total;
-    if ((size_t)total > capacity)
-        return fail(TDPM_ERR_CAPACITY, "detections exceed capacity: " + std::to_string(total));
-    return TDPM_OK;
+    return detect_impl(ctx, scores_id, tau, nullptr, out, capacity, n_out, stream);
+}
+
+tdpm_status tdpm_detect_thresholds(tdpm_ctx *ctx, int32_t scores_id, const float *tau, tdpm_detection *out,
+                                   size_t capacity, size_t *n_out, void *stream)
+{
+    clear_error();
+    if (!tau) return fail(TDPM_ERR_ARG, "NULL thresholds");
+    return detect_impl(ctx, scores_id, 0.f, tau, out, capacity, n_out, stream);
 }
 
 tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_t image, int32_t index_a,

@@ -65,6 +65,7 @@ struct Part {
 
 struct Batch {
     int32_t model = 0, form = 0, precision = 0;
+    size_t n_comps = 0;  // components of the model
     std::vector<Part> parts;
     int32_t scores_id = 0;
     cudaStream_t stream = nullptr;
@@ -104,17 +105,18 @@ void complete_parts(Server *S, const Batch &b, int32_t status, std::vector<std::
     S->cv_done.notify_all();
 }
 
-// Read back a batch's detections and hand them to its requests.
+// Read back a batch's detections (each image with its own request's threshold) and hand them to its requests.
 void finish(tdpm_ctx *ctx, Server *S, Batch &b)
 {
-    float tau = b.parts.front().req->tau;
-    for (const Part &p : b.parts) tau = std::min(tau, p.req->tau);
+    std::vector<float> taus(b.parts.size() * b.n_comps);
+    for (size_t i = 0; i < b.parts.size(); ++i)
+        std::fill(taus.begin() + i * b.n_comps, taus.begin() + (i + 1) * b.n_comps, b.parts[i].req->tau);
     std::vector<tdpm_detection> buf(4096);
     size_t n = 0;
-    tdpm_status st = tdpm_detect(ctx, b.scores_id, tau, buf.data(), buf.size(), &n, b.stream);
+    tdpm_status st = tdpm_detect_thresholds(ctx, b.scores_id, taus.data(), buf.data(), buf.size(), &n, b.stream);
     if (st == TDPM_ERR_CAPACITY) {
         buf.resize(n);
-        st = tdpm_detect(ctx, b.scores_id, tau, buf.data(), buf.size(), &n, b.stream);
+        st = tdpm_detect_thresholds(ctx, b.scores_id, taus.data(), buf.data(), buf.size(), &n, b.stream);
     }
     tdpm_release(ctx, b.scores_id);
     if (st != TDPM_OK) {
@@ -125,8 +127,6 @@ void finish(tdpm_ctx *ctx, Server *S, Batch &b)
     for (size_t i = 0; i < n; ++i) {
         const tdpm_detection &d = buf[i];
         if (d.image < 0 || d.image >= (int)b.parts.size()) continue;
-        const Part &p = b.parts[d.image];
-        if (d.score < p.req->tau) continue;
         per_part[d.image].push_back(d);
         per_part[d.image].back().image = 0;
     }
@@ -192,13 +192,14 @@ void server_loop(tdpm_ctx *ctx, Server *S)
         tdpm_status st = TDPM_OK;
         bool subset = false;
         for (const Part &p : take) subset |= !p.req->components.empty();
-        if (subset) {
-            size_t nc = 0;
-            {
-                std::lock_guard<std::mutex> lk(ctx->mu);
-                const Model *m = get_model(ctx, b.model);
-                nc = m ? m->comps.size() : 0;
-            }
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            const Model *m = get_model(ctx, b.model);
+            b.n_comps = m ? m->comps.size() : 0;
+        }
+        if (!b.n_comps) st = TDPM_ERR_STATE;  // unknown model
+        if (subset && st == TDPM_OK) {
+            const size_t nc = b.n_comps;
             mask.assign(take.size() * nc, 1);
             for (size_t i = 0; i < take.size() && nc; ++i) {
                 const auto &cs = take[i].req->components;
@@ -209,7 +210,6 @@ void server_loop(tdpm_ctx *ctx, Server *S)
                     else mask[i * nc + c] = 1;
                 }
             }
-            if (!nc) st = TDPM_ERR_STATE;
         }
         if (st == TDPM_OK)
             st = batch_arena_bytes(ctx, b.model, pyrs.data(), (int32_t)pyrs.size(), subset ? mask.data() : nullptr,

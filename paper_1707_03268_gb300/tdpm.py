@@ -107,6 +107,8 @@ SIGNATURES = {
     "tdpm_build_pyramid_scores": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _c_i32, _VP,
                                            ctypes.POINTER(_c_i32)]),
     "tdpm_detect": (_c_i32, [_VP, _c_i32, ctypes.c_float, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _VP]),
+    "tdpm_detect_thresholds": (_c_i32, [_VP, _c_i32, _VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                                        _VP]),
     "tdpm_build_batch_scores": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _c_i32, _c_i32, _VP,
                                          ctypes.POINTER(_c_i32)]),
     "tdpm_build_batch_scores_subset": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _VP, _c_i32, _c_i32,
@@ -380,6 +382,19 @@ def tdpm_poll(ctx: int, ticket: int, timeout_ms: int = -1, capacity: int = 4096)
         _inflight_requests.pop((ctx, int(ticket)), None)
     _check(st)
     return out[: n.value], {f: getattr(info, f) for f, _ in ResultInfo._fields_}
+
+
+def tdpm_detect_thresholds(ctx: int, scores_id: int, tau: np.ndarray, capacity: int = 1 << 20, stream=None,
+                           out: Optional[np.ndarray] = None) -> np.ndarray:
+    """tdpm_detect with a threshold per (image, component): tau is [n_images][n_components]."""
+    t = np.ascontiguousarray(tau, dtype=np.float32)
+    if out is None or out.shape[0] < capacity:
+        out = np.zeros(capacity, dtype=DETECTION_DTYPE)
+    n = ctypes.c_size_t()
+    st = lib().tdpm_detect_thresholds(ctx, scores_id, t.ctypes.data, out.ctypes.data if capacity else None,
+                                      int(capacity), ctypes.byref(n), _stream_ptr(stream))
+    _check(st)
+    return out[: n.value]
 
 
 def tdpm_get_maps(ctx: int, scores_id: int, kind: int, index_a: int, index_b: int, stream=None,

@@ -156,3 +156,28 @@ def test_component_subsets_equal_full_batch_filtered(torch, T, ctx):
                     assert b.size == 0
     T.tdpm_release(ctx, full)
     T.tdpm_release(ctx, sub)
+
+
+def test_thresholds_per_image_and_component(torch, T, ctx):
+    """tdpm_detect_thresholds gives exactly the records of tdpm_detect at the lowest threshold that clear their own
+    (image, component) threshold, in the same order; a uniform table equals tdpm_detect."""
+    wl = synth.config_c2()
+    mid = T.tdpm_load_model(ctx, wl.model)
+    pyrs = _batch_images(seed=13)[:3]
+    sid = T.tdpm_build_batch_scores(ctx, mid, [device_pyramid(py, torch) for py in pyrs], T.FORM_FULL, T.PREC_FP32)
+    nc = len(wl.model.components)
+    allp = T.tdpm_detect(ctx, sid, -np.inf)
+    rng = np.random.default_rng(3)
+    tau = np.percentile(allp["score"], rng.uniform(80, 99.5, size=(len(pyrs), nc))).astype(np.float32)
+    got = T.tdpm_detect_thresholds(ctx, sid, tau)
+    low = T.tdpm_detect(ctx, sid, float(tau.min()))
+    want = low[low["score"] >= tau[low["image"], low["component"]]]
+    assert len(got) == len(want) > 0
+    for name in ("image", "component", "level", "y", "x", "score", "part_y", "part_x"):
+        np.testing.assert_array_equal(got[name], want[name])
+    flat = np.full((len(pyrs), nc), float(np.median(tau)), dtype=np.float32)
+    a, b = T.tdpm_detect_thresholds(ctx, sid, flat), T.tdpm_detect(ctx, sid, float(flat[0, 0]))
+    np.testing.assert_array_equal(a, b)
+    with pytest.raises(T.TdpmError):
+        T.tdpm_detect_thresholds(ctx, sid, np.full((len(pyrs), nc), np.nan, dtype=np.float32))
+    T.tdpm_release(ctx, sid)
