@@ -45,7 +45,7 @@ from paper_1707_03268_gb300 import synth  # noqa: E402
 METRIC = "images/sec and p50/p99 latency, decomposed BF16 vs full FP32, at >=99.5% agreement"
 L2_BYTES = 129 * 1024 * 1024
 RANK_SWEEP = {"per_filter": (4, 8, 16, 24, 32, 36), "joint": (16, 32, 64, 128, 256)}
-PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 3}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "bf16x3": 3}
 
 
 def parse():
@@ -139,15 +139,15 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
         groups.setdefault((0,) + comp.root.shape[:2], []).append(comp.root)
         for p in comp.parts:
             groups.setdefault((1,) + p.filt.shape[:2], []).append(p.filt)
-    tc = precision in ("bf16", "bf16x3")
-    fb = {"fp32": 4, "bf16": 2, "bf16x3": 4}[precision]  # feature bytes per channel read by the correlation
+    tc = precision in ("bf16", "bf16x3", "fp8")
+    fb = {"fp32": 4, "bf16": 2, "bf16x3": 4, "fp8": 1}[precision]  # feature bytes per channel read by the correlation
     corr = "corr_tc" if tc else "corr_f32"
     zproj = "zproj_tc" if tc else "zproj_f32"
     out = {corr: [0, 0], zproj: [0, 0], "sep": [0, 0], "recomb_tc": [0, 0], "dt": [0, 0], "assemble": [0, 0],
            "to_bf16": [0, 0]}
     ub = 4 if precision == "bf16x3" else 2  # bytes per U_r value on the joint tensor-core path (hi + lo parts)
     if tc:
-        out["to_bf16"][0] = sum(H * W * 32 * (4 + fb) for (H, W) in sizes)
+        out["to_fp8" if precision == "fp8" else "to_bf16"] = [sum(H * W * 32 * (4 + fb) for (H, W) in sizes), 0]
     for (role, h, w), fl in groups.items():
         K = len(fl)
         if joint:
@@ -387,7 +387,8 @@ def run_bank(args):
     taus = _class_taus(allp, n_comp)
     del allp
 
-    variants = [("full", "fp32", None, None), ("full", "bf16", None, None), ("full", "bf16x3", None, None)]
+    variants = [("full", "fp32", None, None), ("full", "bf16", None, None), ("full", "bf16x3", None, None),
+                ("full", "fp8", None, None)]
     if args.workload == "c3":
         variants += [("decomposed", "bf16", r, "joint") for r in (8, 32, 128)]
         variants += [("decomposed", "bf16x3", 32, "joint"), ("decomposed", "bf16", 8, "per_filter")]
@@ -714,6 +715,14 @@ def main():
         if prec != tdpm.PREC_FP32 or form != tdpm.FORM_FULL:
             fullp = timed(tdpm.FORM_FULL, prec, n_cmp, 2)
             compare[f"full_{args.precision}_images_per_s"] = rate(fullp)
+        # the other tensor-core operand formats of the full form: speed and agreement with the full FP32 form
+        for pname in ("bf16", "fp8"):
+            if pname == args.precision:
+                continue
+            run = timed(tdpm.FORM_FULL, PRECISIONS[pname], n_cmp, 2)
+            k = keys(step(tdpm.FORM_FULL, PRECISIONS[pname]))
+            compare[f"full_{pname}_images_per_s"] = rate(run)
+            compare[f"full_{pname}_agreement_with_full_fp32"] = len(k & full_keys) / max(1, len(k | full_keys))
 
     # ---- oracle leg: CPU baseline and parity of the headline detections (same factors)
     cpu = None
@@ -743,6 +752,7 @@ def main():
                        "precision_note": {"bf16x3": "BF16 tensor cores, operands split hi+lo (3 MMAs per product), "
                                                     "FP32 accumulation",
                                           "bf16": "BF16 tensor cores, FP32 accumulation",
+                                          "fp8": "E4M3 tensor cores (per-tensor scales), FP32 accumulation",
                                           "fp32": "FP32 ALUs"}[args.precision],
                        "rank": args.rank if form == tdpm.FORM_DECOMPOSED else None,
                        "decomposition": args.mode if form == tdpm.FORM_DECOMPOSED else None,

@@ -56,7 +56,10 @@ typedef int32_t tdpm_status;
 /* arithmetic of the correlation, FP32 accumulation always:
  *   FP32     FP32 operands on the FP32 ALUs;
  *   BF16     BF16 operands on the tensor cores (features and tensor-core factors rounded to BF16);
- *   FP8      reserved (not implemented: returns TDPM_ERR_ARG);
+ *   FP8      E4M3 operands on the tensor cores (kind::f8f6f4) for the full correlation and the decomposed channel
+ *            stage: features scaled by 448/0.2 (HOG cells are truncated at 0.2), each bank of filters (or of channel
+ *            factors c_r) by 448 / its largest magnitude, rounded to nearest even; results rescaled in FP32. The
+ *            separable passes and the joint recombination keep FP32 and BF16. Accuracy is reported, not guaranteed;
  *   BF16X3   split BF16 on the tensor cores: every operand x = hi + lo with hi = bf16(x), lo = bf16(x - hi), and each
  *            product is formed as hi*hi + hi*lo + lo*hi (relative error about 2^-16, three MMAs per product). */
 #define TDPM_PREC_FP32 0

@@ -18,6 +18,7 @@
 // Every mbarrier wait is bounded: on expiry the kernel raises the context's error flag and carries on to a clean exit.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -29,7 +30,6 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_THREADS = 128;
 constexpr int TC_STAGES = 4;
-constexpr uint32_t A_STAGE_BYTES = TC_M * 64;  // 128 cells x 32 channels x 2 bytes
 constexpr uint32_t A_PLANE_BYTES = TC_M * 16;  // one 8-channel chunk of 128 cells
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -104,6 +104,21 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3 (format code 0), both K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc_e4m3(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
@@ -145,17 +160,23 @@ __device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
 // plane); NT = N tile width (multiple of 16, <= 256); the input has 32*cb channels in 4*cb planar chunks.
 // SPLIT: operands come as hi and lo BF16 parts (filt_lo, the job's tmap_lo) and every K step issues three MMAs,
 // hi*hi + hi*lo + lo*hi, into the same FP32 accumulator.
-template <bool SPLIT>
+// FP8: E4M3 operands, 32 channels = 32 bytes = two 16-byte chunks per tap ([2][cells][16] planar input, bank
+// [taps][2][ld][16]); one kind::f8f6f4 MMA (K = 32) per tap; the epilogue multiplies by `scale` (the inverse of the
+// product of the two per-tensor scales).
+template <bool SPLIT, bool FP8>
 __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__restrict__ jobs, int n_jobs,
-                                                                const uint16_t *__restrict__ filt,
-                                                                const uint16_t *__restrict__ filt_lo, int K, int ld,
+                                                                const uint8_t *__restrict__ filt,
+                                                                const uint8_t *__restrict__ filt_lo, int K, int ld,
                                                                 int NT, int n_tiles_n, int h, int w, int cb,
-                                                                uint32_t tmem_cols, int stages, int *err)
+                                                                uint32_t tmem_cols, int stages, float scale, int *err)
 {
+    static_assert(!(SPLIT && FP8), "split operands are BF16");
     extern __shared__ __align__(1024) uint8_t sm[];
     constexpr uint32_t NPART = SPLIT ? 2 : 1;
-    const uint32_t b_part_bytes = (uint32_t)NT * 64;
-    const uint32_t a_stage_bytes = NPART * A_STAGE_BYTES, b_stage_bytes = NPART * b_part_bytes;
+    constexpr int CHUNKS = FP8 ? 2 : 4;                              // 16-byte K chunks per tap
+    constexpr uint32_t A_BYTES = TC_M * 16 * CHUNKS;                  // one tap of A
+    const uint32_t b_part_bytes = (uint32_t)NT * 16 * CHUNKS;
+    const uint32_t a_stage_bytes = NPART * A_BYTES, b_stage_bytes = NPART * b_part_bytes;
     uint8_t *a_smem = sm;
     uint8_t *b_smem = sm + stages * a_stage_bytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + stages * b_stage_bytes);
@@ -200,34 +221,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
             const int ts = t / cb, blk = t - ts * cb;
             const int dy = ts / w, dx = ts - dy * w;
             const uint32_t adst = smem_u32(a_smem + s * a_stage_bytes);
-            tma_load_3d(adst, &J->tmap, 0, p0 + dy * W + dx, 4 * blk, full);
-            if (SPLIT) tma_load_3d(adst + A_STAGE_BYTES, &J->tmap_lo, 0, p0 + dy * W + dx, 4 * blk, full);
+            tma_load_3d(adst, &J->tmap, 0, p0 + dy * W + dx, CHUNKS * blk, full);
+            if (SPLIT) tma_load_3d(adst + A_BYTES, &J->tmap_lo, 0, p0 + dy * W + dx, CHUNKS * blk, full);
             const uint32_t bdst = smem_u32(b_smem + s * b_stage_bytes);
-            for (int kc = 0; kc < 4; ++kc) {
-                const size_t off = (((size_t)t * 4 + kc) * ld + n0) * 8;
+            for (int kc = 0; kc < CHUNKS; ++kc) {
+                const size_t off = (((size_t)t * CHUNKS + kc) * ld + n0) * 16;  // bytes
                 bulk_load(bdst + kc * NT * 16, filt + off, (uint32_t)NT * 16, full);
                 if (SPLIT) bulk_load(bdst + b_part_bytes + kc * NT * 16, filt_lo + off, (uint32_t)NT * 16, full);
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: two K=16 steps per tap (channel chunks {0,1} and {2,3})
-        const uint32_t idesc = instr_desc(TC_M, NT);
+        // MMA issuer: BF16, two K=16 steps per tap (channel chunks {0,1} and {2,3}); FP8, one K=32 step
+        const uint32_t idesc = FP8 ? instr_desc_e4m3(TC_M, NT) : instr_desc(TC_M, NT);
         for (int t = 0; t < taps; ++t) {
             const int s = t % stages;
             mbar_wait(full0 + 8 * s, (t / stages) & 1, err);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_base = smem_u32(a_smem + s * a_stage_bytes);
             const uint32_t b_base = smem_u32(b_smem + s * b_stage_bytes);
+            if (FP8) {
+                const uint64_t ad = smem_desc(a_base, A_PLANE_BYTES, 128);
+                const uint64_t bd = smem_desc(b_base, (uint32_t)NT * 16, 128);
+                mma_e4m3(tmem, ad, bd, idesc, t != 0);
+            } else {
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t ad = smem_desc(a_base + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
-                const uint64_t bd = smem_desc(b_base + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
-                mma_bf16(tmem, ad, bd, idesc, (t | ks) != 0);
-                if (SPLIT) {
-                    const uint64_t ad_lo = smem_desc(a_base + A_STAGE_BYTES + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
-                    const uint64_t bd_lo = smem_desc(b_base + b_part_bytes + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
-                    mma_bf16(tmem, ad, bd_lo, idesc, 1u);
-                    mma_bf16(tmem, ad_lo, bd, idesc, 1u);
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t ad = smem_desc(a_base + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
+                    const uint64_t bd = smem_desc(b_base + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
+                    mma_bf16(tmem, ad, bd, idesc, (t | ks) != 0);
+                    if (SPLIT) {
+                        const uint64_t ad_lo = smem_desc(a_base + A_BYTES + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
+                        const uint64_t bd_lo =
+                            smem_desc(b_base + b_part_bytes + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
+                        mma_bf16(tmem, ad, bd_lo, idesc, 1u);
+                        mma_bf16(tmem, ad_lo, bd, idesc, 1u);
+                    }
                 }
             }
             mma_commit(empty0 + 8 * s);
@@ -251,7 +279,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__r
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int k = n0 + c0 + j;
-                if (k < K) out[(size_t)k * plane] = __uint_as_float(r[j]);
+                if (k < K) out[(size_t)k * plane] = FP8 ? __uint_as_float(r[j]) * scale : __uint_as_float(r[j]);
             }
         }
     }
@@ -291,6 +319,34 @@ __global__ void to_bf16_planar_kernel(const ConvJob *__restrict__ jobs, int n_jo
     const size_t o = ((size_t)kc * J.cells + cell) * 8;
     *reinterpret_cast<uint4 *>(J.dst + o) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
     if (J.dst_lo) *reinterpret_cast<uint4 *>(J.dst_lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+}
+
+// FP32 NHWC [cells][32] -> E4M3 [2][cells][16] (x * scale, rounded to nearest even, saturated at +-448): one
+// thread per (cell, 16-channel chunk) item
+__global__ void to_fp8_planar_kernel(const ConvJob *__restrict__ jobs, int n_jobs, long long total, float scale)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].begin <= i) lo = mid; else hi = mid - 1;
+    }
+    const ConvJob &J = jobs[lo];
+    const long long item = i - J.begin;
+    const long long cell = item >> 1;
+    const int kc = (int)(item & 1);
+    const float4 *src = reinterpret_cast<const float4 *>(J.src + cell * FD + kc * 16);
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float4 v = __ldg(src + j);
+        const uint32_t a = __nv_cvt_float2_to_fp8x2(make_float2(v.x * scale, v.y * scale), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t b = __nv_cvt_float2_to_fp8x2(make_float2(v.z * scale, v.w * scale), __NV_SATFINITE, __NV_E4M3);
+        w[j] = a | (b << 16);
+    }
+    uint8_t *dst = reinterpret_cast<uint8_t *>(J.dst) + ((size_t)kc * J.cells + cell) * 16;
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 }  // namespace
@@ -334,19 +390,20 @@ int corr_tc_bank_rows(int K)
     return rows;
 }
 
-size_t corr_tc_smem_bytes(int NT, bool split, int stages)
+size_t corr_tc_smem_bytes(int NT, bool split, bool fp8, int stages)
 {
-    const size_t parts = split ? 2 : 1;
-    return stages * parts * (A_STAGE_BYTES + (size_t)NT * 64) + 8 * (2 * stages + 1) + 16;
+    const size_t parts = split ? 2 : 1, tap_bytes = fp8 ? 32 : 64;  // bytes of one row of one tap
+    return stages * parts * (TC_M + (size_t)NT) * tap_bytes + 8 * (2 * stages + 1) + 16;
 }
 
-cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const uint16_t *filt_tc,
-                           const uint16_t *filt_tc_lo, int K, int ld, int NT, int h, int w, int cb, int *d_err,
-                           cudaStream_t s)
+cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const void *filt_tc, const void *filt_tc_lo,
+                           int K, int ld, int NT, int h, int w, int cb, int *d_err, cudaStream_t s, bool fp8,
+                           float scale)
 {
     if (m_tiles <= 0 || K <= 0) return cudaSuccess;
     if (cb < 1) return cudaErrorInvalidValue;
     const bool split = filt_tc_lo != nullptr;
+    if (split && fp8) return cudaErrorInvalidValue;
     const int taps = h * w * cb;
     const int n_tiles_n = corr_tc_n_tiles(K, NT);
     const int stages = taps < TC_STAGES ? taps : TC_STAGES;
@@ -358,21 +415,28 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const u
     while (cols < (uint32_t)NT) cols <<= 1;
     // keep residency within TMEM: at most 512 / cols CTAs per SM, enforced through the shared memory request
     const int max_ctas = 512 / (int)cols;
-    size_t smem = corr_tc_smem_bytes(NT, split, stages);
+    size_t smem = corr_tc_smem_bytes(NT, split, fp8, stages);
     const size_t floor_bytes = 233472 / (size_t)(max_ctas + 1);
     if (smem < floor_bytes) smem = floor_bytes;
     if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
-    const void *fn = split ? reinterpret_cast<const void *>(corr_tc_kernel<true>)
-                           : reinterpret_cast<const void *>(corr_tc_kernel<false>);
-    cudaError_t e = allow_max_dynamic_smem(fn, split ? 2 : 0);
+    const void *fn = split ? reinterpret_cast<const void *>(corr_tc_kernel<true, false>)
+                     : fp8 ? reinterpret_cast<const void *>(corr_tc_kernel<false, true>)
+                           : reinterpret_cast<const void *>(corr_tc_kernel<false, false>);
+    cudaError_t e = allow_max_dynamic_smem(fn, split ? 2 : fp8 ? 3 : 0);
     if (e != cudaSuccess) return e;
     note_launches(1);
+    const uint8_t *fb = static_cast<const uint8_t *>(filt_tc), *fl = static_cast<const uint8_t *>(filt_tc_lo);
     if (split)
-        corr_tc_kernel<true><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, filt_tc_lo, K, ld, NT,
-                                                                   n_tiles_n, h, w, cb, cols, stages, d_err);
+        corr_tc_kernel<true, false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, fb, fl, K, ld, NT, n_tiles_n,
+                                                                          h, w, cb, cols, stages, 1.f, d_err);
+    else if (fp8)
+        corr_tc_kernel<false, true><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, fb, nullptr, K, ld, NT,
+                                                                          n_tiles_n, h, w, cb, cols, stages, scale,
+                                                                          d_err);
     else
-        corr_tc_kernel<false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, filt_tc, nullptr, K, ld, NT,
-                                                                    n_tiles_n, h, w, cb, cols, stages, d_err);
+        corr_tc_kernel<false, false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, fb, nullptr, K, ld, NT,
+                                                                           n_tiles_n, h, w, cb, cols, stages, 1.f,
+                                                                           d_err);
     return cudaGetLastError();
 }
 
@@ -384,12 +448,25 @@ cudaError_t launch_to_bf16_planar(const ConvJob *d_jobs, int n_jobs, long long t
     return cudaGetLastError();
 }
 
+cudaError_t launch_to_fp8_planar(const ConvJob *d_jobs, int n_jobs, long long total, float scale, cudaStream_t s)
+{
+    if (total <= 0 || n_jobs <= 0) return cudaSuccess;
+    note_launches(1);
+    to_fp8_planar_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(d_jobs, n_jobs, total, scale);
+    return cudaGetLastError();
+}
+
+
 // Tensor map over one BF16 planar array: dims {8 channels, cells, chunks}, box {8, 128, 4}, zero fill outside.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks)
+namespace {
+
+// dims {elems per 16-byte chunk, cells, chunks}, box {elems, 128, the chunks of one tap (32 channels)}, zero fill
+// outside; strides in bytes
+bool encode_tmap(CUtensorMap *map, CUtensorMapDataType type, int elems, void *base, long long cells, int chunks)
 {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -401,14 +478,26 @@ bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells
             return false;
         fn = reinterpret_cast<EncodeTiledFn>(p);
     }
-    if (chunks < 4 || chunks % 4) return false;
-    const cuuint64_t dims[3] = {8, (cuuint64_t)cells, (cuuint64_t)chunks};
+    const cuuint32_t tap_chunks = (cuuint32_t)(FD / elems);
+    if (chunks < (int)tap_chunks || chunks % tap_chunks) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)elems, (cuuint64_t)cells, (cuuint64_t)chunks};
     const cuuint64_t strides[2] = {16, (cuuint64_t)cells * 16};
-    const cuuint32_t box[3] = {8, (cuuint32_t)TC_M, 4};
+    const cuuint32_t box[3] = {(cuuint32_t)elems, (cuuint32_t)TC_M, tap_chunks};
     const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t *>(planar), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks)
+{
+    return encode_tmap(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 8, const_cast<uint16_t *>(planar), cells, chunks);
+}
+
+bool encode_level_tmap_fp8(CUtensorMap *map, const uint8_t *planar, long long cells)
+{
+    return encode_tmap(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 16, const_cast<uint8_t *>(planar), cells, 2);
 }
 
 }  // namespace tdpm

@@ -50,6 +50,8 @@ struct Group {
     int Kpad = 0;                        // FP32 SIMT layout padding (multiple of 64)
     float *d_filt_t = nullptr;           // [h*w*32][Kpad] FP32
     int Npad_tc = 0;                     // tensor-core bank rows (K padded for every candidate N tiling)
+    uint8_t *d_filt_fp8 = nullptr;       // [h*w][2][Npad_tc][16] E4M3 bytes of the filters times fp8_scale
+    float fp8_scale = 1.f;               // per-tensor scale of that bank (448 / max |filter value|)
     uint16_t *d_filt_tc = nullptr;       // [h*w][4][Npad_tc][8] BF16 (hi part: bf16(x))
     uint16_t *d_filt_tc_lo = nullptr;    // lo part bf16(x - bf16(x)), same layout (split-BF16 precision)
     // decomposition, FP64 master copies
@@ -63,6 +65,8 @@ struct Group {
     int Rpad_tc = 0;                     // rows of the channel-factor bank
     uint16_t *d_C_tc = nullptr;          // [1][4][Rpad_tc][8] BF16: the channel factor as a 1x1 "filter bank"
     uint16_t *d_C_tc_lo = nullptr;       // its lo part
+    uint8_t *d_C_fp8 = nullptr;          // [1][2][Rpad_tc][16] E4M3 channel factor times C_fp8_scale
+    float C_fp8_scale = 1.f;
     // joint mode on tensor cores: per-term maps U_r are recombined by S = Lambda U as a GEMM over Upad terms
     int Upad = 0;                        // R rounded up to a multiple of 32 (zero terms beyond R)
     int Npad_lam = 0;                    // rows of the Lambda bank
@@ -179,5 +183,10 @@ tdpm_status upload(T **dst, const std::vector<T> &src)
 
 uint16_t bf16_bits(float x);
 float bf16_round(float x);
+uint8_t e4m3_bits(float x);  // E4M3 encoding, round to nearest even, saturated at +-448
+inline bool valid_precision(int p)
+{
+    return p == TDPM_PREC_FP32 || p == TDPM_PREC_BF16 || p == TDPM_PREC_FP8 || p == TDPM_PREC_BF16X3;
+}
 
 }  // namespace tdpm

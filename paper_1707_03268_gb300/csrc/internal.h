@@ -27,7 +27,7 @@ struct CorrJob {
 
 // Step 1 on tensor cores (full form, or the channel stage of the decomposed form with a 1x1 tap): one (group,
 // level) pair. The tensor map describes the level's BF16 planar copy [4][H*W][8].
-struct alignas(64) TcJob {
+struct alignas(128) TcJob {
     CUtensorMap tmap;         // BF16 (hi part) planar copy of the level
     CUtensorMap tmap_lo;      // lo part (split-BF16 precision only)
     float *out;               // [N][Ho][Wo] (channel stage: [R][H][W])
@@ -114,9 +114,11 @@ int corr_f32_tile_k();
 // times NT (corr_tc_bank_rows). The input has 32*cb channels (cb = 1 for HOG features; cb = terms / 32 for the
 // recombination of per-term maps). filt_tc_lo non-null selects split-BF16 operands (lo parts of the filters; the
 // jobs' tmap_lo must describe the lo parts of the input). d_err: device flag raised when a bounded wait expires.
-cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const uint16_t *filt_tc,
-                           const uint16_t *filt_tc_lo, int K, int ld, int NT, int h, int w, int cb, int *d_err,
-                           cudaStream_t s);
+// fp8: E4M3 operands (bank [h*w*cb][2][ld][16] bytes, input tmap from encode_level_tmap_fp8, no lo parts); the
+// results are multiplied by `scale` (the inverse of the operands' per-tensor scales).
+cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const void *filt_tc, const void *filt_tc_lo,
+                           int K, int ld, int NT, int h, int w, int cb, int *d_err, cudaStream_t s, bool fp8 = false,
+                           float scale = 1.f);
 int corr_tc_tile_m();
 int corr_tc_n_tiles(int K, int NT);
 int corr_tc_default_nt(int K, int taps);     // untuned N tile width for K filters over `taps` K blocks (h*w*cb)
@@ -124,9 +126,15 @@ int corr_tc_nt_candidates(int K, int *out);  // up to 4 widths a tuner may choos
 int corr_tc_bank_rows(int K);                // bank rows (ld) that fit every candidate width
 // Tensor map of a BF16 planar array [chunks][cells][8] (chunks a multiple of 4), box {8, 128, 4}.
 bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks = 4);
+// Tensor map of an E4M3 planar level [2][cells][16] bytes, box {16, 128, 2}.
+bool encode_level_tmap_fp8(CUtensorMap *map, const uint8_t *planar, long long cells);
 
 // FP32 NHWC -> BF16 planar for many levels in one launch (total = sum of 4 * cells).
 cudaError_t launch_to_bf16_planar(const ConvJob *d_jobs, int n_jobs, long long total, cudaStream_t s);
+// FP32 NHWC -> E4M3 planar [2][cells][16] of x * scale (ConvJob.dst holds the bytes; total = sum of 2 * cells).
+cudaError_t launch_to_fp8_planar(const ConvJob *d_jobs, int n_jobs, long long total, float scale, cudaStream_t s);
+// Per-tensor scale of the FP8 features: HOG cells are truncated at 0.2, mapped to the largest E4M3 value 448.
+constexpr float kFp8FeatureScale = 448.f / 0.2f;
 
 // K2: Z projection, SIMT FP32. Ct: [R][32] FP32.
 cudaError_t launch_zproj_simt(const ZJob *d_jobs, int n_jobs, int total_tiles, const float *Ct, int R, cudaStream_t s);

@@ -39,6 +39,35 @@ uint16_t bf16_bits(float x)
 
 float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; largest finite value 448, no infinities) of x, rounded
+// to nearest with ties to even and saturated to +-448: written from the format's definition.
+uint8_t e4m3_bits(float x)
+{
+    const uint8_t sign = std::signbit(x) ? 0x80 : 0;
+    double a = std::fabs((double)x);
+    if (!(a == a)) return 0x7F;  // NaN
+    if (a >= 448.0) return sign | 0x7E;
+    int k = 0;
+    std::frexp(a, &k);            // a = f * 2^k, f in [0.5, 1): leading bit at 2^(k-1)
+    int E = k - 1;
+    if (a == 0.0) return sign;
+    if (E < -6) {
+        // subnormal: multiples of 2^-9
+        const double q = std::nearbyint(std::ldexp(a, 9));  // ties to even (default rounding mode)
+        if (q >= 8.0) return sign | (1 << 3);                // rounds up to the smallest normal 2^-6
+        return sign | (uint8_t)q;
+    }
+    double q = std::nearbyint(std::ldexp(a, 3 - E));  // in [8, 16]
+    if (q >= 16.0) {
+        q = 8.0;
+        ++E;
+    }
+    const int e = E + 7, m = (int)q - 8;
+    if (e > 15 || (e == 15 && m == 7)) return sign | 0x7E;
+    return sign | (uint8_t)((e << 3) | m);
+}
+
+
 void Group::free_factors()
 {
     cudaFree(d_A); cudaFree(d_B); cudaFree(d_Ct); cudaFree(d_lam);
@@ -48,6 +77,8 @@ void Group::free_factors()
     cudaFree(d_C_tc_lo);
     cudaFree(d_lam_tc);
     cudaFree(d_lam_tc_lo);
+    cudaFree(d_C_fp8);
+    d_C_fp8 = nullptr;
     d_rank_off = nullptr;
     d_C_tc = d_C_tc_lo = nullptr;
     d_lam_tc = d_lam_tc_lo = nullptr;
@@ -60,6 +91,8 @@ void Group::free_all()
     cudaFree(d_filt_t);
     cudaFree(d_filt_tc);
     cudaFree(d_filt_tc_lo);
+    cudaFree(d_filt_fp8);
+    d_filt_fp8 = nullptr;
     d_filt_t = nullptr;
     d_filt_tc = d_filt_tc_lo = nullptr;
 }
@@ -80,6 +113,23 @@ namespace {
 
 // Tensor-core filter banks: [taps][4 channel chunks][Npad][8] BF16, zero rows for n >= n_rows; the hi part bf16(x)
 // and the lo part bf16(x - bf16(x)) of the split-BF16 operands.
+// E4M3 bank [taps][2][Npad][16] bytes of value * scale, scale = 448 / max |value| (1 when all are zero).
+tdpm_status upload_fp8_bank(uint8_t **dst, float *scale, int taps, int Npad, int n_rows,
+                            const std::function<float(int, int, int)> &value)
+{
+    float mx = 0.f;
+    for (int t = 0; t < taps; ++t)
+        for (int n = 0; n < n_rows; ++n)
+            for (int c = 0; c < FD; ++c) mx = std::max(mx, std::fabs(value(t, n, c)));
+    *scale = mx > 0.f ? 448.f / mx : 1.f;
+    std::vector<uint8_t> b((size_t)taps * 2 * Npad * 16, 0);
+    for (int t = 0; t < taps; ++t)
+        for (int n = 0; n < n_rows; ++n)
+            for (int c = 0; c < FD; ++c)
+                b[(((size_t)t * 2 + c / 16) * Npad + n) * 16 + (c % 16)] = e4m3_bits(value(t, n, c) * *scale);
+    return upload(dst, b);
+}
+
 tdpm_status upload_tc_bank(uint16_t **dst_hi, uint16_t **dst_lo, int taps, int Npad, int n_rows,
                            const std::function<float(int, int, int)> &value)
 {
@@ -126,6 +176,9 @@ tdpm_status upload_factors(Group &g)
     g.Rpad_tc = corr_tc_bank_rows(R);
     st = upload_tc_bank(&g.d_C_tc, &g.d_C_tc_lo, 1, g.Rpad_tc, R,
                         [&](int, int r, int c) { return (float)g.C[(size_t)c * R + r]; });
+    if (!st)
+        st = upload_fp8_bank(&g.d_C_fp8, &g.C_fp8_scale, 1, g.Rpad_tc, R,
+                             [&](int, int r, int c) { return (float)g.C[(size_t)c * R + r]; });
     if (st || !g.joint) return st;
     g.Upad = (R + 31) / 32 * 32;
     const int cb = g.Upad / 32;
@@ -298,6 +351,9 @@ tdpm_status tdpm_load_model(tdpm_ctx *ctx, const tdpm_model_desc *desc, int32_t 
         g.Npad_tc = corr_tc_bank_rows(g.K);
         if ((st = upload(&g.d_filt_t, ft)) ||
             (st = upload_tc_bank(&g.d_filt_tc, &g.d_filt_tc_lo, taps, g.Npad_tc, g.K, [&](int t, int k, int c) {
+                 return m->filters[g.fids[k]].data[(size_t)t * FD + c];
+             })) ||
+            (st = upload_fp8_bank(&g.d_filt_fp8, &g.fp8_scale, taps, g.Npad_tc, g.K, [&](int t, int k, int c) {
                  return m->filters[g.fids[k]].data[(size_t)t * FD + c];
              }))) {
             for (Group &gg : m->groups) gg.free_all();

@@ -78,10 +78,11 @@ struct Plan {
     int model_id = 0, form = 0, precision = 0, L = 0;  // L: levels of all images (flat index)
     int n_images = 0;
     std::vector<int> img_base, img_L, img_lam;         // per image: first flat level, level count, lambda
-    bool bf = false, split = false, dec = false;
+    bool bf = false, split = false, dec = false;  // bf: the tensor-core path (BF16, split BF16 or FP8 operands)
+    bool fp8 = false;
     std::vector<std::pair<int, int>> sizes;
     size_t arena_bytes = 0, blob_off = 0, blob_bytes = 0;
-    std::vector<size_t> bf_off, bf_lo_off;  // BF16 planar copies of the levels (hi part, lo part)
+    std::vector<size_t> bf_off, bf_lo_off;  // planar copies of the levels: BF16 (hi part, lo part) or E4M3
     std::vector<std::vector<GroupLevel>> glv;
     std::vector<DtPlan> dts;
     std::vector<AsmPlan> asms;
@@ -141,14 +142,16 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         for (int j = 0; j < pyrs[i].n_levels; ++j) P->sizes.push_back({pyrs[i].levels[j].H, pyrs[i].levels[j].W});
     }
     P->L = (int)P->sizes.size();
-    P->bf = prec == TDPM_PREC_BF16 || prec == TDPM_PREC_BF16X3;
+    P->bf = prec == TDPM_PREC_BF16 || prec == TDPM_PREC_BF16X3 || prec == TDPM_PREC_FP8;
+    P->fp8 = prec == TDPM_PREC_FP8;
     P->split = prec == TDPM_PREC_BF16X3;
     P->dec = form == TDPM_FORM_DECOMPOSED;
     const int L = P->L;
     Bump bump;
     if (P->bf) {
         P->bf_off.resize(L);
-        for (int j = 0; j < L; ++j) P->bf_off[j] = bump.take(sizeof(uint16_t) * (size_t)P->sizes[j].first * P->sizes[j].second * FD);
+        const size_t elem = P->fp8 ? 1 : sizeof(uint16_t);
+        for (int j = 0; j < L; ++j) P->bf_off[j] = bump.take(elem * (size_t)P->sizes[j].first * P->sizes[j].second * FD);
         if (P->split) {
             P->bf_lo_off.resize(L);
             for (int j = 0; j < L; ++j)
@@ -235,7 +238,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     Bump jb;
     if (P->bf) {
         P->conv_off = jb.take(sizeof(ConvJob) * L);
-        for (int j = 0; j < L; ++j) P->conv_items += 4ll * P->sizes[j].first * P->sizes[j].second;
+        for (int j = 0; j < L; ++j) P->conv_items += (P->fp8 ? 2ll : 4ll) * P->sizes[j].first * P->sizes[j].second;
     }
     const size_t ng = m.groups.size();
     P->g_jobs_off.assign(ng, 0); P->g_sep_off.assign(ng, 0); P->g_tiles.assign(ng, 0); P->g_sep_tiles.assign(ng, 0);
@@ -306,7 +309,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
             cj[j].dst_lo = P.split ? reinterpret_cast<uint16_t *>(base + P.bf_lo_off[j]) : nullptr;
             cj[j].cells = (long long)P.sizes[j].first * P.sizes[j].second;
             cj[j].begin = begin;
-            begin += 4 * cj[j].cells;
+            begin += (P.fp8 ? 2 : 4) * cj[j].cells;
         }
     }
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
@@ -319,9 +322,11 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
             float *out = reinterpret_cast<float *>(base + gl.out_off);
             if (P.bf) {
                 TcJob &t = reinterpret_cast<TcJob *>(hb + P.g_jobs_off[gi])[i];
-                if (!encode_level_tmap(&t.tmap, reinterpret_cast<const uint16_t *>(base + P.bf_off[gl.j]),
-                                       (long long)H * W))
-                    return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+                const bool ok = P.fp8 ? encode_level_tmap_fp8(&t.tmap, reinterpret_cast<const uint8_t *>(base + P.bf_off[gl.j]),
+                                                              (long long)H * W)
+                                      : encode_level_tmap(&t.tmap, reinterpret_cast<const uint16_t *>(base + P.bf_off[gl.j]),
+                                                          (long long)H * W);
+                if (!ok) return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
                 if (P.split && !encode_level_tmap(&t.tmap_lo, reinterpret_cast<const uint16_t *>(base + P.bf_lo_off[gl.j]),
                                                   (long long)H * W))
                     return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
@@ -419,6 +424,33 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
     return TDPM_OK;
 }
 
+// The plan's features in the tensor-core operand format (BF16 planar, with lo parts for split operands, or E4M3).
+cudaError_t launch_convert(const Plan &P, char *dblob, cudaStream_t s)
+{
+    const ConvJob *cj = reinterpret_cast<const ConvJob *>(dblob + P.conv_off);
+    return P.fp8 ? launch_to_fp8_planar(cj, P.L, P.conv_items, kFp8FeatureScale, s)
+                 : launch_to_bf16_planar(cj, P.L, P.conv_items, s);
+}
+
+// A shape group's tensor-core contraction over its m_tiles M tiles: the full correlation, or the channel stage of the
+// decomposed form, with the bank of the plan's operand format (FP8 results rescaled by the two per-tensor scales).
+cudaError_t launch_group_tc(const Plan &P, const Group &g, const TcJob *jobs, int nj, int m_tiles, int nt, int *err,
+                            cudaStream_t s)
+{
+    if (P.dec) {
+        if (P.fp8)
+            return launch_corr_tc(jobs, nj, m_tiles, g.d_C_fp8, nullptr, g.R, g.Rpad_tc, nt, 1, 1, 1, err, s, true,
+                                  1.f / (g.C_fp8_scale * kFp8FeatureScale));
+        return launch_corr_tc(jobs, nj, m_tiles, g.d_C_tc, P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, nt, 1, 1,
+                              1, err, s);
+    }
+    if (P.fp8)
+        return launch_corr_tc(jobs, nj, m_tiles, g.d_filt_fp8, nullptr, g.K, g.Npad_tc, nt, g.h, g.w, 1, err, s, true,
+                              1.f / (g.fp8_scale * kFp8FeatureScale));
+    return launch_corr_tc(jobs, nj, m_tiles, g.d_filt_tc, P.split ? g.d_filt_tc_lo : nullptr, g.K, g.Npad_tc, nt, g.h,
+                          g.w, 1, err, s);
+}
+
 cudaEvent_t prof_event(tdpm_ctx *ctx)
 {
     if (!ctx->event_pool.empty()) {
@@ -479,8 +511,8 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
     cudaError_t e = cudaMemcpyAsync(dblob, A.host, P.blob_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     if (P.bf) {
-        Prof pr(ctx, s, "to_bf16");
-        e = launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(dblob + P.conv_off), P.L, P.conv_items, s);
+        Prof pr(ctx, s, P.fp8 ? "to_fp8" : "to_bf16");
+        e = launch_convert(P, dblob, s);
         if (e != cudaSuccess) return e;
         pr.end();
     }
@@ -492,14 +524,8 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         const char *jobs = dblob + P.g_jobs_off[gi];
         if (P.bf) {
             Prof pr(ctx, gs, P.dec ? "zproj_tc" : "corr_tc");
-            if (P.dec)
-                e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_C_tc,
-                                   P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, P.g_nt[gi], 1, 1, 1, ctx->d_err,
-                                   gs);
-            else
-                e = launch_corr_tc(reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], g.d_filt_tc,
-                                   P.split ? g.d_filt_tc_lo : nullptr, g.K, g.Npad_tc, P.g_nt[gi], g.h, g.w, 1,
-                                   ctx->d_err, gs);
+            e = launch_group_tc(P, g, reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], P.g_nt[gi], ctx->d_err,
+                                gs);
             if (e != cudaSuccess) return e;
             pr.end();
         } else if (P.dec) {
@@ -578,12 +604,12 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
 // caller's stream, before its first real enqueue (whose launches then overwrite every output). The choice is cached in
 // the context per shape class: (launch kind, N, K blocks, split operands, M tiles rounded up to a power of two), so
 // later plans of the same class (other images, a server's batches) reuse it without timing.
-std::string tune_key(const char *kind, int N, int kblocks, bool split, int m_tiles)
+std::string tune_key(const char *kind, int N, int kblocks, const char *operands, int m_tiles)
 {
     int b = 1;
     while (b < m_tiles) b <<= 1;
-    return std::string(kind) + ":" + std::to_string(N) + ":" + std::to_string(kblocks) + ":" + (split ? "x3" : "x1") +
-           ":" + std::to_string(b);
+    return std::string(kind) + ":" + std::to_string(N) + ":" + std::to_string(kblocks) + ":" + operands + ":" +
+           std::to_string(b);
 }
 
 cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, const Arena &A, cudaStream_t s)
@@ -616,7 +642,7 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, const Arena &A
             staged = true;
             cudaError_t r = cudaMemcpyAsync(dblob, A.host, P.blob_bytes, cudaMemcpyHostToDevice, s);
             if (r == cudaSuccess)
-                r = launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(dblob + P.conv_off), P.L, P.conv_items, s);
+                r = launch_convert(P, dblob, s);
             if (r != cudaSuccess) return r;
         }
         int cand[4];
@@ -639,20 +665,18 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, const Arena &A
         const int nj = (int)P.glv[gi].size();
         if (!nj) continue;
         const TcJob *jobs = reinterpret_cast<const TcJob *>(dblob + P.g_jobs_off[gi]);
-        if (P.dec) {
-            e = choose(tune_key("zproj", g.R, 1, P.split, P.g_tiles[gi]), g.R, [&](int nt) {
-                return launch_corr_tc(jobs, nj, P.g_tiles[gi], g.d_C_tc, P.split ? g.d_C_tc_lo : nullptr, g.R,
-                                      g.Rpad_tc, nt, 1, 1, 1, ctx->d_err, s);
-            }, &P.g_nt[gi]);
-        } else {
-            e = choose(tune_key("corr", g.K, g.h * g.w, P.split, P.g_tiles[gi]), g.K, [&](int nt) {
-                return launch_corr_tc(jobs, nj, P.g_tiles[gi], g.d_filt_tc, P.split ? g.d_filt_tc_lo : nullptr, g.K,
-                                      g.Npad_tc, nt, g.h, g.w, 1, ctx->d_err, s);
-            }, &P.g_nt[gi]);
-        }
+        const char *op = P.fp8 ? "f8" : P.split ? "x3" : "x1";
+        if (P.dec)
+            e = choose(tune_key("zproj", g.R, 1, op, P.g_tiles[gi]), g.R,
+                       [&](int nt) { return launch_group_tc(P, g, jobs, nj, P.g_tiles[gi], nt, ctx->d_err, s); },
+                       &P.g_nt[gi]);
+        else
+            e = choose(tune_key("corr", g.K, g.h * g.w, op, P.g_tiles[gi]), g.K,
+                       [&](int nt) { return launch_group_tc(P, g, jobs, nj, P.g_tiles[gi], nt, ctx->d_err, s); },
+                       &P.g_nt[gi]);
         if (e == cudaSuccess && P.rec_tc(g)) {
             const TcJob *rj = reinterpret_cast<const TcJob *>(dblob + P.g_rec_off[gi]);
-            e = choose(tune_key("recomb", g.K, g.Upad / FD, P.split, P.g_rec_tiles[gi]), g.K, [&](int nt) {
+            e = choose(tune_key("recomb", g.K, g.Upad / FD, P.split ? "x3" : "x1", P.g_rec_tiles[gi]), g.K, [&](int nt) {
                 return launch_corr_tc(rj, nj, P.g_rec_tiles[gi], g.d_lam_tc, P.split ? g.d_lam_tc_lo : nullptr, g.K,
                                       g.Npad_lam, nt, 1, 1, g.Upad / FD, ctx->d_err, s);
             }, &P.g_rec_nt[gi]);
@@ -916,8 +940,7 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
     if (!ctx || !pyrs || !scores_id) return fail(TDPM_ERR_ARG, "NULL argument");
     if (n_images < 1 || n_images > 4096) return fail(TDPM_ERR_ARG, "n_images must be in [1, 4096]");
     if (form != TDPM_FORM_FULL && form != TDPM_FORM_DECOMPOSED) return fail(TDPM_ERR_ARG, "bad form");
-    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16 && precision != TDPM_PREC_BF16X3)
-        return fail(TDPM_ERR_ARG, "unsupported precision (FP8 is not implemented)");
+    if (!valid_precision(precision)) return fail(TDPM_ERR_ARG, "unsupported precision");
     std::vector<const tdpm_level *> lv;
     for (int i = 0; i < n_images; ++i) {
         const tdpm_pyramid &py = pyrs[i];
@@ -1030,8 +1053,7 @@ tdpm_status tdpm_scores_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyrami
     if (!ctx || !pyrs || !bytes) return fail(TDPM_ERR_ARG, "NULL argument");
     if (n_images < 1 || n_images > 4096) return fail(TDPM_ERR_ARG, "n_images must be in [1, 4096]");
     if (form != TDPM_FORM_FULL && form != TDPM_FORM_DECOMPOSED) return fail(TDPM_ERR_ARG, "bad form");
-    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16 && precision != TDPM_PREC_BF16X3)
-        return fail(TDPM_ERR_ARG, "unsupported precision");
+    if (!valid_precision(precision)) return fail(TDPM_ERR_ARG, "unsupported precision");
     for (int i = 0; i < n_images; ++i) {
         const tdpm_pyramid &py = pyrs[i];
         if (py.n_levels <= 0 || py.n_levels > 4096 || !py.levels) return fail(TDPM_ERR_ARG, "empty pyramid");
@@ -1220,8 +1242,7 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
     if (!feat || !filt_host || !out) return fail(TDPM_ERR_ARG, "NULL argument");
     if (H <= 0 || W <= 0 || K <= 0 || h <= 0 || w <= 0 || h > 16 || w > 16 || H > 4096 || W > 4096 || K > 4096)
         return fail(TDPM_ERR_ARG, "bad sizes");
-    if (precision != TDPM_PREC_FP32 && precision != TDPM_PREC_BF16 && precision != TDPM_PREC_BF16X3)
-        return fail(TDPM_ERR_ARG, "unsupported precision");
+    if (!valid_precision(precision)) return fail(TDPM_ERR_ARG, "unsupported precision");
     if (reinterpret_cast<uintptr_t>(feat) % 16) return fail(TDPM_ERR_ARG, "feat not 16-byte aligned");
     const int Ho = H - h + 1, Wo = W - w + 1;
     if (Ho <= 0 || Wo <= 0) return TDPM_OK;
@@ -1251,49 +1272,74 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
             e = launch_corr_f32(reinterpret_cast<const CorrJob *>(db + fbytes), 1, tiles, reinterpret_cast<float *>(db),
                                 K, Kpad, h, w, s);
     } else {
-        // tensor cores: BF16 filter bank(s) and planar BF16 copies of the level; split precision adds the lo parts
-        const bool split = precision == TDPM_PREC_BF16X3;
+        // tensor cores: BF16 filter bank(s) and planar BF16 copies of the level (split precision adds the lo
+        // parts), or an E4M3 bank and an E4M3 planar copy with per-tensor scales
+        const bool split = precision == TDPM_PREC_BF16X3, fp8 = precision == TDPM_PREC_FP8;
         const int Npad = corr_tc_bank_rows(K), NT = corr_tc_default_nt(K, taps);
-        std::vector<uint16_t> fb((size_t)taps * 4 * Npad * 8, 0), fl(fb.size(), 0);
-        for (int k = 0; k < K; ++k)
-            for (int t = 0; t < taps; ++t)
-                for (int c = 0; c < FD; ++c) {
-                    const float x = filt_host[((size_t)k * taps + t) * FD + c];
-                    const size_t i = (((size_t)t * 4 + c / 8) * Npad + k) * 8 + (c % 8);
-                    fb[i] = bf16_bits(x);
-                    fl[i] = bf16_bits(x - bf16_round(x));
-                }
+        std::vector<uint16_t> fb, fl;
+        std::vector<uint8_t> f8;
+        float fscale = 1.f;
+        if (fp8) {
+            float mx = 0.f;
+            for (size_t i = 0; i < (size_t)K * taps * FD; ++i) mx = std::max(mx, std::fabs(filt_host[i]));
+            fscale = mx > 0.f ? 448.f / mx : 1.f;
+            f8.assign((size_t)taps * 2 * Npad * 16, 0);
+            for (int k = 0; k < K; ++k)
+                for (int t = 0; t < taps; ++t)
+                    for (int c = 0; c < FD; ++c)
+                        f8[(((size_t)t * 2 + c / 16) * Npad + k) * 16 + (c % 16)] =
+                            e4m3_bits(filt_host[((size_t)k * taps + t) * FD + c] * fscale);
+        } else {
+            fb.assign((size_t)taps * 4 * Npad * 8, 0);
+            fl.assign(fb.size(), 0);
+            for (int k = 0; k < K; ++k)
+                for (int t = 0; t < taps; ++t)
+                    for (int c = 0; c < FD; ++c) {
+                        const float x = filt_host[((size_t)k * taps + t) * FD + c];
+                        const size_t i = (((size_t)t * 4 + c / 8) * Npad + k) * 8 + (c % 8);
+                        fb[i] = bf16_bits(x);
+                        fl[i] = bf16_bits(x - bf16_round(x));
+                    }
+        }
         const long long cells = (long long)H * W;
-        const size_t fbytes = align256(sizeof(uint16_t) * fb.size());
-        const size_t pbytes = align256(sizeof(uint16_t) * (size_t)cells * FD);
+        const size_t fbytes = align256(fp8 ? f8.size() : sizeof(uint16_t) * fb.size());
+        const size_t pbytes = align256((fp8 ? 1 : sizeof(uint16_t)) * (size_t)cells * FD);
         const size_t parts = split ? 2 : 1;
         CUDA_TRY(cudaMalloc(&dmem, parts * (fbytes + pbytes) + align256(sizeof(ConvJob)) + sizeof(TcJob) + 256));
         char *db = reinterpret_cast<char *>(dmem);
-        uint16_t *bank = reinterpret_cast<uint16_t *>(db);
-        uint16_t *bank_lo = split ? reinterpret_cast<uint16_t *>(db + fbytes) : nullptr;
+        void *bank = db;
+        void *bank_lo = split ? db + fbytes : nullptr;
         uint16_t *planar = reinterpret_cast<uint16_t *>(db + parts * fbytes);
         uint16_t *planar_lo = split ? reinterpret_cast<uint16_t *>(db + parts * fbytes + pbytes) : nullptr;
         char *cjd = db + parts * (fbytes + pbytes), *tjd = cjd + align256(sizeof(ConvJob));
         int *d_err = reinterpret_cast<int *>(tjd + align256(sizeof(TcJob)));
         ConvJob cj{feat, planar, planar_lo, cells, 0};
         TcJob tj{};
-        if (!encode_level_tmap(&tj.tmap, planar, cells) || (split && !encode_level_tmap(&tj.tmap_lo, planar_lo, cells))) {
+        const bool ok = fp8 ? encode_level_tmap_fp8(&tj.tmap, reinterpret_cast<const uint8_t *>(planar), cells)
+                            : encode_level_tmap(&tj.tmap, planar, cells) &&
+                                  (!split || encode_level_tmap(&tj.tmap_lo, planar_lo, cells));
+        if (!ok) {
             cudaFree(dmem);
             return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
         }
         tj.out = out; tj.H = H; tj.W = W; tj.Ho = Ho; tj.Wo = Wo; tj.begin = 0;
         const long long span = (long long)(Ho - 1) * W + Wo;
         const int tiles = (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m());
-        e = cudaMemcpyAsync(bank, fb.data(), sizeof(uint16_t) * fb.size(), cudaMemcpyHostToDevice, s);
+        if (fp8)
+            e = cudaMemcpyAsync(bank, f8.data(), f8.size(), cudaMemcpyHostToDevice, s);
+        else
+            e = cudaMemcpyAsync(bank, fb.data(), sizeof(uint16_t) * fb.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && split)
             e = cudaMemcpyAsync(bank_lo, fl.data(), sizeof(uint16_t) * fl.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(cjd, &cj, sizeof(cj), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tjd, &tj, sizeof(tj), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
-        if (e == cudaSuccess) e = launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(cjd), 1, 4 * cells, s);
+        if (e == cudaSuccess)
+            e = fp8 ? launch_to_fp8_planar(reinterpret_cast<const ConvJob *>(cjd), 1, 2 * cells, kFp8FeatureScale, s)
+                    : launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(cjd), 1, 4 * cells, s);
         if (e == cudaSuccess)
             e = launch_corr_tc(reinterpret_cast<const TcJob *>(tjd), 1, tiles, bank, bank_lo, K, Npad, NT, h, w, 1,
-                               d_err, s);
+                               d_err, s, fp8, fp8 ? 1.f / (fscale * kFp8FeatureScale) : 1.f);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(dmem);

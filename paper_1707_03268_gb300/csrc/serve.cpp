@@ -326,8 +326,7 @@ tdpm_status tdpm_submit(tdpm_ctx *ctx, const tdpm_request *req, uint64_t *ticket
     if (req->n_models < 1 || req->n_models > TDPM_MAX_REQUEST_MODELS)
         return fail(TDPM_ERR_ARG, "n_models must be in [1, TDPM_MAX_REQUEST_MODELS]");
     if (req->form != TDPM_FORM_FULL && req->form != TDPM_FORM_DECOMPOSED) return fail(TDPM_ERR_ARG, "bad form");
-    if (req->precision != TDPM_PREC_FP32 && req->precision != TDPM_PREC_BF16 && req->precision != TDPM_PREC_BF16X3)
-        return fail(TDPM_ERR_ARG, "unsupported precision");
+    if (!valid_precision(req->precision)) return fail(TDPM_ERR_ARG, "unsupported precision");
     if (std::isnan(req->tau)) return fail(TDPM_ERR_ARG, "tau is NaN");
     const tdpm_pyramid &py = *req->pyramid;
     if (py.n_levels <= 0 || py.n_levels > 4096 || !py.levels) return fail(TDPM_ERR_ARG, "empty pyramid");

@@ -281,3 +281,95 @@ def test_autotuned_tiling_matches_default_tiling(torch, T, form, monkeypatch):
         T.tdpm_destroy(c)
     for a, b in zip(*out):
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-6 * max(1.0, float(np.max(np.abs(b)))))
+
+
+# ------------------------------------------------------------------------------------------------- FP8 precision
+FP8_FEATURE_SCALE = np.float32(448.0) / np.float32(0.2)
+
+
+def e4m3(a, scale, torch):
+    """x -> e4m3(x * scale) / scale, the rounding torch applies for float8_e4m3fn (FP32 products, as on the GPU)."""
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)) * float(scale)
+    return (t.to(torch.float8_e4m3fn).float() / float(scale)).numpy().astype(np.float64)
+
+
+def bank_scale(filt):
+    return np.float32(448.0) / np.float32(np.max(np.abs(filt)))
+
+
+@pytest.mark.parametrize("H,W,h,w,K", [(13, 29, 6, 6, 3), (60, 80, 6, 6, 48), (9, 17, 5, 11, 70), (50, 37, 1, 1, 384),
+                                       (23, 45, 6, 6, 257)])
+def test_correlate_fp8_matches_rounded_operands(torch, T, H, W, h, w, K):
+    """E4M3 operands with per-tensor scales (features 448/0.2, filters 448/max|f|) on kind::f8f6f4 tensor cores: the
+    products are exact in FP32, so the result matches the oracle on the rounded operands to FP32 summation error.
+    Against the unrounded operands the error is that of 3-bit mantissas (reported, not a bar)."""
+    rng = np.random.default_rng(H * 1000 + W * 10 + K + 17)
+    feat = rng.uniform(0, 0.2, size=(H, W, 32)).astype(np.float32)
+    filt = rng.normal(0, 0.05, size=(K, h, w, 32)).astype(np.float32)
+    out = torch.full((K, H - h + 1, W - w + 1), float("nan"), device="cuda")
+    T.tdpm_correlate(torch.from_numpy(feat).cuda(), filt, out, precision=T.PREC_FP8)
+    got = out.cpu().numpy()
+    assert np.isfinite(got).all()
+    fq, kq = e4m3(feat, FP8_FEATURE_SCALE, torch), e4m3(filt, bank_scale(filt), torch)
+    worst = 0.0
+    for k in range(K):
+        assert rel_err(got[k], orc.correlate(fq, kq[k])) <= 1e-5, k
+        worst = max(worst, rel_err(got[k], orc.correlate(feat, filt[k])))
+    assert worst < 0.2
+
+
+def _fp8_model(model, torch):
+    """The model with every shape group's filters rounded as the library's E4M3 banks round them."""
+    groups = {}
+    for c in model.components:
+        groups.setdefault((0,) + c.root.shape[:2], []).append(c.root)
+        for p in c.parts:
+            groups.setdefault((1,) + p.filt.shape[:2], []).append(p.filt)
+    scale = {k: bank_scale(np.stack(v)) for k, v in groups.items()}
+    comps = []
+    for c in model.components:
+        parts = [synth.Part(filt=e4m3(p.filt, scale[(1,) + p.filt.shape[:2]], torch), anchor=p.anchor, deform=p.deform)
+                 for p in c.parts]
+        comps.append(synth.Component(root=e4m3(c.root, scale[(0,) + c.root.shape[:2]], torch), parts=parts,
+                                     bias=c.bias))
+    return synth.Model(comps)
+
+
+def test_full_fp8_end_to_end(torch, T, ctx):
+    """The whole path with the full form on FP8 tensor cores, against the oracle on the rounded operands; the
+    agreement with the FP64 scores of the unrounded model is reported by the benchmark."""
+    wl = synth.config_c2()
+    pyr = wl.pyramids[0]
+    mid = T.tdpm_load_model(ctx, wl.model)
+    sid = T.tdpm_build_pyramid_scores(ctx, mid, device_pyramid(pyr, torch), T.FORM_FULL, T.PREC_FP8)
+    rounded = synth.Pyramid([e4m3(l, FP8_FEATURE_SCALE, torch).astype(np.float32) for l in pyr.levels], pyr.lam)
+    ref = orc.score_pyramid(_fp8_model(wl.model, torch), rounded)
+    for m in ref:
+        got = T.tdpm_get_maps(ctx, sid, T.MAP_FINAL_SCORE, m["component"], m["level"])
+        assert rel_err(got, m["score"]) <= 1e-4
+    tau = float(np.percentile(orc.all_scores(ref), 99))
+    assert agreement(det_keys(T.tdpm_detect(ctx, sid, tau)), det_keys(orc.detect(ref, tau))) >= 0.995
+    T.tdpm_release(ctx, sid)
+
+
+def test_decomposed_fp8_channel_stage(torch, T, ctx):
+    """Decomposed form with the channel stage on FP8 tensor cores (E4M3 features and c_r); 1-D passes in FP32."""
+    wl = synth.config_c2()
+    pyr = wl.pyramids[0]
+    mid = T.tdpm_load_model(ctx, wl.model)
+    T.tdpm_decompose(ctx, mid, 8, T.DECOMP_PER_FILTER, max_iters=60, seed=3)
+    sid = T.tdpm_build_pyramid_scores(ctx, mid, device_pyramid(pyr, torch), T.FORM_DECOMPOSED, T.PREC_FP8)
+    n_f, n_g = T.tdpm_model_info(ctx, mid)
+    filters = [None] * n_f
+    for g in range(n_g):
+        info = T.tdpm_group_info(ctx, mid, g)
+        A, B, C, Lam = T.tdpm_get_factors(ctx, mid, g)
+        Cq = e4m3(C.T.astype(np.float32), bank_scale(C.astype(np.float32)), torch).T
+        F = orc.joint_reconstruct(Lam, A, B, Cq)
+        for k, fid in enumerate(info["filter_ids"]):
+            filters[fid] = F[k]
+    rounded = synth.Pyramid([e4m3(l, FP8_FEATURE_SCALE, torch).astype(np.float32) for l in pyr.levels], pyr.lam)
+    for m in orc.score_pyramid(wl.model, rounded, filters=filters):
+        got = T.tdpm_get_maps(ctx, sid, T.MAP_FINAL_SCORE, m["component"], m["level"])
+        assert rel_err(got, m["score"]) <= 1e-4
+    T.tdpm_release(ctx, sid)
