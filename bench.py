@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--precision", default=None, choices=sorted(PRECISIONS))
     ap.add_argument("--rank", type=int, default=None, help="CP rank per filter (per_filter) or per shape group (joint)")
     ap.add_argument("--mode", default=None, choices=["per_filter", "joint"])
+    ap.add_argument("--variants", default=None,
+                    help="c3/c4: comma-separated subset of the variants to run, e.g. full_bf16,full_fp8")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="c5: length of the arrival stream")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="c5: mean arrival rate (requests/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -202,6 +204,30 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
                 out["dt"][0] += Hs * Ws * 4 + 2 * (Hs * X * 8) + Y * X * 8
             out["assemble"][0] += Y * X * 4 * (n + 2)
     return {k: {"bytes": v[0], "flops": v[1]} for k, v in out.items()}
+
+
+def measured_traffic(workload: str, form: str, precision: str, mode: str, stage: str):
+    """DRAM bytes per image of a stage from the committed ncu capture of the same configuration
+    (profiles/roofline_traffic.json), or None when there is none or when a kernel source it was measured on has changed
+    since (its SHA-256 no longer matches)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            table = json.load(f)
+    except Exception:
+        return None
+    cfg = table.get("configs", {}).get(f"{workload}:{form}:{precision}:{mode}", {})
+    e = cfg.get(stage)
+    if not e:
+        return None
+    for path, sha in e.get("sources", {}).items():
+        try:
+            with open(os.path.join(ROOT, path), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != sha:
+                    return None
+        except OSError:
+            return None
+    return e.get("dram_bytes_per_image")
 
 
 def fp32_alu_peak_tflops(sm_mhz: float) -> float:
@@ -398,6 +424,14 @@ def run_bank(args):
             args.mode if args.form == "decomposed" else None)
     if head not in variants:
         variants.append(head)
+
+    def vlabel(v):
+        return f"{v[0]}_{v[1]}" + (f"_{v[3]}_r{v[2]}" if v[2] else "")
+    if args.variants:
+        keep = set(args.variants.split(","))
+        variants = [v for v in variants if vlabel(v) in keep]
+        if variants and head not in variants:
+            head = variants[0]
     rng = np.random.default_rng(0)
     filters = wl.model.filters()
     sample_maps = [(int(rng.integers(0, len(filters))), None) for _ in range(12)]
@@ -422,7 +456,7 @@ def run_bank(args):
         stages = {n: ms for n, (ms, _) in tdpm.tdpm_profile_read(ctx).items()}
         if ref_keys is None:
             ref_keys = k
-        label = f"{form_s}_{prec_s}" + (f"_{mode}_r{r}" if r else "")
+        label = vlabel((form_s, prec_s, r, mode))
         # error of sampled filter maps (image 0) against the FP64 oracle: the exact filters, and for the decomposed
         # form also the filters rebuilt from the library's factors (parity of the arithmetic, same factors)
         sid = tdpm.tdpm_build_batch_scores(ctx, mid, dps[:1], form, prec, stream)
@@ -450,7 +484,7 @@ def run_bank(args):
                           "max_rel_error_vs_fp64_exact_filters": err_exact,
                           "max_rel_error_vs_fp64_same_factors": err_same if rebuilt is not None else None,
                           "stages_ms_per_step": stages, "decomposition_report": rep}
-    hl = f"{head[0]}_{head[1]}" + (f"_{head[3]}_r{head[2]}" if head[2] else "")
+    hl = vlabel(head)
     h = results[hl]
     line = {"metric": METRIC, "value": h["images_per_s"], "unit": "images/s", "n_gpus": 1, "steps": steps,
             "warmup": warmup, "ms_per_step": None, "p50_ms": h["p50_ms_per_step"], "p99_ms": h["p99_ms_per_step"],
@@ -669,6 +703,8 @@ def main():
     sm_mhz = (clk or {}).get("sm_mhz") or 1920.0
     rooflines = {name: stage_roofline(name, ms / n_prof, n / n_prof, model, peaks, sm_mhz)
                  for name, (ms, n) in stages.items() if name in model}
+    for name, r in rooflines.items():
+        r["traffic"] = measured_traffic(args.workload, args.form, args.precision, args.mode, name)
     dom_name = max(stages.items(), key=lambda kv: kv[1][0])[0]
     roofline = rooflines.get(dom_name)
 
