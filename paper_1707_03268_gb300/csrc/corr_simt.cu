@@ -307,32 +307,27 @@ __global__ void __launch_bounds__(SQ_THREADS) sep_kernel(const SepJob *__restric
     }
 }
 
-// Per-filter mode, warp form (no shared memory, no block barrier). A warp owns one filter k and a block of SW_ROWS
-// output rows x (32 - (w-1)) output columns. Lane l owns column x0 + l: for each term it loads the block's
-// SW_ROWS + h - 1 values of Z_r in that column at once (independent loads), forms T_r = a_r o_y Z_r row by row from
-// registers, takes T_r at columns x .. x+w-1 from lanes l .. l+w-1 by shuffles for the x pass, and accumulates
-// lambda_r U_r in registers across the filter's terms. The loads of term r+1 are issued before term r is computed,
-// so one memory latency is hidden behind each term's arithmetic. The multiply-add order (dy ascending, then dx
-// ascending, then the terms) is that of sep_kernel, so both give identical results.
-constexpr int SW_ROWS = 16, SW_WARPS = 8;
+// Per-filter mode, warp form (no block barrier). A warp owns one filter k and a block of SW_ROWS output rows x
+// (32 - (w-1)) output columns. For each of the filter's terms, lane l copies the block's SW_ROWS + h - 1 values of Z_r
+// in column x0 + l into the warp's own shared-memory buffer with cp.async (double-buffered: term r+1 is in flight while
+// term r is computed; the waits are per warp). The y pass slides an h-deep window down the column (one shared load
+// per row), the x pass takes T_r at columns x .. x+w-1 from lanes l .. l+w-1 by shuffles, and lambda_r U_r
+// accumulates in registers across the filter's terms. The multiply-add order (dy ascending, then dx ascending, then
+// the terms) is that of sep_kernel, so both give identical results.
+constexpr int SW_ROWS = 8, SW_WARPS = 4;
 
 template <int HH, int WW>
-struct SepTerm {
-    float a[HH], b[WW], l;
-    float z[SW_ROWS + HH - 1];
-};
-
-template <int HH, int WW>
-__global__ void __launch_bounds__(SW_WARPS * 32, 2) sep_warp_kernel(const SepJob *__restrict__ jobs, int n_jobs,
-                                                                 long long total, const float *__restrict__ A,
-                                                                 const float *__restrict__ B,
-                                                                 const float *__restrict__ lam,
-                                                                 const int *__restrict__ rank_off, int K, int R)
+__global__ void __launch_bounds__(SW_WARPS * 32, 7) sep_warp_kernel(const SepJob *__restrict__ jobs, int n_jobs,
+                                                                long long total, const float *__restrict__ A,
+                                                                const float *__restrict__ B,
+                                                                const float *__restrict__ lam,
+                                                                const int *__restrict__ rank_off, int K, int R)
 {
     constexpr int SW = 32 - (WW - 1);  // output columns per warp
     constexpr int NZ = SW_ROWS + HH - 1;
-    const int lane = threadIdx.x & 31;
-    const long long task = (long long)blockIdx.x * SW_WARPS + (threadIdx.x >> 5);
+    __shared__ float zs[SW_WARPS][2][NZ][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long task = (long long)blockIdx.x * SW_WARPS + warp;
     if (task >= total) return;
     const SepJob &J = jobs[find_job(jobs, n_jobs, task)];
     long long local = task - J.begin;
@@ -343,53 +338,64 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 2) sep_warp_kernel(const SepJob
     const int x = x0 + lane;
     const int W = J.W;
     const size_t plane = (size_t)J.H * W;
-    // Rows: output row y < Ho reads Z rows y .. y+h-1 <= H-1, so no row is out of range. Columns: a lane past the
-    // last column reads column W-1 instead; its T only reaches outputs at x >= Wo, which are not written.
+    // Rows: output row y < Ho reads Z rows y .. y+h-1 <= H-1, so no row is out of range (rows past the block's last
+    // needed row repeat it). Columns: a lane past the last column reads column W-1 instead; its T only reaches
+    // outputs at x >= Wo, which are not written.
     const int xc = x < W ? x : W - 1;
     const int n_out = min(SW_ROWS, J.Ho - y0), n_in = n_out + HH - 1;  // output rows, Z rows of the block
     const float *zbase = J.Z + (size_t)y0 * W + xc;
-    float acc[SW_ROWS];
-#pragma unroll
-    for (int i = 0; i < SW_ROWS; ++i) acc[i] = 0.f;
-
-    auto load = [&](SepTerm<HH, WW> &t, int r) {
-#pragma unroll
-        for (int i = 0; i < HH; ++i) t.a[i] = __ldg(A + (size_t)i * R + r);
-#pragma unroll
-        for (int i = 0; i < WW; ++i) t.b[i] = __ldg(B + (size_t)i * R + r);
-        t.l = __ldg(lam + r);
+    float(*buf)[NZ][32] = zs[warp];
+    auto issue = [&](int r, int b) {
         const float *zp = zbase + (size_t)r * plane;
         // an opaque copy of the row stride: the row offsets are recomputed per term, not held live across the loop
         int ws = W;
         asm volatile("" : "+r"(ws));
+        // a running row pointer: each address depends on the previous one, so none is precomputed and held
 #pragma unroll
-        for (int i = 0; i < NZ; ++i) t.z[i] = __ldg(zp + min(i, n_in - 1) * ws);  // rows past the block: repeats
+        for (int i = 0; i < NZ; ++i) {
+            cp_async_f32(&buf[b][i][lane], zp, true);
+            if (i < n_in - 1) zp += ws;
+        }
+        cp_async_commit();
     };
-    auto run = [&](const SepTerm<HH, WW> &t) {
+    float acc[SW_ROWS];
+#pragma unroll
+    for (int i = 0; i < SW_ROWS; ++i) acc[i] = 0.f;
+    const int r_begin = rank_off[k], r_end = rank_off[k + 1];
+    if (r_begin < r_end) issue(r_begin, 0);
+    for (int r = r_begin; r < r_end; ++r) {
+        const int b = (r - r_begin) & 1;
+        float a[HH], bb[WW];
+#pragma unroll
+        for (int i = 0; i < HH; ++i) a[i] = __ldg(A + (size_t)i * R + r);
+#pragma unroll
+        for (int i = 0; i < WW; ++i) bb[i] = __ldg(B + (size_t)i * R + r);
+        const float l = __ldg(lam + r);
+        if (r + 1 < r_end) {
+            issue(r + 1, b ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        const float(*z)[32] = buf[b];
+        float win[HH];
+#pragma unroll
+        for (int i = 0; i < HH - 1; ++i) win[i] = z[i][lane];
 #pragma unroll
         for (int i = 0; i < SW_ROWS; ++i) {
             if (i < n_out) {  // warp-uniform
+                win[(i + HH - 1) % HH] = z[i + HH - 1][lane];
                 float tv = 0.f;
 #pragma unroll
-                for (int dy = 0; dy < HH; ++dy) tv = fmaf(t.a[dy], t.z[i + dy], tv);
+                for (int dy = 0; dy < HH; ++dy) tv = fmaf(a[dy], win[(i + dy) % HH], tv);
                 float u = 0.f;
 #pragma unroll
-                for (int dx = 0; dx < WW; ++dx) u = fmaf(t.b[dx], dx ? __shfl_down_sync(0xffffffffu, tv, dx) : tv, u);
-                acc[i] = fmaf(t.l, u, acc[i]);
+                for (int dx = 0; dx < WW; ++dx) u = fmaf(bb[dx], dx ? __shfl_down_sync(0xffffffffu, tv, dx) : tv, u);
+                acc[i] = fmaf(l, u, acc[i]);
             }
         }
-    };
-
-    const int r_begin = rank_off[k], r_end = rank_off[k + 1];
-    SepTerm<HH, WW> t0, t1;
-    if (r_begin < r_end) load(t0, r_begin);
-    for (int r = r_begin; r < r_end; r += 2) {
-        if (r + 1 < r_end) load(t1, r + 1);
-        run(t0);
-        if (r + 1 < r_end) {
-            if (r + 2 < r_end) load(t0, r + 2);
-            run(t1);
-        }
+        __syncwarp();  // every lane is done with buffer b before it is refilled (two terms later)
     }
     if (lane >= SW || x >= J.Wo) return;
     float *o = J.out + (size_t)k * J.Ho * J.Wo + x;
