@@ -290,11 +290,13 @@ tdpm_status tdpm_profile_reset(tdpm_ctx *ctx);
 
 /* Tile shapes picked by the context's autotuner (not in the paper). The first build of a new plan times the N tile
  * widths its tensor-core launches may use on the plan's own inputs and keeps the fastest per shape class; set the
- * environment variable TDPM_AUTOTUNE=0 before tdpm_create to use the untuned defaults. Entry `index`: its shape class
- * ("kind:N:K blocks:operands:M tiles", NUL-terminated, truncated to key_cap) and the chosen width; *n_entries
+ * environment variable TDPM_AUTOTUNE=0 before tdpm_create to use the untuned defaults. The candidates are every
+ * balanced N tile width in two kernel forms: one CTA per tile, or persistent CTAs with two TMEM accumulators (the
+ * epilogue of one tile overlapping the MMAs of the next). Entry `index`: its shape class ("kind:N:K blocks:
+ * operands:M tiles", NUL-terminated, truncated to key_cap), the chosen width and form (1 = persistent); *n_entries
  * receives the number of entries (an index out of range only sets it). */
 tdpm_status tdpm_autotune_read(tdpm_ctx *ctx, int32_t index, char *key, size_t key_cap, int32_t *tile_n,
-                               int32_t *n_entries);
+                               int32_t *persistent, int32_t *n_entries);
 
 /* ================================================================================ serving (continuous batching) */
 /* Not in the paper: a request loop around the scoring path. A server thread owned by the context takes submitted

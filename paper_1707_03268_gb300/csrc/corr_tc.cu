@@ -28,8 +28,6 @@ namespace tdpm {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 128;
-constexpr int TC_STAGES = 4;
 constexpr uint32_t A_PLANE_BYTES = TC_M * 16;  // one 8-channel chunk of 128 cells
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -53,6 +51,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase)
         : "r"(bar), "r"(phase)
         : "memory");
     return ok != 0;
+}
+
+// Wait for the phase with `parity` to complete, ignoring the error flag; gives up after ~2^28 cycles. Used only to let
+// a CTA's own copies land before it exits.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1ll << 28)) return;
 }
 
 // Wait for the phase with `parity` to complete. Gives up after ~2^30 cycles (about half a second), raising *err;
@@ -155,7 +162,200 @@ __device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
     return lo;
 }
 
-// grid: one CTA per (M tile, N tile), M tiles numbered across the jobs (a job's begin is its first M tile), so the job
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// A tile is one (M tile, N tile) pair; M tiles are numbered across the jobs (a job's begin is its first M tile), so
+// the job tables do not depend on the N tiling.
+struct TileRef {
+    const TcJob *J;
+    int p0, n0;
+};
+
+__device__ __forceinline__ TileRef tile_ref(const TcJob *jobs, int n_jobs, int tile, int n_tiles_n, int NT)
+{
+    const int nt = tile % n_tiles_n, mg = tile / n_tiles_n;
+    const TcJob *J = jobs + find_job(jobs, n_jobs, mg);
+    return TileRef{J, (mg - J->begin) * TC_M, nt * NT};
+}
+
+// Persistent: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... with three roles.
+//   warp 0 lane 0  producer: per tap of every tile, one TMA box of the input (128 cells x one tap's 32 channels) and
+//                  the tap's N-tile slice of the bank (1-D bulk copies), into a ring of `stages` shared-memory slots
+//                  that runs on across tile boundaries;
+//   warp 1 lane 0  MMA issuer: the tile's taps into one of two TMEM accumulators (tiles alternate), then a commit that
+//                  hands the accumulator to the epilogue;
+//   warps 2..      epilogue (TC_EPI warps): drain the accumulator with 32x32b loads (warp w reads TMEM lanes
+//                  32 (w % 4) .. +31; the TC_EPI / 4 warps of one quadrant split its columns in 16-column chunks)
+//                  and store rows of the output maps, then hand the accumulator back; it overlaps the next tile's
+//                  MMAs.
+// filt: [h*w*cb][CHUNKS][ld][16 bytes] (tap-major, then channel block); NT = N tile width (multiple of 16, <= 256);
+// the input has 32*cb channels in CHUNKS*cb planar 16-byte chunks.
+// SPLIT: operands come as hi and lo BF16 parts (filt_lo, the job's tmap_lo) and every K step issues three MMAs,
+// hi*hi + hi*lo + lo*hi, into the same FP32 accumulator.
+// FP8: E4M3 operands, 32 channels = 32 bytes = two 16-byte chunks per tap ([2][cells][16] planar input, bank
+// [taps][2][ld][16]); one kind::f8f6f4 MMA (K = 32) per tap; the epilogue multiplies by `scale` (the inverse of the
+// product of the two per-tensor scales).
+constexpr int TC_EPI = 16;                      // epilogue warps (a multiple of 4)
+constexpr int TC_THREADS_P = 64 + 32 * TC_EPI;
+
+template <bool SPLIT, bool FP8>
+__global__ void __launch_bounds__(TC_THREADS_P, 1) corr_tc_persistent_kernel(const TcJob *__restrict__ jobs, int n_jobs,
+                                                                  int total_tiles, const uint8_t *__restrict__ filt,
+                                                                  const uint8_t *__restrict__ filt_lo, int K, int ld,
+                                                                  int NT, int n_tiles_n, int h, int w, int cb,
+                                                                  uint32_t acc_cols, int stages, float scale, int *err)
+{
+    static_assert(!(SPLIT && FP8), "split operands are BF16");
+    extern __shared__ __align__(1024) uint8_t sm[];
+    constexpr uint32_t NPART = SPLIT ? 2 : 1;
+    constexpr int CHUNKS = FP8 ? 2 : 4;                              // 16-byte K chunks per tap
+    constexpr uint32_t A_BYTES = TC_M * 16 * CHUNKS;                  // one tap of A
+    const uint32_t b_part_bytes = (uint32_t)NT * 16 * CHUNKS;
+    const uint32_t a_stage_bytes = NPART * A_BYTES, b_stage_bytes = NPART * b_part_bytes;
+    uint8_t *a_smem = sm;
+    uint8_t *b_smem = sm + stages * a_stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + stages * b_stage_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 4);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + stages);
+    const uint32_t acc_full0 = smem_u32(bars + 2 * stages), acc_empty0 = smem_u32(bars + 2 * stages + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int taps = h * w * cb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full0 + 8 * b, 1);
+            mbar_init(acc_empty0 + 8 * b, 32 * TC_EPI);  // every epilogue thread arrives
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * acc_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        int g = 0;
+        for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+            const TileRef T = tile_ref(jobs, n_jobs, tile, n_tiles_n, NT);
+            const int W = T.J->W;
+            for (int t = 0; t < taps; ++t, ++g) {
+                const int s = g % stages;
+                if (g >= stages) mbar_wait(empty0 + 8 * s, ((g / stages) - 1) & 1, err);
+                const uint32_t full = full0 + 8 * s;
+                mbar_expect_tx(full, a_stage_bytes + b_stage_bytes);
+                const int ts = t / cb, blk = t - ts * cb;
+                const int dy = ts / w, dx = ts - dy * w;
+                const uint32_t adst = smem_u32(a_smem + s * a_stage_bytes);
+                tma_load_3d(adst, &T.J->tmap, 0, T.p0 + dy * W + dx, CHUNKS * blk, full);
+                if (SPLIT) tma_load_3d(adst + A_BYTES, &T.J->tmap_lo, 0, T.p0 + dy * W + dx, CHUNKS * blk, full);
+                const uint32_t bdst = smem_u32(b_smem + s * b_stage_bytes);
+                for (int kc = 0; kc < CHUNKS; ++kc) {
+                    const size_t off = (((size_t)t * CHUNKS + kc) * ld + T.n0) * 16;  // bytes
+                    bulk_load(bdst + kc * NT * 16, filt + off, (uint32_t)NT * 16, full);
+                    if (SPLIT) bulk_load(bdst + b_part_bytes + kc * NT * 16, filt_lo + off, (uint32_t)NT * 16, full);
+                }
+            }
+        }
+        // the last fill of every slot has landed before the CTA can exit (immediate unless a wait gave up)
+        for (int k = g - stages < 0 ? 0 : g - stages; k < g; ++k) mbar_drain(full0 + 8 * (k % stages), (k / stages) & 1);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: BF16, two K=16 steps per tap (channel chunks {0,1} and {2,3}); FP8, one K=32 step
+        const uint32_t idesc = FP8 ? instr_desc_e4m3(TC_M, NT) : instr_desc(TC_M, NT);
+        int g = 0, li = 0;
+        for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++li) {
+            const int b = li & 1;
+            if (li >= 2) mbar_wait(acc_empty0 + 8 * b, ((li >> 1) - 1) & 1, err);  // epilogue done with it
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + (uint32_t)b * acc_cols;
+            for (int t = 0; t < taps; ++t, ++g) {
+                const int s = g % stages;
+                mbar_wait(full0 + 8 * s, (g / stages) & 1, err);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a_base = smem_u32(a_smem + s * a_stage_bytes);
+                const uint32_t b_base = smem_u32(b_smem + s * b_stage_bytes);
+                if (FP8) {
+                    const uint64_t ad = smem_desc(a_base, A_PLANE_BYTES, 128);
+                    const uint64_t bd = smem_desc(b_base, (uint32_t)NT * 16, 128);
+                    mma_e4m3(acc, ad, bd, idesc, t != 0);
+                } else {
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ad = smem_desc(a_base + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
+                        const uint64_t bd = smem_desc(b_base + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
+                        mma_bf16(acc, ad, bd, idesc, (t | ks) != 0);
+                        if (SPLIT) {
+                            const uint64_t ad_lo =
+                                smem_desc(a_base + A_BYTES + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
+                            const uint64_t bd_lo =
+                                smem_desc(b_base + b_part_bytes + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
+                            mma_bf16(acc, ad, bd_lo, idesc, 1u);
+                            mma_bf16(acc, ad_lo, bd, idesc, 1u);
+                        }
+                    }
+                }
+                mma_commit(empty0 + 8 * s);  // the slot is free once these MMAs have read it
+            }
+            mma_commit(acc_full0 + 8 * b);   // the accumulator is complete once every MMA has finished
+        }
+    } else if (warp >= 2) {
+        // epilogue: TMEM lane m of the accumulator holds position p0 + m; columns are the N tile's filters
+        const int q = warp & 3;              // the TMEM lane quadrant this warp may read
+        const int cg = (warp - 2) >> 2;      // its share of the columns: chunks cg, cg + TC_EPI/4, ...
+        constexpr int NCG = TC_EPI / 4;
+        int li = 0;
+        for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++li) {
+            const int b = li & 1;
+            mbar_wait(acc_full0 + 8 * b, (li >> 1) & 1, err);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const TileRef T = tile_ref(jobs, n_jobs, tile, n_tiles_n, NT);
+            const int W = T.J->W, Ho = T.J->Ho, Wo = T.J->Wo;
+            const int p = T.p0 + q * 32 + lane;
+            const int y = p / W, x = p - y * W;
+            const bool valid = (y < Ho) && (x < Wo);
+            float *out = T.J->out + (size_t)y * Wo + x;
+            const size_t plane = (size_t)Ho * Wo;
+            for (int c0 = 16 * cg; c0 < NT; c0 += 16 * NCG) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * acc_cols + (uint32_t)c0, r);
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int k = T.n0 + c0 + j;
+                        if (k < K) out[(size_t)k * plane] = FP8 ? __uint_as_float(r[j]) * scale : __uint_as_float(r[j]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(acc_empty0 + 8 * b);
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * acc_cols)
+                     : "memory");
+}
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_TILE_STAGES = 4;
+
+// Tile form: one CTA per (M tile, N tile), M tiles numbered across the jobs (a job's begin is its first M tile), so the job
 // tables do not depend on the N tiling; filt: [h*w*cb][4][ld][8] BF16 (tap-major, then channel block, ld rows per
 // plane); NT = N tile width (multiple of 16, <= 256); the input has 32*cb channels in 4*cb planar chunks.
 // SPLIT: operands come as hi and lo BF16 parts (filt_lo, the job's tmap_lo) and every K step issues three MMAs,
@@ -164,7 +364,7 @@ __device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
 // [taps][2][ld][16]); one kind::f8f6f4 MMA (K = 32) per tap; the epilogue multiplies by `scale` (the inverse of the
 // product of the two per-tensor scales).
 template <bool SPLIT, bool FP8>
-__global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_kernel(const TcJob *__restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_tile_kernel(const TcJob *__restrict__ jobs, int n_jobs,
                                                                 const uint8_t *__restrict__ filt,
                                                                 const uint8_t *__restrict__ filt_lo, int K, int ld,
                                                                 int NT, int n_tiles_n, int h, int w, int cb,
@@ -393,50 +593,104 @@ int corr_tc_bank_rows(int K)
 size_t corr_tc_smem_bytes(int NT, bool split, bool fp8, int stages)
 {
     const size_t parts = split ? 2 : 1, tap_bytes = fp8 ? 32 : 64;  // bytes of one row of one tap
-    return stages * parts * (TC_M + (size_t)NT) * tap_bytes + 8 * (2 * stages + 1) + 16;
+    return stages * parts * (TC_M + (size_t)NT) * tap_bytes + 8 * (2 * stages + 4) + 16;
 }
+
+namespace {
+int sm_count()
+{
+    static int n[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!n[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        n[dev] = v;
+    }
+    return n[dev];
+}
+}  // namespace
 
 cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const void *filt_tc, const void *filt_tc_lo,
                            int K, int ld, int NT, int h, int w, int cb, int *d_err, cudaStream_t s, bool fp8,
-                           float scale)
+                           float scale, bool persistent)
 {
     if (m_tiles <= 0 || K <= 0) return cudaSuccess;
     if (cb < 1) return cudaErrorInvalidValue;
     const bool split = filt_tc_lo != nullptr;
     if (split && fp8) return cudaErrorInvalidValue;
-    const int taps = h * w * cb;
     const int n_tiles_n = corr_tc_n_tiles(K, NT);
-    const int stages = taps < TC_STAGES ? taps : TC_STAGES;
     // every N tile's bulk copies stay inside the bank's ld rows
     if (NT % 16 != 0 || NT < 16 || NT > 256 || n_tiles_n * NT > ld) return cudaErrorInvalidValue;
     if ((long long)m_tiles * n_tiles_n > 0x7fffffffll) return cudaErrorInvalidValue;
     const int total_tiles = m_tiles * n_tiles_n;
-    uint32_t cols = 32;
-    while (cols < (uint32_t)NT) cols <<= 1;
-    // keep residency within TMEM: at most 512 / cols CTAs per SM, enforced through the shared memory request
-    const int max_ctas = 512 / (int)cols;
+    const uint8_t *fb = static_cast<const uint8_t *>(filt_tc), *fl = static_cast<const uint8_t *>(filt_tc_lo);
+    if (!persistent) {
+        // tile form: one CTA per tile, at most 512 / cols CTAs per SM (TMEM), enforced through the shared memory
+        // request
+        const int taps = h * w * cb;
+        const int stages = taps < TC_TILE_STAGES ? taps : TC_TILE_STAGES;
+        uint32_t cols = 32;
+        while (cols < (uint32_t)NT) cols <<= 1;
+        const int max_ctas = 512 / (int)cols;
+        size_t smem = corr_tc_smem_bytes(NT, split, fp8, stages);
+        const size_t floor_bytes = 233472 / (size_t)(max_ctas + 1);
+        if (smem < floor_bytes) smem = floor_bytes;
+        if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
+        const void *fn = split ? reinterpret_cast<const void *>(corr_tc_tile_kernel<true, false>)
+                         : fp8 ? reinterpret_cast<const void *>(corr_tc_tile_kernel<false, true>)
+                               : reinterpret_cast<const void *>(corr_tc_tile_kernel<false, false>);
+        cudaError_t e = allow_max_dynamic_smem(fn, split ? 2 : fp8 ? 3 : 0);
+        if (e != cudaSuccess) return e;
+        note_launches(1);
+        if (split)
+            corr_tc_tile_kernel<true, false><<<total_tiles, TC_THREADS, smem, s>>>(
+                d_jobs, n_jobs, fb, fl, K, ld, NT, n_tiles_n, h, w, cb, cols, stages, 1.f, d_err);
+        else if (fp8)
+            corr_tc_tile_kernel<false, true><<<total_tiles, TC_THREADS, smem, s>>>(
+                d_jobs, n_jobs, fb, nullptr, K, ld, NT, n_tiles_n, h, w, cb, cols, stages, scale, d_err);
+        else
+            corr_tc_tile_kernel<false, false><<<total_tiles, TC_THREADS, smem, s>>>(
+                d_jobs, n_jobs, fb, nullptr, K, ld, NT, n_tiles_n, h, w, cb, cols, stages, 1.f, d_err);
+        return cudaGetLastError();
+    }
+    uint32_t acc_cols = 32;
+    while (acc_cols < (uint32_t)NT) acc_cols <<= 1;
+    // two accumulators per CTA; at most 512 / (2 acc_cols) CTAs per SM fit in TMEM, enforced through the shared
+    // memory request so that no CTA waits in tcgen05.alloc
+    const int max_ctas = 512 / (2 * (int)acc_cols);
+    // ring depth: as many slots as the shared memory of one of those CTAs holds (2..12); the ring runs on across tiles,
+    // so even a single-tap contraction keeps several tiles' operands in flight
+    const size_t per_cta = (size_t)kMaxDynamicSmem / (size_t)max_ctas - 1024;
+    const size_t slot = corr_tc_smem_bytes(NT, split, fp8, 1) - corr_tc_smem_bytes(NT, split, fp8, 0);
+    int stages = (int)std::min<size_t>(12, (per_cta - corr_tc_smem_bytes(NT, split, fp8, 0)) / slot);
+    stages = std::max(2, stages);
     size_t smem = corr_tc_smem_bytes(NT, split, fp8, stages);
     const size_t floor_bytes = 233472 / (size_t)(max_ctas + 1);
     if (smem < floor_bytes) smem = floor_bytes;
     if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
-    const void *fn = split ? reinterpret_cast<const void *>(corr_tc_kernel<true, false>)
-                     : fp8 ? reinterpret_cast<const void *>(corr_tc_kernel<false, true>)
-                           : reinterpret_cast<const void *>(corr_tc_kernel<false, false>);
-    cudaError_t e = allow_max_dynamic_smem(fn, split ? 2 : fp8 ? 3 : 0);
+    const void *fn = split ? reinterpret_cast<const void *>(corr_tc_persistent_kernel<true, false>)
+                     : fp8 ? reinterpret_cast<const void *>(corr_tc_persistent_kernel<false, true>)
+                           : reinterpret_cast<const void *>(corr_tc_persistent_kernel<false, false>);
+    cudaError_t e = allow_max_dynamic_smem(fn, split ? 5 : fp8 ? 6 : 4);
     if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TC_THREADS_P, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, std::min(per_sm, max_ctas));
+    const int grid = std::min(total_tiles, sm_count() * per_sm);
     note_launches(1);
-    const uint8_t *fb = static_cast<const uint8_t *>(filt_tc), *fl = static_cast<const uint8_t *>(filt_tc_lo);
     if (split)
-        corr_tc_kernel<true, false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, fb, fl, K, ld, NT, n_tiles_n,
-                                                                          h, w, cb, cols, stages, 1.f, d_err);
+        corr_tc_persistent_kernel<true, false><<<grid, TC_THREADS_P, smem, s>>>(d_jobs, n_jobs, total_tiles, fb, fl, K, ld, NT,
+                                                                     n_tiles_n, h, w, cb, acc_cols, stages, 1.f, d_err);
     else if (fp8)
-        corr_tc_kernel<false, true><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, fb, nullptr, K, ld, NT,
-                                                                          n_tiles_n, h, w, cb, cols, stages, scale,
-                                                                          d_err);
+        corr_tc_persistent_kernel<false, true><<<grid, TC_THREADS_P, smem, s>>>(d_jobs, n_jobs, total_tiles, fb, nullptr, K, ld,
+                                                                     NT, n_tiles_n, h, w, cb, acc_cols, stages, scale,
+                                                                     d_err);
     else
-        corr_tc_kernel<false, false><<<total_tiles, TC_THREADS, smem, s>>>(d_jobs, n_jobs, fb, nullptr, K, ld, NT,
-                                                                           n_tiles_n, h, w, cb, cols, stages, 1.f,
-                                                                           d_err);
+        corr_tc_persistent_kernel<false, false><<<grid, TC_THREADS_P, smem, s>>>(d_jobs, n_jobs, total_tiles, fb, nullptr, K, ld,
+                                                                      NT, n_tiles_n, h, w, cb, acc_cols, stages, 1.f,
+                                                                      d_err);
     return cudaGetLastError();
 }
 

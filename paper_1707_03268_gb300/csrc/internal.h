@@ -116,14 +116,17 @@ int corr_f32_tile_k();
 // jobs' tmap_lo must describe the lo parts of the input). d_err: device flag raised when a bounded wait expires.
 // fp8: E4M3 operands (bank [h*w*cb][2][ld][16] bytes, input tmap from encode_level_tmap_fp8, no lo parts); the
 // results are multiplied by `scale` (the inverse of the operands' per-tensor scales).
+// persistent: one CTA per SM slot walks many tiles, with two TMEM accumulators so that the epilogue of one tile
+// overlaps the MMAs of the next; otherwise one CTA per tile. Both give the same results.
 cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const void *filt_tc, const void *filt_tc_lo,
                            int K, int ld, int NT, int h, int w, int cb, int *d_err, cudaStream_t s, bool fp8 = false,
-                           float scale = 1.f);
+                           float scale = 1.f, bool persistent = false);
 int corr_tc_tile_m();
 int corr_tc_n_tiles(int K, int NT);
 int corr_tc_default_nt(int K, int taps);     // untuned N tile width for K filters over `taps` K blocks (h*w*cb)
 int corr_tc_nt_candidates(int K, int *out);  // up to 4 widths a tuner may choose; returns their number
 int corr_tc_bank_rows(int K);                // bank rows (ld) that fit every candidate width
+constexpr int kTcPersistent = 1 << 16;       // tile configuration code: N tile width | kTcPersistent
 // Tensor map of a BF16 planar array [chunks][cells][8] (chunks a multiple of 4), box {8, 128, 4}.
 bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks = 4);
 // Tensor map of an E4M3 planar level [2][cells][16] bytes, box {16, 128, 2}.

@@ -95,7 +95,8 @@ struct Plan {
     long long conv_items = 0;
     std::vector<size_t> g_jobs_off, g_sep_off, g_rec_off;
     std::vector<int> g_tiles, g_rec_tiles;  // tensor-core launches: M tiles (the N tiling is chosen at launch)
-    std::vector<int> g_nt, g_rec_nt;        // N tile widths of the group's tensor-core launches (tuned or default)
+    // tile configuration of the group's tensor-core launches (tuned or default): N tile width | persistent << 16
+    std::vector<int> g_nt, g_rec_nt;
     bool tuned = false;
     std::vector<long long> g_sep_tiles;
     size_t dt_off = 0, asm_off = 0;
@@ -275,8 +276,11 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         P->g_tiles[gi] = tiles;
         P->g_sep_tiles[gi] = sep_tiles;
         P->g_rec_tiles[gi] = rec_tiles;
-        P->g_nt[gi] = P->dec ? corr_tc_default_nt(g.R, 1) : corr_tc_default_nt(g.K, g.h * g.w);
-        P->g_rec_nt[gi] = P->rec_tc(g) ? corr_tc_default_nt(g.K, g.Upad / FD) : 0;
+        // untuned: the balanced width; the persistent form for split operands (three MMAs per step keep the tensor
+        // cores busy enough for the accumulator double buffer to pay), the tile form otherwise
+        const int persist = P->split ? kTcPersistent : 0;
+        P->g_nt[gi] = (P->dec ? corr_tc_default_nt(g.R, 1) : corr_tc_default_nt(g.K, g.h * g.w)) | persist;
+        P->g_rec_nt[gi] = P->rec_tc(g) ? corr_tc_default_nt(g.K, g.Upad / FD) | persist : 0;
     }
     P->dt_off = jb.take(sizeof(DtJob) * std::max<size_t>(1, P->dts.size()));
     P->asm_off = jb.take(sizeof(AsmJob) * std::max<size_t>(1, P->asms.size()));
@@ -434,21 +438,32 @@ cudaError_t launch_convert(const Plan &P, char *dblob, cudaStream_t s)
 
 // A shape group's tensor-core contraction over its m_tiles M tiles: the full correlation, or the channel stage of the
 // decomposed form, with the bank of the plan's operand format (FP8 results rescaled by the two per-tensor scales).
-cudaError_t launch_group_tc(const Plan &P, const Group &g, const TcJob *jobs, int nj, int m_tiles, int nt, int *err,
+// code: N tile width | kTcPersistent for the persistent form.
+cudaError_t launch_group_tc(const Plan &P, const Group &g, const TcJob *jobs, int nj, int m_tiles, int code, int *err,
                             cudaStream_t s)
 {
+    const int nt = code & 0xffff;
+    const bool pers = (code & kTcPersistent) != 0;
     if (P.dec) {
         if (P.fp8)
             return launch_corr_tc(jobs, nj, m_tiles, g.d_C_fp8, nullptr, g.R, g.Rpad_tc, nt, 1, 1, 1, err, s, true,
-                                  1.f / (g.C_fp8_scale * kFp8FeatureScale));
+                                  1.f / (g.C_fp8_scale * kFp8FeatureScale), pers);
         return launch_corr_tc(jobs, nj, m_tiles, g.d_C_tc, P.split ? g.d_C_tc_lo : nullptr, g.R, g.Rpad_tc, nt, 1, 1,
-                              1, err, s);
+                              1, err, s, false, 1.f, pers);
     }
     if (P.fp8)
         return launch_corr_tc(jobs, nj, m_tiles, g.d_filt_fp8, nullptr, g.K, g.Npad_tc, nt, g.h, g.w, 1, err, s, true,
-                              1.f / (g.fp8_scale * kFp8FeatureScale));
+                              1.f / (g.fp8_scale * kFp8FeatureScale), pers);
     return launch_corr_tc(jobs, nj, m_tiles, g.d_filt_tc, P.split ? g.d_filt_tc_lo : nullptr, g.K, g.Npad_tc, nt, g.h,
-                          g.w, 1, err, s);
+                          g.w, 1, err, s, false, 1.f, pers);
+}
+
+// The joint recombination S = Lambda U of a group (code as for launch_group_tc).
+cudaError_t launch_group_recomb(const Plan &P, const Group &g, const TcJob *jobs, int nj, int m_tiles, int code,
+                                int *err, cudaStream_t s)
+{
+    return launch_corr_tc(jobs, nj, m_tiles, g.d_lam_tc, P.split ? g.d_lam_tc_lo : nullptr, g.K, g.Npad_lam,
+                          code & 0xffff, 1, 1, g.Upad / FD, err, s, false, 1.f, (code & kTcPersistent) != 0);
 }
 
 cudaEvent_t prof_event(tdpm_ctx *ctx)
@@ -549,9 +564,8 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         }
         if (P.rec_tc(g)) {
             Prof pr(ctx, gs, "recomb_tc");
-            e = launch_corr_tc(reinterpret_cast<const TcJob *>(dblob + P.g_rec_off[gi]), nj, P.g_rec_tiles[gi],
-                               g.d_lam_tc, P.split ? g.d_lam_tc_lo : nullptr, g.K, g.Npad_lam, P.g_rec_nt[gi], 1,
-                               1, g.Upad / FD, ctx->d_err, gs);
+            e = launch_group_recomb(P, g, reinterpret_cast<const TcJob *>(dblob + P.g_rec_off[gi]), nj,
+                                    P.g_rec_tiles[gi], P.g_rec_nt[gi], ctx->d_err, gs);
             if (e != cudaSuccess) return e;
             pr.end();
         }
@@ -645,18 +659,23 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, const Arena &A
                 r = launch_convert(P, dblob, s);
             if (r != cudaSuccess) return r;
         }
+        // every balanced width, in the tile form and in the persistent form
         int cand[4];
         const int nc = corr_tc_nt_candidates(N, cand);
         float best = 0.f;
-        for (int i = 0; i < nc; ++i) {
-            float ms = 0.f;
-            const cudaError_t r = time_ms([&] { return launch_nt(cand[i]); }, &ms);
-            if (r != cudaSuccess) return r;
-            if (i == 0 || ms < best) {
-                best = ms;
-                *chosen = cand[i];
+        bool first = true;
+        for (int i = 0; i < nc; ++i)
+            for (int pers = 0; pers < 2; ++pers) {
+                const int code = cand[i] | (pers ? kTcPersistent : 0);
+                float ms = 0.f;
+                const cudaError_t r = time_ms([&] { return launch_nt(code); }, &ms);
+                if (r != cudaSuccess) return r;
+                if (first || ms < best) {
+                    best = ms;
+                    *chosen = code;
+                    first = false;
+                }
             }
-        }
         ctx->tune_cache[key] = *chosen;
         return cudaSuccess;
     };
@@ -676,10 +695,9 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, const Arena &A
                        &P.g_nt[gi]);
         if (e == cudaSuccess && P.rec_tc(g)) {
             const TcJob *rj = reinterpret_cast<const TcJob *>(dblob + P.g_rec_off[gi]);
-            e = choose(tune_key("recomb", g.K, g.Upad / FD, P.split ? "x3" : "x1", P.g_rec_tiles[gi]), g.K, [&](int nt) {
-                return launch_corr_tc(rj, nj, P.g_rec_tiles[gi], g.d_lam_tc, P.split ? g.d_lam_tc_lo : nullptr, g.K,
-                                      g.Npad_lam, nt, 1, 1, g.Upad / FD, ctx->d_err, s);
-            }, &P.g_rec_nt[gi]);
+            e = choose(tune_key("recomb", g.K, g.Upad / FD, P.split ? "x3" : "x1", P.g_rec_tiles[gi]), g.K,
+                       [&](int code) { return launch_group_recomb(P, g, rj, nj, P.g_rec_tiles[gi], code, ctx->d_err, s); },
+                       &P.g_rec_nt[gi]);
         }
     }
     if (ev0) cudaEventDestroy(ev0);
@@ -1173,7 +1191,7 @@ tdpm_status tdpm_profile_read(tdpm_ctx *ctx, int32_t index, char *name, size_t n
 }
 
 tdpm_status tdpm_autotune_read(tdpm_ctx *ctx, int32_t index, char *key, size_t key_cap, int32_t *tile_n,
-                               int32_t *n_entries)
+                               int32_t *persistent, int32_t *n_entries)
 {
     clear_error();
     if (!ctx || !n_entries) return fail(TDPM_ERR_ARG, "NULL argument");
@@ -1186,7 +1204,8 @@ tdpm_status tdpm_autotune_read(tdpm_ctx *ctx, int32_t index, char *key, size_t k
         std::strncpy(key, it->first.c_str(), key_cap - 1);
         key[key_cap - 1] = 0;
     }
-    if (tile_n) *tile_n = it->second;
+    if (tile_n) *tile_n = it->second & 0xffff;
+    if (persistent) *persistent = (it->second & kTcPersistent) ? 1 : 0;
     return TDPM_OK;
 }
 

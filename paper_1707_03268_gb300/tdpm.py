@@ -136,7 +136,7 @@ SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_i32)]),
     "tdpm_profile_reset": (_c_i32, [_VP]),
     "tdpm_autotune_read": (_c_i32, [_VP, _c_i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(_c_i32),
-                                    ctypes.POINTER(_c_i32)]),
+                                    ctypes.POINTER(_c_i32), ctypes.POINTER(_c_i32)]),
 }
 
 _LIB: Optional[ctypes.CDLL] = None
@@ -485,13 +485,13 @@ def tdpm_profile_reset(ctx: int) -> None:
 
 
 def tdpm_autotune_read(ctx: int) -> dict:
-    """{shape class: chosen N tile width} picked by the context's autotuner so far."""
+    """{shape class: "<N tile width>" or "<N tile width>/persistent"} picked by the context's autotuner so far."""
     n = _c_i32()
-    _check(lib().tdpm_autotune_read(ctx, -1, None, 0, None, ctypes.byref(n)))
+    _check(lib().tdpm_autotune_read(ctx, -1, None, 0, None, None, ctypes.byref(n)))
     out = {}
     for i in range(n.value):
         key = ctypes.create_string_buffer(128)
-        nt = _c_i32()
-        _check(lib().tdpm_autotune_read(ctx, i, key, 128, ctypes.byref(nt), ctypes.byref(n)))
-        out[key.value.decode()] = nt.value
+        nt, pers = _c_i32(), _c_i32()
+        _check(lib().tdpm_autotune_read(ctx, i, key, 128, ctypes.byref(nt), ctypes.byref(pers), ctypes.byref(n)))
+        out[key.value.decode()] = f"{nt.value}/persistent" if pers.value else str(nt.value)
     return out
