@@ -2,34 +2,28 @@
 //   D[p] = max_q f[q] - (lin*(q-p) + quad*(q-p)^2),  the smallest maximising q,
 // run as an x pass over every row of a part score map and a y pass over every sampled column of its result.
 //
-// One warp owns one line: it stages the line in shared memory and reduces its maximum M. Each lane then takes output
-// positions p and scans the candidates q in increasing order, keeping the first strict maximum, exactly like the
-// brute-force definition. The scan is restricted to the window where the deformation cost is at most
-// (M - f[p]) + margin: any q outside it has f[q] - cost <= M - cost < f[p] - margin, so it can never beat the
-// candidate q = p (whose value is f[p] exactly). The margin covers FP32 rounding of the evaluated values, so the
-// window never changes the result of the full scan, in exact or in FP32 arithmetic; it only skips hopeless
-// candidates (for the default deformation costs the window spans a few to a few tens of cells).
+// The scan of one output p (dt_scan): the candidates q within +-DT_R0 of p are evaluated in increasing index order
+// (the first strict maximum is the smallest maximiser), with the costs of those displacements taken once per line.
+// Then the result is checked against the line maximum M: on each side, beyond the cost's vertex, a cost above
+// (M - best) + margin at distance DT_R0 + 1 rules out every farther candidate (its f[q] - cost <= M - cost < best -
+// margin). Typical windows are 3-8 candidates wide; an output whose window is wider continues with an outward scan
+// over the exactly bounded window (left candidates win ties, right ones must be strictly better). The margin covers
+// FP32 rounding of the evaluated values, so the result is the brute-force one.
 //
-// x pass: line = row y of S (length W); outputs at p = x_off + x_step*k, written transposed: V[k][y], IV[k][y].
-// y pass: line = row k of V (length H, contiguous); outputs at p = y_off + y_step*i: D[i][k], A[i][k] =
-//         (qy << 16) | IV[k][qy].
+// x pass: one CTA per (job, 8 rows), one warp per row: the row is staged in shared memory, and the lanes take the
+//         sampled columns p = x_off + x_step*k; results V[y][k], IV[y][k] (row-major [H][nx]: the lanes of a warp
+//         store contiguous words).
+// y pass: one CTA per (job, 8 consecutive sampled columns): the 8 columns of V are staged transposed in shared
+//         memory, one warp per column takes the sampled rows p = y_off + y_step*i, and the results are staged and
+//         written back as rows of 8: D[i][k], A[i][k] = (qy << 16) | IV[qy][k].
+// Both passes find their job with one binary search per CTA (the jobs' xbegin / ybegin count CTAs).
 #include "internal.h"
 
 namespace tdpm {
 namespace {
 
 constexpr int DT_WARPS = 8;
-
-__device__ __forceinline__ int find_line_job(const DtJob *jobs, int n, int idx, bool xpass)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        const int b = xpass ? jobs[mid].xbegin : jobs[mid].ybegin;
-        if (b <= idx) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
+constexpr int DT_R0 = 4;
 
 // Candidate window [lo, hi] of output p for a line of length n with maximum mx.
 __device__ __forceinline__ void dt_window(float lin, float quad, float mx, float fp, int p, int n, int &lo, int &hi)
@@ -44,22 +38,105 @@ __device__ __forceinline__ void dt_window(float lin, float quad, float mx, float
     hi = min(hi, n - 1);
 }
 
+// Per-line constants of the scan.
+struct DtLine {
+    float lin, quad, mx;
+    float cst[2 * DT_R0 + 1];  // cost of displacement k - DT_R0
+    float cl1, cr1;            // costs at -(DT_R0+1) and +(DT_R0+1)
+    bool past_l, past_r;       // DT_R0+1 lies beyond the vertex of the left / right cost
+};
+
+__device__ __forceinline__ void dt_line_init(DtLine &c, float lin, float quad, float mx)
+{
+    c.lin = lin;
+    c.quad = quad;
+    c.mx = mx;
+#pragma unroll
+    for (int k = 0; k <= 2 * DT_R0; ++k) {
+        const float dd = (float)(k - DT_R0);
+        c.cst[k] = fmaf(quad, dd * dd, lin * dd);
+    }
+    const float f1 = (float)(DT_R0 + 1);
+    c.cl1 = fmaf(quad, f1 * f1, -lin * f1);
+    c.cr1 = fmaf(quad, f1 * f1, lin * f1);
+    c.past_l = f1 >= lin / (2.f * quad);
+    c.past_r = f1 >= -lin / (2.f * quad);
+}
+
+// The transformed value and smallest maximiser of output p of line L (length n).
+__device__ __forceinline__ void dt_scan(const DtLine &c, const float *L, int n, int p, float &best_out, int &arg_out)
+{
+    float best = -INFINITY;
+    int arg = p;
+#pragma unroll
+    for (int k = 0; k <= 2 * DT_R0; ++k) {
+        const int q = p + k - DT_R0;
+        if (q >= 0 && q < n) {
+            const float v = L[q] - c.cst[k];
+            if (v > best) {
+                best = v;
+                arg = q;
+            }
+        }
+    }
+    const float T = (c.mx - best) + 1e-5f * (1.f + fabsf(c.mx) + fabsf(best));
+    const bool done_l = p - DT_R0 - 1 < 0 || (c.past_l && c.cl1 > T);
+    const bool done_r = p + DT_R0 + 1 >= n || (c.past_r && c.cr1 > T);
+    if (!(done_l && done_r)) {
+        int lo, hi;
+        dt_window(c.lin, c.quad, c.mx, best, p, n, lo, hi);
+        for (int d = DT_R0 + 1; p - d >= lo || p + d <= hi; ++d) {
+            const float fd = (float)d;
+            if (p - d >= lo) {
+                // smallest index seen so far: it also wins a tie
+                const float v = L[p - d] - fmaf(c.quad, fd * fd, -c.lin * fd);
+                if (v >= best) {
+                    best = v;
+                    arg = p - d;
+                    dt_window(c.lin, c.quad, c.mx, best, p, n, lo, hi);
+                }
+            }
+            if (p + d <= hi) {
+                const float v = L[p + d] - fmaf(c.quad, fd * fd, c.lin * fd);
+                if (v > best) {
+                    best = v;
+                    arg = p + d;
+                    dt_window(c.lin, c.quad, c.mx, best, p, n, lo, hi);
+                }
+            }
+        }
+    }
+    best_out = best;
+    arg_out = arg;
+}
+
+// Job of CTA b: the last job whose first CTA is <= b (one search per CTA, shared through shared memory).
 template <bool XPASS>
-__global__ void __launch_bounds__(DT_WARPS * 32) dt_line_kernel(const DtJob *__restrict__ jobs, int n_jobs,
-                                                                int total_lines, int nmax)
+__device__ __forceinline__ int cta_job(const DtJob *jobs, int n, int b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int first = XPASS ? jobs[mid].xbegin : jobs[mid].ybegin;
+        if (first <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(DT_WARPS * 32) dt_x_kernel(const DtJob *__restrict__ jobs, int n_jobs, int nmax)
 {
     extern __shared__ float lines[];
+    __shared__ int s_job;
+    if (threadIdx.x == 0) s_job = cta_job<true>(jobs, n_jobs, blockIdx.x);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gl = blockIdx.x * DT_WARPS + warp;
-    if (gl >= total_lines) return;
-    const DtJob &J = jobs[find_line_job(jobs, n_jobs, gl, XPASS)];
-    const int line = gl - (XPASS ? J.xbegin : J.ybegin);
-    const int n = XPASS ? J.W : J.H;
-    const float *in = XPASS ? J.S + (size_t)line * J.W : J.V + (size_t)line * J.H;
-    const float lin = XPASS ? J.lx : J.ly, quad = XPASS ? J.qx : J.qy;
-    const int off = XPASS ? J.x_off : J.y_off, step = XPASS ? J.x_step : J.y_step, m = XPASS ? J.nx : J.ny;
+    // the job's fields in registers: stores through its pointers could alias the job table otherwise
+    const DtJob J = jobs[s_job];
+    const int line = (blockIdx.x - J.xbegin) * DT_WARPS + warp;
+    if (line >= J.H) return;
+    const int n = J.W;
+    const float *in = J.S + (size_t)line * n;
     float *L = lines + (size_t)warp * nmax;
-
     float mx = -INFINITY;
     for (int q = lane; q < n; q += 32) {
         const float v = __ldg(in + q);
@@ -69,60 +146,88 @@ __global__ void __launch_bounds__(DT_WARPS * 32) dt_line_kernel(const DtJob *__r
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     __syncwarp();
+    DtLine c;
+    dt_line_init(c, J.lx, J.qx, mx);
+    float *V = J.V + (size_t)line * J.nx;
+    int32_t *IV = J.IV + (size_t)line * J.nx;
+    for (int k = lane; k < J.nx; k += 32) {
+        float best;
+        int arg;
+        dt_scan(c, L, n, J.x_off + J.x_step * k, best, arg);
+        V[k] = best;
+        IV[k] = arg;
+    }
+}
 
-    for (int i = lane; i < m; i += 32) {
-        const int p = off + step * i;
-        // start from q = p and walk outwards; every improvement of the best value shrinks the window
-        float best = L[p];
-        int arg = p, lo, hi;
-        dt_window(lin, quad, mx, best, p, n, lo, hi);
-        for (int d = 1; p - d >= lo || p + d <= hi; ++d) {
-            const float fd = (float)d;
-            if (p - d >= lo) {
-                // smallest index seen so far: it also wins a tie
-                const float v = L[p - d] - fmaf(quad, fd * fd, -lin * fd);
-                if (v >= best) {
-                    best = v;
-                    arg = p - d;
-                    dt_window(lin, quad, mx, best, p, n, lo, hi);
-                }
-            }
-            if (p + d <= hi) {
-                const float v = L[p + d] - fmaf(quad, fd * fd, lin * fd);
-                if (v > best) {
-                    best = v;
-                    arg = p + d;
-                    dt_window(lin, quad, mx, best, p, n, lo, hi);
-                }
-            }
+// shared memory: 8 columns of length H (stride colstride, odd) and the staged results (8 x ny values and argmaxes)
+__global__ void __launch_bounds__(DT_WARPS * 32) dt_y_kernel(const DtJob *__restrict__ jobs, int n_jobs, int colstride,
+                                                             int outstride)
+{
+    extern __shared__ float sm[];
+    __shared__ int s_job;
+    if (threadIdx.x == 0) s_job = cta_job<false>(jobs, n_jobs, blockIdx.x);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const DtJob J = jobs[s_job];
+    const int k0 = (blockIdx.x - J.ybegin) * DT_WARPS;
+    const int ncols = min(DT_WARPS, J.nx - k0);
+    const int H = J.H, nx = J.nx, ny = J.ny;
+    float *col = sm;                                              // [8][colstride]
+    float *outD = sm + DT_WARPS * colstride;                      // [8][outstride]
+    int32_t *outA = reinterpret_cast<int32_t *>(outD + DT_WARPS * outstride);
+    // stage the 8 columns transposed: rows of V are read 8 words at a time
+    for (int idx = threadIdx.x; idx < H * DT_WARPS; idx += DT_WARPS * 32) {
+        const int y = idx >> 3, c = idx & 7;
+        if (c < ncols) col[c * colstride + y] = J.V[(size_t)y * nx + k0 + c];
+    }
+    __syncthreads();
+    if (warp < ncols) {
+        const float *L = col + warp * colstride;
+        float mx = -INFINITY;
+        for (int q = lane; q < H; q += 32) mx = fmaxf(mx, L[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        DtLine c;
+        dt_line_init(c, J.ly, J.qy, mx);
+        const int k = k0 + warp;
+        for (int i = lane; i < ny; i += 32) {
+            float best;
+            int arg;
+            dt_scan(c, L, H, J.y_off + J.y_step * i, best, arg);
+            outD[warp * outstride + i] = best;
+            outA[warp * outstride + i] = (arg << 16) | J.IV[(size_t)arg * nx + k];
         }
-        if (XPASS) {
-            J.V[(size_t)i * J.H + line] = best;
-            J.IV[(size_t)i * J.H + line] = arg;
-        } else {
-            J.D[(size_t)i * J.nx + line] = best;
-            J.A[(size_t)i * J.nx + line] = (arg << 16) | J.IV[(size_t)line * J.H + arg];
+    }
+    __syncthreads();
+    // write rows of 8 results
+    for (int idx = threadIdx.x; idx < ny * DT_WARPS; idx += DT_WARPS * 32) {
+        const int i = idx >> 3, c = idx & 7;
+        if (c < ncols) {
+            J.D[(size_t)i * nx + k0 + c] = outD[c * outstride + i];
+            J.A[(size_t)i * nx + k0 + c] = outA[c * outstride + i];
         }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_lines, int y_lines, int max_W, int max_H, cudaStream_t s)
+int dt_lines_per_cta() { return DT_WARPS; }
+
+cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_ctas, int y_ctas, int max_W, int max_H, cudaStream_t s)
 {
     if (n_jobs <= 0) return cudaSuccess;
     if (max_W > 800 || max_H > 800) return cudaErrorInvalidValue;
     const size_t smem_x = sizeof(float) * DT_WARPS * (size_t)max_W;
-    const size_t smem_y = sizeof(float) * DT_WARPS * (size_t)max_H;
-    note_launches((x_lines > 0) + (y_lines > 0));
-    if (x_lines > 0)
-        dt_line_kernel<true><<<(x_lines + DT_WARPS - 1) / DT_WARPS, DT_WARPS * 32, smem_x, s>>>(d_jobs, n_jobs, x_lines,
-                                                                                                max_W);
-    cudaError_t e = cudaGetLastError();
+    // y pass: a column has H <= max_H values; outputs per column ny <= H
+    const int colstride = max_H | 1, outstride = max_H | 1;
+    const size_t smem_y = sizeof(float) * DT_WARPS * (size_t)(colstride + 2 * outstride);
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(dt_y_kernel), 7);
     if (e != cudaSuccess) return e;
-    if (y_lines > 0)
-        dt_line_kernel<false><<<(y_lines + DT_WARPS - 1) / DT_WARPS, DT_WARPS * 32, smem_y, s>>>(d_jobs, n_jobs,
-                                                                                                 y_lines, max_H);
+    note_launches((x_ctas > 0) + (y_ctas > 0));
+    if (x_ctas > 0) dt_x_kernel<<<x_ctas, DT_WARPS * 32, smem_x, s>>>(d_jobs, n_jobs, max_W);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (y_ctas > 0) dt_y_kernel<<<y_ctas, DT_WARPS * 32, smem_y, s>>>(d_jobs, n_jobs, colstride, outstride);
     return cudaGetLastError();
 }
 

@@ -88,7 +88,8 @@ tdpm_status tdpm_dt_noalloc(const float *S, int32_t H, int32_t W, const float d[
     cudaStream_t s = (cudaStream_t)stream;
     // the job record is copied from this stack frame; a pageable copy is staged before cudaMemcpyAsync returns
     CUDA_TRY(cudaMemcpyAsync(sb, &J, sizeof(DtJob), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(launch_dt(reinterpret_cast<const DtJob *>(sb), 1, H, nx, W, H, s));
+    const int lpc = dt_lines_per_cta();
+    CUDA_TRY(launch_dt(reinterpret_cast<const DtJob *>(sb), 1, (H + lpc - 1) / lpc, (nx + lpc - 1) / lpc, W, H, s));
     return TDPM_OK;
 }
 

@@ -70,12 +70,12 @@ struct DtJob {
     float lx, qx, ly, qy;     // d0 (dx), d1 (dx^2), d2 (dy), d3 (dy^2)
     int x_off, x_step, nx;    // sampled columns
     int y_off, y_step, ny;    // sampled rows
-    float *V;                 // x-pass values, transposed  [nx][H]
-    int32_t *IV;              // x-pass argmax, transposed  [nx][H]
+    float *V;                 // x-pass values  [H][nx]
+    int32_t *IV;              // x-pass argmax  [H][nx]
     float *D;                 // result         [ny][nx]
     int32_t *A;               // (qy << 16) | qx [ny][nx]
-    int xbegin;               // first line of this job in the x pass (one line per row)
-    int ybegin;               // first line of this job in the y pass (one line per sampled column)
+    int xbegin;               // first CTA of this job in the x pass (ceil(H / dt_lines_per_cta()) CTAs per job)
+    int ybegin;               // first CTA of this job in the y pass (ceil(nx / dt_lines_per_cta()) CTAs per job)
 };
 
 // Step 3: one (component, root level) pair.
@@ -155,8 +155,9 @@ cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, long long total_items, 
 // tiles_y; the jobs' begin fields are the running sums of these counts.
 long long sep_job_items(int mode, int h, int w, int Ho, int Wo, int K, int *tiles_x, int *tiles_y);
 
-// K5/K6: distance transform passes (x_lines = sum of map rows, y_lines = sum of sampled columns; sides <= 800).
-cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_lines, int y_lines, int max_W, int max_H, cudaStream_t s);
+// K5/K6: distance transform passes (x_ctas / y_ctas: the CTA totals the jobs' xbegin / ybegin count; sides <= 800).
+cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_ctas, int y_ctas, int max_W, int max_H, cudaStream_t s);
+int dt_lines_per_cta();
 
 // K7: assembly (shift and sum), then detection count / scan / write.
 cudaError_t launch_assemble(const AsmJob *d_jobs, int n_jobs, long long total, cudaStream_t s);

@@ -45,11 +45,16 @@ cudaError_t allow_max_dynamic_smem(const void *func, int slot)
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (slot < 0 || slot >= 8 || dev < 0 || dev >= 64)
-        return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynamicSmem);
-    if (done[slot][dev].load(std::memory_order_acquire)) return cudaSuccess;
-    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynamicSmem);
-    if (e == cudaSuccess) done[slot][dev].store(true, std::memory_order_release);
+    if (slot >= 0 && slot < 8 && dev >= 0 && dev < 64 && done[slot][dev].load(std::memory_order_acquire))
+        return cudaSuccess;
+    // the opt-in maximum minus the kernel's own static shared memory
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMaxDynamicSmem - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess && slot >= 0 && slot < 8 && dev >= 0 && dev < 64)
+        done[slot][dev].store(true, std::memory_order_release);
     return e;
 }
 
@@ -100,7 +105,7 @@ struct Plan {
     bool tuned = false;
     std::vector<long long> g_sep_tiles;
     size_t dt_off = 0, asm_off = 0;
-    int x_warps = 0, y_warps = 0, max_W = 1, max_H = 1;
+    int x_warps = 0, y_warps = 0, max_W = 1, max_H = 1;  // x_warps / y_warps: CTAs of the two DT passes
     std::vector<std::pair<size_t, int>> patches;  // blob offsets of caller level pointers
 
     // joint decomposition with tensor-core operands: the separable stage writes U_r and Lambda U runs as a GEMM
@@ -287,8 +292,8 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     P->blob_bytes = align256(jb.off);
     P->arena_bytes = P->blob_off + P->blob_bytes;
     for (const DtPlan &p : P->dts) {
-        P->x_warps += p.Hs;
-        P->y_warps += p.X;
+        P->x_warps += (p.Hs + dt_lines_per_cta() - 1) / dt_lines_per_cta();  // CTAs of the two passes
+        P->y_warps += (p.X + dt_lines_per_cta() - 1) / dt_lines_per_cta();
         P->max_W = std::max(P->max_W, p.Ws);
         P->max_H = std::max(P->max_H, p.Hs);
     }
@@ -402,8 +407,8 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
         d.D = reinterpret_cast<float *>(base + p.d_off);
         d.A = reinterpret_cast<int32_t *>(base + p.a_off);
         d.xbegin = xw; d.ybegin = yw;
-        xw += p.Hs;
-        yw += p.X;
+        xw += (p.Hs + dt_lines_per_cta() - 1) / dt_lines_per_cta();
+        yw += (p.X + dt_lines_per_cta() - 1) / dt_lines_per_cta();
     }
     AsmJob *aj = reinterpret_cast<AsmJob *>(hb + P.asm_off);
     long long pos = 0;
@@ -1250,7 +1255,8 @@ tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int3
     J.xbegin = 0; J.ybegin = 0;
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaMemcpyAsync(sb, &J, sizeof(DtJob), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(launch_dt(reinterpret_cast<const DtJob *>(sb), 1, H, nx, W, H, s));
+    const int lpc = dt_lines_per_cta();
+    CUDA_TRY(launch_dt(reinterpret_cast<const DtJob *>(sb), 1, (H + lpc - 1) / lpc, (nx + lpc - 1) / lpc, W, H, s));
     return TDPM_OK;
 }
 
