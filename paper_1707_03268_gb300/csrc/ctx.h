@@ -104,6 +104,7 @@ struct Arena {
     std::vector<const void *> levels;    // level pointers patched into the blob
     cudaGraphExec_t graph = nullptr;
     int uses = 0;
+    bool blob_on_device = false;         // the device copy of the job tables matches the host blob
 };
 
 struct Scores {

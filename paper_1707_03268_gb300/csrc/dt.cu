@@ -16,7 +16,7 @@
 // y pass: one CTA per (job, 8 consecutive sampled columns): the 8 columns of V are staged transposed in shared
 //         memory, one warp per column takes the sampled rows p = y_off + y_step*i, and the results are staged and
 //         written back as rows of 8: D[i][k], A[i][k] = (qy << 16) | IV[qy][k].
-// Both passes find their job with one binary search per CTA (the jobs' xbegin / ybegin count CTAs).
+// Both passes find their job with a 32-ary warp search (the jobs' xbegin / ybegin count CTAs).
 #include "internal.h"
 
 namespace tdpm {
@@ -110,15 +110,20 @@ __device__ __forceinline__ void dt_scan(const DtLine &c, const float *L, int n, 
     arg_out = arg;
 }
 
-// Job of CTA b: the last job whose first CTA is <= b (one search per CTA, shared through shared memory).
+// Job of CTA b: the last job whose first CTA is <= b (the first CTAs increase strictly). A 32-ary search by one warp:
+// each lane probes one of 32 evenly spaced jobs of the remaining range and a ballot keeps the last one at or below
+// b, so a range of n jobs takes about log32(n) dependent loads. All lanes return the same job.
 template <bool XPASS>
-__device__ __forceinline__ int cta_job(const DtJob *jobs, int n, int b)
+__device__ __forceinline__ int cta_job(const DtJob *jobs, int n, int b, int lane)
 {
-    int lo = 0, hi = n - 1;
+    int lo = 0, hi = n - 1;  // invariant: first(lo) <= b
     while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        const int first = XPASS ? jobs[mid].xbegin : jobs[mid].ybegin;
-        if (first <= b) lo = mid; else hi = mid - 1;
+        const int stride = (hi - lo + 32) / 32;
+        const int probe = lo + lane * stride;
+        const bool ok = probe <= hi && (XPASS ? jobs[probe].xbegin : jobs[probe].ybegin) <= b;
+        const int k = __popc(__ballot_sync(0xffffffffu, ok));  // >= 1: lane 0 probes lo
+        lo += (k - 1) * stride;
+        hi = min(hi, lo + stride - 1);
     }
     return lo;
 }
@@ -126,12 +131,10 @@ __device__ __forceinline__ int cta_job(const DtJob *jobs, int n, int b)
 __global__ void __launch_bounds__(DT_WARPS * 32) dt_x_kernel(const DtJob *__restrict__ jobs, int n_jobs, int nmax)
 {
     extern __shared__ float lines[];
-    __shared__ int s_job;
-    if (threadIdx.x == 0) s_job = cta_job<true>(jobs, n_jobs, blockIdx.x);
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // the job's fields in registers: stores through its pointers could alias the job table otherwise
-    const DtJob J = jobs[s_job];
+    // every warp finds the job itself (no block barrier); the job's fields in registers: stores through its pointers
+    // could alias the job table otherwise
+    const DtJob J = jobs[cta_job<true>(jobs, n_jobs, blockIdx.x, lane)];
     const int line = (blockIdx.x - J.xbegin) * DT_WARPS + warp;
     if (line >= J.H) return;
     const int n = J.W;
@@ -164,11 +167,8 @@ __global__ void __launch_bounds__(DT_WARPS * 32) dt_y_kernel(const DtJob *__rest
                                                              int outstride)
 {
     extern __shared__ float sm[];
-    __shared__ int s_job;
-    if (threadIdx.x == 0) s_job = cta_job<false>(jobs, n_jobs, blockIdx.x);
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const DtJob J = jobs[s_job];
+    const DtJob J = jobs[cta_job<false>(jobs, n_jobs, blockIdx.x, lane)];
     const int k0 = (blockIdx.x - J.ybegin) * DT_WARPS;
     const int ncols = min(DT_WARPS, J.nx - k0);
     const int H = J.H, nx = J.nx, ny = J.ny;

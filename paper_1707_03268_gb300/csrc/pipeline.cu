@@ -525,11 +525,11 @@ void prof_collect(tdpm_ctx *ctx)
 }
 
 // Every stage of the plan on stream s.
+// Every stage of the plan on stream s (the job tables must already be on the device).
 cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A, cudaStream_t s)
 {
     char *dblob = A.dev + P.blob_off;
-    cudaError_t e = cudaMemcpyAsync(dblob, A.host, P.blob_bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     if (P.bf) {
         Prof pr(ctx, s, P.fp8 ? "to_fp8" : "to_bf16");
         e = launch_convert(P, dblob, s);
@@ -631,7 +631,7 @@ std::string tune_key(const char *kind, int N, int kblocks, const char *operands,
            std::to_string(b);
 }
 
-cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, const Arena &A, cudaStream_t s)
+cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, Arena &A, cudaStream_t s)
 {
     P.tuned = true;
     if (!P.bf) return cudaSuccess;
@@ -659,9 +659,10 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, const Arena &A
         }
         if (!staged) {
             staged = true;
-            cudaError_t r = cudaMemcpyAsync(dblob, A.host, P.blob_bytes, cudaMemcpyHostToDevice, s);
-            if (r == cudaSuccess)
-                r = launch_convert(P, dblob, s);
+            cudaError_t r = cudaSuccess;
+            if (!A.blob_on_device) r = cudaMemcpyAsync(dblob, A.host, P.blob_bytes, cudaMemcpyHostToDevice, s);
+            if (r == cudaSuccess) A.blob_on_device = true;
+            if (r == cudaSuccess) r = launch_convert(P, dblob, s);
             if (r != cudaSuccess) return r;
         }
         // every balanced width, in the tile form and in the persistent form
@@ -1014,6 +1015,7 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
             return st;
         }
         A.plan_uid = plan->uid;
+        A.blob_on_device = false;
     } else {
         bool same = A.levels.size() == lv.size();
         for (size_t j = 0; same && j < lv.size(); ++j) same = A.levels[j] == lv[j]->data;
@@ -1022,6 +1024,7 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
                 *reinterpret_cast<const float **>(A.host + pt.first) = lv[pt.second]->data;
             A.levels.assign(lv.size(), nullptr);
             for (size_t j = 0; j < lv.size(); ++j) A.levels[j] = lv[j]->data;
+            A.blob_on_device = false;
         }
     }
     cudaError_t e = cudaSuccess;
@@ -1033,6 +1036,17 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
             arena_put(ctx, A);
             return fail(TDPM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
         }
+    }
+    // the job tables go to the device only when the host blob changed (new plan or new level pointers); a reused
+    // arena keeps them, so repeated batches of the same shapes copy nothing but their own inputs
+    if (!A.blob_on_device) {
+        e = cudaMemcpyAsync(A.dev + plan->blob_off, A.host, plan->blob_bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(s);
+            arena_put(ctx, A);
+            return fail(TDPM_ERR_CUDA, std::string("job tables: ") + cudaGetErrorString(e));
+        }
+        A.blob_on_device = true;
     }
     const bool graphs = ctx->use_graphs && !ctx->prof;
     if (graphs && !A.graph && A.uses >= 1) {
