@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="c5: length of the arrival stream")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="c5: mean arrival rate (requests/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fuse", action="store_true",
+                    help="decomposed per-filter form: channel stage and separable passes as two launches")
     ap.add_argument("--no-compare", action="store_true", help="skip the full-form comparison runs")
     ap.add_argument("--no-sweep", action="store_true", help="skip the rank sweep")
     args = ap.parse_args()
@@ -131,8 +133,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------ roofline model
-def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
-    """Algorithmic DRAM bytes and flops per stage for one image: every input read once, every output written once."""
+FUSED_SHAPES = {(6, 6), (5, 11), (7, 7), (11, 5)}  # filter shapes with a compiled fused decomposed kernel
+
+
+def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool, fused: bool = True):
+    """Algorithmic DRAM bytes and flops per stage for one image: every input read once, every output written once.
+    The fused decomposed kernel ("zsep_tc") reads the features and writes the filter maps; its flops are those of the
+    separable passes and the recombination (FP32 ALU work; its channel-stage MMAs are a small tensor-core load)."""
     sizes = pyr.sizes
     lam = pyr.lam
     L = len(sizes)
@@ -146,7 +153,7 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
     corr = "corr_tc" if tc else "corr_f32"
     zproj = "zproj_tc" if tc else "zproj_f32"
     out = {corr: [0, 0], zproj: [0, 0], "sep": [0, 0], "recomb_tc": [0, 0], "dt": [0, 0], "assemble": [0, 0],
-           "to_bf16": [0, 0]}
+           "to_bf16": [0, 0], "zsep_tc": [0, 0]}
     ub = 4 if precision == "bf16x3" else 2  # bytes per U_r value on the joint tensor-core path (hi + lo parts)
     if tc:
         out["to_fp8" if precision == "fp8" else "to_bf16"] = [sum(H * W * 32 * (4 + fb) for (H, W) in sizes), 0]
@@ -165,6 +172,10 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool):
             if form == "full":
                 out[corr][0] += H * W * 32 * fb + K * Ho * Wo * 4
                 out[corr][1] += 2 * h * w * 32 * K * Ho * Wo
+            elif (fused and not joint and precision in ("bf16", "bf16x3") and (h, w) in FUSED_SHAPES
+                  and min(rank, h * w) <= 64):
+                out["zsep_tc"][0] += H * W * 32 * fb + K * Ho * Wo * 4
+                out["zsep_tc"][1] += 2 * K * Ho * Wo * (R // K) * (h + w + 1)
             else:
                 out[zproj][0] += H * W * 32 * fb + R * H * W * 4
                 out[zproj][1] += 2 * 32 * R * H * W
@@ -236,7 +247,7 @@ def fp32_alu_peak_tflops(sm_mhz: float) -> float:
 
 
 TENSOR_STAGES = ("corr_tc", "zproj_tc", "recomb_tc")
-ALU_STAGES = ("corr_f32", "zproj_f32", "sep")
+ALU_STAGES = ("corr_f32", "zproj_f32", "sep", "zsep_tc")
 
 
 def stage_roofline(name, ms_per_image, launches_per_image, model, peaks, sm_mhz):
@@ -385,6 +396,7 @@ def run_bank(args):
     wl = synth.config_c3() if args.workload == "c3" else synth.config_c4()
     n_comp = len(wl.model.components)
     ctx = tdpm.tdpm_create(0)
+    tdpm.tdpm_set_fusion(ctx, not args.no_fuse)
     mid = tdpm.tdpm_load_model(ctx, wl.model)
     dps = [tdpm.DevicePyramid([torch.from_numpy(l).cuda() for l in p.levels], p.lam) for p in wl.pyramids]
     cells = sum(l.shape[0] * l.shape[1] for p in wl.pyramids for l in p.levels)
@@ -420,6 +432,7 @@ def run_bank(args):
         variants += [("decomposed", "bf16x3", 32, "joint"), ("decomposed", "bf16", 8, "per_filter")]
     else:
         variants += [("decomposed", "bf16", 8, "joint"), ("decomposed", "bf16x3", 8, "joint")]
+    variants += [("decomposed", "bf16x3", 8, "per_filter")]
     head = (args.form, args.precision, args.rank if args.form == "decomposed" else None,
             args.mode if args.form == "decomposed" else None)
     if head not in variants:
@@ -514,6 +527,7 @@ def run_serve(args):
     for _ in range(20):
         comps.extend(synth.make_dpm_class(rng))
     ctx = tdpm.tdpm_create(0)
+    tdpm.tdpm_set_fusion(ctx, not args.no_fuse)
     bank = tdpm.tdpm_load_model(ctx, synth.Model(comps))
     form = tdpm.FORM_FULL if args.form == "full" else tdpm.FORM_DECOMPOSED
     prec = PRECISIONS[args.precision]
@@ -617,6 +631,7 @@ def main():
     pyr = wl.pyramids[0]
     tau = load_tau()
     ctx = tdpm.tdpm_create(local)
+    tdpm.tdpm_set_fusion(ctx, not args.no_fuse)
     mid = tdpm.tdpm_load_model(ctx, wl.model)
     levels = [torch.from_numpy(l).cuda() for l in pyr.levels]
     dp = tdpm.DevicePyramid(levels, pyr.lam)
@@ -693,7 +708,7 @@ def main():
     prof_run = timed(form, prec, max(10, args.steps // 4), 1, prof=True)
     stages = prof_run["stages"]
     n_prof = len(prof_run["ms"])
-    model = stage_bytes(wl, pyr, args.form, args.precision, args.rank, joint)
+    model = stage_bytes(wl, pyr, args.form, args.precision, args.rank, joint, fused=not args.no_fuse)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -792,6 +807,7 @@ def main():
                                           "fp32": "FP32 ALUs"}[args.precision],
                        "rank": args.rank if form == tdpm.FORM_DECOMPOSED else None,
                        "decomposition": args.mode if form == tdpm.FORM_DECOMPOSED else None,
+                       "fused": (not args.no_fuse) if form == tdpm.FORM_DECOMPOSED else None,
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": main_run["launches"],

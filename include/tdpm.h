@@ -275,7 +275,7 @@ uint64_t tdpm_kernel_launches(void);
 
 /* When enabled, every stage the context enqueues is bracketed by CUDA events recorded on the stage's own stream, and
  * the device time is accumulated per stage name ("to_bf16", "corr_tc", "corr_f32", "zproj_tc", "zproj_f32", "sep",
- * "recomb_tc", "dt", "assemble", "detect"). While enabled, the shape groups' correlation chains run one after another
+ * "zsep_tc", "recomb_tc", "dt", "assemble", "detect"). While enabled, the shape groups' correlation chains run one after another
  * on the caller's stream instead of concurrently, so that each stage is timed alone. Disabled by default. */
 tdpm_status tdpm_profile_enable(tdpm_ctx *ctx, int32_t enable);
 
@@ -297,6 +297,15 @@ tdpm_status tdpm_profile_reset(tdpm_ctx *ctx);
  * receives the number of entries (an index out of range only sets it). */
 tdpm_status tdpm_autotune_read(tdpm_ctx *ctx, int32_t index, char *key, size_t key_cap, int32_t *tile_n,
                                int32_t *persistent, int32_t *n_entries);
+
+/* Kernel fusion of the decomposed form (Sec. 4) with per-filter factors and BF16 or split-BF16 operands. enable = 1
+ * (the default; the environment variable TDPM_FUSE=0 before tdpm_create sets 0): the channel stage (Z_r = phi o c_r,
+ * on the tensor cores) and the separable passes with the recombination run as ONE kernel per shape group, the
+ * rank-1 maps Z_r staying in shared memory (stage name "zsep_tc" in the profile). Shapes with a compiled fused form:
+ * 6x6, 5x11, 7x7, 11x5, each filter with at most 64 terms; other groups, joint factors, FP32 and FP8 run unfused.
+ * enable = 0: two launches per group with Z_r in device memory ("zproj_tc", then "sep"). Both give bit-identical
+ * score maps. Applies to score builds started afterwards (plans are cached per setting). */
+tdpm_status tdpm_set_fusion(tdpm_ctx *ctx, int32_t enable);
 
 /* ================================================================================ serving (continuous batching) */
 /* Not in the paper: a request loop around the scoring path. A server thread owned by the context takes submitted

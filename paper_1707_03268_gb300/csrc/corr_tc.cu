@@ -23,133 +23,13 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "tc_ptx.h"
 
 namespace tdpm {
 namespace {
 
 constexpr int TC_M = 128;
 constexpr uint32_t A_PLANE_BYTES = TC_M * 16;  // one 8-channel chunk of 128 cells
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for the phase with `parity` to complete, ignoring the error flag; gives up after ~2^28 cycles. Used only to let
-// a CTA's own copies land before it exits.
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > (1ll << 28)) return;
-}
-
-// Wait for the phase with `parity` to complete. Gives up after ~2^30 cycles (about half a second), raising *err;
-// once any CTA has raised *err, later waits return at once, so a failing launch ends within about a second.
-__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int *err)
-{
-    if (mbar_try_wait(bar, parity)) return;
-    if (*reinterpret_cast<volatile int *>(err)) return;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1ll << 30)) {
-            atomicExch(err, 1);
-            return;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-// tcgen05 shared-memory matrix descriptor, no swizzle, K-major: lbo = byte distance between core matrices along K,
-// sbo = byte distance between 8-row core-matrix groups along M (or N).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t instr_desc(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3 (format code 0), both K-major, M x N.
-__host__ __device__ constexpr uint32_t instr_desc_e4m3(int M, int N)
-{
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 template <class Job>
 __device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
@@ -162,10 +42,6 @@ __device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
     return lo;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 // A tile is one (M tile, N tile) pair; M tiles are numbered across the jobs (a job's begin is its first M tile), so
 // the job tables do not depend on the N tiling.
@@ -720,7 +596,7 @@ namespace {
 
 // dims {elems per 16-byte chunk, cells, chunks}, box {elems, 128, the chunks of one tap (32 channels)}, zero fill
 // outside; strides in bytes
-bool encode_tmap(CUtensorMap *map, CUtensorMapDataType type, int elems, void *base, long long cells, int chunks)
+EncodeTiledFn encode_fn()
 {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -729,9 +605,16 @@ bool encode_tmap(CUtensorMap *map, CUtensorMapDataType type, int elems, void *ba
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess || !p)
-            return false;
+            return nullptr;
         fn = reinterpret_cast<EncodeTiledFn>(p);
     }
+    return fn;
+}
+
+bool encode_tmap(CUtensorMap *map, CUtensorMapDataType type, int elems, void *base, long long cells, int chunks)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
     const cuuint32_t tap_chunks = (cuuint32_t)(FD / elems);
     if (chunks < (int)tap_chunks || chunks % tap_chunks) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)elems, (cuuint64_t)cells, (cuuint64_t)chunks};
@@ -747,6 +630,19 @@ bool encode_tmap(CUtensorMap *map, CUtensorMapDataType type, int elems, void *ba
 bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks)
 {
     return encode_tmap(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 8, const_cast<uint16_t *>(planar), cells, chunks);
+}
+
+bool encode_level_tmap_tiles(CUtensorMap *map, const uint16_t *planar, int H, int W)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || H <= 0 || W <= 0) return false;
+    const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, 4};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
+    const cuuint32_t box[4] = {8, 32, 4, 4};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(planar), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool encode_level_tmap_fp8(CUtensorMap *map, const uint8_t *planar, long long cells)

@@ -103,6 +103,7 @@ struct Arena {
     uint64_t plan_uid = 0;               // plan whose job tables the host blob currently holds (0: none)
     std::vector<const void *> levels;    // level pointers patched into the blob
     cudaGraphExec_t graph = nullptr;
+    int graph_kernels = 0;               // kernel launches captured in `graph` (counted again at each replay)
     int uses = 0;
     bool blob_on_device = false;         // the device copy of the job tables matches the host blob
 };
@@ -152,6 +153,7 @@ struct tdpm_ctx {
     int *d_err = nullptr;                // raised by bounded device waits
     int *h_err = nullptr;                // pinned mirror
     bool use_graphs = true;
+    bool fuse = true;                    // fused channel stage + separable passes where possible (tdpm_set_fusion)
     bool autotune = true;                // time the N tilings of a new plan's tensor-core launches (TDPM_AUTOTUNE=0: off)
     std::map<std::string, int> tune_cache;  // shape class of a tensor-core launch -> chosen N tile width
     // profiling

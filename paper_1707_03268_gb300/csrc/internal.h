@@ -36,6 +36,24 @@ struct alignas(128) TcJob {
     int pad[3];
 };
 
+// Step 1, decomposed form, per-filter mode, channel stage and separable passes fused on the tensor cores: one
+// (group, level) pair. The tensor maps describe the level's BF16 planar copy as [4][H][W][8] (box {8, 32, 4, 4}).
+struct alignas(128) ZsJob {
+    CUtensorMap tmap;         // hi part
+    CUtensorMap tmap_lo;      // lo part (split-BF16 precision only)
+    float *out;               // [K][Ho][Wo]
+    int H, W, Ho, Wo;
+    int tiles_x;              // spatial tiles of this job along x
+    int begin;                // first spatial tile of this job (tiles numbered across the jobs of a launch)
+    int pad[2];
+};
+
+// A filter group of the fused launch: filters [k0, k1) of the shape group, whose terms [t0, t0 + n) (n <= nmax) are
+// the N = n rounded up to 16 columns of one MMA.
+struct ZsGroup {
+    int k0, k1, t0, n;
+};
+
 // Step 1, decomposed form, stage Z on the FP32 SIMT path: Z[r][cell] = sum_c C[c][r] phi[cell][c].
 struct ZJob {
     const float *feat;
@@ -99,8 +117,10 @@ void note_launches(int n);
 
 // Raise a kernel's dynamic shared memory limit to the per-block maximum, once per device. Launches still request only
 // what they use; a fixed limit keeps captured CUDA graphs valid whatever order their launches were recorded in.
+// slot: a distinct number per kernel (0 .. kSmemSlots-1) under which the setting is remembered.
 cudaError_t allow_max_dynamic_smem(const void *func, int slot);
 constexpr int kMaxDynamicSmem = 232448;
+constexpr int kSmemSlots = 16;
 
 // K8: FP32 SIMT direct correlation. filt_t: [h*w*32][Kpad] (filter index fastest), Kpad a multiple of 64.
 cudaError_t launch_corr_f32(const CorrJob *d_jobs, int n_jobs, int total_tiles, const float *filt_t, int K, int Kpad,
@@ -131,6 +151,22 @@ constexpr int kTcPersistent = 1 << 16;       // tile configuration code: N tile 
 bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks = 4);
 // Tensor map of an E4M3 planar level [2][cells][16] bytes, box {16, 128, 2}.
 bool encode_level_tmap_fp8(CUtensorMap *map, const uint8_t *planar, long long cells);
+
+// Tensor map of a BF16 planar level [4][H][W][8] as a 4-D array, box {8, 32 columns, 4 rows, 4 chunks}.
+bool encode_level_tmap_tiles(CUtensorMap *map, const uint16_t *planar, int H, int W);
+
+// K2+K3+K4 fused (per-filter mode, BF16 or split-BF16 operands): the channel stage on the tensor cores and the
+// separable passes with the recombination, over `tiles` spatial tiles (the jobs' begin fields number them) times
+// n_fg filter groups. cbank / cbank_lo: the channel-factor bank [1][4][ld][8] BF16 (hi, lo or null); every group
+// needs t0 + n rounded up to 16 <= ld. A, B, lam, rank_off as for launch_sep; nmax = 32 or 64 (zsep_nmax) bounds
+// the terms of a group. Shapes: zsep_shape (the filter shapes of the separable warp form).
+bool zsep_shape(int h, int w);
+void zsep_tile(int h, int w, int *tile_cols, int *tile_rows);  // output columns and rows of one spatial tile
+int zsep_nmax(int max_rank);                                     // 32, 64, or 0 when a filter has more terms
+cudaError_t launch_zsep_tc(const ZsJob *d_jobs, int n_jobs, int tiles, const ZsGroup *d_fg, int n_fg,
+                           const void *cbank, const void *cbank_lo, int ld, const float *A, const float *B,
+                           const float *lam, const int *rank_off, int R, int nmax, int h, int w, int *d_err,
+                           cudaStream_t s);
 
 // FP32 NHWC -> BF16 planar for many levels in one launch (total = sum of 4 * cells).
 cudaError_t launch_to_bf16_planar(const ConvJob *d_jobs, int n_jobs, long long total, cudaStream_t s);

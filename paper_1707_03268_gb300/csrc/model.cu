@@ -245,6 +245,8 @@ tdpm_status tdpm_create(tdpm_ctx **out, int32_t device, size_t mem_budget_bytes)
     c->use_graphs = !(g && g[0] == '0');
     const char *at = std::getenv("TDPM_AUTOTUNE");
     c->autotune = !(at && at[0] == '0');
+    const char *fu = std::getenv("TDPM_FUSE");
+    c->fuse = !(fu && fu[0] == '0');
     *out = c;
     return TDPM_OK;
 }

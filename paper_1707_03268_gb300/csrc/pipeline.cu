@@ -37,15 +37,22 @@ struct Bump {
 };
 }  // namespace
 
-void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+// while a thread captures a graph its launches are counted into the graph (they run at each replay, not now)
+thread_local int *t_capture_launches = nullptr;
+
+void note_launches(int n)
+{
+    if (t_capture_launches) *t_capture_launches += n;
+    else g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+}
 
 cudaError_t allow_max_dynamic_smem(const void *func, int slot)
 {
-    static std::atomic<bool> done[8][64];
+    static std::atomic<bool> done[kSmemSlots][64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (slot >= 0 && slot < 8 && dev >= 0 && dev < 64 && done[slot][dev].load(std::memory_order_acquire))
+    if (slot >= 0 && slot < kSmemSlots && dev >= 0 && dev < 64 && done[slot][dev].load(std::memory_order_acquire))
         return cudaSuccess;
     // the opt-in maximum minus the kernel's own static shared memory
     cudaFuncAttributes fa{};
@@ -53,7 +60,7 @@ cudaError_t allow_max_dynamic_smem(const void *func, int slot)
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kMaxDynamicSmem - (int)fa.sharedSizeBytes);
-    if (e == cudaSuccess && slot >= 0 && slot < 8 && dev >= 0 && dev < 64)
+    if (e == cudaSuccess && slot >= 0 && slot < kSmemSlots && dev >= 0 && dev < 64)
         done[slot][dev].store(true, std::memory_order_release);
     return e;
 }
@@ -104,6 +111,12 @@ struct Plan {
     std::vector<int> g_nt, g_rec_nt;
     bool tuned = false;
     std::vector<long long> g_sep_tiles;
+    // decomposed per-filter groups on tensor cores with the fused kernel: no Z maps; spatial tiles in g_tiles, filter
+    // groups (ZsGroup table at g_fg_off) and their width bound
+    std::vector<char> g_fused;
+    std::vector<size_t> g_fg_off;
+    std::vector<int> g_n_fg, g_nmax;
+    std::vector<std::vector<ZsGroup>> g_fg;
     size_t dt_off = 0, asm_off = 0;
     int x_warps = 0, y_warps = 0, max_W = 1, max_H = 1;  // x_warps / y_warps: CTAs of the two DT passes
     std::vector<std::pair<size_t, int>> patches;  // blob offsets of caller level pointers
@@ -118,10 +131,10 @@ namespace {
 
 // mask: null (every component of every image) or [n][components], nonzero = score that component on that image
 std::string plan_key(int model_id, const Model &m, int form, int prec, const tdpm_pyramid *pyrs, int n,
-                     const uint8_t *mask)
+                     const uint8_t *mask, bool fuse)
 {
     std::string k = std::to_string(model_id) + ":" + std::to_string(m.version) + ":" + std::to_string(form) + ":" +
-                    std::to_string(prec) + ":" + std::to_string(n);
+                    std::to_string(prec) + ":" + std::to_string(n) + (fuse ? ":f" : ":u");
     for (int i = 0; i < n; ++i) {
         k += "|" + std::to_string(pyrs[i].lambda);
         for (int j = 0; j < pyrs[i].n_levels; ++j)
@@ -134,8 +147,31 @@ std::string plan_key(int model_id, const Model &m, int form, int prec, const tdp
     return k;
 }
 
+// The filter groups of a per-filter decomposed shape group for the fused kernel: consecutive filters while their
+// terms fit nmax (and the bank rows an MMA of the rounded-up width reads exist). Empty when the group cannot be fused.
+std::vector<ZsGroup> fused_groups(const Group &g, int *nmax_out)
+{
+    std::vector<ZsGroup> out;
+    if (g.joint || !zsep_shape(g.h, g.w) || (int)g.rank_off.size() != g.K + 1) return out;
+    int max_rank = 0;
+    for (int k = 0; k < g.K; ++k) max_rank = std::max(max_rank, g.rank_off[k + 1] - g.rank_off[k]);
+    const int nmax = zsep_nmax(max_rank);
+    if (!nmax || max_rank <= 0) return out;
+    for (int k0 = 0; k0 < g.K;) {
+        const int t0 = g.rank_off[k0];
+        int k1 = k0 + 1;
+        while (k1 < g.K && g.rank_off[k1 + 1] - t0 <= nmax) ++k1;
+        const int n = g.rank_off[k1] - t0;
+        if (t0 + (n + 15) / 16 * 16 > g.Rpad_tc) return {};
+        out.push_back(ZsGroup{k0, k1, t0, n});
+        k0 = k1;
+    }
+    *nmax_out = nmax;
+    return out;
+}
+
 std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid *pyrs, int n_images, int form,
-                                int prec, const uint8_t *mask)
+                                int prec, const uint8_t *mask, bool fuse)
 {
     auto P = std::make_shared<Plan>();
     P->uid = g_plan_uid.fetch_add(1);
@@ -165,6 +201,19 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         }
     }
     P->glv.resize(m.groups.size());
+    const size_t ngr = m.groups.size();
+    P->g_fused.assign(ngr, 0); P->g_fg_off.assign(ngr, 0); P->g_n_fg.assign(ngr, 0); P->g_nmax.assign(ngr, 0);
+    P->g_fg.assign(ngr, {});
+    for (size_t gi = 0; gi < ngr; ++gi) {
+        // the fused kernel: BF16 or split-BF16 operands, per-filter factors, a compiled shape
+        if (!fuse || !P->bf || P->fp8 || !P->dec) break;
+        int nmax = 0;
+        P->g_fg[gi] = fused_groups(m.groups[gi], &nmax);
+        if (P->g_fg[gi].empty()) continue;
+        P->g_fused[gi] = 1;
+        P->g_n_fg[gi] = (int)P->g_fg[gi].size();
+        P->g_nmax[gi] = nmax;
+    }
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
         const Group &g = m.groups[gi];
         for (int im = 0; im < n_images; ++im) {
@@ -177,7 +226,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
                 if (Ho <= 0 || Wo <= 0) continue;
                 GroupLevel gl{j, 0, 0, Ho, Wo};
                 gl.out_off = bump.take(sizeof(float) * (size_t)g.K * Ho * Wo);
-                if (P->dec) gl.z_off = bump.take(sizeof(float) * (size_t)g.R * H * W);
+                if (P->dec && !P->g_fused[gi]) gl.z_off = bump.take(sizeof(float) * (size_t)g.R * H * W);
                 if (P->rec_tc(g)) {
                     gl.u_off = bump.take(sizeof(uint16_t) * (size_t)g.Upad * Ho * Wo);
                     if (P->split) gl.u_lo_off = bump.take(sizeof(uint16_t) * (size_t)g.Upad * Ho * Wo);
@@ -253,8 +302,20 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     for (size_t gi = 0; gi < ng; ++gi) {
         const Group &g = m.groups[gi];
         const size_t nj = std::max<size_t>(1, P->glv[gi].size());
-        const size_t job_bytes = P->bf ? sizeof(TcJob) : (P->dec ? sizeof(ZJob) : sizeof(CorrJob));
+        const size_t job_bytes = P->g_fused[gi] ? sizeof(ZsJob)
+                                 : P->bf        ? sizeof(TcJob)
+                                                : (P->dec ? sizeof(ZJob) : sizeof(CorrJob));
         P->g_jobs_off[gi] = jb.take(job_bytes * nj);
+        if (P->g_fused[gi]) {
+            P->g_fg_off[gi] = jb.take(sizeof(ZsGroup) * P->g_fg[gi].size());
+            int tc, tr;
+            zsep_tile(g.h, g.w, &tc, &tr);
+            long long tiles = 0;
+            for (const GroupLevel &gl : P->glv[gi])
+                tiles += (long long)((gl.Wo + tc - 1) / tc) * ((gl.Ho + tr - 1) / tr);
+            P->g_tiles[gi] = (int)std::min<long long>(tiles, 0x7fffffff);
+            continue;
+        }
         if (P->dec) P->g_sep_off[gi] = jb.take(sizeof(SepJob) * nj);
         if (P->rec_tc(g)) P->g_rec_off[gi] = jb.take(sizeof(TcJob) * nj);
         int tiles = 0, rec_tiles = 0;
@@ -323,6 +384,27 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
     }
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
         const Group &g = m.groups[gi];
+        if (P.g_fused[gi]) {
+            int tc, tr, begin = 0;
+            zsep_tile(g.h, g.w, &tc, &tr);
+            for (size_t i = 0; i < P.glv[gi].size(); ++i) {
+                const GroupLevel &gl = P.glv[gi][i];
+                const int H = P.sizes[gl.j].first, W = P.sizes[gl.j].second;
+                ZsJob &z = reinterpret_cast<ZsJob *>(hb + P.g_jobs_off[gi])[i];
+                if (!encode_level_tmap_tiles(&z.tmap, reinterpret_cast<const uint16_t *>(base + P.bf_off[gl.j]), H, W) ||
+                    (P.split && !encode_level_tmap_tiles(&z.tmap_lo,
+                                                         reinterpret_cast<const uint16_t *>(base + P.bf_lo_off[gl.j]),
+                                                         H, W)))
+                    return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+                z.out = reinterpret_cast<float *>(base + gl.out_off);
+                z.H = H; z.W = W; z.Ho = gl.Ho; z.Wo = gl.Wo;
+                z.tiles_x = (gl.Wo + tc - 1) / tc;
+                z.begin = begin;
+                begin += z.tiles_x * ((gl.Ho + tr - 1) / tr);
+            }
+            std::memcpy(hb + P.g_fg_off[gi], P.g_fg[gi].data(), sizeof(ZsGroup) * P.g_fg[gi].size());
+            continue;
+        }
         int begin = 0, rec_begin = 0;
         long long sep_begin = 0;
         for (size_t i = 0; i < P.glv[gi].size(); ++i) {
@@ -542,6 +624,16 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         const int nj = (int)P.glv[gi].size();
         cudaError_t e = cudaSuccess;
         const char *jobs = dblob + P.g_jobs_off[gi];
+        if (P.g_fused[gi]) {
+            Prof pr(ctx, gs, "zsep_tc");
+            e = launch_zsep_tc(reinterpret_cast<const ZsJob *>(jobs), nj, P.g_tiles[gi],
+                               reinterpret_cast<const ZsGroup *>(dblob + P.g_fg_off[gi]), P.g_n_fg[gi], g.d_C_tc,
+                               P.split ? g.d_C_tc_lo : nullptr, g.Rpad_tc, g.d_A, g.d_B, g.d_lam, g.d_rank_off, g.R,
+                               P.g_nmax[gi], g.h, g.w, ctx->d_err, gs);
+            if (e != cudaSuccess) return e;
+            pr.end();
+            return cudaSuccess;
+        }
         if (P.bf) {
             Prof pr(ctx, gs, P.dec ? "zproj_tc" : "corr_tc");
             e = launch_group_tc(P, g, reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], P.g_nt[gi], ctx->d_err,
@@ -688,7 +780,7 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, Arena &A, cuda
     for (size_t gi = 0; gi < m.groups.size() && e == cudaSuccess; ++gi) {
         const Group &g = m.groups[gi];
         const int nj = (int)P.glv[gi].size();
-        if (!nj) continue;
+        if (!nj || P.g_fused[gi]) continue;  // the fused kernel has no N tiling to choose
         const TcJob *jobs = reinterpret_cast<const TcJob *>(dblob + P.g_jobs_off[gi]);
         const char *op = P.fp8 ? "f8" : P.split ? "x3" : "x1";
         if (P.dec)
@@ -857,10 +949,10 @@ tdpm_status batch_arena_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyrami
     if (!m) return fail(TDPM_ERR_STATE, "unknown model id");
     if (form == TDPM_FORM_DECOMPOSED && !m->decomposed)
         return fail(TDPM_ERR_STATE, "decomposed form requested before tdpm_decompose");
-    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask);
+    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask, ctx->fuse);
     auto pit = ctx->plans.find(key);
     if (pit == ctx->plans.end()) {
-        auto plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask);
+        auto plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask, ctx->fuse);
         if (ctx->plans.size() > 256) ctx->plans.clear();
         pit = ctx->plans.emplace(key, plan).first;
     }
@@ -987,13 +1079,13 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
     if (form == TDPM_FORM_DECOMPOSED && !m->decomposed)
         return fail(TDPM_ERR_STATE, "decomposed form requested before tdpm_decompose");
     cudaStream_t s = (cudaStream_t)stream;
-    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask);
+    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask, ctx->fuse);
     std::shared_ptr<Plan> plan;
     auto pit = ctx->plans.find(key);
     if (pit != ctx->plans.end()) {
         plan = pit->second;
     } else {
-        plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask);
+        plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask, ctx->fuse);
         if (plan->max_W > 800 || plan->max_H > 800)
             return fail(TDPM_ERR_ARG, "part score maps wider or taller than 800 cells are not supported");
         if (ctx->plans.size() > 256) ctx->plans.clear();
@@ -1053,7 +1145,11 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
+            int captured = 0;
+            t_capture_launches = &captured;
             const cudaError_t eq = enqueue(ctx, *plan, *m, A, ctx->cap_stream);
+            t_capture_launches = nullptr;
+            A.graph_kernels = captured;
             e = cudaStreamEndCapture(ctx->cap_stream, &g);
             if (eq != cudaSuccess) e = eq;
         }
@@ -1065,8 +1161,12 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
             e = cudaSuccess;  // fall back to direct launches below
         }
     }
-    if (graphs && A.graph) e = cudaGraphLaunch(A.graph, s);
-    else e = enqueue(ctx, *plan, *m, A, s);
+    if (graphs && A.graph) {
+        e = cudaGraphLaunch(A.graph, s);
+        if (e == cudaSuccess) note_launches(A.graph_kernels);
+    } else {
+        e = enqueue(ctx, *plan, *m, A, s);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sc->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(sc->done, s);
     if (e != cudaSuccess) {
@@ -1178,6 +1278,15 @@ tdpm_status tdpm_release(tdpm_ctx *ctx, int32_t scores_id)
 
 // ------------------------------------------------------------------------------------------------ instrumentation
 uint64_t tdpm_kernel_launches(void) { return g_launches.load(); }
+
+tdpm_status tdpm_set_fusion(tdpm_ctx *ctx, int32_t enable)
+{
+    clear_error();
+    if (!ctx) return fail(TDPM_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->fuse = enable != 0;
+    return TDPM_OK;
+}
 
 tdpm_status tdpm_profile_enable(tdpm_ctx *ctx, int32_t enable)
 {

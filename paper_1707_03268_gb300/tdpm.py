@@ -132,6 +132,7 @@ SIGNATURES = {
                                  _VP, _VP]),
     "tdpm_kernel_launches": (ctypes.c_uint64, []),
     "tdpm_profile_enable": (_c_i32, [_VP, _c_i32]),
+    "tdpm_set_fusion": (_c_i32, [_VP, _c_i32]),
     "tdpm_profile_read": (_c_i32, [_VP, _c_i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_i32)]),
     "tdpm_profile_reset": (_c_i32, [_VP]),
@@ -461,6 +462,11 @@ def unpack_arg(a: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
 # --------------------------------------------------------------------------------------------------- instrumentation
 def tdpm_kernel_launches() -> int:
     return int(lib().tdpm_kernel_launches())
+
+
+def tdpm_set_fusion(ctx: int, enable: bool = True) -> None:
+    """Fused (one kernel) or two-launch channel stage + separable passes of the decomposed per-filter form."""
+    _check(lib().tdpm_set_fusion(ctx, 1 if enable else 0))
 
 
 def tdpm_profile_enable(ctx: int, enable: bool = True) -> None:

@@ -268,6 +268,7 @@ def test_autotuned_tiling_matches_default_tiling(torch, T, form, monkeypatch):
     for tune in ("1", "0"):
         monkeypatch.setenv("TDPM_AUTOTUNE", tune)
         c = T.tdpm_create(0)
+        T.tdpm_set_fusion(c, False)  # the two-launch form: its channel stage has N tilings to tune
         mid = T.tdpm_load_model(c, wl.model)
         if f == T.FORM_DECOMPOSED:
             T.tdpm_decompose(c, mid, 8, T.DECOMP_PER_FILTER, max_iters=60, seed=1)
