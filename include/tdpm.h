@@ -294,7 +294,10 @@ tdpm_status tdpm_profile_reset(tdpm_ctx *ctx);
  * balanced N tile width in two kernel forms: one CTA per tile, or persistent CTAs with two TMEM accumulators (the
  * epilogue of one tile overlapping the MMAs of the next). Entry `index`: its shape class ("kind:N:K blocks:
  * operands:M tiles", NUL-terminated, truncated to key_cap), the chosen width and form (1 = persistent); *n_entries
- * receives the number of entries (an index out of range only sets it). */
+ * receives the number of entries (an index out of range only sets it). Entries of the fused decomposed kernel (keys
+ * "zsep:16h+w:terms per group:operands:items") choose among its forms instead: *tile_n receives the form (0: one CTA
+ * per item; 1: persistent, two feature stages; 2: persistent, two Z buffers; 3: both; 4: persistent, one of each)
+ * and *persistent is 0. */
 tdpm_status tdpm_autotune_read(tdpm_ctx *ctx, int32_t index, char *key, size_t key_cap, int32_t *tile_n,
                                int32_t *persistent, int32_t *n_entries);
 

@@ -154,6 +154,7 @@ struct tdpm_ctx {
     int *h_err = nullptr;                // pinned mirror
     bool use_graphs = true;
     bool fuse = true;                    // fused channel stage + separable passes where possible (tdpm_set_fusion)
+    int zsep_form = -1;                  // fused kernel form forced by TDPM_ZSEP_FORM (-1: default / tuned)
     bool autotune = true;                // time the N tilings of a new plan's tensor-core launches (TDPM_AUTOTUNE=0: off)
     std::map<std::string, int> tune_cache;  // shape class of a tensor-core launch -> chosen N tile width
     // profiling

@@ -43,9 +43,12 @@ struct alignas(128) ZsJob {
     CUtensorMap tmap_lo;      // lo part (split-BF16 precision only)
     float *out;               // [K][Ho][Wo]
     int H, W, Ho, Wo;
-    int tiles_x;              // spatial tiles of this job along x
-    int begin;                // first spatial tile of this job (tiles numbered across the jobs of a launch)
-    int pad[2];
+    int pad[4];
+};
+
+// A spatial tile of the fused launch: its job, origin (first output column and row) and valid output rows.
+struct ZsTile {
+    int job, x0, y0, rows;
 };
 
 // A filter group of the fused launch: filters [k0, k1) of the shape group, whose terms [t0, t0 + n) (n <= nmax) are
@@ -120,7 +123,7 @@ void note_launches(int n);
 // slot: a distinct number per kernel (0 .. kSmemSlots-1) under which the setting is remembered.
 cudaError_t allow_max_dynamic_smem(const void *func, int slot);
 constexpr int kMaxDynamicSmem = 232448;
-constexpr int kSmemSlots = 16;
+constexpr int kSmemSlots = 24;
 
 // K8: FP32 SIMT direct correlation. filt_t: [h*w*32][Kpad] (filter index fastest), Kpad a multiple of 64.
 cudaError_t launch_corr_f32(const CorrJob *d_jobs, int n_jobs, int total_tiles, const float *filt_t, int K, int Kpad,
@@ -156,17 +159,27 @@ bool encode_level_tmap_fp8(CUtensorMap *map, const uint8_t *planar, long long ce
 bool encode_level_tmap_tiles(CUtensorMap *map, const uint16_t *planar, int H, int W);
 
 // K2+K3+K4 fused (per-filter mode, BF16 or split-BF16 operands): the channel stage on the tensor cores and the
-// separable passes with the recombination, over `tiles` spatial tiles (the jobs' begin fields number them) times
+// separable passes with the recombination, over `tiles` spatial tiles (records d_tiles, each naming its job) times
 // n_fg filter groups. cbank / cbank_lo: the channel-factor bank [1][4][ld][8] BF16 (hi, lo or null); every group
 // needs t0 + n rounded up to 16 <= ld. A, B, lam, rank_off as for launch_sep; nmax = 32 or 64 (zsep_nmax) bounds
 // the terms of a group. Shapes: zsep_shape (the filter shapes of the separable warp form).
 bool zsep_shape(int h, int w);
 void zsep_tile(int h, int w, int *tile_cols, int *tile_rows);  // output columns and rows of one spatial tile
 int zsep_nmax(int max_rank);                                     // 32, 64, or 0 when a filter has more terms
-cudaError_t launch_zsep_tc(const ZsJob *d_jobs, int n_jobs, int tiles, const ZsGroup *d_fg, int n_fg,
+// form: ZSEP_TILE, one CTA per item; or a persistent form, one CTA per SM walking the items with a producer warp
+// ahead of the compute warps (two TMEM accumulators), with one or two feature stages and one or two Z buffers
+// (zsep_form_fits tells which fit). The persistent forms read the groups' packed factor records d_frec: per filter
+// group, zsep_record_bytes bytes: a_r[0..h), b_r[0..w), lambda_r, zero-padded to zsep_factor_stride floats per term
+// for nmax terms (zero beyond the group's terms), then the rank offsets of the group's filters minus t0 (nmax + 2
+// ints). All forms give the same results.
+enum ZsepForm { ZSEP_TILE = 0, ZSEP_PERSIST_S2 = 1, ZSEP_PERSIST_Z2 = 2, ZSEP_PERSIST_S2Z2 = 3, ZSEP_PERSIST_S1 = 4 };
+cudaError_t launch_zsep_tc(const ZsJob *d_jobs, const ZsTile *d_tiles, int tiles, const ZsGroup *d_fg, int n_fg,
                            const void *cbank, const void *cbank_lo, int ld, const float *A, const float *B,
-                           const float *lam, const int *rank_off, int R, int nmax, int h, int w, int *d_err,
-                           cudaStream_t s);
+                           const float *lam, const int *rank_off, int R, const void *d_frec, int nmax, int h, int w,
+                           int *d_err, cudaStream_t s, int form);
+bool zsep_form_fits(int h, int w, bool split, int nmax, int form);
+int zsep_record_bytes(int h, int w, int nmax);
+int zsep_factor_stride(int h, int w);
 
 // FP32 NHWC -> BF16 planar for many levels in one launch (total = sum of 4 * cells).
 cudaError_t launch_to_bf16_planar(const ConvJob *d_jobs, int n_jobs, long long total, cudaStream_t s);

@@ -247,6 +247,8 @@ tdpm_status tdpm_create(tdpm_ctx **out, int32_t device, size_t mem_budget_bytes)
     c->autotune = !(at && at[0] == '0');
     const char *fu = std::getenv("TDPM_FUSE");
     c->fuse = !(fu && fu[0] == '0');
+    const char *zf = std::getenv("TDPM_ZSEP_FORM");
+    if (zf && zf[0] >= '0' && zf[0] <= '4' && zf[1] == 0) c->zsep_form = zf[0] - '0';
     *out = c;
     return TDPM_OK;
 }

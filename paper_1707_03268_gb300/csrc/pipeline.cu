@@ -114,7 +114,9 @@ struct Plan {
     // decomposed per-filter groups on tensor cores with the fused kernel: no Z maps; spatial tiles in g_tiles, filter
     // groups (ZsGroup table at g_fg_off) and their width bound
     std::vector<char> g_fused;
-    std::vector<size_t> g_fg_off;
+    std::vector<size_t> g_fg_off, g_tile_off, g_frec_off;
+    std::vector<std::vector<uint8_t>> g_frec;  // packed factor records of the filter groups (persistent forms)
+    bool zsep_forced = false;                  // the fused kernel's form was fixed by the context (not tuned)
     std::vector<int> g_n_fg, g_nmax;
     std::vector<std::vector<ZsGroup>> g_fg;
     size_t dt_off = 0, asm_off = 0;
@@ -131,10 +133,10 @@ namespace {
 
 // mask: null (every component of every image) or [n][components], nonzero = score that component on that image
 std::string plan_key(int model_id, const Model &m, int form, int prec, const tdpm_pyramid *pyrs, int n,
-                     const uint8_t *mask, bool fuse)
+                     const uint8_t *mask, bool fuse, int zsep_form)
 {
     std::string k = std::to_string(model_id) + ":" + std::to_string(m.version) + ":" + std::to_string(form) + ":" +
-                    std::to_string(prec) + ":" + std::to_string(n) + (fuse ? ":f" : ":u");
+                    std::to_string(prec) + ":" + std::to_string(n) + (fuse ? ":f" : ":u") + std::to_string(zsep_form);
     for (int i = 0; i < n; ++i) {
         k += "|" + std::to_string(pyrs[i].lambda);
         for (int j = 0; j < pyrs[i].n_levels; ++j)
@@ -171,7 +173,7 @@ std::vector<ZsGroup> fused_groups(const Group &g, int *nmax_out)
 }
 
 std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid *pyrs, int n_images, int form,
-                                int prec, const uint8_t *mask, bool fuse)
+                                int prec, const uint8_t *mask, bool fuse, int zsep_form)
 {
     auto P = std::make_shared<Plan>();
     P->uid = g_plan_uid.fetch_add(1);
@@ -202,7 +204,8 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     }
     P->glv.resize(m.groups.size());
     const size_t ngr = m.groups.size();
-    P->g_fused.assign(ngr, 0); P->g_fg_off.assign(ngr, 0); P->g_n_fg.assign(ngr, 0); P->g_nmax.assign(ngr, 0);
+    P->g_fused.assign(ngr, 0); P->g_fg_off.assign(ngr, 0); P->g_tile_off.assign(ngr, 0); P->g_frec_off.assign(ngr, 0);
+    P->g_frec.assign(ngr, {}); P->g_n_fg.assign(ngr, 0); P->g_nmax.assign(ngr, 0);
     P->g_fg.assign(ngr, {});
     for (size_t gi = 0; gi < ngr; ++gi) {
         // the fused kernel: BF16 or split-BF16 operands, per-filter factors, a compiled shape
@@ -213,6 +216,24 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         P->g_fused[gi] = 1;
         P->g_n_fg[gi] = (int)P->g_fg[gi].size();
         P->g_nmax[gi] = nmax;
+        // packed factor records: the same FP32 values as the group's device factor copies
+        const Group &g = m.groups[gi];
+        const int rec = zsep_record_bytes(g.h, g.w, nmax), fs = zsep_factor_stride(g.h, g.w);
+        std::vector<uint8_t> &out = P->g_frec[gi];
+        out.assign((size_t)rec * P->g_fg[gi].size(), 0);
+        for (size_t f = 0; f < P->g_fg[gi].size(); ++f) {
+            const ZsGroup &G = P->g_fg[gi][f];
+            float *fv = reinterpret_cast<float *>(out.data() + f * rec);
+            int *ro = reinterpret_cast<int *>(fv + (size_t)nmax * fs);
+            for (int k = G.k0; k < G.k1; ++k)
+                for (int r = g.rank_off[k]; r < g.rank_off[k + 1]; ++r) {
+                    float *t = fv + (size_t)(r - G.t0) * fs;
+                    for (int i = 0; i < g.h; ++i) t[i] = (float)g.A[(size_t)i * g.R + r];
+                    for (int i = 0; i < g.w; ++i) t[g.h + i] = (float)g.B[(size_t)i * g.R + r];
+                    t[g.h + g.w] = (float)g.Lam[(size_t)k * g.R + r];
+                }
+            for (int i = 0; i <= G.k1 - G.k0; ++i) ro[i] = g.rank_off[G.k0 + i] - G.t0;
+        }
     }
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
         const Group &g = m.groups[gi];
@@ -314,6 +335,16 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
             for (const GroupLevel &gl : P->glv[gi])
                 tiles += (long long)((gl.Wo + tc - 1) / tc) * ((gl.Ho + tr - 1) / tr);
             P->g_tiles[gi] = (int)std::min<long long>(tiles, 0x7fffffff);
+            P->g_tile_off[gi] = jb.take(sizeof(ZsTile) * std::max(1, P->g_tiles[gi]));
+            P->g_frec_off[gi] = jb.take(P->g_frec[gi].size());
+            // untuned: the persistent form with two feature stages where it fits
+            P->g_nt[gi] = zsep_form_fits(g.h, g.w, P->split, P->g_nmax[gi], ZSEP_PERSIST_S2) ? ZSEP_PERSIST_S2
+                          : zsep_form_fits(g.h, g.w, P->split, P->g_nmax[gi], ZSEP_PERSIST_S1) ? ZSEP_PERSIST_S1
+                                                                                              : ZSEP_TILE;
+            if (zsep_form >= 0 && zsep_form_fits(g.h, g.w, P->split, P->g_nmax[gi], zsep_form)) {
+                P->g_nt[gi] = zsep_form;  // fixed by the context
+                P->zsep_forced = true;
+            }
             continue;
         }
         if (P->dec) P->g_sep_off[gi] = jb.take(sizeof(SepJob) * nj);
@@ -385,8 +416,9 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
         const Group &g = m.groups[gi];
         if (P.g_fused[gi]) {
-            int tc, tr, begin = 0;
+            int tc, tr;
             zsep_tile(g.h, g.w, &tc, &tr);
+            ZsTile *tl = reinterpret_cast<ZsTile *>(hb + P.g_tile_off[gi]);
             for (size_t i = 0; i < P.glv[gi].size(); ++i) {
                 const GroupLevel &gl = P.glv[gi][i];
                 const int H = P.sizes[gl.j].first, W = P.sizes[gl.j].second;
@@ -398,11 +430,11 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
                     return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
                 z.out = reinterpret_cast<float *>(base + gl.out_off);
                 z.H = H; z.W = W; z.Ho = gl.Ho; z.Wo = gl.Wo;
-                z.tiles_x = (gl.Wo + tc - 1) / tc;
-                z.begin = begin;
-                begin += z.tiles_x * ((gl.Ho + tr - 1) / tr);
+                for (int y0 = 0; y0 < gl.Ho; y0 += tr)
+                    for (int x0 = 0; x0 < gl.Wo; x0 += tc) *tl++ = ZsTile{(int)i, x0, y0, std::min(tr, gl.Ho - y0)};
             }
             std::memcpy(hb + P.g_fg_off[gi], P.g_fg[gi].data(), sizeof(ZsGroup) * P.g_fg[gi].size());
+            std::memcpy(hb + P.g_frec_off[gi], P.g_frec[gi].data(), P.g_frec[gi].size());
             continue;
         }
         int begin = 0, rec_begin = 0;
@@ -626,10 +658,11 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         const char *jobs = dblob + P.g_jobs_off[gi];
         if (P.g_fused[gi]) {
             Prof pr(ctx, gs, "zsep_tc");
-            e = launch_zsep_tc(reinterpret_cast<const ZsJob *>(jobs), nj, P.g_tiles[gi],
+            e = launch_zsep_tc(reinterpret_cast<const ZsJob *>(jobs),
+                               reinterpret_cast<const ZsTile *>(dblob + P.g_tile_off[gi]), P.g_tiles[gi],
                                reinterpret_cast<const ZsGroup *>(dblob + P.g_fg_off[gi]), P.g_n_fg[gi], g.d_C_tc,
                                P.split ? g.d_C_tc_lo : nullptr, g.Rpad_tc, g.d_A, g.d_B, g.d_lam, g.d_rank_off, g.R,
-                               P.g_nmax[gi], g.h, g.w, ctx->d_err, gs);
+                               dblob + P.g_frec_off[gi], P.g_nmax[gi], g.h, g.w, ctx->d_err, gs, P.g_nt[gi]);
             if (e != cudaSuccess) return e;
             pr.end();
             return cudaSuccess;
@@ -742,8 +775,10 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, Arena &A, cuda
         if (r == cudaSuccess) r = cudaEventElapsedTime(ms, ev0, ev1);
         return r;
     };
+    // time every candidate configuration code (or, with none given, every balanced N tile width in the tile and the
+    // persistent form) and keep the fastest
     auto choose = [&](const std::string &key, int N, const std::function<cudaError_t(int)> &launch_nt,
-                      int *chosen) -> cudaError_t {
+                      int *chosen, std::vector<int> codes = {}) -> cudaError_t {
         auto it = ctx->tune_cache.find(key);
         if (it != ctx->tune_cache.end()) {
             *chosen = it->second;
@@ -757,30 +792,49 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, Arena &A, cuda
             if (r == cudaSuccess) r = launch_convert(P, dblob, s);
             if (r != cudaSuccess) return r;
         }
-        // every balanced width, in the tile form and in the persistent form
-        int cand[4];
-        const int nc = corr_tc_nt_candidates(N, cand);
+        if (codes.empty()) {
+            int cand[4];
+            const int nc = corr_tc_nt_candidates(N, cand);
+            for (int i = 0; i < nc; ++i)
+                for (int pers = 0; pers < 2; ++pers) codes.push_back(cand[i] | (pers ? kTcPersistent : 0));
+        }
         float best = 0.f;
         bool first = true;
-        for (int i = 0; i < nc; ++i)
-            for (int pers = 0; pers < 2; ++pers) {
-                const int code = cand[i] | (pers ? kTcPersistent : 0);
-                float ms = 0.f;
-                const cudaError_t r = time_ms([&] { return launch_nt(code); }, &ms);
-                if (r != cudaSuccess) return r;
-                if (first || ms < best) {
-                    best = ms;
-                    *chosen = code;
-                    first = false;
-                }
+        for (int code : codes) {
+            float ms = 0.f;
+            const cudaError_t r = time_ms([&] { return launch_nt(code); }, &ms);
+            if (r != cudaSuccess) return r;
+            if (first || ms < best) {
+                best = ms;
+                *chosen = code;
+                first = false;
             }
+        }
         ctx->tune_cache[key] = *chosen;
         return cudaSuccess;
     };
     for (size_t gi = 0; gi < m.groups.size() && e == cudaSuccess; ++gi) {
         const Group &g = m.groups[gi];
         const int nj = (int)P.glv[gi].size();
-        if (!nj || P.g_fused[gi]) continue;  // the fused kernel has no N tiling to choose
+        if (!nj) continue;
+        if (P.g_fused[gi] && P.zsep_forced) continue;
+        if (P.g_fused[gi]) {
+            // the fused kernel: its forms (one CTA per item, or persistent with one or two feature stages / Z buffers)
+            std::vector<int> forms;
+            for (int f : {ZSEP_TILE, ZSEP_PERSIST_S2, ZSEP_PERSIST_Z2, ZSEP_PERSIST_S2Z2, ZSEP_PERSIST_S1})
+                if (zsep_form_fits(g.h, g.w, P.split, P.g_nmax[gi], f)) forms.push_back(f);
+            const std::string key = tune_key("zsep", g.h * 16 + g.w, P.g_nmax[gi], P.split ? "x3" : "x1",
+                                             P.g_tiles[gi] * P.g_n_fg[gi]);
+            e = choose(key, 0, [&](int form) {
+                return launch_zsep_tc(reinterpret_cast<const ZsJob *>(dblob + P.g_jobs_off[gi]),
+                                      reinterpret_cast<const ZsTile *>(dblob + P.g_tile_off[gi]), P.g_tiles[gi],
+                                      reinterpret_cast<const ZsGroup *>(dblob + P.g_fg_off[gi]), P.g_n_fg[gi],
+                                      g.d_C_tc, P.split ? g.d_C_tc_lo : nullptr, g.Rpad_tc, g.d_A, g.d_B, g.d_lam,
+                                      g.d_rank_off, g.R, dblob + P.g_frec_off[gi], P.g_nmax[gi], g.h, g.w, ctx->d_err,
+                                      s, form);
+            }, &P.g_nt[gi], forms);
+            continue;
+        }
         const TcJob *jobs = reinterpret_cast<const TcJob *>(dblob + P.g_jobs_off[gi]);
         const char *op = P.fp8 ? "f8" : P.split ? "x3" : "x1";
         if (P.dec)
@@ -949,10 +1003,10 @@ tdpm_status batch_arena_bytes(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyrami
     if (!m) return fail(TDPM_ERR_STATE, "unknown model id");
     if (form == TDPM_FORM_DECOMPOSED && !m->decomposed)
         return fail(TDPM_ERR_STATE, "decomposed form requested before tdpm_decompose");
-    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask, ctx->fuse);
+    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask, ctx->fuse, ctx->zsep_form);
     auto pit = ctx->plans.find(key);
     if (pit == ctx->plans.end()) {
-        auto plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask, ctx->fuse);
+        auto plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask, ctx->fuse, ctx->zsep_form);
         if (ctx->plans.size() > 256) ctx->plans.clear();
         pit = ctx->plans.emplace(key, plan).first;
     }
@@ -1079,13 +1133,13 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
     if (form == TDPM_FORM_DECOMPOSED && !m->decomposed)
         return fail(TDPM_ERR_STATE, "decomposed form requested before tdpm_decompose");
     cudaStream_t s = (cudaStream_t)stream;
-    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask, ctx->fuse);
+    const std::string key = plan_key(model_id, *m, form, precision, pyrs, n_images, mask, ctx->fuse, ctx->zsep_form);
     std::shared_ptr<Plan> plan;
     auto pit = ctx->plans.find(key);
     if (pit != ctx->plans.end()) {
         plan = pit->second;
     } else {
-        plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask, ctx->fuse);
+        plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask, ctx->fuse, ctx->zsep_form);
         if (plan->max_W > 800 || plan->max_H > 800)
             return fail(TDPM_ERR_ARG, "part score maps wider or taller than 800 cells are not supported");
         if (ctx->plans.size() > 256) ctx->plans.clear();

@@ -490,8 +490,13 @@ def tdpm_profile_reset(ctx: int) -> None:
     _check(lib().tdpm_profile_reset(ctx))
 
 
+ZSEP_FORMS = {0: "tile", 1: "persistent/2 stages", 2: "persistent/2 Z buffers", 3: "persistent/2 stages/2 Z buffers",
+              4: "persistent"}
+
+
 def tdpm_autotune_read(ctx: int) -> dict:
-    """{shape class: "<N tile width>" or "<N tile width>/persistent"} picked by the context's autotuner so far."""
+    """{shape class: "<N tile width>" or "<N tile width>/persistent", or for the fused decomposed kernel its form}
+    picked by the context's autotuner so far."""
     n = _c_i32()
     _check(lib().tdpm_autotune_read(ctx, -1, None, 0, None, None, ctypes.byref(n)))
     out = {}
@@ -499,5 +504,9 @@ def tdpm_autotune_read(ctx: int) -> dict:
         key = ctypes.create_string_buffer(128)
         nt, pers = _c_i32(), _c_i32()
         _check(lib().tdpm_autotune_read(ctx, i, key, 128, ctypes.byref(nt), ctypes.byref(pers), ctypes.byref(n)))
-        out[key.value.decode()] = f"{nt.value}/persistent" if pers.value else str(nt.value)
+        k = key.value.decode()
+        if k.startswith("zsep:"):
+            out[k] = ZSEP_FORMS.get(nt.value, str(nt.value))
+        else:
+            out[k] = f"{nt.value}/persistent" if pers.value else str(nt.value)
     return out

@@ -162,3 +162,35 @@ def test_unfusable_groups_fall_back(torch, T, ctx):
             np.testing.assert_array_equal(a, T.tdpm_get_maps(ctx, plain, T.MAP_FILTER_SCORE, fid, j))
     T.tdpm_release(ctx, fused)
     T.tdpm_release(ctx, plain)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_every_fused_form_gives_the_same_maps(torch, T, prec, monkeypatch):
+    """The fused kernel's forms (one CTA per item; persistent with one or two feature stages and Z buffers, forced
+    through TDPM_ZSEP_FORM; a form that does not fit a shape falls back to the default) give identical maps."""
+    wl = synth.config_c2()
+    pyrs = _images(5)
+    p = T.PREC_BF16X3 if prec == "bf16x3" else T.PREC_BF16
+    results = []
+    for form in ("0", "1", "2", "3", "4"):
+        monkeypatch.setenv("TDPM_ZSEP_FORM", form)
+        c = T.tdpm_create(0)
+        mid = T.tdpm_load_model(c, wl.model)
+        T.tdpm_decompose(c, mid, 8, T.DECOMP_PER_FILTER, max_iters=40, seed=2)
+        n_f, _ = T.tdpm_model_info(c, mid)
+        sid = T.tdpm_build_batch_scores(c, mid, [device_pyramid(py, torch) for py in pyrs], T.FORM_DECOMPOSED, p)
+        maps = {}
+        for i, py in enumerate(pyrs):
+            for fid in range(n_f):
+                for j in range(len(py.levels)):
+                    try:
+                        maps[(i, fid, j)] = T.tdpm_get_maps(c, sid, T.MAP_FILTER_SCORE, fid, j, image=i)
+                    except T.TdpmError:
+                        pass
+        results.append(maps)
+        T.tdpm_destroy(c)
+    assert len(results[0]) > 100
+    for other in results[1:]:
+        assert other.keys() == results[0].keys()
+        for key, a in results[0].items():
+            np.testing.assert_array_equal(other[key], a)
