@@ -210,9 +210,9 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool, fuse
             for p in comp.parts:
                 hp, wp = p.filt.shape[:2]
                 Hs, Ws = Hp - hp + 1, Wp - wp + 1
-                # x pass: read the part map, write values + argmax at X sampled columns of every row;
-                # y pass: read them back, write values + argmax at the Y x X anchored positions
-                out["dt"][0] += Hs * Ws * 4 + 2 * (Hs * X * 8) + Y * X * 8
+                # fused passes: read the part map once, write values + argmax at the Y x X anchored positions (the
+                # x-pass intermediate stays in shared memory)
+                out["dt"][0] += Hs * Ws * 4 + Y * X * 8
             out["assemble"][0] += Y * X * 4 * (n + 2)
     return {k: {"bytes": v[0], "flops": v[1]} for k, v in out.items()}
 

@@ -200,7 +200,9 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
 
 /* Step 4: every scored position with s >= tau, ordered by (image, component, level, y, x), copied to the host array
  * `out` (capacity records). Blocks until `stream` has finished. *n_out = number of detections, even when it exceeds
- * capacity (then ERR_CAPACITY and the first `capacity` records are written). */
+ * capacity (then ERR_CAPACITY and the first `capacity` records are written). Records of `out` past *n_out (within
+ * capacity) may be overwritten: the count and a prefix of the records come back in one copy, sized from the previous
+ * read-back of the same plan. */
 tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detection *out, size_t capacity,
                         size_t *n_out, void *stream);
 

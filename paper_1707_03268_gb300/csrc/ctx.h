@@ -8,6 +8,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -152,6 +153,8 @@ struct tdpm_ctx {
     size_t tau_cap = 0;
     int *d_err = nullptr;                // raised by bounded device waits
     int *h_err = nullptr;                // pinned mirror
+    long long *h_total = nullptr;        // pinned: detection count read back with the records
+    std::unordered_map<uint64_t, size_t> det_last;  // plan uid -> detections of its last read-back (copy size hint)
     bool use_graphs = true;
     bool fuse = true;                    // fused channel stage + separable passes where possible (tdpm_set_fusion)
     int zsep_form = -1;                  // fused kernel form forced by TDPM_ZSEP_FORM (-1: default / tuned)

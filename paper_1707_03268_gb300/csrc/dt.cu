@@ -17,6 +17,12 @@
 //         memory, one warp per column takes the sampled rows p = y_off + y_step*i, and the results are staged and
 //         written back as rows of 8: D[i][k], A[i][k] = (qy << 16) | IV[qy][k].
 // Both passes find their job with a 32-ary warp search (the jobs' xbegin / ybegin count CTAs).
+//
+// Fused form (dt_xy_kernel, the one the scoring path runs): one CTA per (job, strip of 32 sampled columns). The x pass
+// (warp per row, the row staged in shared memory, lane = sampled column of the strip) writes V and IV column-major
+// into shared memory (odd column stride: conflict-free), with per-warp column maxima; the y pass takes lane = column,
+// warp = sampled row, so each warp writes 32 consecutive results. The intermediate never reaches device memory; the
+// scans and line maxima are those of the two-pass form, so the results are identical.
 #include "internal.h"
 
 namespace tdpm {
@@ -209,9 +215,91 @@ __global__ void __launch_bounds__(DT_WARPS * 32) dt_y_kernel(const DtJob *__rest
     }
 }
 
+constexpr int DT_KS = 32;  // sampled columns per CTA of the fused form
+
+// shared memory: V and IV of the strip [32][hstride] each (hstride odd, >= H), one staged row per warp [wmax], and the
+// warps' partial column maxima [8][32]
+__global__ void __launch_bounds__(DT_WARPS * 32, 4) dt_xy_kernel(const DtJob *__restrict__ jobs, int n_jobs, int hstride,
+                                                              int wmax)
+{
+    extern __shared__ float sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const DtJob J = jobs[cta_job<true>(jobs, n_jobs, blockIdx.x, lane)];  // xbegin: first CTA (strip) of the job
+    const int k0 = (blockIdx.x - J.xbegin) * DT_KS;
+    const int ncols = min(DT_KS, J.nx - k0);
+    float *Vs = sm;
+    int32_t *IVs = reinterpret_cast<int32_t *>(sm + DT_KS * hstride);
+    float *L = sm + 2 * DT_KS * hstride + warp * wmax;
+    float *pmax = sm + 2 * DT_KS * hstride + DT_WARPS * wmax;
+    const int H = J.H, n = J.W;
+    const bool active = lane < ncols;
+    const int px = J.x_off + J.x_step * (k0 + lane);  // this lane's sampled column
+    float cmax = -INFINITY;                           // its column maximum over this warp's rows
+    for (int y = warp; y < H; y += DT_WARPS) {
+        const float *in = J.S + (size_t)y * n;
+        float mx = -INFINITY;
+        for (int q = lane; q < n; q += 32) {
+            const float v = __ldg(in + q);
+            L[q] = v;
+            mx = fmaxf(mx, v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        __syncwarp();
+        if (active) {
+            DtLine c;
+            dt_line_init(c, J.lx, J.qx, mx);
+            float best;
+            int arg;
+            dt_scan(c, L, n, px, best, arg);
+            Vs[lane * hstride + y] = best;
+            IVs[lane * hstride + y] = arg;
+            cmax = fmaxf(cmax, best);
+        }
+        __syncwarp();  // the row buffer is refilled next
+    }
+    pmax[warp * 32 + lane] = cmax;
+    __syncthreads();
+    if (!active) return;
+    float mx = pmax[lane];
+#pragma unroll
+    for (int w = 1; w < DT_WARPS; ++w) mx = fmaxf(mx, pmax[w * 32 + lane]);
+    DtLine c;
+    dt_line_init(c, J.ly, J.qy, mx);
+    const float *col = Vs + lane * hstride;
+    const int32_t *icol = IVs + lane * hstride;
+    const int k = k0 + lane;
+    for (int i = warp; i < J.ny; i += DT_WARPS) {
+        float best;
+        int arg;
+        dt_scan(c, col, H, J.y_off + J.y_step * i, best, arg);
+        J.D[(size_t)i * J.nx + k] = best;
+        J.A[(size_t)i * J.nx + k] = (arg << 16) | icol[arg];
+    }
+}
+
 }  // namespace
 
 int dt_lines_per_cta() { return DT_WARPS; }
+int dt_strip_columns() { return DT_KS; }
+
+size_t dt_fused_smem_bytes(int max_W, int max_H)
+{
+    return sizeof(float) * (2 * (size_t)DT_KS * (size_t)(max_H | 1) + (size_t)DT_WARPS * max_W + DT_WARPS * 32);
+}
+
+cudaError_t launch_dt_fused(const DtJob *d_jobs, int n_jobs, int ctas, int max_W, int max_H, cudaStream_t s)
+{
+    if (n_jobs <= 0 || ctas <= 0) return cudaSuccess;
+    if (max_W > 800 || max_H > 800 || max_W < 1 || max_H < 1) return cudaErrorInvalidValue;
+    const size_t smem = dt_fused_smem_bytes(max_W, max_H);
+    if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(dt_xy_kernel), 6 + 18);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    dt_xy_kernel<<<ctas, DT_WARPS * 32, smem, s>>>(d_jobs, n_jobs, max_H | 1, max_W);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_ctas, int y_ctas, int max_W, int max_H, cudaStream_t s)
 {

@@ -123,7 +123,7 @@ void note_launches(int n);
 // slot: a distinct number per kernel (0 .. kSmemSlots-1) under which the setting is remembered.
 cudaError_t allow_max_dynamic_smem(const void *func, int slot);
 constexpr int kMaxDynamicSmem = 232448;
-constexpr int kSmemSlots = 24;
+constexpr int kSmemSlots = 32;
 
 // K8: FP32 SIMT direct correlation. filt_t: [h*w*32][Kpad] (filter index fastest), Kpad a multiple of 64.
 cudaError_t launch_corr_f32(const CorrJob *d_jobs, int n_jobs, int total_tiles, const float *filt_t, int K, int Kpad,
@@ -207,6 +207,11 @@ long long sep_job_items(int mode, int h, int w, int Ho, int Wo, int K, int *tile
 // K5/K6: distance transform passes (x_ctas / y_ctas: the CTA totals the jobs' xbegin / ybegin count; sides <= 800).
 cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_ctas, int y_ctas, int max_W, int max_H, cudaStream_t s);
 int dt_lines_per_cta();
+// K5+K6 fused: one CTA per (job, strip of dt_strip_columns() sampled columns), the jobs' xbegin counting those CTAs;
+// V and IV stay in shared memory (the jobs' V / IV are not used). Results identical to launch_dt.
+cudaError_t launch_dt_fused(const DtJob *d_jobs, int n_jobs, int ctas, int max_W, int max_H, cudaStream_t s);
+int dt_strip_columns();
+size_t dt_fused_smem_bytes(int max_W, int max_H);
 
 // K7: assembly (shift and sum), then detection count / scan / write.
 cudaError_t launch_assemble(const AsmJob *d_jobs, int n_jobs, long long total, cudaStream_t s);

@@ -230,7 +230,8 @@ tdpm_status tdpm_create(tdpm_ctx **out, int32_t device, size_t mem_budget_bytes)
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, 16);  // error flag at 0, detection count at 8
+    if (e == cudaSuccess) c->h_total = reinterpret_cast<long long *>(reinterpret_cast<char *>(c->h_err) + 8);
     if (e != cudaSuccess) {
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
         for (cudaStream_t st : c->side) cudaStreamDestroy(st);

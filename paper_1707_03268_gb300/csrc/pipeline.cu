@@ -120,7 +120,7 @@ struct Plan {
     std::vector<int> g_n_fg, g_nmax;
     std::vector<std::vector<ZsGroup>> g_fg;
     size_t dt_off = 0, asm_off = 0;
-    int x_warps = 0, y_warps = 0, max_W = 1, max_H = 1;  // x_warps / y_warps: CTAs of the two DT passes
+    int dt_ctas = 0, max_W = 1, max_H = 1;  // CTAs of the fused distance transform (strips of sampled columns)
     std::vector<std::pair<size_t, int>> patches;  // blob offsets of caller level pointers
 
     // joint decomposition with tensor-core operands: the separable stage writes U_r and Lambda U runs as a GEMM
@@ -291,8 +291,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
                 dp.X = X; dp.Y = Y; dp.vx = Pp.vx; dp.vy = Pp.vy;
                 std::memcpy(dp.d, Pp.d, sizeof(dp.d));
                 dp.s_off = P->filter_maps.at({Pp.fid, l}).off;
-                dp.v_off = bump.take(sizeof(float) * (size_t)dp.Hs * X);
-                dp.iv_off = bump.take(sizeof(int32_t) * (size_t)dp.Hs * X);
+                dp.v_off = dp.iv_off = 0;  // the fused distance transform keeps V and IV in shared memory
                 dp.d_off = bump.take(sizeof(float) * (size_t)Y * X);
                 dp.a_off = bump.take(sizeof(int32_t) * (size_t)Y * X);
                 P->dt_maps[{Pp.fid, j}] = MapRef{dp.d_off, Y, X};
@@ -384,8 +383,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     P->blob_bytes = align256(jb.off);
     P->arena_bytes = P->blob_off + P->blob_bytes;
     for (const DtPlan &p : P->dts) {
-        P->x_warps += (p.Hs + dt_lines_per_cta() - 1) / dt_lines_per_cta();  // CTAs of the two passes
-        P->y_warps += (p.X + dt_lines_per_cta() - 1) / dt_lines_per_cta();
+        P->dt_ctas += (p.X + dt_strip_columns() - 1) / dt_strip_columns();
         P->max_W = std::max(P->max_W, p.Ws);
         P->max_H = std::max(P->max_H, p.Hs);
     }
@@ -507,7 +505,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
         }
     }
     DtJob *dj = reinterpret_cast<DtJob *>(hb + P.dt_off);
-    int xw = 0, yw = 0;
+    int xw = 0;
     for (size_t i = 0; i < P.dts.size(); ++i) {
         const DtPlan &p = P.dts[i];
         DtJob &d = dj[i];
@@ -516,13 +514,13 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
         d.lx = p.d[0]; d.qx = p.d[1]; d.ly = p.d[2]; d.qy = p.d[3];
         d.x_off = p.vx; d.x_step = 2; d.nx = p.X;
         d.y_off = p.vy; d.y_step = 2; d.ny = p.Y;
-        d.V = reinterpret_cast<float *>(base + p.v_off);
-        d.IV = reinterpret_cast<int32_t *>(base + p.iv_off);
+        d.V = nullptr;
+        d.IV = nullptr;
         d.D = reinterpret_cast<float *>(base + p.d_off);
         d.A = reinterpret_cast<int32_t *>(base + p.a_off);
-        d.xbegin = xw; d.ybegin = yw;
-        xw += (p.Hs + dt_lines_per_cta() - 1) / dt_lines_per_cta();
-        yw += (p.X + dt_lines_per_cta() - 1) / dt_lines_per_cta();
+        d.xbegin = xw;  // first CTA (strip of sampled columns) of the job in the fused launch
+        d.ybegin = 0;
+        xw += (p.X + dt_strip_columns() - 1) / dt_strip_columns();
     }
     AsmJob *aj = reinterpret_cast<AsmJob *>(hb + P.asm_off);
     long long pos = 0;
@@ -730,8 +728,8 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
     }
     {
         Prof pr(ctx, s, "dt");
-        e = launch_dt(reinterpret_cast<const DtJob *>(dblob + P.dt_off), (int)P.dts.size(), P.x_warps, P.y_warps,
-                      P.max_W, P.max_H, s);
+        e = launch_dt_fused(reinterpret_cast<const DtJob *>(dblob + P.dt_off), (int)P.dts.size(), P.dt_ctas, P.max_W,
+                            P.max_H, s);
         if (e != cudaSuccess) return e;
         pr.end();
     }
@@ -1052,18 +1050,18 @@ tdpm_status detect_impl(tdpm_ctx *ctx, int32_t scores_id, float tau, const float
         CUDA_TRY(cudaMemcpyAsync(ctx->d_job_tau, jt.data(), sizeof(float) * jt.size(), cudaMemcpyHostToDevice, s));
         d_job_tau = ctx->d_job_tau;
     }
-    // count and scan, read the count back, then write only the records that will be copied
+    // count, scan and the ordered write of up to `want` records in one go, then ONE read-back: the count, the device
+    // error flag and a prefix of the records as long as this plan's last count; a second copy only when more were
+    // found (and a second write only when the device buffer was too short)
     Prof pr(ctx, s, "detect");
     CUDA_TRY(launch_detect_count(jobs, (int)P.asms.size(), P.total, tau, d_job_tau, counts, offsets, P.n_det_blocks,
                                  d_total, s));
-    long long total = 0;
-    CUDA_TRY(cudaMemcpyAsync(&total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if ((st = check_device_flag(ctx))) return st;
-    const size_t n = std::min<size_t>((size_t)total, capacity);
-    if (n > ctx->rec_cap) {
-        const size_t cap = std::max(n, ctx->rec_cap * 2);
+    const size_t limit = std::min<size_t>((size_t)std::max<long long>(P.total, 0), capacity);
+    auto grow = [&](size_t need) -> tdpm_status {
+        if (need <= ctx->rec_cap) return TDPM_OK;
+        const size_t cap = std::max(need, ctx->rec_cap * 2);
         if (ctx->d_records) {
+            cudaStreamSynchronize(s);
             cudaFree(ctx->d_records);
             ctx->used -= std::min(ctx->used, ctx->rec_cap * sizeof(tdpm_detection));
             ctx->d_records = nullptr;
@@ -1074,13 +1072,41 @@ tdpm_status detect_impl(tdpm_ctx *ctx, int32_t scores_id, float tau, const float
         CUDA_TRY(cudaMalloc(&ctx->d_records, cap * sizeof(tdpm_detection)));
         ctx->rec_cap = cap;
         ctx->used += cap * sizeof(tdpm_detection);
+        return TDPM_OK;
+    };
+    auto hint = ctx->det_last.find(P.uid);
+    const size_t last = hint == ctx->det_last.end() ? 4096 : hint->second;
+    const size_t want = std::min(limit, std::max(ctx->rec_cap, last + last / 8 + 64));
+    if ((st = grow(want))) return st;
+    if (want)
+        CUDA_TRY(launch_detect_write(jobs, (int)P.asms.size(), P.total, tau, d_job_tau, offsets, P.n_det_blocks,
+                                     ctx->d_records, (long long)want, sc->model_id, s));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    const size_t first = hint == ctx->det_last.end() ? 0 : std::min(want, last);
+    if (first) CUDA_TRY(cudaMemcpyAsync(out, ctx->d_records, first * sizeof(tdpm_detection), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (*ctx->h_err) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        *ctx->h_err = 0;
+        return fail(TDPM_ERR_TIMEOUT, "a bounded device wait expired; results of the last scoring are invalid");
     }
-    if (n) {
+    const long long total = *ctx->h_total;
+    const size_t n = std::min<size_t>((size_t)total, capacity);
+    if (n > want) {
+        // the device buffer was too short: write again into a larger one
+        if ((st = grow(n))) return st;
         CUDA_TRY(launch_detect_write(jobs, (int)P.asms.size(), P.total, tau, d_job_tau, offsets, P.n_det_blocks,
                                      ctx->d_records, (long long)n, sc->model_id, s));
         CUDA_TRY(cudaMemcpyAsync(out, ctx->d_records, n * sizeof(tdpm_detection), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
+    } else if (n > first) {
+        CUDA_TRY(cudaMemcpyAsync(out + first, ctx->d_records + first, (n - first) * sizeof(tdpm_detection),
+                                 cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
     }
+    if (ctx->det_last.size() > 4096) ctx->det_last.clear();  // hints of plans long gone
+    ctx->det_last[P.uid] = n;
     pr.end();
     CUDA_TRY(cudaEventRecord(sc->done, s));
     *n_out = (size_t)total;
@@ -1432,8 +1458,9 @@ tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int3
     J.xbegin = 0; J.ybegin = 0;
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaMemcpyAsync(sb, &J, sizeof(DtJob), cudaMemcpyHostToDevice, s));
-    const int lpc = dt_lines_per_cta();
-    CUDA_TRY(launch_dt(reinterpret_cast<const DtJob *>(sb), 1, (H + lpc - 1) / lpc, (nx + lpc - 1) / lpc, W, H, s));
+    // the fused form (the scratch's V / IV areas stay unused; tdpm_dt_noalloc runs the two-pass form)
+    CUDA_TRY(launch_dt_fused(reinterpret_cast<const DtJob *>(sb), 1, (nx + dt_strip_columns() - 1) / dt_strip_columns(),
+                             W, H, s));
     return TDPM_OK;
 }
 
