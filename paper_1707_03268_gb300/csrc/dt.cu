@@ -6,9 +6,10 @@
 // (the first strict maximum is the smallest maximiser), with the costs of those displacements taken once per line.
 // Then the result is checked against the line maximum M: on each side, beyond the cost's vertex, a cost above
 // (M - best) + margin at distance DT_R0 + 1 rules out every farther candidate (its f[q] - cost <= M - cost < best -
-// margin). Typical windows are 3-8 candidates wide; an output whose window is wider continues with an outward scan
-// over the exactly bounded window (left candidates win ties, right ones must be strictly better). The margin covers
-// FP32 rounding of the evaluated values, so the result is the brute-force one.
+// margin). With DPM-like deformation costs almost every output finishes there (away from the line ends the window
+// needs no bounds checks); an output whose window is wider continues with an outward scan over the exactly bounded
+// window (left candidates win ties, right ones must be strictly better). The margin covers FP32 rounding of the
+// evaluated values, so the result is the brute-force one.
 //
 // x pass: one CTA per (job, 8 rows), one warp per row: the row is staged in shared memory, and the lanes take the
 //         sampled columns p = x_off + x_step*k; results V[y][k], IV[y][k] (row-major [H][nx]: the lanes of a warp
@@ -74,14 +75,27 @@ __device__ __forceinline__ void dt_scan(const DtLine &c, const float *L, int n, 
 {
     float best = -INFINITY;
     int arg = p;
+    if (p >= DT_R0 && p + DT_R0 < n) {
+        // interior: the whole window is inside the line
+        const float *Lp = L + (p - DT_R0);
 #pragma unroll
-    for (int k = 0; k <= 2 * DT_R0; ++k) {
-        const int q = p + k - DT_R0;
-        if (q >= 0 && q < n) {
-            const float v = L[q] - c.cst[k];
+        for (int k = 0; k <= 2 * DT_R0; ++k) {
+            const float v = Lp[k] - c.cst[k];
             if (v > best) {
                 best = v;
-                arg = q;
+                arg = p + k - DT_R0;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k <= 2 * DT_R0; ++k) {
+            const int q = p + k - DT_R0;
+            if (q >= 0 && q < n) {
+                const float v = L[q] - c.cst[k];
+                if (v > best) {
+                    best = v;
+                    arg = q;
+                }
             }
         }
     }
@@ -217,35 +231,57 @@ __global__ void __launch_bounds__(DT_WARPS * 32) dt_y_kernel(const DtJob *__rest
 
 constexpr int DT_KS = 32;  // sampled columns per CTA of the fused form
 
-// shared memory: V and IV of the strip [32][hstride] each (hstride odd, >= H), one staged row per warp [wmax], and the
-// warps' partial column maxima [8][32]
-__global__ void __launch_bounds__(DT_WARPS * 32, 4) dt_xy_kernel(const DtJob *__restrict__ jobs, int n_jobs, int hstride,
-                                                              int wmax)
+__device__ __forceinline__ void dt_cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void dt_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void dt_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// shared memory: V and IV of the strip [32][hstride] each (hstride odd, >= H), nbuf staged rows per warp
+// [nbuf][wmax] (two: the next row is copied in with cp.async while the current one is scanned; one: it is refilled
+// after use), and the warps' partial column maxima [8][32]. cta_jobs: the job of every CTA (null: searched in the
+// jobs' xbegin).
+__global__ void __launch_bounds__(DT_WARPS * 32, 4) dt_xy_kernel(const DtJob *__restrict__ jobs, int n_jobs,
+                                                              const int *__restrict__ cta_jobs, int hstride, int wmax,
+                                                              int nbuf)
 {
     extern __shared__ float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const DtJob J = jobs[cta_job<true>(jobs, n_jobs, blockIdx.x, lane)];  // xbegin: first CTA (strip) of the job
+    const int ji = cta_jobs ? __ldg(cta_jobs + blockIdx.x) : cta_job<true>(jobs, n_jobs, blockIdx.x, lane);
+    const DtJob J = jobs[ji];  // xbegin: first CTA (strip) of the job
     const int k0 = (blockIdx.x - J.xbegin) * DT_KS;
     const int ncols = min(DT_KS, J.nx - k0);
     float *Vs = sm;
     int32_t *IVs = reinterpret_cast<int32_t *>(sm + DT_KS * hstride);
-    float *L = sm + 2 * DT_KS * hstride + warp * wmax;
-    float *pmax = sm + 2 * DT_KS * hstride + DT_WARPS * wmax;
+    float *rows = sm + 2 * DT_KS * hstride + nbuf * warp * wmax;
+    float *pmax = sm + 2 * DT_KS * hstride + nbuf * DT_WARPS * wmax;
     const int H = J.H, n = J.W;
     const bool active = lane < ncols;
     const int px = J.x_off + J.x_step * (k0 + lane);  // this lane's sampled column
     float cmax = -INFINITY;                           // its column maximum over this warp's rows
-    for (int y = warp; y < H; y += DT_WARPS) {
+    auto fetch = [&](int y, float *dst) {
         const float *in = J.S + (size_t)y * n;
-        float mx = -INFINITY;
-        for (int q = lane; q < n; q += 32) {
-            const float v = __ldg(in + q);
-            L[q] = v;
-            mx = fmaxf(mx, v);
+        for (int q = lane; q < n; q += 32) dt_cp_async4(dst + q, in + q);
+        dt_cp_commit();
+    };
+    if (warp < H) fetch(warp, rows);
+    int buf = 0;
+    for (int y = warp; y < H; y += DT_WARPS) {
+        float *L = rows + buf * wmax;
+        if (nbuf == 2 && y + DT_WARPS < H) {
+            fetch(y + DT_WARPS, rows + (buf ^ 1) * wmax);
+            dt_cp_wait<1>();
+        } else {
+            dt_cp_wait<0>();
         }
+        __syncwarp();
+        float mx = -INFINITY;
+        for (int q = lane; q < n; q += 32) mx = fmaxf(mx, L[q]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        __syncwarp();
         if (active) {
             DtLine c;
             dt_line_init(c, J.lx, J.qx, mx);
@@ -256,7 +292,9 @@ __global__ void __launch_bounds__(DT_WARPS * 32, 4) dt_xy_kernel(const DtJob *__
             IVs[lane * hstride + y] = arg;
             cmax = fmaxf(cmax, best);
         }
-        __syncwarp();  // the row buffer is refilled next
+        __syncwarp();  // every lane is done with this buffer before it is refilled
+        if (nbuf == 2) buf ^= 1;
+        else if (y + DT_WARPS < H) fetch(y + DT_WARPS, rows);
     }
     pmax[warp * 32 + lane] = cmax;
     __syncthreads();
@@ -283,21 +321,23 @@ __global__ void __launch_bounds__(DT_WARPS * 32, 4) dt_xy_kernel(const DtJob *__
 int dt_lines_per_cta() { return DT_WARPS; }
 int dt_strip_columns() { return DT_KS; }
 
-size_t dt_fused_smem_bytes(int max_W, int max_H)
+size_t dt_fused_smem_bytes(int max_W, int max_H, int nbuf)
 {
-    return sizeof(float) * (2 * (size_t)DT_KS * (size_t)(max_H | 1) + (size_t)DT_WARPS * max_W + DT_WARPS * 32);
+    return sizeof(float) * (2 * (size_t)DT_KS * (size_t)(max_H | 1) + (size_t)nbuf * DT_WARPS * max_W + DT_WARPS * 32);
 }
 
-cudaError_t launch_dt_fused(const DtJob *d_jobs, int n_jobs, int ctas, int max_W, int max_H, cudaStream_t s)
+cudaError_t launch_dt_fused(const DtJob *d_jobs, int n_jobs, const int *d_cta_jobs, int ctas, int max_W, int max_H,
+                            cudaStream_t s)
 {
     if (n_jobs <= 0 || ctas <= 0) return cudaSuccess;
     if (max_W > 800 || max_H > 800 || max_W < 1 || max_H < 1) return cudaErrorInvalidValue;
-    const size_t smem = dt_fused_smem_bytes(max_W, max_H);
+    const int nbuf = dt_fused_smem_bytes(max_W, max_H, 2) <= (size_t)kMaxDynamicSmem ? 2 : 1;
+    const size_t smem = dt_fused_smem_bytes(max_W, max_H, nbuf);
     if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(dt_xy_kernel), 6 + 18);
     if (e != cudaSuccess) return e;
     note_launches(1);
-    dt_xy_kernel<<<ctas, DT_WARPS * 32, smem, s>>>(d_jobs, n_jobs, max_H | 1, max_W);
+    dt_xy_kernel<<<ctas, DT_WARPS * 32, smem, s>>>(d_jobs, n_jobs, d_cta_jobs, max_H | 1, max_W, nbuf);
     return cudaGetLastError();
 }
 

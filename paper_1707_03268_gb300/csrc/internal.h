@@ -209,9 +209,10 @@ cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_ctas, int y_ctas, i
 int dt_lines_per_cta();
 // K5+K6 fused: one CTA per (job, strip of dt_strip_columns() sampled columns), the jobs' xbegin counting those CTAs;
 // V and IV stay in shared memory (the jobs' V / IV are not used). Results identical to launch_dt.
-cudaError_t launch_dt_fused(const DtJob *d_jobs, int n_jobs, int ctas, int max_W, int max_H, cudaStream_t s);
+// d_cta_jobs: the job of each CTA (null: found by a search of the jobs' xbegin).
+cudaError_t launch_dt_fused(const DtJob *d_jobs, int n_jobs, const int *d_cta_jobs, int ctas, int max_W, int max_H,
+                            cudaStream_t s);
 int dt_strip_columns();
-size_t dt_fused_smem_bytes(int max_W, int max_H);
 
 // K7: assembly (shift and sum), then detection count / scan / write.
 cudaError_t launch_assemble(const AsmJob *d_jobs, int n_jobs, long long total, cudaStream_t s);

@@ -119,7 +119,7 @@ struct Plan {
     bool zsep_forced = false;                  // the fused kernel's form was fixed by the context (not tuned)
     std::vector<int> g_n_fg, g_nmax;
     std::vector<std::vector<ZsGroup>> g_fg;
-    size_t dt_off = 0, asm_off = 0;
+    size_t dt_off = 0, asm_off = 0, dt_cta_off = 0;  // dt_cta_off: the job of every distance-transform CTA
     int dt_ctas = 0, max_W = 1, max_H = 1;  // CTAs of the fused distance transform (strips of sampled columns)
     std::vector<std::pair<size_t, int>> patches;  // blob offsets of caller level pointers
 
@@ -379,6 +379,11 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         P->g_rec_nt[gi] = P->rec_tc(g) ? corr_tc_default_nt(g.K, g.Upad / FD) | persist : 0;
     }
     P->dt_off = jb.take(sizeof(DtJob) * std::max<size_t>(1, P->dts.size()));
+    {
+        long long ctas = 0;
+        for (const DtPlan &p : P->dts) ctas += (p.X + dt_strip_columns() - 1) / dt_strip_columns();
+        P->dt_cta_off = jb.take(sizeof(int) * (size_t)std::max<long long>(1, ctas));
+    }
     P->asm_off = jb.take(sizeof(AsmJob) * std::max<size_t>(1, P->asms.size()));
     P->blob_bytes = align256(jb.off);
     P->arena_bytes = P->blob_off + P->blob_bytes;
@@ -520,7 +525,10 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
         d.A = reinterpret_cast<int32_t *>(base + p.a_off);
         d.xbegin = xw;  // first CTA (strip of sampled columns) of the job in the fused launch
         d.ybegin = 0;
-        xw += (p.X + dt_strip_columns() - 1) / dt_strip_columns();
+        const int strips = (p.X + dt_strip_columns() - 1) / dt_strip_columns();
+        int *cj = reinterpret_cast<int *>(hb + P.dt_cta_off) + xw;
+        for (int t = 0; t < strips; ++t) cj[t] = (int)i;
+        xw += strips;
     }
     AsmJob *aj = reinterpret_cast<AsmJob *>(hb + P.asm_off);
     long long pos = 0;
@@ -728,8 +736,8 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
     }
     {
         Prof pr(ctx, s, "dt");
-        e = launch_dt_fused(reinterpret_cast<const DtJob *>(dblob + P.dt_off), (int)P.dts.size(), P.dt_ctas, P.max_W,
-                            P.max_H, s);
+        e = launch_dt_fused(reinterpret_cast<const DtJob *>(dblob + P.dt_off), (int)P.dts.size(),
+                            reinterpret_cast<const int *>(dblob + P.dt_cta_off), P.dt_ctas, P.max_W, P.max_H, s);
         if (e != cudaSuccess) return e;
         pr.end();
     }
@@ -1459,8 +1467,8 @@ tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int3
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaMemcpyAsync(sb, &J, sizeof(DtJob), cudaMemcpyHostToDevice, s));
     // the fused form (the scratch's V / IV areas stay unused; tdpm_dt_noalloc runs the two-pass form)
-    CUDA_TRY(launch_dt_fused(reinterpret_cast<const DtJob *>(sb), 1, (nx + dt_strip_columns() - 1) / dt_strip_columns(),
-                             W, H, s));
+    CUDA_TRY(launch_dt_fused(reinterpret_cast<const DtJob *>(sb), 1, nullptr,
+                             (nx + dt_strip_columns() - 1) / dt_strip_columns(), W, H, s));
     return TDPM_OK;
 }
 
