@@ -262,6 +262,8 @@ __global__ void __launch_bounds__(DT_WARPS * 32, 4) dt_xy_kernel(const DtJob *__
     const bool active = lane < ncols;
     const int px = J.x_off + J.x_step * (k0 + lane);  // this lane's sampled column
     float cmax = -INFINITY;                           // its column maximum over this warp's rows
+    DtLine cx;
+    dt_line_init(cx, J.lx, J.qx, 0.f);  // per-line constants; the line maximum is set per row
     auto fetch = [&](int y, float *dst) {
         const float *in = J.S + (size_t)y * n;
         for (int q = lane; q < n; q += 32) dt_cp_async4(dst + q, in + q);
@@ -283,11 +285,10 @@ __global__ void __launch_bounds__(DT_WARPS * 32, 4) dt_xy_kernel(const DtJob *__
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (active) {
-            DtLine c;
-            dt_line_init(c, J.lx, J.qx, mx);
+            cx.mx = mx;
             float best;
             int arg;
-            dt_scan(c, L, n, px, best, arg);
+            dt_scan(cx, L, n, px, best, arg);
             Vs[lane * hstride + y] = best;
             IVs[lane * hstride + y] = arg;
             cmax = fmaxf(cmax, best);
