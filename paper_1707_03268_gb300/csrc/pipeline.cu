@@ -336,10 +336,8 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
             P->g_tiles[gi] = (int)std::min<long long>(tiles, 0x7fffffff);
             P->g_tile_off[gi] = jb.take(sizeof(ZsTile) * std::max(1, P->g_tiles[gi]));
             P->g_frec_off[gi] = jb.take(P->g_frec[gi].size());
-            // untuned: the persistent form with two feature stages where it fits
-            P->g_nt[gi] = zsep_form_fits(g.h, g.w, P->split, P->g_nmax[gi], ZSEP_PERSIST_S2) ? ZSEP_PERSIST_S2
-                          : zsep_form_fits(g.h, g.w, P->split, P->g_nmax[gi], ZSEP_PERSIST_S1) ? ZSEP_PERSIST_S1
-                                                                                              : ZSEP_TILE;
+            // untuned: one CTA per item (the tuner's usual choice for the large part groups)
+            P->g_nt[gi] = ZSEP_TILE;
             if (zsep_form >= 0 && zsep_form_fits(g.h, g.w, P->split, P->g_nmax[gi], zsep_form)) {
                 P->g_nt[gi] = zsep_form;  // fixed by the context
                 P->zsep_forced = true;
