@@ -161,21 +161,20 @@ bool encode_level_tmap_tiles(CUtensorMap *map, const uint16_t *planar, int H, in
 // K2+K3+K4 fused (per-filter mode, BF16 or split-BF16 operands): the channel stage on the tensor cores and the
 // separable passes with the recombination, over `tiles` spatial tiles (records d_tiles, each naming its job) times
 // n_fg filter groups. cbank / cbank_lo: the channel-factor bank [1][4][ld][8] BF16 (hi, lo or null); every group
-// needs t0 + n rounded up to 16 <= ld. A, B, lam, rank_off as for launch_sep; nmax = 32 or 64 (zsep_nmax) bounds
-// the terms of a group. Shapes: zsep_shape (the filter shapes of the separable warp form).
+// needs t0 + n rounded up to 16 <= ld. nmax = 32 or 64 (zsep_nmax) bounds the terms of a group. Shapes: zsep_shape
+// (the filter shapes of the separable warp form).
 bool zsep_shape(int h, int w);
 void zsep_tile(int h, int w, int *tile_cols, int *tile_rows);  // output columns and rows of one spatial tile
 int zsep_nmax(int max_rank);                                     // 32, 64, or 0 when a filter has more terms
 // form: ZSEP_TILE, one CTA per item; or a persistent form, one CTA per SM walking the items with a producer warp
 // ahead of the compute warps (two TMEM accumulators), with one or two feature stages and one or two Z buffers
-// (zsep_form_fits tells which fit). The persistent forms read the groups' packed factor records d_frec: per filter
+// (zsep_form_fits tells which fit). Every form reads the groups' packed factor records d_frec: per filter
 // group, zsep_record_bytes bytes: a_r[0..h), b_r[0..w), lambda_r, zero-padded to zsep_factor_stride floats per term
 // for nmax terms (zero beyond the group's terms), then the rank offsets of the group's filters minus t0 (nmax + 2
 // ints). All forms give the same results.
 enum ZsepForm { ZSEP_TILE = 0, ZSEP_PERSIST_S2 = 1, ZSEP_PERSIST_Z2 = 2, ZSEP_PERSIST_S2Z2 = 3, ZSEP_PERSIST_S1 = 4 };
 cudaError_t launch_zsep_tc(const ZsJob *d_jobs, const ZsTile *d_tiles, int tiles, const ZsGroup *d_fg, int n_fg,
-                           const void *cbank, const void *cbank_lo, int ld, const float *A, const float *B,
-                           const float *lam, const int *rank_off, int R, const void *d_frec, int nmax, int h, int w,
+                           const void *cbank, const void *cbank_lo, int ld, const void *d_frec, int nmax, int h, int w,
                            int *d_err, cudaStream_t s, int form);
 bool zsep_form_fits(int h, int w, bool split, int nmax, int form);
 int zsep_record_bytes(int h, int w, int nmax);

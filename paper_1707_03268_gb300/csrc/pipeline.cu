@@ -665,8 +665,8 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
             e = launch_zsep_tc(reinterpret_cast<const ZsJob *>(jobs),
                                reinterpret_cast<const ZsTile *>(dblob + P.g_tile_off[gi]), P.g_tiles[gi],
                                reinterpret_cast<const ZsGroup *>(dblob + P.g_fg_off[gi]), P.g_n_fg[gi], g.d_C_tc,
-                               P.split ? g.d_C_tc_lo : nullptr, g.Rpad_tc, g.d_A, g.d_B, g.d_lam, g.d_rank_off, g.R,
-                               dblob + P.g_frec_off[gi], P.g_nmax[gi], g.h, g.w, ctx->d_err, gs, P.g_nt[gi]);
+                               P.split ? g.d_C_tc_lo : nullptr, g.Rpad_tc, dblob + P.g_frec_off[gi], P.g_nmax[gi], g.h,
+                               g.w, ctx->d_err, gs, P.g_nt[gi]);
             if (e != cudaSuccess) return e;
             pr.end();
             return cudaSuccess;
@@ -833,9 +833,8 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, Arena &A, cuda
                 return launch_zsep_tc(reinterpret_cast<const ZsJob *>(dblob + P.g_jobs_off[gi]),
                                       reinterpret_cast<const ZsTile *>(dblob + P.g_tile_off[gi]), P.g_tiles[gi],
                                       reinterpret_cast<const ZsGroup *>(dblob + P.g_fg_off[gi]), P.g_n_fg[gi],
-                                      g.d_C_tc, P.split ? g.d_C_tc_lo : nullptr, g.Rpad_tc, g.d_A, g.d_B, g.d_lam,
-                                      g.d_rank_off, g.R, dblob + P.g_frec_off[gi], P.g_nmax[gi], g.h, g.w, ctx->d_err,
-                                      s, form);
+                                      g.d_C_tc, P.split ? g.d_C_tc_lo : nullptr, g.Rpad_tc, dblob + P.g_frec_off[gi],
+                                      P.g_nmax[gi], g.h, g.w, ctx->d_err, s, form);
             }, &P.g_nt[gi], forms);
             continue;
         }

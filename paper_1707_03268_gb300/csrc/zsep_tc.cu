@@ -50,6 +50,14 @@ struct ZsFactors {
     static constexpr int STRIDE = (HH + WW + 1 + 3) & ~3;
 };
 
+// A filter group's packed record: factors [nmax][STRIDE] floats, then the rank offsets of its filters minus t0
+// (nmax + 2 ints), rounded up to 16 bytes (one bulk copy).
+template <int HH, int WW>
+__host__ __device__ constexpr uint32_t zs_record_bytes(int nmax)
+{
+    return ((uint32_t)nmax * ZsFactors<HH, WW>::STRIDE * 4 + (uint32_t)(nmax + 2) * 4 + 15) & ~15u;
+}
+
 // One task of the separable passes: filter terms [tb, te) of the group, output rows i0 .. i0+RB-1 of the tile (ni of
 // them valid), lane = column. Rows past the tile's valid ones are computed and not stored, so the unrolled row loop
 // has no branch and the rows' multiply-add chains interleave; their Z reads run at most two rows past the term's
@@ -98,8 +106,7 @@ template <int HH, int WW, bool SPLIT>
 __global__ void __launch_bounds__(ZS_THREADS, 3)
     zsep_tc_kernel(const ZsJob *__restrict__ jobs, const ZsTile *__restrict__ tiles, const ZsGroup *__restrict__ fgs,
                    int n_fg, const uint8_t *__restrict__ cbank, const uint8_t *__restrict__ cbank_lo, int ld,
-                   const float *__restrict__ A, const float *__restrict__ B, const float *__restrict__ lam,
-                   const int *__restrict__ rank_off, int R, int nmax, uint32_t tmem_cols, int *err)
+                   const uint8_t *__restrict__ frec, int nmax, uint32_t tmem_cols, int *err)
 {
     using S = ZsShape<HH>;
     constexpr int MT = S::MT, TYZ = S::TYZ, TY = S::TY;
@@ -110,9 +117,10 @@ __global__ void __launch_bounds__(ZS_THREADS, 3)
     uint8_t *uni = sm;                                                  // feature tiles, then Z [nmax][TYZ][32]
     uint8_t *bsm = sm + zs_union_bytes(MT, NPART, nmax);                // [NPART][4][nmax][16 bytes]
     constexpr int FS = ZsFactors<HH, WW>::STRIDE;
-    float *fs = reinterpret_cast<float *>(bsm + NPART * 4 * nmax * 16);  // per term: a_r, b_r, lambda_r [nmax][FS]
-    int *ro = reinterpret_cast<int *>(fs + nmax * FS);                  // rank_off of the group's filters, - t0
-    uint64_t *bars = reinterpret_cast<uint64_t *>(ro + nmax + 2);
+    const uint32_t rec = zs_record_bytes<HH, WW>(nmax);
+    float *fs = reinterpret_cast<float *>(bsm + NPART * 4 * nmax * 16);  // the group's record: factors [nmax][FS],
+    int *ro = reinterpret_cast<int *>(fs + nmax * FS);                  // then the rank offsets of its filters - t0
+    uint64_t *bars = reinterpret_cast<uint64_t *>(bsm + NPART * 4 * nmax * 16 + rec);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2);
     const uint32_t full = smem_u32(bars), done = smem_u32(bars + 1);
 
@@ -129,13 +137,14 @@ __global__ void __launch_bounds__(ZS_THREADS, 3)
             mbar_init(full, 1);
             mbar_init(done, 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            mbar_expect_tx(full, MT * NPART * ZS_A_TILE + NPART * 4 * (uint32_t)N * 16);
+            mbar_expect_tx(full, MT * NPART * ZS_A_TILE + NPART * 4 * (uint32_t)N * 16 + rec);
 #pragma unroll
             for (int t = 0; t < MT; ++t) {
                 const uint32_t dst = smem_u32(uni + t * NPART * ZS_A_TILE);
                 tma_load_4d(dst, &J->tmap, 0, TL.x0, TL.y0 + 4 * t, 0, full);
                 if (SPLIT) tma_load_4d(dst + ZS_A_TILE, &J->tmap_lo, 0, TL.x0, TL.y0 + 4 * t, 0, full);
             }
+            bulk_load(smem_u32(fs), frec + (size_t)fgi * rec, rec, full);
             const uint32_t bdst = smem_u32(bsm);
 #pragma unroll
             for (int kc = 0; kc < 4; ++kc) {
@@ -154,22 +163,6 @@ __global__ void __launch_bounds__(ZS_THREADS, 3)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    // the group's factors (zero beyond its terms) and its filters' term ranges, while the copies and MMAs run (read
-    // after the barrier that follows the TMEM drain)
-    if (threadIdx.x != 0) {
-        const int lg = nmax == 32 ? 5 : 6;
-        for (int i = threadIdx.x - 1; i < FS * nmax; i += ZS_THREADS - 1) {
-            const int k = i >> lg, j = i & (nmax - 1);  // k: factor row (a, b, lambda, pad), j: term
-            const int r = G.t0 + j;
-            float v = 0.f;
-            if (j < G.n && k < HH + WW + 1)
-                v = k < HH ? __ldg(A + (size_t)k * R + r)
-                  : k < HH + WW ? __ldg(B + (size_t)(k - HH) * R + r) : __ldg(lam + r);
-            fs[j * FS + k] = v;
-        }
-        if (threadIdx.x - 1 <= G.k1 - G.k0) ro[threadIdx.x - 1] = __ldg(rank_off + G.k0 + threadIdx.x - 1) - G.t0;
-    }
-
     if (threadIdx.x == 0) {
         mbar_wait(full, 0, err);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -194,6 +187,7 @@ __global__ void __launch_bounds__(ZS_THREADS, 3)
         }
         mma_commit(done);
     }
+    mbar_wait(full, 0, err);  // the factor record (complete before the MMAs were issued)
     mbar_wait(done, 0, err);
     __syncwarp();  // warp 0 reconverges (lane 0 issued the MMAs) before the warp-wide TMEM loads
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -270,12 +264,6 @@ struct ZsMeta {          // per-item tile record staged by the producer
     float *out;          // output of the group's first filter at the tile's origin
     int plane, Wo, x0, rows, nf, n;
 };
-
-template <int HH, int WW>
-__host__ __device__ constexpr uint32_t zs_record_bytes(int nmax)
-{
-    return ((uint32_t)nmax * ZsFactors<HH, WW>::STRIDE * 4 + (uint32_t)(nmax + 2) * 4 + 15) & ~15u;
-}
 
 template <int HH, int WW, bool SPLIT>
 __global__ void __launch_bounds__(ZP_THREADS, 1)
@@ -476,9 +464,9 @@ size_t zsep_persistent_smem_bytes(int h, int w, bool split, int nmax, int stages
 size_t zsep_smem_bytes(int h, int w, bool split, int nmax)
 {
     const int mt = h <= 7 ? 4 : 6, npart = split ? 2 : 1;
-    const int fs = (h + w + 1 + 3) & ~3;
-    return (size_t)zs_union_bytes(mt, npart, nmax) + (size_t)npart * 4 * nmax * 16 + (size_t)fs * nmax * 4 +
-           (size_t)(nmax + 2) * 4 + 2 * 8 + 16;
+    const size_t rec = h == 6 ? zs_record_bytes<6, 6>(nmax) : h == 5 ? zs_record_bytes<5, 11>(nmax)
+                     : h == 7 ? zs_record_bytes<7, 7>(nmax) : zs_record_bytes<11, 5>(nmax);
+    return (size_t)zs_union_bytes(mt, npart, nmax) + (size_t)npart * 4 * nmax * 16 + rec + 2 * 8 + 16;
 }
 
 }  // namespace
@@ -532,12 +520,11 @@ int zs_sm_count()
 }  // namespace
 
 cudaError_t launch_zsep_tc(const ZsJob *d_jobs, const ZsTile *d_tiles, int tiles, const ZsGroup *d_fg, int n_fg,
-                           const void *cbank, const void *cbank_lo, int ld, const float *A, const float *B,
-                           const float *lam, const int *rank_off, int R, const void *d_frec, int nmax, int h, int w,
+                           const void *cbank, const void *cbank_lo, int ld, const void *d_frec, int nmax, int h, int w,
                            int *d_err, cudaStream_t s, int form)
 {
     if (tiles <= 0 || n_fg <= 0) return cudaSuccess;
-    if (!zsep_shape(h, w) || (nmax != 32 && nmax != 64)) return cudaErrorInvalidValue;
+    if (!zsep_shape(h, w) || (nmax != 32 && nmax != 64) || !d_frec) return cudaErrorInvalidValue;
     if ((long long)tiles * n_fg > 0x7fffffffll) return cudaErrorInvalidValue;
     const bool split = cbank_lo != nullptr;
     const int mt = h <= 7 ? 4 : 6;
@@ -592,8 +579,9 @@ cudaError_t launch_zsep_tc(const ZsJob *d_jobs, const ZsTile *d_tiles, int tiles
         e = allow_max_dynamic_smem(reinterpret_cast<const void *>(zsep_tc_kernel<HH, WW, SP>), SLOT);           \
         if (e != cudaSuccess) return e;                                                                           \
         note_launches(1);                                                                                         \
-        zsep_tc_kernel<HH, WW, SP><<<grid, ZS_THREADS, smem, s>>>(d_jobs, d_tiles, d_fg, n_fg, cb, cl, ld, A, B,  \
-                                                                  lam, rank_off, R, nmax, cols, d_err);           \
+        zsep_tc_kernel<HH, WW, SP><<<grid, ZS_THREADS, smem, s>>>(d_jobs, d_tiles, d_fg, n_fg, cb, cl, ld,        \
+                                                                  static_cast<const uint8_t *>(d_frec), nmax,    \
+                                                                  cols, d_err);                                   \
     } while (0)
     if (split) {
         if (h == 6) TDPM_ZSEP(6, 6, true, 8);
