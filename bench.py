@@ -44,6 +44,7 @@ from paper_1707_03268_gb300 import synth  # noqa: E402
 
 METRIC = "images/sec and p50/p99 latency, decomposed BF16 vs full FP32, at >=99.5% agreement"
 L2_BYTES = 129 * 1024 * 1024
+AUTO_RANK_E = (0.25, 0.5, 1.0, 2.0, 4.0)  # the rank criterion's constant (Sec. 4 leaves it open)
 RANK_SWEEP = {"per_filter": (4, 8, 16, 24, 32, 36), "joint": (16, 32, 64, 128, 256)}
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "bf16x3": 3}
 
@@ -810,6 +811,22 @@ def main():
                         "images_per_s": rate(run), "max_rel_error": rr["max_rel_error"],
                         "mean_rel_error": rr["mean_rel_error"], "gain_formula_1": rr["gain"]}
 
+    # ---- rank detection (Sec. 4): per filter the smallest rank meeting the error criterion with constant e
+    auto_sweep = None
+    if form == tdpm.FORM_DECOMPOSED and args.mode == "per_filter" and not args.no_sweep and compare is not None:
+        auto_sweep = {}
+        for e in AUTO_RANK_E:
+            t0 = time.perf_counter()
+            rr, ranks = tdpm.tdpm_decompose_auto(ctx, mid, e, 36, max_iters=500, seed=1)
+            secs = time.perf_counter() - t0
+            a = keys(step(form, prec))
+            run = timed(form, prec, 50, 2)
+            auto_sweep[e] = {"ranks_mean": float(np.mean(ranks)), "ranks_min": int(ranks.min()),
+                             "ranks_max": int(ranks.max()), "gain_formula_1": rr["gain"],
+                             "max_rel_error": rr["max_rel_error"], "mean_rel_error": rr["mean_rel_error"],
+                             "agreement_with_full_fp32": len(a & full_keys) / max(1, len(a | full_keys)),
+                             "images_per_s": rate(run), "decompose_seconds": secs}
+
     line = {"metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main_run["total_ms"] / args.steps, "p50_ms": p50, "p99_ms": p99,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -830,7 +847,7 @@ def main():
             "gpu_launches": main_run["launches"],
             "stages_ms_per_image": {k: v[0] / n_prof for k, v in stages.items()},
             "roofline": roofline, "rooflines": rooflines, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
-            "compare": compare, "decomposition_report": rep, "rank_sweep": sweep,
+            "compare": compare, "decomposition_report": rep, "rank_sweep": sweep, "auto_rank_sweep": auto_sweep,
             "autotune": tdpm.tdpm_autotune_read(ctx),
             "wall_s_timed": main_run["wall_s"]}
     if rank == 0:

@@ -164,6 +164,17 @@ tdpm_status tdpm_group_info(tdpm_ctx *ctx, int32_t model_id, int32_t group, int3
 tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_t mode, int32_t max_iters, double tol,
                            uint64_t seed, tdpm_decomp_report *report);
 
+/* Rank detection (Sec. 4) with per-filter decomposition: for every filter f (h x w x 32), the smallest r in
+ * [1, max_rank] with ||f - CP(f, r)||_F < e * (r (h + w + 32) / (h w 32))^2, CP(f, r) being the rank-r ALS
+ * decomposition of tdpm_decompose (same iterations, tolerance and seed). r is searched upward from 1: the paper starts
+ * a binary search, but the error of an ALS fit need not decrease with r, so only the scan finds the smallest r. A
+ * filter that meets the test at no r <= max_rank keeps rank max_rank (the exact slice form, error 0, when max_rank >=
+ * h*w). e: the criterion's constant, which the paper leaves open (> 0). ranks (optional): the chosen rank of every
+ * filter, indexed by filter id (tdpm_model_info's n_filters entries). The factors replace any earlier decomposition;
+ * the report is that of tdpm_decompose. Errors: ERR_ARG (e <= 0 or not finite, max_rank <= 0), ERR_STATE. */
+tdpm_status tdpm_decompose_auto(tdpm_ctx *ctx, int32_t model_id, double e, int32_t max_rank, int32_t max_iters,
+                                double tol, uint64_t seed, int32_t *ranks, tdpm_decomp_report *report);
+
 /* FP64 factors of shape group g: A [h][R], B [w][R], C [32][R], Lambda [n_filters][R] (row-major). Any output may be
  * NULL. Errors: ERR_STATE (not decomposed). */
 tdpm_status tdpm_get_factors(tdpm_ctx *ctx, int32_t model_id, int32_t group, double *A, double *B, double *C,

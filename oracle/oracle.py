@@ -10,6 +10,7 @@ code with the CUDA library. FP32 inputs are widened to FP64 and every quantity i
 * ``cp_full_rank``         an exact decomposition with R = h*w slices (Sec. 4: every tensor has a CP form)
 * ``cp_als``               alternating least squares, one exact least-squares solve per factor (Sec. 4, ALS cycle)
 * ``gain``                 formula (1) of Sec. 4
+* ``select_rank``          the rank detection of Sec. 4: the smallest r meeting the error criterion
 * ``score_pyramid``        steps 1-3 for every component and root level (Sec. 2 score; Algorithm 1 steps 12-13)
 * ``detect``               step 4, threshold (Algorithm 1 steps 15-16)
 
@@ -233,6 +234,28 @@ def rank_criterion_holds(F: np.ndarray, F_r: np.ndarray, r: int, e: float) -> bo
     """Sec. 4 rank detection test: ||f - CP(f, r)||_F < e * (r (N+M+L) / (N M L))^2."""
     N, M, L = F.shape
     return float(np.linalg.norm(_f64(F) - _f64(F_r))) < e * (r * (N + M + L) / (N * M * L)) ** 2
+
+
+def select_rank(F: np.ndarray, e: float, max_rank: int, max_iters: int = 500, tol: float = 1e-10,
+                seed: int = 0, restarts: int = 3) -> Tuple[int, bool]:
+    """Sec. 4 rank detection for one filter: the smallest r = 1, 2, ... with ||f - CP(f, r)||_F < e (r (N+M+L) /
+    (N M L))^2. CP(f, r) is the best of ``restarts`` runs of ``cp_als`` from seeds seed, seed + 1, ... (one ALS run
+    from a random start can stall with a term unused); at r >= N*M it is the exact slice form of ``cp_full_rank``
+    (error 0). Returns (r, met): met is False when no r <= max_rank meets the test (r is then max_rank)."""
+    N, M, L = F.shape
+    for r in range(1, max_rank + 1):
+        if r >= N * M:
+            w0, A0, B0, C0 = cp_full_rank(F)
+            return r, rank_criterion_holds(F, cp_reconstruct(w0, [A0, B0, C0]), r, e)
+        fits = []
+        for s in range(restarts):
+            w, U, _ = cp_als(F, r, max_iters=max_iters, tol=tol, seed=seed + s)
+            Fr = cp_reconstruct(w, U)
+            fits.append((float(np.linalg.norm(_f64(F) - Fr)), s, Fr))
+        best = min(fits, key=lambda t: t[:2])[2]
+        if rank_criterion_holds(F, best, r, e):
+            return r, True
+    return max_rank, False
 
 
 # ----------------------------------------------------------------------------------------------------------------------

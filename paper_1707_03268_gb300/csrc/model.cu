@@ -403,15 +403,36 @@ tdpm_status tdpm_group_info(tdpm_ctx *ctx, int32_t model_id, int32_t group, int3
     return TDPM_OK;
 }
 
-tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_t mode, int32_t max_iters, double tol,
-                           uint64_t seed, tdpm_decomp_report *report)
+}  // extern "C"
+
+namespace {
+
+// ||T - sum_j w_j u0_j (x) u1_j (x) u2_j||_F of an order-3 CP result (FP64).
+double cp_abs_error(const std::vector<double> &T, const CpResult &cr, int n0, int n1, int n2)
 {
-    clear_error();
-    if (!ctx) return fail(TDPM_ERR_ARG, "ctx is NULL");
-    if (rank <= 0) return fail(TDPM_ERR_ARG, "rank must be > 0");
-    if (mode != TDPM_DECOMP_PER_FILTER && mode != TDPM_DECOMP_JOINT) return fail(TDPM_ERR_ARG, "bad mode");
-    if (max_iters <= 0) return fail(TDPM_ERR_ARG, "max_iters must be > 0");
-    if (!(tol >= 0.0)) return fail(TDPM_ERR_ARG, "tol must be >= 0");
+    const int R = (int)cr.weights.size();
+    double e2 = 0.0;
+    for (int i = 0; i < n0; ++i)
+        for (int j = 0; j < n1; ++j)
+            for (int c = 0; c < n2; ++c) {
+                double v = 0.0;
+                for (int r = 0; r < R; ++r)
+                    v += cr.weights[r] * cr.U[0][(size_t)i * R + r] * cr.U[1][(size_t)j * R + r] *
+                         cr.U[2][(size_t)c * R + r];
+                const double d = T[((size_t)i * n1 + j) * n2 + c] - v;
+                e2 += d * d;
+            }
+    return std::sqrt(e2);
+}
+
+// Decomposition of every shape group of a model. Per filter (Sec. 4): rank `rank` for every filter or, with autorank,
+// the smallest r in [1, max_rank] meeting the rank criterion ||f - CP(f, r)||_F < e (r (h+w+32) / (h w 32))^2
+// (a filter meeting it at no r <= max_rank keeps max_rank); a rank >= h*w is the exact slice form (error 0). Joint:
+// one CP per shape group of rank `rank`. ranks_out: the filters' ranks by filter id (per filter mode), may be null.
+tdpm_status decompose_model(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_t mode, bool autorank, double e,
+                            int32_t max_rank, int32_t max_iters, double tol, uint64_t seed, int32_t *ranks_out,
+                            tdpm_decomp_report *report)
+{
     std::lock_guard<std::mutex> lk(ctx->mu);
     tdpm_status st = set_device(ctx);
     if (st) return st;
@@ -424,26 +445,42 @@ tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_
         g.joint = mode == TDPM_DECOMP_JOINT;
         g.rel_err.assign(K, 0.0);
         if (!g.joint) {
-            // Sec. 4: one rank-R CP per filter; rank >= h*w uses the exact slice form a_r = e_dy, b_r = e_dx,
+            // Sec. 4: one CP per filter; a rank >= h*w uses the exact slice form a_r = e_dy, b_r = e_dx,
             // c_r = F[dy][dx][:]
-            const bool exact = rank >= hw;
-            const int Rk = exact ? hw : rank;
             std::vector<CpResult> res(K);
-            if (!exact) {
-                const unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)K));
-                std::vector<std::thread> pool;
-                for (unsigned t = 0; t < nt; ++t)
-                    pool.emplace_back([&, t]() {
-                        for (int k = (int)t; k < K; k += (int)nt) {
-                            const FilterH &F = m->filters[g.fids[k]];
-                            std::vector<double> T(F.data.begin(), F.data.end());
-                            res[k] = cp_als(T.data(), {h, w, FD}, rank, max_iters, tol, seed + (uint64_t)g.fids[k]);
+            std::vector<int> Rk(K, rank >= hw ? hw : rank);
+            const unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)K));
+            std::vector<std::thread> pool;
+            for (unsigned t = 0; t < nt; ++t)
+                pool.emplace_back([&, t]() {
+                    for (int k = (int)t; k < K; k += (int)nt) {
+                        const FilterH &F = m->filters[g.fids[k]];
+                        std::vector<double> T(F.data.begin(), F.data.end());
+                        const uint64_t sd = seed + (uint64_t)g.fids[k];
+                        if (!autorank) {
+                            if (Rk[k] < hw) res[k] = cp_als(T.data(), {h, w, FD}, Rk[k], max_iters, tol, sd);
+                            continue;
                         }
-                    });
-                for (auto &th : pool) th.join();
-            }
+                        // the smallest rank meeting the criterion, scanning upward (the criterion's error side
+                        // comes from ALS, which need not decrease in r, so no bisection)
+                        const double shape = (double)(h + w + FD) / ((double)hw * FD);
+                        const int top = std::min(max_rank, hw - 1);
+                        bool met = false;
+                        int iters = 0;
+                        for (int r = 1; r <= top && !met; ++r) {
+                            CpResult cr = cp_als(T.data(), {h, w, FD}, r, max_iters, tol, sd);
+                            iters += cr.iters;
+                            met = cp_abs_error(T, cr, h, w, FD) < e * (r * shape) * (r * shape);
+                            res[k] = std::move(cr);
+                            Rk[k] = r;
+                        }
+                        if (!met && max_rank >= hw) Rk[k] = hw;  // the exact form: error 0
+                        res[k].iters = iters;
+                    }
+                });
+            for (auto &th : pool) th.join();
             g.rank_off.assign(K + 1, 0);
-            for (int k = 0; k < K; ++k) g.rank_off[k + 1] = g.rank_off[k] + Rk;
+            for (int k = 0; k < K; ++k) g.rank_off[k + 1] = g.rank_off[k] + Rk[k];
             g.R = g.rank_off[K];
             const int R = g.R;
             g.A.assign((size_t)h * R, 0.0);
@@ -453,7 +490,8 @@ tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_
             for (int k = 0; k < K; ++k) {
                 const FilterH &F = m->filters[g.fids[k]];
                 const int off = g.rank_off[k];
-                if (exact) {
+                if (ranks_out) ranks_out[g.fids[k]] = Rk[k];
+                if (Rk[k] >= hw) {
                     for (int dy = 0; dy < h; ++dy)
                         for (int dx = 0; dx < w; ++dx) {
                             const int r = off + dy * w + dx;
@@ -466,11 +504,12 @@ tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_
                 } else {
                     const CpResult &cr = res[k];
                     total_iters += cr.iters;
-                    for (int j = 0; j < rank; ++j) {
+                    const int rk = Rk[k];
+                    for (int j = 0; j < rk; ++j) {
                         const int r = off + j;
-                        for (int dy = 0; dy < h; ++dy) g.A[(size_t)dy * R + r] = cr.U[0][(size_t)dy * rank + j];
-                        for (int dx = 0; dx < w; ++dx) g.B[(size_t)dx * R + r] = cr.U[1][(size_t)dx * rank + j];
-                        for (int c = 0; c < FD; ++c) g.C[(size_t)c * R + r] = cr.U[2][(size_t)c * rank + j];
+                        for (int dy = 0; dy < h; ++dy) g.A[(size_t)dy * R + r] = cr.U[0][(size_t)dy * rk + j];
+                        for (int dx = 0; dx < w; ++dx) g.B[(size_t)dx * R + r] = cr.U[1][(size_t)dx * rk + j];
+                        for (int c = 0; c < FD; ++c) g.C[(size_t)c * R + r] = cr.U[2][(size_t)c * rk + j];
                         g.Lam[(size_t)k * R + r] = cr.weights[j];
                     }
                 }
@@ -561,6 +600,35 @@ tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_
         report->gain = dec > 0 ? full / dec : 0.0;
     }
     return TDPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_t mode, int32_t max_iters, double tol,
+                           uint64_t seed, tdpm_decomp_report *report)
+{
+    clear_error();
+    if (!ctx) return fail(TDPM_ERR_ARG, "ctx is NULL");
+    if (rank <= 0) return fail(TDPM_ERR_ARG, "rank must be > 0");
+    if (mode != TDPM_DECOMP_PER_FILTER && mode != TDPM_DECOMP_JOINT) return fail(TDPM_ERR_ARG, "bad mode");
+    if (max_iters <= 0) return fail(TDPM_ERR_ARG, "max_iters must be > 0");
+    if (!(tol >= 0.0)) return fail(TDPM_ERR_ARG, "tol must be >= 0");
+    return decompose_model(ctx, model_id, rank, mode, false, 0.0, 0, max_iters, tol, seed, nullptr, report);
+}
+
+tdpm_status tdpm_decompose_auto(tdpm_ctx *ctx, int32_t model_id, double e, int32_t max_rank, int32_t max_iters,
+                                double tol, uint64_t seed, int32_t *ranks, tdpm_decomp_report *report)
+{
+    clear_error();
+    if (!ctx) return fail(TDPM_ERR_ARG, "ctx is NULL");
+    if (!(e > 0.0) || !std::isfinite(e)) return fail(TDPM_ERR_ARG, "e must be finite and > 0");
+    if (max_rank <= 0) return fail(TDPM_ERR_ARG, "max_rank must be > 0");
+    if (max_iters <= 0) return fail(TDPM_ERR_ARG, "max_iters must be > 0");
+    if (!(tol >= 0.0)) return fail(TDPM_ERR_ARG, "tol must be >= 0");
+    return decompose_model(ctx, model_id, max_rank, TDPM_DECOMP_PER_FILTER, true, e, max_rank, max_iters, tol, seed,
+                           ranks, report);
 }
 
 tdpm_status tdpm_get_factors(tdpm_ctx *ctx, int32_t model_id, int32_t group, double *A, double *B, double *C,

@@ -101,6 +101,8 @@ SIGNATURES = {
     "tdpm_group_info": (_c_i32, [_VP, _c_i32, _c_i32] + [ctypes.POINTER(_c_i32)] * 6 + [_c_i32]),
     "tdpm_decompose": (_c_i32, [_VP, _c_i32, _c_i32, _c_i32, _c_i32, ctypes.c_double, ctypes.c_uint64,
                                 ctypes.POINTER(DecompReport)]),
+    "tdpm_decompose_auto": (_c_i32, [_VP, _c_i32, ctypes.c_double, _c_i32, _c_i32, ctypes.c_double, ctypes.c_uint64,
+                                     _VP, ctypes.POINTER(DecompReport)]),
     "tdpm_get_factors": (_c_i32, [_VP, _c_i32, _c_i32] + [ctypes.POINTER(ctypes.c_double)] * 4),
     "tdpm_save_factors": (_c_i32, [_VP, _c_i32, ctypes.c_char_p]),
     "tdpm_load_factors": (_c_i32, [_VP, _c_i32, ctypes.c_char_p]),
@@ -251,6 +253,18 @@ def tdpm_decompose(ctx: int, model_id: int, rank: int, mode: int = DECOMP_PER_FI
     _check(lib().tdpm_decompose(ctx, model_id, int(rank), int(mode), int(max_iters), float(tol), int(seed),
                                 ctypes.byref(rep)))
     return {f: getattr(rep, f) for f, _ in DecompReport._fields_}
+
+
+def tdpm_decompose_auto(ctx: int, model_id: int, e: float, max_rank: int, max_iters: int = 500, tol: float = 1e-10,
+                        seed: int = 0) -> Tuple[dict, np.ndarray]:
+    """Per-filter decomposition at the smallest rank meeting the paper's rank criterion with constant e (Sec. 4).
+    Returns the report and the chosen rank of every filter (by filter id)."""
+    n_f, _ = tdpm_model_info(ctx, model_id)
+    ranks = np.zeros(n_f, dtype=np.int32)
+    rep = DecompReport()
+    _check(lib().tdpm_decompose_auto(ctx, model_id, float(e), int(max_rank), int(max_iters), float(tol), int(seed),
+                                     ranks.ctypes.data, ctypes.byref(rep)))
+    return {f: getattr(rep, f) for f, _ in DecompReport._fields_}, ranks
 
 
 def tdpm_get_factors(ctx: int, model_id: int, group: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:

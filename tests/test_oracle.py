@@ -358,3 +358,25 @@ def test_pyramid_shape_matches_dpm_convention():
     for j in range(synth.LAMBDA, len(sizes)):
         (H, W), (Hp, Wp) = sizes[j], sizes[j - synth.LAMBDA]
         assert Hp >= 2 * H and Wp >= 2 * W
+
+
+def test_select_rank_finds_planted_rank():
+    """Sec. 4 rank detection on filters of known rank k (a sum of k outer products, FP32): the criterion fails below k
+    (the missing terms carry about a fifth of the norm, far above e (r (N+M+L) / NML)^2 at e = 1) and holds at k (the
+    ALS fit is exact up to FP32 rounding), so the smallest r meeting it is k."""
+    rng = np.random.default_rng(31)
+    for k in (1, 2, 4):
+        F = synth.make_filter(rng, 6, 6, "dpm", n_terms=k, decay=0.8)
+        r, met = orc.select_rank(F, 1.0, 12, max_iters=500, seed=1)
+        assert met and r == k, (k, r, met)
+
+
+def test_select_rank_cap_and_exact_form():
+    """A full-rank filter with a tiny e meets the test only with the exact slice form (r = h*w, error 0); a cap below
+    h*w returns the cap, unmet."""
+    rng = np.random.default_rng(32)
+    F = rng.normal(0.0, 0.05, size=(2, 2, 32)).astype(np.float32)
+    r, met = orc.select_rank(F, 1e-12, 10, max_iters=50)
+    assert (r, met) == (4, True)
+    r, met = orc.select_rank(F, 1e-12, 3, max_iters=50)
+    assert (r, met) == (3, False)
