@@ -73,32 +73,40 @@ __device__ __forceinline__ void dt_line_init(DtLine &c, float lin, float quad, f
 // The transformed value and smallest maximiser of output p of line L (length n).
 __device__ __forceinline__ void dt_scan(const DtLine &c, const float *L, int n, int p, float &best_out, int &arg_out)
 {
-    float best = -INFINITY;
-    int arg = p;
+    // the window's values (minus infinity outside the line), then its first maximum by a pairwise tree: a right
+    // operand (larger indices) replaces a left one only when strictly greater, exactly as in a left-to-right scan, so
+    // the smallest maximiser wins; the tree's depth is 4 instead of a chain of 9 dependent compares
+    static_assert(DT_R0 == 4, "the reduction tree below is written for a 9-candidate window");
+    float v[2 * DT_R0 + 1];
     if (p >= DT_R0 && p + DT_R0 < n) {
-        // interior: the whole window is inside the line
-        const float *Lp = L + (p - DT_R0);
+        const float *Lp = L + (p - DT_R0);  // interior: the whole window is inside the line
 #pragma unroll
-        for (int k = 0; k <= 2 * DT_R0; ++k) {
-            const float v = Lp[k] - c.cst[k];
-            if (v > best) {
-                best = v;
-                arg = p + k - DT_R0;
-            }
-        }
+        for (int k = 0; k <= 2 * DT_R0; ++k) v[k] = Lp[k] - c.cst[k];
     } else {
 #pragma unroll
         for (int k = 0; k <= 2 * DT_R0; ++k) {
             const int q = p + k - DT_R0;
-            if (q >= 0 && q < n) {
-                const float v = L[q] - c.cst[k];
-                if (v > best) {
-                    best = v;
-                    arg = q;
-                }
-            }
+            v[k] = q >= 0 && q < n ? L[q] - c.cst[k] : -INFINITY;
         }
     }
+    auto first_max = [](float &va, int &ka, float vb, int kb) {
+        if (vb > va) {
+            va = vb;
+            ka = kb;
+        }
+    };
+    int k0 = 0, k2 = 2, k4 = 4, k6 = 6;
+    float b0 = v[0], b2 = v[2], b4 = v[4], b6 = v[6];
+    first_max(b0, k0, v[1], 1);
+    first_max(b2, k2, v[3], 3);
+    first_max(b4, k4, v[5], 5);
+    first_max(b6, k6, v[7], 7);
+    first_max(b0, k0, b2, k2);
+    first_max(b4, k4, b6, k6);
+    first_max(b0, k0, b4, k4);
+    first_max(b0, k0, v[8], 8);
+    float best = b0;
+    int arg = p + k0 - DT_R0;
     const float T = (c.mx - best) + 1e-5f * (1.f + fabsf(c.mx) + fabsf(best));
     const bool done_l = p - DT_R0 - 1 < 0 || (c.past_l && c.cl1 > T);
     const bool done_r = p + DT_R0 + 1 >= n || (c.past_r && c.cr1 > T);
