@@ -314,6 +314,13 @@ tdpm_status tdpm_profile_reset(tdpm_ctx *ctx);
 tdpm_status tdpm_autotune_read(tdpm_ctx *ctx, int32_t index, char *key, size_t key_cap, int32_t *tile_n,
                                int32_t *persistent, int32_t *n_entries);
 
+/* Failure-detection self-test (not in the paper). Launches one kernel whose mbarrier wait can never complete: the
+ * wait is the bounded one of every tensor-core kernel, so it gives up after its limit (about half a second), raises
+ * the context's device error flag and the kernel exits. Returns ERR_TIMEOUT, the status any call reports after an
+ * expired device wait, having cleared the flag: the context stays usable. ERR_STATE if the expiry was not reported.
+ * No fault, trap or hang is involved. */
+tdpm_status tdpm_selftest_bounded_wait(tdpm_ctx *ctx);
+
 /* Kernel fusion of the decomposed form (Sec. 4) with per-filter factors and BF16 or split-BF16 operands. enable = 1
  * (the default; the environment variable TDPM_FUSE=0 before tdpm_create sets 0): the channel stage (Z_r = phi o c_r,
  * on the tensor cores) and the separable passes with the recombination run as ONE kernel per shape group, the

@@ -225,4 +225,7 @@ cudaError_t launch_detect_write(const AsmJob *d_jobs, int n_jobs, long long tota
                                 int model, cudaStream_t s);
 int detect_positions_per_block();
 
+// Failure-detection self-test: one kernel whose bounded mbarrier wait expires (nothing arrives); it raises *d_err.
+cudaError_t launch_bounded_wait_probe(int *d_err, cudaStream_t s);
+
 }  // namespace tdpm

@@ -1364,6 +1364,21 @@ tdpm_status tdpm_release(tdpm_ctx *ctx, int32_t scores_id)
 // ------------------------------------------------------------------------------------------------ instrumentation
 uint64_t tdpm_kernel_launches(void) { return g_launches.load(); }
 
+tdpm_status tdpm_selftest_bounded_wait(tdpm_ctx *ctx)
+{
+    clear_error();
+    if (!ctx) return fail(TDPM_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    tdpm_status st = set_device(ctx);
+    if (st) return st;
+    cudaStream_t s = ctx->cap_stream;  // a stream of the context's own, idle outside graph capture
+    CUDA_TRY(launch_bounded_wait_probe(ctx->d_err, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    st = check_device_flag(ctx);  // clears the flag it finds raised
+    if (st == TDPM_OK) return fail(TDPM_ERR_STATE, "the bounded wait did not report its expiry");
+    return st;
+}
+
 tdpm_status tdpm_set_fusion(tdpm_ctx *ctx, int32_t enable)
 {
     clear_error();

@@ -135,6 +135,7 @@ SIGNATURES = {
     "tdpm_kernel_launches": (ctypes.c_uint64, []),
     "tdpm_profile_enable": (_c_i32, [_VP, _c_i32]),
     "tdpm_set_fusion": (_c_i32, [_VP, _c_i32]),
+    "tdpm_selftest_bounded_wait": (_c_i32, [_VP]),
     "tdpm_profile_read": (_c_i32, [_VP, _c_i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_i32)]),
     "tdpm_profile_reset": (_c_i32, [_VP]),
@@ -476,6 +477,11 @@ def unpack_arg(a: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
 # --------------------------------------------------------------------------------------------------- instrumentation
 def tdpm_kernel_launches() -> int:
     return int(lib().tdpm_kernel_launches())
+
+
+def tdpm_selftest_bounded_wait(ctx: int) -> int:
+    """Run the failure-detection self-test; returns the status it reports (ERR_TIMEOUT when the expiry is seen)."""
+    return int(lib().tdpm_selftest_bounded_wait(ctx))
 
 
 def tdpm_set_fusion(ctx: int, enable: bool = True) -> None:
