@@ -222,6 +222,18 @@ tdpm_status tdpm_detect(tdpm_ctx *ctx, int32_t scores_id, float tau, tdpm_detect
 tdpm_status tdpm_detect_thresholds(tdpm_ctx *ctx, int32_t scores_id, const float *tau, tdpm_detection *out,
                                    size_t capacity, size_t *n_out, void *stream);
 
+/* Step 4 followed by greedy non-maximum suppression (not in the paper: the DPM convention), on the device. The
+ * detections with s >= tau are grouped by (image, class), class = component_class[component] (n_components entries,
+ * ids >= 0; NULL = one class). A detection's box is its component's root filter at its level: cells of
+ * cell0 * 2^(level / lambda) image pixels (cell0 = the pixel size of a level-0 cell, e.g. 4 for sbin 8 with a 2x
+ * first octave), box [x c, x c + w0 c) x [y c, y c + h0 c). Within a group the detections are taken by score (ties:
+ * record order); each one not yet suppressed is kept and suppresses every later one whose box it covers by more than
+ * `overlap` (in [0, 1]) of that later box's own area. Boxes and overlaps are FP64. The kept records are written to
+ * `out` in the order of tdpm_detect; *n_out = their number (ERR_CAPACITY as tdpm_detect). */
+tdpm_status tdpm_detect_nms(tdpm_ctx *ctx, int32_t scores_id, float tau, const int32_t *component_class,
+                            double overlap, double cell0, tdpm_detection *out, size_t capacity, size_t *n_out,
+                            void *stream);
+
 /* Map kinds for tdpm_get_maps */
 #define TDPM_MAP_FILTER_SCORE 0 /* index_a = filter id, index_b = level: correlation map [H-h+1][W-w+1] FP32 */
 #define TDPM_MAP_FINAL_SCORE 1  /* index_a = component, index_b = root level: score map [Y][X] FP32 */

@@ -13,6 +13,7 @@ code with the CUDA library. FP32 inputs are widened to FP64 and every quantity i
 * ``select_rank``          the rank detection of Sec. 4: the smallest r meeting the error criterion
 * ``score_pyramid``        steps 1-3 for every component and root level (Sec. 2 score; Algorithm 1 steps 12-13)
 * ``detect``               step 4, threshold (Algorithm 1 steps 15-16)
+* ``nms``                  greedy non-maximum suppression of detections (a DPM convention; the paper has none)
 
 Readings of points the paper leaves open (they are listed with reasons in the design notes): valid correlation with no
 padding; the part level of root level j is j - lam and part i of a root at (y, x) is anchored at (2y + vy, 2x + vx);
@@ -326,6 +327,46 @@ def detect(scored: Sequence[Dict], tau: float) -> List[Tuple]:
                          tuple(int(v) for v in m["part_y"][:, y, x]), tuple(int(v) for v in m["part_x"][:, y, x])))
     dets.sort(key=lambda d: (d[0], d[1], d[2], d[3]))
     return dets
+
+
+def nms(dets: Sequence[Tuple], root_hw: Sequence[Tuple[int, int]], cell0: float, lam: int, overlap: float = 0.5,
+        component_class: Optional[Sequence[int]] = None) -> List[int]:
+    """Greedy non-maximum suppression, per (image, class). The paper has no NMS; this is the DPM convention.
+
+    ``dets``: records (image, component, level, y, x, score), ``level`` counted within the image. A detection's box is
+    its component's root filter (h0 x w0 cells, ``root_hw``) at its level, whose cells measure
+    cell0 * 2 ** (level / lam) image pixels: [x c, x c + w0 c) x [y c, y c + h0 c). Within a group the detections
+    are taken by score, highest first (ties: earlier record first); each one not yet suppressed is kept and
+    suppresses every later one whose box it covers by more than ``overlap`` of that later box's area. Returns the
+    kept records' indices, ascending. Boxes and overlaps are computed in FP64, each product and sum rounded once."""
+    cls = component_class
+    boxes = []
+    for (img, comp, level, y, x, score) in dets:
+        c = cell0 * 2.0 ** (level / lam)
+        h0, w0 = root_hw[comp]
+        x1, y1 = x * c, y * c
+        boxes.append((x1, y1, x1 + w0 * c, y1 + h0 * c))
+    groups: Dict[Tuple[int, int], List[int]] = {}
+    for i, d in enumerate(dets):
+        groups.setdefault((d[0], cls[d[1]] if cls is not None else 0), []).append(i)
+    kept = []
+    for members in groups.values():
+        order = sorted(members, key=lambda i: (-dets[i][5], i))
+        alive = {i: True for i in order}
+        for a, i in enumerate(order):
+            if not alive[i]:
+                continue
+            kept.append(i)
+            bi = boxes[i]
+            for j in order[a + 1:]:
+                if not alive[j]:
+                    continue
+                bj = boxes[j]
+                iw = min(bi[2], bj[2]) - max(bi[0], bj[0])
+                ih = min(bi[3], bj[3]) - max(bi[1], bj[1])
+                if iw > 0 and ih > 0 and (iw * ih) / ((bj[2] - bj[0]) * (bj[3] - bj[1])) > overlap:
+                    alive[j] = False
+    return sorted(kept)
 
 
 def all_scores(scored: Sequence[Dict]) -> np.ndarray:

@@ -155,6 +155,8 @@ struct tdpm_ctx {
     int *h_err = nullptr;                // pinned mirror
     long long *h_total = nullptr;        // pinned: detection count read back with the records
     std::unordered_map<uint64_t, size_t> det_last;  // plan uid -> detections of its last read-back (copy size hint)
+    void *d_nms = nullptr;               // grow-only scratch of tdpm_detect_nms
+    size_t nms_cap = 0;
     bool use_graphs = true;
     bool fuse = true;                    // fused channel stage + separable passes where possible (tdpm_set_fusion)
     int zsep_form = -1;                  // fused kernel form forced by TDPM_ZSEP_FORM (-1: default / tuned)

@@ -225,6 +225,16 @@ cudaError_t launch_detect_write(const AsmJob *d_jobs, int n_jobs, long long tota
                                 int model, cudaStream_t s);
 int detect_positions_per_block();
 
+// Greedy NMS per (image, class) of n detection records on the device (see nms.cu for the convention). d_cls: the
+// class of each component (null: one class); d_root_h / d_root_w: root filter size per component; d_cell: cell size
+// in image pixels per (image, level) [n_images][max_levels]. The kept records go to d_out in their original order
+// and their number to *d_n_out. d_scratch: at least nms_scratch_bytes(n, n_images * n_classes) bytes.
+size_t nms_scratch_bytes(long long n, int n_groups);
+cudaError_t launch_nms(const tdpm_detection *d_rec, long long n, const int32_t *d_cls, int n_classes, int n_images,
+                       const int32_t *d_root_h, const int32_t *d_root_w, const double *d_cell, int max_levels,
+                       double overlap, void *d_scratch, size_t scratch_bytes, tdpm_detection *d_out,
+                       long long *d_n_out, cudaStream_t s);
+
 // Failure-detection self-test: one kernel whose bounded mbarrier wait expires (nothing arrives); it raises *d_err.
 cudaError_t launch_bounded_wait_probe(int *d_err, cudaStream_t s);
 

@@ -276,6 +276,7 @@ void tdpm_destroy(tdpm_ctx *ctx)
         for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
         cudaStreamDestroy(ctx->cap_stream);
         if (ctx->d_records) cudaFree(ctx->d_records);
+        if (ctx->d_nms) cudaFree(ctx->d_nms);
         if (ctx->d_job_tau) cudaFree(ctx->d_job_tau);
         for (cudaStream_t st : ctx->side) cudaStreamDestroy(st);
         for (cudaEvent_t ev : ctx->join_ev) cudaEventDestroy(ev);

@@ -1309,6 +1309,104 @@ tdpm_status tdpm_detect_thresholds(tdpm_ctx *ctx, int32_t scores_id, const float
     return detect_impl(ctx, scores_id, 0.f, tau, out, capacity, n_out, stream);
 }
 
+tdpm_status tdpm_detect_nms(tdpm_ctx *ctx, int32_t scores_id, float tau, const int32_t *component_class,
+                            double overlap, double cell0, tdpm_detection *out, size_t capacity, size_t *n_out,
+                            void *stream)
+{
+    clear_error();
+    if (!ctx || !n_out || (capacity > 0 && !out)) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (!(overlap >= 0.0 && overlap <= 1.0)) return fail(TDPM_ERR_ARG, "overlap must be in [0, 1]");
+    if (!(cell0 > 0.0) || !std::isfinite(cell0)) return fail(TDPM_ERR_ARG, "cell0 must be finite and > 0");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    tdpm_status st = set_device(ctx);
+    if (st) return st;
+    Scores *sc = get_scores(ctx, scores_id);
+    if (!sc) return fail(TDPM_ERR_STATE, "unknown scores id");
+    const Model *m = get_model(ctx, sc->model_id);
+    if (!m) return fail(TDPM_ERR_STATE, "the scores' model was unloaded");
+    const Plan &P = *sc->plan;
+    const int nc = (int)m->comps.size();
+    int n_classes = 1;
+    if (component_class)
+        for (int c = 0; c < nc; ++c) {
+            if (component_class[c] < 0) return fail(TDPM_ERR_ARG, "negative class id");
+            n_classes = std::max(n_classes, component_class[c] + 1);
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    char *base = sc->arena.dev;
+    const AsmJob *jobs = reinterpret_cast<const AsmJob *>(base + P.blob_off + P.asm_off);
+    int *counts = reinterpret_cast<int *>(base + P.counts_off), *offsets = reinterpret_cast<int *>(base + P.offsets_off);
+    long long *d_total = reinterpret_cast<long long *>(base + P.total_off);
+    CUDA_TRY(cudaStreamWaitEvent(s, sc->done, 0));
+    // every detection on the device
+    CUDA_TRY(launch_detect_count(jobs, (int)P.asms.size(), P.total, tau, nullptr, counts, offsets, P.n_det_blocks,
+                                 d_total, s));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if ((st = check_device_flag(ctx))) return st;
+    const long long n = *ctx->h_total;
+    if (n > (1ll << 30)) return fail(TDPM_ERR_CAPACITY, "more than 2^30 detections above tau for NMS");
+    // scratch: every record, the kept ones, the NMS working set, the per-component and per-level tables
+    int max_levels = 1;
+    for (int L : P.img_L) max_levels = std::max(max_levels, L);
+    const size_t rec_b = sizeof(tdpm_detection) * (size_t)std::max<long long>(n, 1);
+    const size_t work_b = nms_scratch_bytes(n, P.n_images * n_classes);
+    auto a256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t cls_b = a256(4 * (size_t)nc * 3), cell_b = a256(8 * (size_t)P.n_images * max_levels);
+    const size_t need = 2 * a256(rec_b) + a256(work_b) + cls_b + cell_b + 256;
+    if (need > ctx->nms_cap) {
+        if (ctx->d_nms) {
+            cudaFree(ctx->d_nms);
+            ctx->used -= std::min(ctx->used, ctx->nms_cap);
+            ctx->d_nms = nullptr;
+            ctx->nms_cap = 0;
+        }
+        if (ctx->budget && ctx->used + need > ctx->budget) return fail(TDPM_ERR_OOM, "NMS scratch exceeds the budget");
+        CUDA_TRY(cudaMalloc(&ctx->d_nms, need));
+        ctx->nms_cap = need;
+        ctx->used += need;
+    }
+    char *q = static_cast<char *>(ctx->d_nms);
+    auto *d_rec = reinterpret_cast<tdpm_detection *>(q);
+    auto *d_kept = reinterpret_cast<tdpm_detection *>(q + a256(rec_b));
+    void *d_work = q + 2 * a256(rec_b);
+    char *tab = q + 2 * a256(rec_b) + a256(work_b);
+    auto *d_cls = reinterpret_cast<int32_t *>(tab);
+    auto *d_rh = d_cls + nc, *d_rw = d_rh + nc;
+    auto *d_cell = reinterpret_cast<double *>(tab + cls_b);
+    auto *d_nk = reinterpret_cast<long long *>(tab + cls_b + cell_b);
+    // the tables: classes, root filter sizes, and the cell size of every (image, level) in image pixels
+    std::vector<int32_t> tabs((size_t)nc * 3);
+    for (int c = 0; c < nc; ++c) {
+        tabs[c] = component_class ? component_class[c] : 0;
+        tabs[nc + c] = m->filters[m->comps[c].root_fid].h;
+        tabs[2 * nc + c] = m->filters[m->comps[c].root_fid].w;
+    }
+    std::vector<double> cells((size_t)P.n_images * max_levels, 0.0);
+    for (int im = 0; im < P.n_images; ++im)
+        for (int j = 0; j < P.img_L[im]; ++j)
+            cells[(size_t)im * max_levels + j] = cell0 * std::pow(2.0, (double)j / (double)P.img_lam[im]);
+    CUDA_TRY(cudaMemcpyAsync(d_cls, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_cell, cells.data(), 8 * cells.size(), cudaMemcpyHostToDevice, s));
+    if (n > 0)
+        CUDA_TRY(launch_detect_write(jobs, (int)P.asms.size(), P.total, tau, nullptr, offsets, P.n_det_blocks, d_rec, n,
+                                     sc->model_id, s));
+    CUDA_TRY(launch_nms(d_rec, n, component_class ? d_cls : nullptr, n_classes, P.n_images, d_rh, d_rw, d_cell,
+                        max_levels, overlap, d_work, work_b, d_kept, d_nk, s));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_total, d_nk, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const long long kept = *ctx->h_total;
+    const size_t nk = std::min<size_t>((size_t)kept, capacity);
+    if (nk) {
+        CUDA_TRY(cudaMemcpyAsync(out, d_kept, nk * sizeof(tdpm_detection), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    CUDA_TRY(cudaEventRecord(sc->done, s));
+    *n_out = (size_t)kept;
+    if ((size_t)kept > capacity) return fail(TDPM_ERR_CAPACITY, "kept detections exceed capacity: " + std::to_string(kept));
+    return TDPM_OK;
+}
+
 tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_t image, int32_t index_a,
                           int32_t index_b, void *out_host, size_t capacity_bytes, int32_t *rows, int32_t *cols,
                           void *stream)

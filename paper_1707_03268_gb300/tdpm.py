@@ -136,6 +136,8 @@ SIGNATURES = {
     "tdpm_profile_enable": (_c_i32, [_VP, _c_i32]),
     "tdpm_set_fusion": (_c_i32, [_VP, _c_i32]),
     "tdpm_selftest_bounded_wait": (_c_i32, [_VP]),
+    "tdpm_detect_nms": (_c_i32, [_VP, _c_i32, ctypes.c_float, _VP, ctypes.c_double, ctypes.c_double, _VP,
+                                 ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _VP]),
     "tdpm_profile_read": (_c_i32, [_VP, _c_i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_i32)]),
     "tdpm_profile_reset": (_c_i32, [_VP]),
@@ -329,6 +331,20 @@ def tdpm_detect(ctx: int, scores_id: int, tau: float, capacity: int = 1 << 20, s
     st = lib().tdpm_detect(ctx, scores_id, float(tau), out.ctypes.data if capacity else None, int(capacity),
                            ctypes.byref(n), _stream_ptr(stream))
     _check(st)
+    return out[: n.value]
+
+
+def tdpm_detect_nms(ctx: int, scores_id: int, tau: float, component_class: Optional[Sequence[int]] = None,
+                    overlap: float = 0.5, cell0: float = 4.0, capacity: int = 1 << 20, stream=None,
+                    out: Optional[np.ndarray] = None) -> np.ndarray:
+    """Detections with score >= tau after greedy non-maximum suppression per (image, class) on the device."""
+    if out is None or out.shape[0] < capacity:
+        out = np.zeros(capacity, dtype=DETECTION_DTYPE)
+    cls = None if component_class is None else np.ascontiguousarray(component_class, dtype=np.int32)
+    n = ctypes.c_size_t()
+    _check(lib().tdpm_detect_nms(ctx, scores_id, float(tau), None if cls is None else cls.ctypes.data, float(overlap),
+                                 float(cell0), out.ctypes.data if capacity else None, int(capacity), ctypes.byref(n),
+                                 _stream_ptr(stream)))
     return out[: n.value]
 
 

@@ -380,3 +380,30 @@ def test_select_rank_cap_and_exact_form():
     assert (r, met) == (4, True)
     r, met = orc.select_rank(F, 1e-12, 3, max_iters=50)
     assert (r, met) == (3, False)
+
+
+def test_nms_keeps_the_best_of_overlapping_boxes():
+    """Hand-made cases: the highest box of a cluster survives, a box covered by more than `overlap` of its own area
+    goes, one covered by exactly half stays (strictly greater suppresses), other images and classes are independent,
+    and score ties go to the earlier record."""
+    root_hw = [(4, 4), (4, 4)]
+    dets = [
+        (0, 0, 0, 0, 0, 1.0),   # box [0,4)x[0,4) at cell 1 (level 0, cell0 = 1)
+        (0, 0, 0, 0, 1, 2.0),   # [1,5): covers 3/4 of box 0 -> box 0 suppressed
+        (0, 0, 0, 0, 3, 1.5),   # [3,7): overlap with box 1 is 2/4 = 0.5, not > 0.5 -> kept
+        (1, 0, 0, 0, 0, 0.5),   # another image: independent
+        (0, 1, 0, 0, 1, 0.1),   # another class (component 1 -> class 1): independent
+        (0, 0, 0, 10, 10, 2.0), # far away, tie in score with record 1 -> both kept
+    ]
+    kept = orc.nms(dets, root_hw, cell0=1.0, lam=10, overlap=0.5, component_class=[0, 1])
+    assert kept == [1, 2, 3, 4, 5]
+    # one class for both components: record 4 overlaps record 1 (same box) and has a lower score -> suppressed
+    kept = orc.nms(dets, root_hw, cell0=1.0, lam=10, overlap=0.5, component_class=[0, 0])
+    assert kept == [1, 2, 3, 5]
+    # level scale: level 10 with lam 10 doubles the cell, so (y, x) = (0, 1) covers [2, 10) and hides a level-0 box at
+    # [2, 6) entirely (its own area is the reference)
+    dets2 = [(0, 0, 10, 0, 1, 3.0), (0, 0, 0, 0, 2, 1.0)]
+    assert orc.nms(dets2, root_hw, cell0=1.0, lam=10) == [0]
+    # ties: the earlier record wins
+    dets3 = [(0, 0, 0, 0, 0, 1.0), (0, 0, 0, 0, 0, 1.0)]
+    assert orc.nms(dets3, root_hw, cell0=1.0, lam=10) == [0]
