@@ -234,6 +234,46 @@ tdpm_status tdpm_detect_nms(tdpm_ctx *ctx, int32_t scores_id, float tau, const i
                             double overlap, double cell0, tdpm_detection *out, size_t capacity, size_t *n_out,
                             void *stream);
 
+/* ---------------------------------------------------------------- convolution shortening (Sec. 4, Algorithm 1) */
+/* A root hypothesis (a record's component, level, y, x) is pruned as soon as, for some filter of its component, the
+ * partial sum of the filter's first q CP terms at the hypothesis falls below the filter's threshold t_q. Filters are
+ * visited root first, then the parts in model order; the root is evaluated at (y, x) on the record's level, part i
+ * at its anchor (2y + vy_i, 2x + vx_i) on the level lambda below. Term r of a filter at window phi is
+ * lambda_r sum_{dy,dx,c} phi[dy][dx][c] a_r[dy] b_r[dx] c_r[c]; a filter's terms are taken in decreasing |lambda_r|
+ * (ties by term index). Partial sums are FP32 from the FP32 levels and FP32 factors. The model must be decomposed per
+ * filter (ERR_STATE otherwise), and `pyrs` must describe the very device levels the scores set was built from, still
+ * alive and unchanged (ERR_ARG when the count, a size, lambda or a level pointer differs). */
+typedef struct {
+    int64_t candidates;      /* records tested (those with s >= tau) */
+    int64_t pruned;          /* of them, pruned by a threshold */
+    int64_t terms_evaluated; /* CP terms evaluated before each hypothesis's exit, summed */
+    int64_t terms_total;     /* CP terms of every filter of every candidate's component (the work without exits) */
+} tdpm_cascade_stats;
+
+/* Every filter's partial sums at caller records (host array, e.g. from tdpm_detect), without exits: out is a host
+ * array [n][max_slots][max_terms]; out[i][s][q] = the partial sum of the first q + 1 terms of slot s (0 = root, 1 + p
+ * = part p) of record i's component; NaN beyond a filter's rank or slot count. ERR_CAPACITY when max_slots is below
+ * 1 + the largest part count or max_terms below the largest per-filter rank; ERR_ARG for a record outside the scores
+ * set or whose window leaves its level. */
+tdpm_status tdpm_cascade_partials(tdpm_ctx *ctx, int32_t scores_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                                  const tdpm_detection *records, size_t n, float *out, int32_t max_slots,
+                                  int32_t max_terms, void *stream);
+
+/* Thresholds of Sec. 4 from positive examples: t[f][q] = min over the positives (host records of the scores set) of
+ * filter f's partial sum of its first q + 1 terms, the tightest values that prune no positive. t is a host array
+ * [n_filters][stride], stride >= the largest per-filter rank; filters of components with no positive, and entries
+ * beyond a filter's rank, get -inf (never prune). */
+tdpm_status tdpm_cascade_thresholds(tdpm_ctx *ctx, int32_t scores_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                                    const tdpm_detection *positives, size_t n, float *t, int32_t stride, void *stream);
+
+/* Step 4 with convolution shortening: the detections with s >= tau that no threshold prunes (host thresholds
+ * [n_filters][stride] as tdpm_cascade_thresholds writes them), in the order of tdpm_detect, evaluated on the device
+ * one warp per hypothesis with an exit at the first partial sum below its threshold. *n_out and ERR_CAPACITY as
+ * tdpm_detect; stats (may be NULL) receives the pruning counts. ERR_ARG for a NaN threshold or tau. */
+tdpm_status tdpm_detect_cascade(tdpm_ctx *ctx, int32_t scores_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                                const float *t, int32_t stride, float tau, tdpm_detection *out, size_t capacity,
+                                size_t *n_out, tdpm_cascade_stats *stats, void *stream);
+
 /* Map kinds for tdpm_get_maps */
 #define TDPM_MAP_FILTER_SCORE 0 /* index_a = filter id, index_b = level: correlation map [H-h+1][W-w+1] FP32 */
 #define TDPM_MAP_FINAL_SCORE 1  /* index_a = component, index_b = root level: score map [Y][X] FP32 */

@@ -14,6 +14,7 @@ code with the CUDA library. FP32 inputs are widened to FP64 and every quantity i
 * ``score_pyramid``        steps 1-3 for every component and root level (Sec. 2 score; Algorithm 1 steps 12-13)
 * ``detect``               step 4, threshold (Algorithm 1 steps 15-16)
 * ``nms``                  greedy non-maximum suppression of detections (a DPM convention; the paper has none)
+* ``cascade_*``            convolution shortening (Sec. 4 thresholds t_i, Algorithm 1 steps 4-9)
 
 Readings of points the paper leaves open (they are listed with reasons in the design notes): valid correlation with no
 padding; the part level of root level j is j - lam and part i of a root at (y, x) is anchored at (2y + vy, 2x + vx);
@@ -367,6 +368,72 @@ def nms(dets: Sequence[Tuple], root_hw: Sequence[Tuple[int, int]], cell0: float,
                 if iw > 0 and ih > 0 and (iw * ih) / ((bj[2] - bj[0]) * (bj[3] - bj[1])) > overlap:
                     alive[j] = False
     return sorted(kept)
+
+
+def cascade_order(lam: np.ndarray) -> List[int]:
+    """A filter's CP terms in the order the cascade adds them: decreasing |lambda_r|, ties by term index (reading of
+    "the first i summands" of Sec. 4)."""
+    return sorted(range(len(lam)), key=lambda r: (-abs(float(lam[r])), r))
+
+
+def cascade_partials(model, pyramid, factors: Sequence[Tuple[np.ndarray, ...]], rec: Tuple[int, int, int, int]
+                     ) -> List[np.ndarray]:
+    """Partial sums of every filter of a root hypothesis (Sec. 4 formula for t_i; Algorithm 1 steps 4-6).
+
+    ``rec`` = (component, root level j, y, x); ``factors[fid]`` = (lam [R], A [h][R], B [w][R], C [32][R]), the
+    per-filter CP decomposition of filter fid (model order). Slot 0 is the root at (y, x) on level j, slot 1 + i part
+    i at its anchor (2y + vy, 2x + vx) on level j - lam. Term r at window phi is
+    lam_r * sum_{dy,dx,c} phi[dy][dx][c] A[dy][r] B[dx][r] C[c][r]; entry q of a slot is the sum of its first q + 1
+    terms in ``cascade_order``. FP64."""
+    c, j, y, x = rec
+    fid = sum(1 + len(comp.parts) for comp in model.components[:c])
+    comp = model.components[c]
+    wins = [(j, y, x)] + [(j - pyramid.lam, 2 * y + p.anchor[0], 2 * x + p.anchor[1]) for p in comp.parts]
+    out = []
+    for s, (lv, y0, x0) in enumerate(wins):
+        lam, A, B, C = (_f64(a) for a in factors[fid + s])
+        h, w = A.shape[0], B.shape[0]
+        phi = _f64(pyramid.levels[lv][y0:y0 + h, x0:x0 + w, :])
+        assert phi.shape == (h, w, C.shape[0]), "window outside its level"
+        terms = lam * np.einsum("ijc,ir,jr,cr->r", phi, A, B, C)
+        out.append(np.cumsum(terms[cascade_order(lam)]))
+    return out
+
+
+def cascade_thresholds(model, pyramid_of, factors, positives: Sequence[Tuple[int, int, int, int, int]]
+                       ) -> Dict[int, np.ndarray]:
+    """t_q of every filter with positives (Sec. 4): the minimum over the positives of its partial sum of the first
+    q + 1 terms. ``positives`` = (image, component, level, y, x); ``pyramid_of(image)`` gives that image's pyramid.
+    Returns {fid: t [R_fid]}; filters of components without positives are absent (never pruned)."""
+    t: Dict[int, np.ndarray] = {}
+    for (img, c, j, y, x) in positives:
+        fid = sum(1 + len(comp.parts) for comp in model.components[:c])
+        for s, p in enumerate(cascade_partials(model, pyramid_of(img), factors, (c, j, y, x))):
+            t[fid + s] = p.copy() if fid + s not in t else np.minimum(t[fid + s], p)
+    return t
+
+
+def cascade_walk(model, pyramid, factors, thresholds: Dict[int, np.ndarray], rec: Tuple[int, int, int, int]
+                 ) -> Tuple[bool, int]:
+    """Algorithm 1 steps 3-11 for one hypothesis: the filters in model order, each one's terms in cascade order,
+    stopping at the first partial sum below its threshold. Returns (pruned, terms evaluated)."""
+    c = rec[0]
+    fid = sum(1 + len(comp.parts) for comp in model.components[:c])
+    evaluated = 0
+    for s, p in enumerate(cascade_partials(model, pyramid, factors, rec)):
+        t = thresholds.get(fid + s)
+        for q in range(len(p)):
+            evaluated += 1
+            if t is not None and p[q] < t[q]:
+                return True, evaluated
+    return False, evaluated
+
+
+def cascade_detect(model, pyramid, factors, thresholds: Dict[int, np.ndarray], dets: Sequence[Tuple]) -> List[int]:
+    """Algorithm 1's result set D among the step-4 detections ``dets`` (records starting (component, level, y, x),
+    as ``detect`` returns them): the indices of those the cascade does not prune, ascending. A pruned hypothesis
+    leaves D whatever its score, and one that survives is in D exactly when s >= tau, so D is this subset."""
+    return [i for i, d in enumerate(dets) if not cascade_walk(model, pyramid, factors, thresholds, tuple(d[:4]))[0]]
 
 
 def all_scores(scored: Sequence[Dict]) -> np.ndarray:

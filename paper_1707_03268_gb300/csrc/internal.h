@@ -235,6 +235,41 @@ cudaError_t launch_nms(const tdpm_detection *d_rec, long long n, const int32_t *
                        double overlap, void *d_scratch, size_t scratch_bytes, tdpm_detection *d_out,
                        long long *d_n_out, cudaStream_t s);
 
+// Convolution shortening (Sec. 4, Algorithm 1) over detection records. Per (component, filter slot) one CascFilter:
+// slot 0 the root, slot 1 + i part i. A term r of the filter is lam[r] * sum phi a_r b_r c_r over its window.
+struct CascFilter {
+    const float *A, *B, *Ct, *lam;  // the filter's shape group: A [h][R], B [w][R], Ct [R][32], lam [R] (FP32)
+    const int *order;               // the filter's terms in visiting order (nterms entries, indices into R)
+    const float *thr;               // threshold of each visiting position (nterms entries)
+    int R, nterms, h, w, vy, vx, part;
+};
+struct CascLevel {
+    const float *data;  // FP32 NHWC level of the caller's pyramid (null: absent)
+    int H, W;
+};
+struct CascArgs {
+    const tdpm_detection *rec = nullptr;
+    long long n = 0;
+    const CascFilter *filt = nullptr;
+    const int *comp_first = nullptr, *comp_count = nullptr;  // per component: first slot in filt, slot count
+    const CascLevel *levels = nullptr;                       // [n_images][max_levels]
+    int max_levels = 0;
+    const int *img_lam = nullptr;                            // per image: levels per octave
+    bool apply_thr = false;                                  // exit at the first partial sum below its threshold
+    float *partials = nullptr;                               // [n][max_slots][max_terms] evaluated partial sums, or null
+    int max_slots = 0, max_terms = 0;
+    uint8_t *alive = nullptr;                                // [n]: 1 = not pruned, or null
+    unsigned long long *stats = nullptr;  // [4] (zeroed by the caller): terms evaluated, terms of all filters, pruned,
+                                          // windows out of range (never read)
+};
+cudaError_t launch_cascade(const CascArgs &args, cudaStream_t s);
+
+// Ordered compaction: the records whose flag is nonzero go to d_out in record order, their number to *d_n_out.
+// d_scratch: at least compact_scratch_bytes(n) bytes.
+size_t compact_scratch_bytes(long long n);
+cudaError_t launch_compact_records(const tdpm_detection *d_rec, const uint8_t *d_flags, long long n, void *d_scratch,
+                                   size_t scratch_bytes, tdpm_detection *d_out, long long *d_n_out, cudaStream_t s);
+
 // Failure-detection self-test: one kernel whose bounded mbarrier wait expires (nothing arrives); it raises *d_err.
 cudaError_t launch_bounded_wait_probe(int *d_err, cudaStream_t s);
 

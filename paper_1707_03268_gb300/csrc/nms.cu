@@ -196,8 +196,13 @@ __global__ void nms_mark_kernel(const unsigned long long *__restrict__ keys, con
     if (p < n) kept[(uint32_t)keys[p]] = keep[p];
 }
 
-// Kept records per block of NMS_CBLOCK.
-__global__ void __launch_bounds__(NMS_CBLOCK) nms_block_count_kernel(const uint8_t *__restrict__ kept, long long n,
+size_t align256z(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+namespace {
+// Flagged records per block of NMS_CBLOCK.
+__global__ void __launch_bounds__(NMS_CBLOCK) compact_count_kernel(const uint8_t *__restrict__ kept, long long n,
                                                                      int *__restrict__ bcount)
 {
     __shared__ int ws[NMS_CBLOCK / 32];
@@ -213,8 +218,8 @@ __global__ void __launch_bounds__(NMS_CBLOCK) nms_block_count_kernel(const uint8
     }
 }
 
-// The kept records of each block at the block's offset, in record order.
-__global__ void __launch_bounds__(NMS_CBLOCK) nms_write_kernel(const tdpm_detection *__restrict__ rec,
+// The flagged records of each block at the block's offset, in record order.
+__global__ void __launch_bounds__(NMS_CBLOCK) compact_write_kernel(const tdpm_detection *__restrict__ rec,
                                                                const uint8_t *__restrict__ kept, long long n,
                                                                const int *__restrict__ boff,
                                                                tdpm_detection *__restrict__ out)
@@ -231,16 +236,34 @@ __global__ void __launch_bounds__(NMS_CBLOCK) nms_write_kernel(const tdpm_detect
     if (k) out[boff[blockIdx.x] + before + __popc(b & ((1u << lane) - 1u))] = rec[i];
 }
 
-size_t align256z(size_t b) { return (b + 255) & ~(size_t)255; }
-
 }  // namespace
+
+size_t compact_scratch_bytes(long long n)
+{
+    const size_t nb = ((size_t)std::max<long long>(n, 1) + NMS_CBLOCK - 1) / NMS_CBLOCK;
+    return 2 * align256z(4 * nb);
+}
+
+cudaError_t launch_compact_records(const tdpm_detection *d_rec, const uint8_t *d_flags, long long n, void *d_scratch,
+                                   size_t scratch_bytes, tdpm_detection *d_out, long long *d_n_out, cudaStream_t s)
+{
+    if (n <= 0) return cudaMemsetAsync(d_n_out, 0, sizeof(long long), s);
+    if (n > (1ll << 30) || scratch_bytes < compact_scratch_bytes(n)) return cudaErrorInvalidValue;
+    const int nb = (int)((n + NMS_CBLOCK - 1) / NMS_CBLOCK);
+    auto *bcount = static_cast<int *>(d_scratch);
+    auto *boff = reinterpret_cast<int *>(static_cast<char *>(d_scratch) + align256z(4 * (size_t)nb));
+    note_launches(3);
+    compact_count_kernel<<<nb, NMS_CBLOCK, 0, s>>>(d_flags, n, bcount);
+    nms_scan_kernel<<<1, NMS_THREADS, 0, s>>>(bcount, nb, boff, d_n_out);
+    compact_write_kernel<<<nb, NMS_CBLOCK, 0, s>>>(d_rec, d_flags, n, boff, d_out);
+    return cudaGetLastError();
+}
 
 size_t nms_scratch_bytes(long long n, int n_groups)
 {
     const size_t nn = (size_t)std::max<long long>(n, 1);
-    const size_t nb = (nn + NMS_CBLOCK - 1) / NMS_CBLOCK;
     return align256z(8 * nn) + align256z(sizeof(NmsBox) * nn) + 2 * align256z(nn) +
-           3 * align256z(4 * (size_t)std::max(n_groups, 1)) + 2 * align256z(4 * nb);
+           3 * align256z(4 * (size_t)std::max(n_groups, 1)) + compact_scratch_bytes(n);
 }
 
 cudaError_t launch_nms(const tdpm_detection *d_rec, long long n, const int32_t *d_cls, int n_classes, int n_images,
@@ -253,7 +276,6 @@ cudaError_t launch_nms(const tdpm_detection *d_rec, long long n, const int32_t *
         return cudaErrorInvalidValue;
     const int n_groups = n_images * n_classes;
     if (scratch_bytes < nms_scratch_bytes(n, n_groups)) return cudaErrorInvalidValue;
-    const int nb = (int)((n + NMS_CBLOCK - 1) / NMS_CBLOCK);
     char *p = static_cast<char *>(d_scratch);
     auto take = [&](size_t b) {
         char *q = p;
@@ -267,24 +289,22 @@ cudaError_t launch_nms(const tdpm_detection *d_rec, long long n, const int32_t *
     auto *counts = reinterpret_cast<int *>(take(4 * (size_t)n_groups));
     auto *offsets = reinterpret_cast<int *>(take(4 * (size_t)n_groups));
     auto *cursor = reinterpret_cast<int *>(take(4 * (size_t)n_groups));
-    auto *bcount = reinterpret_cast<int *>(take(4 * (size_t)nb));
-    auto *boff = reinterpret_cast<int *>(take(4 * (size_t)nb));
+    void *cscratch = p;
+    const size_t cbytes = scratch_bytes - (size_t)(p - static_cast<char *>(d_scratch));
     cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void *>(nms_group_kernel), 25);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(counts, 0, 4 * (size_t)n_groups, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(cursor, 0, 4 * (size_t)n_groups, s)) != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    note_launches(8);
+    note_launches(5);
     nms_count_kernel<<<blocks, 256, 0, s>>>(d_rec, n, d_cls, n_classes, counts);
     nms_scan_kernel<<<1, NMS_THREADS, 0, s>>>(counts, n_groups, offsets, nullptr);
     nms_scatter_kernel<<<blocks, 256, 0, s>>>(d_rec, n, d_cls, n_classes, offsets, cursor, keys);
     nms_group_kernel<<<n_groups, NMS_THREADS, NMS_SMEM_BYTES, s>>>(d_rec, keys, offsets, counts, d_root_h, d_root_w,
                                                                    d_cell, max_levels, boxes, overlap, keep);
     nms_mark_kernel<<<blocks, 256, 0, s>>>(keys, keep, n, kept);
-    nms_block_count_kernel<<<nb, NMS_CBLOCK, 0, s>>>(kept, n, bcount);
-    nms_scan_kernel<<<1, NMS_THREADS, 0, s>>>(bcount, nb, boff, d_n_out);
-    nms_write_kernel<<<nb, NMS_CBLOCK, 0, s>>>(d_rec, kept, n, boff, d_out);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_compact_records(d_rec, kept, n, cscratch, cbytes, d_out, d_n_out, s);
 }
 
 }  // namespace tdpm

@@ -1309,6 +1309,76 @@ tdpm_status tdpm_detect_thresholds(tdpm_ctx *ctx, int32_t scores_id, const float
     return detect_impl(ctx, scores_id, 0.f, tau, out, capacity, n_out, stream);
 }
 
+namespace {
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// The records of a scores set with score >= tau, written to the context's post-processing scratch (grow-only,
+// shared by the calls below; they hold the context lock and finish before they return). Counts first (one
+// synchronisation), then makes room for the records plus `extra(n)` bytes and writes them. *d_rec: the records,
+// *d_extra: 256-aligned, right after them.
+tdpm_status scratch_records(tdpm_ctx *ctx, Scores *sc, float tau, cudaStream_t s,
+                            const std::function<size_t(long long)> &extra, long long &n, tdpm_detection *&d_rec,
+                            char *&d_extra)
+{
+    const Plan &P = *sc->plan;
+    char *base = sc->arena.dev;
+    const AsmJob *jobs = reinterpret_cast<const AsmJob *>(base + P.blob_off + P.asm_off);
+    int *counts = reinterpret_cast<int *>(base + P.counts_off), *offsets = reinterpret_cast<int *>(base + P.offsets_off);
+    long long *d_total = reinterpret_cast<long long *>(base + P.total_off);
+    CUDA_TRY(cudaStreamWaitEvent(s, sc->done, 0));
+    CUDA_TRY(launch_detect_count(jobs, (int)P.asms.size(), P.total, tau, nullptr, counts, offsets, P.n_det_blocks,
+                                 d_total, s));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    tdpm_status st = check_device_flag(ctx);
+    if (st) return st;
+    n = *ctx->h_total;
+    if (n > (1ll << 30)) return fail(TDPM_ERR_CAPACITY, "more than 2^30 detections above tau");
+    const size_t rec_b = a256(sizeof(tdpm_detection) * (size_t)std::max<long long>(n, 1));
+    const size_t need = rec_b + a256(extra(n)) + 256;
+    if (need > ctx->nms_cap) {
+        if (ctx->d_nms) {
+            cudaFree(ctx->d_nms);
+            ctx->used -= std::min(ctx->used, ctx->nms_cap);
+            ctx->d_nms = nullptr;
+            ctx->nms_cap = 0;
+        }
+        if (ctx->budget && ctx->used + need > ctx->budget)
+            return fail(TDPM_ERR_OOM, "post-processing scratch exceeds the budget");
+        CUDA_TRY(cudaMalloc(&ctx->d_nms, need));
+        ctx->nms_cap = need;
+        ctx->used += need;
+    }
+    d_rec = static_cast<tdpm_detection *>(ctx->d_nms);
+    d_extra = static_cast<char *>(ctx->d_nms) + rec_b;
+    if (n > 0)
+        CUDA_TRY(launch_detect_write(jobs, (int)P.asms.size(), P.total, tau, nullptr, offsets, P.n_det_blocks, d_rec, n,
+                                     sc->model_id, s));
+    return TDPM_OK;
+}
+
+// Copies the kept records (count at d_n) back and records the set's use.
+tdpm_status read_kept(tdpm_ctx *ctx, Scores *sc, const long long *d_n, const tdpm_detection *d_kept,
+                      tdpm_detection *out, size_t capacity, size_t *n_out, cudaStream_t s)
+{
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_total, d_n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const long long kept = *ctx->h_total;
+    const size_t nk = std::min<size_t>((size_t)kept, capacity);
+    if (nk) {
+        CUDA_TRY(cudaMemcpyAsync(out, d_kept, nk * sizeof(tdpm_detection), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    CUDA_TRY(cudaEventRecord(sc->done, s));
+    *n_out = (size_t)kept;
+    if ((size_t)kept > capacity)
+        return fail(TDPM_ERR_CAPACITY, "kept detections exceed capacity: " + std::to_string(kept));
+    return TDPM_OK;
+}
+
+}  // namespace
+
 tdpm_status tdpm_detect_nms(tdpm_ctx *ctx, int32_t scores_id, float tau, const int32_t *component_class,
                             double overlap, double cell0, tdpm_detection *out, size_t capacity, size_t *n_out,
                             void *stream)
@@ -1317,6 +1387,7 @@ tdpm_status tdpm_detect_nms(tdpm_ctx *ctx, int32_t scores_id, float tau, const i
     if (!ctx || !n_out || (capacity > 0 && !out)) return fail(TDPM_ERR_ARG, "NULL argument");
     if (!(overlap >= 0.0 && overlap <= 1.0)) return fail(TDPM_ERR_ARG, "overlap must be in [0, 1]");
     if (!(cell0 > 0.0) || !std::isfinite(cell0)) return fail(TDPM_ERR_ARG, "cell0 must be finite and > 0");
+    if (std::isnan(tau)) return fail(TDPM_ERR_ARG, "tau is NaN");
     std::lock_guard<std::mutex> lk(ctx->mu);
     tdpm_status st = set_device(ctx);
     if (st) return st;
@@ -1333,44 +1404,23 @@ tdpm_status tdpm_detect_nms(tdpm_ctx *ctx, int32_t scores_id, float tau, const i
             n_classes = std::max(n_classes, component_class[c] + 1);
         }
     cudaStream_t s = (cudaStream_t)stream;
-    char *base = sc->arena.dev;
-    const AsmJob *jobs = reinterpret_cast<const AsmJob *>(base + P.blob_off + P.asm_off);
-    int *counts = reinterpret_cast<int *>(base + P.counts_off), *offsets = reinterpret_cast<int *>(base + P.offsets_off);
-    long long *d_total = reinterpret_cast<long long *>(base + P.total_off);
-    CUDA_TRY(cudaStreamWaitEvent(s, sc->done, 0));
-    // every detection on the device
-    CUDA_TRY(launch_detect_count(jobs, (int)P.asms.size(), P.total, tau, nullptr, counts, offsets, P.n_det_blocks,
-                                 d_total, s));
-    CUDA_TRY(cudaMemcpyAsync(ctx->h_total, d_total, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if ((st = check_device_flag(ctx))) return st;
-    const long long n = *ctx->h_total;
-    if (n > (1ll << 30)) return fail(TDPM_ERR_CAPACITY, "more than 2^30 detections above tau for NMS");
-    // scratch: every record, the kept ones, the NMS working set, the per-component and per-level tables
     int max_levels = 1;
     for (int L : P.img_L) max_levels = std::max(max_levels, L);
-    const size_t rec_b = sizeof(tdpm_detection) * (size_t)std::max<long long>(n, 1);
-    const size_t work_b = nms_scratch_bytes(n, P.n_images * n_classes);
-    auto a256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // after the records: the kept records, the NMS working set, the per-component and per-level tables
     const size_t cls_b = a256(4 * (size_t)nc * 3), cell_b = a256(8 * (size_t)P.n_images * max_levels);
-    const size_t need = 2 * a256(rec_b) + a256(work_b) + cls_b + cell_b + 256;
-    if (need > ctx->nms_cap) {
-        if (ctx->d_nms) {
-            cudaFree(ctx->d_nms);
-            ctx->used -= std::min(ctx->used, ctx->nms_cap);
-            ctx->d_nms = nullptr;
-            ctx->nms_cap = 0;
-        }
-        if (ctx->budget && ctx->used + need > ctx->budget) return fail(TDPM_ERR_OOM, "NMS scratch exceeds the budget");
-        CUDA_TRY(cudaMalloc(&ctx->d_nms, need));
-        ctx->nms_cap = need;
-        ctx->used += need;
-    }
-    char *q = static_cast<char *>(ctx->d_nms);
-    auto *d_rec = reinterpret_cast<tdpm_detection *>(q);
-    auto *d_kept = reinterpret_cast<tdpm_detection *>(q + a256(rec_b));
-    void *d_work = q + 2 * a256(rec_b);
-    char *tab = q + 2 * a256(rec_b) + a256(work_b);
+    auto extra = [&](long long n) {
+        return a256(sizeof(tdpm_detection) * (size_t)std::max<long long>(n, 1)) +
+               a256(nms_scratch_bytes(n, P.n_images * n_classes)) + cls_b + cell_b + 256;
+    };
+    long long n = 0;
+    tdpm_detection *d_rec = nullptr;
+    char *q = nullptr;
+    if ((st = scratch_records(ctx, sc, tau, s, extra, n, d_rec, q))) return st;
+    const size_t work_b = nms_scratch_bytes(n, P.n_images * n_classes);
+    auto *d_kept = reinterpret_cast<tdpm_detection *>(q);
+    q += a256(sizeof(tdpm_detection) * (size_t)std::max<long long>(n, 1));
+    void *d_work = q;
+    char *tab = q + a256(work_b);
     auto *d_cls = reinterpret_cast<int32_t *>(tab);
     auto *d_rh = d_cls + nc, *d_rw = d_rh + nc;
     auto *d_cell = reinterpret_cast<double *>(tab + cls_b);
@@ -1388,23 +1438,354 @@ tdpm_status tdpm_detect_nms(tdpm_ctx *ctx, int32_t scores_id, float tau, const i
             cells[(size_t)im * max_levels + j] = cell0 * std::pow(2.0, (double)j / (double)P.img_lam[im]);
     CUDA_TRY(cudaMemcpyAsync(d_cls, tabs.data(), 4 * tabs.size(), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(d_cell, cells.data(), 8 * cells.size(), cudaMemcpyHostToDevice, s));
-    if (n > 0)
-        CUDA_TRY(launch_detect_write(jobs, (int)P.asms.size(), P.total, tau, nullptr, offsets, P.n_det_blocks, d_rec, n,
-                                     sc->model_id, s));
     CUDA_TRY(launch_nms(d_rec, n, component_class ? d_cls : nullptr, n_classes, P.n_images, d_rh, d_rw, d_cell,
                         max_levels, overlap, d_work, work_b, d_kept, d_nk, s));
-    CUDA_TRY(cudaMemcpyAsync(ctx->h_total, d_nk, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    const long long kept = *ctx->h_total;
-    const size_t nk = std::min<size_t>((size_t)kept, capacity);
-    if (nk) {
-        CUDA_TRY(cudaMemcpyAsync(out, d_kept, nk * sizeof(tdpm_detection), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
+    return read_kept(ctx, sc, d_nk, d_kept, out, capacity, n_out, s);
+}
+
+// ------------------------------------------------------------------------------ convolution shortening (Sec. 4)
+namespace {
+
+// Device tables of one cascade call, packed in one host blob and copied with one transfer: the filter slots of every
+// component (root, then parts), each filter's term order (decreasing |lambda_r|, ties by index) and thresholds, and
+// the caller's levels. Needs per-filter factors (Sec. 4); the pyramids must be those the scores set was built from.
+struct CascSetup {
+    std::vector<char> blob;
+    size_t filt_off = 0, first_off = 0, count_off = 0, lev_off = 0, lam_off = 0;
+    int max_levels = 1, max_slots = 1, max_terms = 1, n_comps = 0;
+    std::vector<int> comp_slots;  // per component: filter slots (1 + parts)
+    std::vector<int> slot_fid;    // per (component, slot) in order: the filter id
+    std::vector<int> fid_terms;   // per filter: its number of terms
+    CascArgs args;                // pointer fields relative to the device copy of the blob
+};
+
+tdpm_status casc_setup(const Model &m, const Plan &P, const Arena &A, const tdpm_pyramid *pyrs, int n_images,
+                       const float *thr, int thr_stride, char *d_blob, CascSetup &C)
+{
+    if (!m.decomposed || m.decomp_mode != TDPM_DECOMP_PER_FILTER)
+        return fail(TDPM_ERR_STATE, "the cascade needs the model decomposed per filter (Sec. 4)");
+    if (!pyrs || n_images != P.n_images)
+        return fail(TDPM_ERR_ARG, "pass the pyramids the scores set was built from");
+    C.max_levels = 1;
+    for (int L : P.img_L) C.max_levels = std::max(C.max_levels, L);
+    std::vector<CascLevel> lv((size_t)n_images * C.max_levels, CascLevel{nullptr, 0, 0});
+    for (int im = 0; im < n_images; ++im) {
+        const tdpm_pyramid &py = pyrs[im];
+        if (py.n_levels != P.img_L[im] || py.lambda != P.img_lam[im] || !py.levels)
+            return fail(TDPM_ERR_ARG, "pyramid " + std::to_string(im) + " differs from the scored one");
+        for (int j = 0; j < py.n_levels; ++j) {
+            const tdpm_level &L = py.levels[j];
+            const auto &sz = P.sizes[(size_t)P.img_base[im] + j];
+            const size_t flat = (size_t)P.img_base[im] + j;
+            if (!L.data || L.H != sz.first || L.W != sz.second || flat >= A.levels.size() || A.levels[flat] != L.data)
+                return fail(TDPM_ERR_ARG, "pyramid " + std::to_string(im) + " level " + std::to_string(j) +
+                                              " is not the level the scores set was built from");
+            lv[(size_t)im * C.max_levels + j] = CascLevel{L.data, L.H, L.W};
+        }
     }
-    CUDA_TRY(cudaEventRecord(sc->done, s));
-    *n_out = (size_t)kept;
-    if ((size_t)kept > capacity) return fail(TDPM_ERR_CAPACITY, "kept detections exceed capacity: " + std::to_string(kept));
+    C.n_comps = (int)m.comps.size();
+    C.fid_terms.assign(m.filters.size(), 0);
+    std::vector<std::vector<int>> order(m.filters.size());
+    for (size_t f = 0; f < m.filters.size(); ++f) {
+        const FilterH &F = m.filters[f];
+        const Group &g = m.groups[F.group];
+        const int r0 = g.rank_off[F.gidx], r1 = g.rank_off[F.gidx + 1];
+        for (int r = r0; r < r1; ++r) order[f].push_back(r);
+        std::stable_sort(order[f].begin(), order[f].end(), [&](int a, int b) {
+            return std::fabs(g.Lam[(size_t)F.gidx * g.R + a]) > std::fabs(g.Lam[(size_t)F.gidx * g.R + b]);
+        });
+        C.fid_terms[f] = r1 - r0;
+        C.max_terms = std::max(C.max_terms, r1 - r0);
+    }
+    if (thr && thr_stride < C.max_terms)
+        return fail(TDPM_ERR_ARG, "threshold stride below the largest rank " + std::to_string(C.max_terms));
+    C.comp_slots.clear();
+    C.slot_fid.clear();
+    for (const CompH &c : m.comps) {
+        C.comp_slots.push_back(1 + (int)c.parts.size());
+        C.slot_fid.push_back(c.root_fid);
+        for (const PartH &p : c.parts) C.slot_fid.push_back(p.fid);
+        C.max_slots = std::max(C.max_slots, 1 + (int)c.parts.size());
+    }
+    // blob: CascFilter[slots] | first[nc] | count[nc] | levels | img_lam | per slot: order, thresholds
+    const size_t n_slots = C.slot_fid.size();
+    Bump b;
+    C.filt_off = b.take(sizeof(CascFilter) * n_slots);
+    C.first_off = b.take(4 * (size_t)C.n_comps);
+    C.count_off = b.take(4 * (size_t)C.n_comps);
+    C.lev_off = b.take(sizeof(CascLevel) * lv.size());
+    C.lam_off = b.take(4 * (size_t)n_images);
+    std::vector<size_t> ord_off(n_slots), thr_off(n_slots);
+    for (size_t k = 0; k < n_slots; ++k) {
+        ord_off[k] = b.take(4 * (size_t)std::max(1, C.fid_terms[C.slot_fid[k]]));
+        thr_off[k] = b.take(4 * (size_t)std::max(1, C.fid_terms[C.slot_fid[k]]));
+    }
+    C.blob.assign(align256(b.off), 0);
+    char *hb = C.blob.data();
+    size_t k = 0;
+    for (int ci = 0; ci < C.n_comps; ++ci) {
+        const CompH &c = m.comps[ci];
+        reinterpret_cast<int *>(hb + C.first_off)[ci] = (int)k;
+        reinterpret_cast<int *>(hb + C.count_off)[ci] = C.comp_slots[ci];
+        for (int sl = 0; sl < C.comp_slots[ci]; ++sl, ++k) {
+            const int fid = C.slot_fid[k];
+            const FilterH &F = m.filters[fid];
+            const Group &g = m.groups[F.group];
+            CascFilter cf{};
+            cf.A = g.d_A;
+            cf.B = g.d_B;
+            cf.Ct = g.d_Ct;
+            cf.lam = g.d_lam;
+            cf.order = reinterpret_cast<const int *>(d_blob + ord_off[k]);
+            cf.thr = reinterpret_cast<const float *>(d_blob + thr_off[k]);
+            cf.R = g.R;
+            cf.nterms = C.fid_terms[fid];
+            cf.h = F.h;
+            cf.w = F.w;
+            cf.part = sl > 0;
+            cf.vy = sl > 0 ? c.parts[sl - 1].vy : 0;
+            cf.vx = sl > 0 ? c.parts[sl - 1].vx : 0;
+            reinterpret_cast<CascFilter *>(hb + C.filt_off)[k] = cf;
+            int *o = reinterpret_cast<int *>(hb + ord_off[k]);
+            float *t = reinterpret_cast<float *>(hb + thr_off[k]);
+            for (int q = 0; q < cf.nterms; ++q) {
+                o[q] = order[fid][q];
+                t[q] = thr ? thr[(size_t)fid * thr_stride + q] : -INFINITY;
+                if (std::isnan(t[q])) return fail(TDPM_ERR_ARG, "a threshold is NaN");
+            }
+        }
+    }
+    std::memcpy(hb + C.lev_off, lv.data(), sizeof(CascLevel) * lv.size());
+    std::memcpy(hb + C.lam_off, P.img_lam.data(), 4 * (size_t)n_images);
+    C.args = CascArgs{};
+    C.args.filt = reinterpret_cast<const CascFilter *>(d_blob + C.filt_off);
+    C.args.comp_first = reinterpret_cast<const int *>(d_blob + C.first_off);
+    C.args.comp_count = reinterpret_cast<const int *>(d_blob + C.count_off);
+    C.args.levels = reinterpret_cast<const CascLevel *>(d_blob + C.lev_off);
+    C.args.max_levels = C.max_levels;
+    C.args.img_lam = reinterpret_cast<const int *>(d_blob + C.lam_off);
     return TDPM_OK;
+}
+
+// Size of the blob casc_setup will build (a dry run on a throwaway device base).
+size_t casc_blob_bytes(const Model &m, const Plan &P, int n_images)
+{
+    size_t n_slots = 0, terms = 0;
+    for (const CompH &c : m.comps) n_slots += 1 + c.parts.size();
+    for (const CompH &c : m.comps) {
+        auto add = [&](int fid) {
+            const FilterH &F = m.filters[fid];
+            const Group &g = m.groups[F.group];
+            terms += (size_t)std::max(1, g.rank_off.empty() ? 0 : g.rank_off[F.gidx + 1] - g.rank_off[F.gidx]);
+        };
+        add(c.root_fid);
+        for (const PartH &p : c.parts) add(p.fid);
+    }
+    int max_levels = 1;
+    for (int L : P.img_L) max_levels = std::max(max_levels, L);
+    return sizeof(CascFilter) * n_slots + 8 * m.comps.size() + sizeof(CascLevel) * (size_t)n_images * max_levels +
+           4 * (size_t)n_images + 8 * terms + 256 * (6 + 2 * n_slots);
+}
+
+tdpm_status casc_begin(tdpm_ctx *ctx, int32_t scores_id, Scores *&sc, const Model *&m)
+{
+    tdpm_status st = set_device(ctx);
+    if (st) return st;
+    sc = get_scores(ctx, scores_id);
+    if (!sc) return fail(TDPM_ERR_STATE, "unknown scores id");
+    m = get_model(ctx, sc->model_id);
+    if (!m) return fail(TDPM_ERR_STATE, "the scores' model was unloaded");
+    if (!m->decomposed || m->decomp_mode != TDPM_DECOMP_PER_FILTER)
+        return fail(TDPM_ERR_STATE, "the cascade needs the model decomposed per filter (Sec. 4)");
+    return TDPM_OK;
+}
+
+// Partial sums at caller records (no exits): out [n][max_slots][max_terms] on the host, NaN where not evaluated.
+tdpm_status casc_partials(tdpm_ctx *ctx, Scores *sc, const Model &m, const tdpm_pyramid *pyrs, int n_images,
+                          const tdpm_detection *records, size_t n, std::vector<float> &out, CascSetup &C,
+                          cudaStream_t s)
+{
+    const Plan &P = *sc->plan;
+    const size_t blob_b = casc_blob_bytes(m, P, n_images);
+    // validate the records on the host: component, image and level ranges (windows are checked on the device)
+    for (size_t i = 0; i < n; ++i) {
+        const tdpm_detection &d = records[i];
+        if (d.image < 0 || d.image >= P.n_images || d.component < 0 || d.component >= (int)m.comps.size() ||
+            d.level < 0 || d.level >= P.img_L[d.image])
+            return fail(TDPM_ERR_ARG, "record " + std::to_string(i) + " is outside the scores set");
+    }
+    // size the partials with a dry setup first (max_slots, max_terms)
+    tdpm_status st = casc_setup(m, P, sc->arena, pyrs, n_images, nullptr, 0, nullptr, C);
+    if (st) return st;
+    const size_t rec_b = a256(sizeof(tdpm_detection) * std::max<size_t>(n, 1));
+    const size_t part_b = a256(4 * std::max<size_t>(n, 1) * C.max_slots * C.max_terms);
+    const size_t need = rec_b + part_b + a256(blob_b) + a256(32) + 256;
+    if (need > ctx->nms_cap) {
+        if (ctx->d_nms) {
+            cudaFree(ctx->d_nms);
+            ctx->used -= std::min(ctx->used, ctx->nms_cap);
+            ctx->d_nms = nullptr;
+            ctx->nms_cap = 0;
+        }
+        if (ctx->budget && ctx->used + need > ctx->budget)
+            return fail(TDPM_ERR_OOM, "post-processing scratch exceeds the budget");
+        CUDA_TRY(cudaMalloc(&ctx->d_nms, need));
+        ctx->nms_cap = need;
+        ctx->used += need;
+    }
+    char *q = static_cast<char *>(ctx->d_nms);
+    auto *d_rec = reinterpret_cast<tdpm_detection *>(q);
+    auto *d_part = reinterpret_cast<float *>(q + rec_b);
+    char *d_blob = q + rec_b + part_b;
+    auto *d_stats = reinterpret_cast<unsigned long long *>(d_blob + a256(blob_b));
+    if ((st = casc_setup(m, P, sc->arena, pyrs, n_images, nullptr, 0, d_blob, C))) return st;
+    if (C.blob.size() > a256(blob_b)) return fail(TDPM_ERR_STATE, "cascade table larger than its estimate");
+    out.assign(std::max<size_t>(n, 1) * C.max_slots * C.max_terms, NAN);
+    CUDA_TRY(cudaStreamWaitEvent(s, sc->done, 0));
+    if (n) {
+        CUDA_TRY(cudaMemcpyAsync(d_rec, records, sizeof(tdpm_detection) * n, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(d_part, out.data(), 4 * out.size(), cudaMemcpyHostToDevice, s));
+    }
+    CUDA_TRY(cudaMemcpyAsync(d_blob, C.blob.data(), C.blob.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(d_stats, 0, 32, s));
+    CascArgs a = C.args;
+    a.rec = d_rec;
+    a.n = (long long)n;
+    a.partials = d_part;
+    a.max_slots = C.max_slots;
+    a.max_terms = C.max_terms;
+    a.stats = d_stats;
+    CUDA_TRY(launch_cascade(a, s));
+    unsigned long long h_stats[4] = {0, 0, 0, 0};
+    if (n) CUDA_TRY(cudaMemcpyAsync(out.data(), d_part, 4 * out.size(), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(h_stats, d_stats, sizeof(h_stats), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaEventRecord(sc->done, s));
+    if (h_stats[3]) return fail(TDPM_ERR_ARG, "a record's filter window lies outside its level");
+    return TDPM_OK;
+}
+
+}  // namespace
+
+tdpm_status tdpm_cascade_partials(tdpm_ctx *ctx, int32_t scores_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                                  const tdpm_detection *records, size_t n, float *out, int32_t max_slots,
+                                  int32_t max_terms, void *stream)
+{
+    clear_error();
+    if (!ctx || (n > 0 && (!records || !out))) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (n > (1u << 24)) return fail(TDPM_ERR_ARG, "at most 2^24 records");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Scores *sc = nullptr;
+    const Model *m = nullptr;
+    tdpm_status st = casc_begin(ctx, scores_id, sc, m);
+    if (st) return st;
+    CascSetup C;
+    std::vector<float> part;
+    if ((st = casc_partials(ctx, sc, *m, pyrs, n_images, records, n, part, C, (cudaStream_t)stream))) return st;
+    if (max_slots < C.max_slots || max_terms < C.max_terms)
+        return fail(TDPM_ERR_CAPACITY, "partials need max_slots >= " + std::to_string(C.max_slots) +
+                                           " and max_terms >= " + std::to_string(C.max_terms));
+    for (size_t i = 0; i < n; ++i)
+        for (int sl = 0; sl < max_slots; ++sl)
+            for (int q = 0; q < max_terms; ++q)
+                out[((size_t)i * max_slots + sl) * max_terms + q] =
+                    sl < C.max_slots && q < C.max_terms ? part[((size_t)i * C.max_slots + sl) * C.max_terms + q] : NAN;
+    return TDPM_OK;
+}
+
+tdpm_status tdpm_cascade_thresholds(tdpm_ctx *ctx, int32_t scores_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                                    const tdpm_detection *positives, size_t n, float *t, int32_t stride, void *stream)
+{
+    clear_error();
+    if (!ctx || !t || (n > 0 && !positives)) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (n > (1u << 24)) return fail(TDPM_ERR_ARG, "at most 2^24 positives");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Scores *sc = nullptr;
+    const Model *m = nullptr;
+    tdpm_status st = casc_begin(ctx, scores_id, sc, m);
+    if (st) return st;
+    CascSetup C;
+    std::vector<float> part;
+    if ((st = casc_partials(ctx, sc, *m, pyrs, n_images, positives, n, part, C, (cudaStream_t)stream))) return st;
+    if (stride < C.max_terms) return fail(TDPM_ERR_ARG, "stride below the largest rank " + std::to_string(C.max_terms));
+    // t[fid][q] = min over the positives of the filter's partial sum of its first q + 1 terms; -inf without positives
+    const size_t nf = m->filters.size();
+    for (size_t f = 0; f < nf; ++f)
+        for (int q = 0; q < stride; ++q) t[f * stride + q] = -INFINITY;
+    std::vector<char> seen(nf, 0);
+    for (size_t i = 0; i < n; ++i) {
+        const int ci = positives[i].component;
+        int k = 0;
+        for (int c = 0; c < ci; ++c) k += C.comp_slots[c];
+        for (int sl = 0; sl < C.comp_slots[ci]; ++sl) {
+            const int fid = C.slot_fid[(size_t)k + sl];
+            float *tf = t + (size_t)fid * stride;
+            for (int q = 0; q < C.fid_terms[fid]; ++q) {
+                const float p = part[((size_t)i * C.max_slots + sl) * C.max_terms + q];
+                tf[q] = seen[fid] ? std::min(tf[q], p) : p;
+            }
+            seen[fid] = 1;
+        }
+    }
+    return TDPM_OK;
+}
+
+tdpm_status tdpm_detect_cascade(tdpm_ctx *ctx, int32_t scores_id, const tdpm_pyramid *pyrs, int32_t n_images,
+                                const float *t, int32_t stride, float tau, tdpm_detection *out, size_t capacity,
+                                size_t *n_out, tdpm_cascade_stats *stats, void *stream)
+{
+    clear_error();
+    if (!ctx || !t || !n_out || (capacity > 0 && !out)) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (std::isnan(tau)) return fail(TDPM_ERR_ARG, "tau is NaN");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Scores *sc = nullptr;
+    const Model *m = nullptr;
+    tdpm_status st = casc_begin(ctx, scores_id, sc, m);
+    if (st) return st;
+    const Plan &P = *sc->plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    CascSetup C;
+    if ((st = casc_setup(*m, P, sc->arena, pyrs, n_images, t, stride, nullptr, C))) return st;  // validation before any work
+    const size_t blob_b = casc_blob_bytes(*m, P, n_images);
+    // after the records: the kept records, the flags, the tables, the statistics, the compaction scratch
+    auto extra = [&](long long n) {
+        const size_t nn = (size_t)std::max<long long>(n, 1);
+        return a256(sizeof(tdpm_detection) * nn) + a256(nn) + a256(blob_b) + a256(40) + compact_scratch_bytes(n);
+    };
+    long long n = 0;
+    tdpm_detection *d_rec = nullptr;
+    char *q = nullptr;
+    if ((st = scratch_records(ctx, sc, tau, s, extra, n, d_rec, q))) return st;
+    const size_t nn = (size_t)std::max<long long>(n, 1);
+    auto *d_kept = reinterpret_cast<tdpm_detection *>(q);
+    auto *d_alive = reinterpret_cast<uint8_t *>(q + a256(sizeof(tdpm_detection) * nn));
+    char *d_blob = q + a256(sizeof(tdpm_detection) * nn) + a256(nn);
+    auto *d_stats = reinterpret_cast<unsigned long long *>(d_blob + a256(blob_b));
+    auto *d_nk = reinterpret_cast<long long *>(d_stats + 4);
+    void *d_cs = d_blob + a256(blob_b) + a256(40);
+    if ((st = casc_setup(*m, P, sc->arena, pyrs, n_images, t, stride, d_blob, C))) return st;
+    if (C.blob.size() > a256(blob_b)) return fail(TDPM_ERR_STATE, "cascade table larger than its estimate");
+    CUDA_TRY(cudaMemcpyAsync(d_blob, C.blob.data(), C.blob.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(d_stats, 0, 40, s));
+    CascArgs a = C.args;
+    a.rec = d_rec;
+    a.n = n;
+    a.apply_thr = true;
+    a.alive = d_alive;
+    a.stats = d_stats;
+    CUDA_TRY(launch_cascade(a, s));
+    CUDA_TRY(launch_compact_records(d_rec, d_alive, n, d_cs, compact_scratch_bytes(n), d_kept, d_nk, s));
+    unsigned long long h_stats[4] = {0, 0, 0, 0};
+    CUDA_TRY(cudaMemcpyAsync(h_stats, d_stats, sizeof(h_stats), cudaMemcpyDeviceToHost, s));
+    if ((st = read_kept(ctx, sc, d_nk, d_kept, out, capacity, n_out, s)) && st != TDPM_ERR_CAPACITY) return st;
+    if (h_stats[3]) return fail(TDPM_ERR_STATE, "a record's filter window lies outside its level");
+    if (stats) {
+        stats->candidates = n;
+        stats->pruned = (int64_t)h_stats[2];
+        stats->terms_evaluated = (int64_t)h_stats[0];
+        stats->terms_total = (int64_t)h_stats[1];
+    }
+    return st;
 }
 
 tdpm_status tdpm_get_maps(tdpm_ctx *ctx, int32_t scores_id, int32_t kind, int32_t image, int32_t index_a,

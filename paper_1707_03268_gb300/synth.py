@@ -191,6 +191,30 @@ def make_dpm_class(rng: np.random.Generator, kind: str = "dpm", **filter_kw) -> 
 
 
 # --------------------------------------------------------------------------------------------------------------------
+# planted object instances (positive examples for the thresholds of Sec. 4)
+# --------------------------------------------------------------------------------------------------------------------
+def plant_objects(rng: np.random.Generator, pyramid: Pyramid, model: Model,
+                  placements: Sequence[Tuple[int, int, int, int]], strength: float = 1.0,
+                  noise: float = 0.02) -> Pyramid:
+    """A copy of ``pyramid`` with an object instance at each placement (component, root level j, y, x): the root
+    window at (y, x) on level j and every part window at its anchor (2y + vy, 2x + vx) on level j - lam are set to
+    0.1 + 0.1 * strength * f / max|f| plus N(0, noise) per entry, clipped to [0, 0.2] (features that line up with
+    the filter f). Placements must be valid root positions (the root and every anchored part inside their levels)."""
+    levels = [l.copy() for l in pyramid.levels]
+    for (c, j, y, x) in placements:
+        comp = model.components[c]
+        wins = [(j, y, x, comp.root)] + [(j - pyramid.lam, 2 * y + p.anchor[0], 2 * x + p.anchor[1], p.filt)
+                                         for p in comp.parts]
+        for (lv, y0, x0, f) in wins:
+            h, w = f.shape[:2]
+            L = levels[lv]
+            assert 0 <= y0 and 0 <= x0 and y0 + h <= L.shape[0] and x0 + w <= L.shape[1], "placement out of range"
+            pat = 0.1 + 0.1 * strength * f / np.max(np.abs(f)) + rng.normal(0.0, noise, size=f.shape)
+            L[y0:y0 + h, x0:x0 + w, :] = np.clip(pat, 0.0, HOG_TRUNC).astype(np.float32)
+    return Pyramid(levels=levels, lam=pyramid.lam)
+
+
+# --------------------------------------------------------------------------------------------------------------------
 # strict-suite inputs: values exactly representable in FP32 so that every rounding order gives the same bits
 # --------------------------------------------------------------------------------------------------------------------
 def make_integer_map(rng: np.random.Generator, H: int, W: int, lo: int = -64, hi: int = 64) -> np.ndarray:

@@ -84,6 +84,11 @@ class DecompReport(ctypes.Structure):
                 ("max_rel_error", ctypes.c_double), ("mean_rel_error", ctypes.c_double), ("gain", ctypes.c_double)]
 
 
+class CascadeStats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int64), ("pruned", ctypes.c_int64), ("terms_evaluated", ctypes.c_int64),
+                ("terms_total", ctypes.c_int64)]
+
+
 DETECTION_DTYPE = np.dtype([("image", np.int32), ("model", np.int32), ("component", np.int32), ("level", np.int32),
                             ("y", np.int32), ("x", np.int32), ("score", np.float32), ("n_parts", np.int32),
                             ("part_y", np.int32, MAX_PARTS), ("part_x", np.int32, MAX_PARTS)])
@@ -138,6 +143,13 @@ SIGNATURES = {
     "tdpm_selftest_bounded_wait": (_c_i32, [_VP]),
     "tdpm_detect_nms": (_c_i32, [_VP, _c_i32, ctypes.c_float, _VP, ctypes.c_double, ctypes.c_double, _VP,
                                  ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _VP]),
+    "tdpm_cascade_partials": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _VP, ctypes.c_size_t, _VP,
+                                       _c_i32, _c_i32, _VP]),
+    "tdpm_cascade_thresholds": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _VP, ctypes.c_size_t, _VP,
+                                         _c_i32, _VP]),
+    "tdpm_detect_cascade": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _VP, _c_i32, ctypes.c_float,
+                                     _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(CascadeStats), _VP]),
     "tdpm_profile_read": (_c_i32, [_VP, _c_i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_i32)]),
     "tdpm_profile_reset": (_c_i32, [_VP]),
@@ -346,6 +358,62 @@ def tdpm_detect_nms(ctx: int, scores_id: int, tau: float, component_class: Optio
                                  float(cell0), out.ctypes.data if capacity else None, int(capacity), ctypes.byref(n),
                                  _stream_ptr(stream)))
     return out[: n.value]
+
+
+def _pyr_array(pyramids: Sequence[DevicePyramid]):
+    return (PyramidDesc * len(pyramids))(*[p.desc for p in pyramids])
+
+
+def cascade_terms_bound(ctx: int, model_id: int) -> int:
+    """An upper bound on any filter's number of CP terms: per shape group min(the group's terms, h * w)."""
+    _, ng = tdpm_model_info(ctx, model_id)
+    return max(min(g["rank"], g["h"] * g["w"]) for g in (tdpm_group_info(ctx, model_id, i) for i in range(ng)))
+
+
+def _records(recs: np.ndarray) -> np.ndarray:
+    recs = np.ascontiguousarray(recs)
+    assert recs.dtype == DETECTION_DTYPE
+    return recs
+
+
+def tdpm_cascade_partials(ctx: int, scores_id: int, pyramids: Sequence[DevicePyramid], records: np.ndarray,
+                          model_id: int, stream=None) -> np.ndarray:
+    """Partial sums [n][1 + MAX_PARTS][T] of every filter of each record's component (slot 0 root, 1 + p part p), T =
+    cascade_terms_bound; NaN where a filter has fewer terms or slots."""
+    recs = _records(records)
+    T = cascade_terms_bound(ctx, model_id)
+    out = np.empty((max(len(recs), 1), 1 + MAX_PARTS, T), np.float32)
+    _check(lib().tdpm_cascade_partials(ctx, scores_id, _pyr_array(pyramids), len(pyramids), recs.ctypes.data,
+                                       len(recs), out.ctypes.data, 1 + MAX_PARTS, T, _stream_ptr(stream)))
+    return out[: len(recs)]
+
+
+def tdpm_cascade_thresholds(ctx: int, scores_id: int, pyramids: Sequence[DevicePyramid], positives: np.ndarray,
+                            model_id: int, stream=None) -> np.ndarray:
+    """Sec. 4 thresholds [n_filters][T] from positive records (-inf for filters without positives and beyond a
+    filter's rank)."""
+    recs = _records(positives)
+    T = cascade_terms_bound(ctx, model_id)
+    nf, _ = tdpm_model_info(ctx, model_id)
+    t = np.empty((nf, T), np.float32)
+    _check(lib().tdpm_cascade_thresholds(ctx, scores_id, _pyr_array(pyramids), len(pyramids), recs.ctypes.data,
+                                         len(recs), t.ctypes.data, T, _stream_ptr(stream)))
+    return t
+
+
+def tdpm_detect_cascade(ctx: int, scores_id: int, pyramids: Sequence[DevicePyramid], thresholds: np.ndarray,
+                        tau: float, capacity: int = 1 << 20, stream=None,
+                        out: Optional[np.ndarray] = None) -> Tuple[np.ndarray, dict]:
+    """Detections with score >= tau that the convolution-shortening cascade keeps, and its pruning counts."""
+    t = np.ascontiguousarray(thresholds, dtype=np.float32)
+    if out is None or out.shape[0] < capacity:
+        out = np.zeros(capacity, dtype=DETECTION_DTYPE)
+    n = ctypes.c_size_t()
+    st = CascadeStats()
+    _check(lib().tdpm_detect_cascade(ctx, scores_id, _pyr_array(pyramids), len(pyramids), t.ctypes.data,
+                                     int(t.shape[1]), float(tau), out.ctypes.data if capacity else None,
+                                     int(capacity), ctypes.byref(n), ctypes.byref(st), _stream_ptr(stream)))
+    return out[: n.value], {f: getattr(st, f) for f, _ in CascadeStats._fields_}
 
 
 def tdpm_build_batch_scores_subset(ctx: int, model_id: int, pyramids: Sequence[DevicePyramid],

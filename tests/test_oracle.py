@@ -407,3 +407,73 @@ def test_nms_keeps_the_best_of_overlapping_boxes():
     # ties: the earlier record wins
     dets3 = [(0, 0, 0, 0, 0, 1.0), (0, 0, 0, 0, 0, 1.0)]
     assert orc.nms(dets3, root_hw, cell0=1.0, lam=10) == [0]
+
+
+# ---------------------------------------------------------------------------------------------------------------------
+# convolution shortening (Sec. 4 thresholds, Algorithm 1)
+# ---------------------------------------------------------------------------------------------------------------------
+def _cascade_workload(seed=31, R=3):
+    model, pyr = _tiny_workload(seed)
+    factors = []
+    for f in model.filters():
+        w, (A, B, C), _ = orc.cp_als(f.astype(np.float64), R, max_iters=60, seed=1)
+        factors.append((w, A, B, C))
+    comp = model.components[0]
+    Y, X = orc.root_domain(pyr.sizes[1], pyr.sizes[0], comp.root.shape[:2],
+                           [(p.filt.shape[:2], p.anchor) for p in comp.parts])
+    recs = [(0, 1, y, x) for y in range(Y) for x in range(X)]
+    return model, pyr, factors, recs
+
+
+def test_cascade_partials_end_at_the_decomposed_filter_response():
+    """Linearity (Sec. 4): the last partial sum of each slot is the response of the filter rebuilt from its factors, at
+    the root position for the root and at the anchor for each part (direct correlation, another code path)."""
+    model, pyr, factors, recs = _cascade_workload()
+    comp = model.components[0]
+    rebuilt = [orc.cp_reconstruct(w, [A, B, C]) for (w, A, B, C) in factors]
+    root_map = orc.correlate(pyr.levels[1], rebuilt[0])
+    part_maps = [orc.correlate(pyr.levels[0], rebuilt[1 + i]) for i in range(len(comp.parts))]
+    for (c, j, y, x) in recs:
+        P = orc.cascade_partials(model, pyr, factors, (c, j, y, x))
+        assert len(P) == 1 + len(comp.parts) and all(len(p) == 3 for p in P)
+        assert P[0][-1] == pytest.approx(root_map[y, x], rel=1e-12, abs=1e-12)
+        for i, p in enumerate(comp.parts):
+            assert P[1 + i][-1] == pytest.approx(part_maps[i][2 * y + p.anchor[0], 2 * x + p.anchor[1]],
+                                                 rel=1e-12, abs=1e-12)
+
+
+def test_cascade_adds_the_heaviest_term_first():
+    """The first partial sum is the term of largest |lambda| alone, evaluated as three 1-D correlations."""
+    model, pyr, factors, recs = _cascade_workload()
+    w, A, B, C = factors[0]
+    r = int(np.argmax(np.abs(w)))
+    assert orc.cascade_order(w)[0] == r
+    one = w[r] * orc.correlate_rank1(pyr.levels[1], A[:, r], B[:, r], C[:, r])
+    for (c, j, y, x) in recs[:7]:
+        assert orc.cascade_partials(model, pyr, factors, (c, j, y, x))[0][0] == pytest.approx(one[y, x], rel=1e-12,
+                                                                                              abs=1e-12)
+    assert orc.cascade_order(np.array([0.5, -2.0, 2.0, 1.0])) == [1, 2, 3, 0]  # ties by index
+
+
+def test_cascade_thresholds_are_the_tightest_that_keep_every_positive():
+    """Sec. 4: with thresholds from a set of positives no positive is pruned, and raising any single threshold above
+    its value prunes at least one of them; with no thresholds the cascade keeps every detection."""
+    model, pyr, factors, recs = _cascade_workload()
+    rng = np.random.default_rng(5)
+    pos = [recs[i] for i in rng.choice(len(recs), size=6, replace=False)]
+    t = orc.cascade_thresholds(model, lambda img: pyr, factors, [(0,) + p for p in pos])
+    assert sorted(t) == [0, 1, 2]
+    for p in pos:
+        assert orc.cascade_walk(model, pyr, factors, t, p) == (False, 9)
+    for fid, tf in t.items():
+        for q in range(len(tf)):
+            t2 = {k: v.copy() for k, v in t.items()}
+            t2[fid][q] = np.nextafter(tf[q], np.inf)
+            assert any(orc.cascade_walk(model, pyr, factors, t2, p)[0] for p in pos)
+    dets = orc.detect(orc.score_pyramid(model, pyr), -np.inf)
+    assert orc.cascade_detect(model, pyr, factors, {}, dets) == list(range(len(dets)))
+    # the walk stops at the first partial sum below its threshold and counts the terms it evaluated
+    big = {0: np.array([np.inf, np.inf, np.inf])}
+    assert orc.cascade_walk(model, pyr, factors, big, recs[0]) == (True, 1)
+    part = {2: np.array([-np.inf, np.inf, np.inf])}
+    assert orc.cascade_walk(model, pyr, factors, part, recs[0]) == (True, 3 + 3 + 2)
