@@ -615,6 +615,85 @@ def run_serve(args):
 
 
 # ------------------------------------------------------------------------------------------------ main arm
+def _host_ms(fn, reps=20):
+    fn()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    return (time.perf_counter() - t0) * 1e3 / reps
+
+
+def nms_measure(tdpm, ctx, mid, dp, form, prec, tau, stream):
+    """Greedy NMS of the headline detections, with every component in one class and with one class per component."""
+    sid = tdpm.tdpm_build_pyramid_scores(ctx, mid, dp, form, prec, stream)
+    dets = tdpm.tdpm_detect(ctx, sid, tau, stream=stream)
+    out = {"detections": len(dets)}
+    for name, cls in (("one_class", None), ("per_component", list(range(6)))):
+        kept = tdpm.tdpm_detect_nms(ctx, sid, tau, cls, 0.5, 4.0, stream=stream)
+        out[name] = {"kept": len(kept), "ms_per_call_host": _host_ms(
+            lambda: tdpm.tdpm_detect_nms(ctx, sid, tau, cls, 0.5, 4.0, stream=stream))}
+    out["detect_ms_per_call_host"] = _host_ms(lambda: tdpm.tdpm_detect(ctx, sid, tau, stream=stream))
+    tdpm.tdpm_release(ctx, sid)
+    return out
+
+
+def cascade_measure(torch, tdpm, ctx, mid, wl, form, prec, tau, stream, n_train=4, per_comp=5):
+    """Thresholds of Sec. 4 from planted positives on n_train training images of the workload's size (per_comp
+    instances of every component each), then the cascade on the workload image with two planted instances per
+    component: pruned share of all root hypotheses, CP terms evaluated, recall of the planted instances, and the
+    detections kept at the headline threshold."""
+    pyr = wl.pyramids[0]
+    rng = np.random.default_rng(11)
+
+    def dev(p):
+        return tdpm.DevicePyramid([torch.from_numpy(np.ascontiguousarray(l)).cuda() for l in p.levels], p.lam)
+
+    def places(base, k):
+        sid = tdpm.tdpm_build_pyramid_scores(ctx, mid, dev(base), form, prec, stream)
+        allr = tdpm.tdpm_detect(ctx, sid, -np.inf, stream=stream)
+        tdpm.tdpm_release(ctx, sid)
+        out = []
+        for c in range(len(wl.model.components)):
+            idx = np.nonzero(allr["component"] == c)[0]
+            for i in sorted(rng.choice(idx, size=k, replace=False)):
+                out.append((c, int(allr["level"][i]), int(allr["y"][i]), int(allr["x"][i])))
+        return out
+
+    def records(pl):
+        r = np.zeros(len(pl), dtype=tdpm.DETECTION_DTYPE)
+        for i, (im, c, j, y, x) in enumerate(pl):
+            r[i]["image"], r[i]["component"], r[i]["level"], r[i]["y"], r[i]["x"] = im, c, j, y, x
+        return r
+
+    train, pos = [], []
+    for im in range(n_train):
+        base = synth.make_pyramid(rng, pyr.sizes, pyr.lam)
+        pl = places(base, per_comp)
+        train.append(dev(synth.plant_objects(rng, base, wl.model, pl)))
+        pos += [(im,) + p for p in pl]
+    s_train = tdpm.tdpm_build_batch_scores(ctx, mid, train, form, prec, stream)
+    t = tdpm.tdpm_cascade_thresholds(ctx, s_train, train, records(pos), mid, stream)
+    tdpm.tdpm_release(ctx, s_train)
+    pl_test = places(pyr, 2)
+    d_test = dev(synth.plant_objects(rng, pyr, wl.model, pl_test))
+    s_test = tdpm.tdpm_build_pyramid_scores(ctx, mid, d_test, form, prec, stream)
+    kept, st = tdpm.tdpm_detect_cascade(ctx, s_test, [d_test], t, -np.inf, stream=stream)
+    kkeys = set(zip(kept["component"].tolist(), kept["level"].tolist(), kept["y"].tolist(), kept["x"].tolist()))
+    dense = tdpm.tdpm_detect(ctx, s_test, tau, stream=stream)
+    kept_tau, _ = tdpm.tdpm_detect_cascade(ctx, s_test, [d_test], t, tau, stream=stream)
+    out = {"positives": len(pos), "training_images": n_train, "hypotheses": st["candidates"],
+           "pruned_fraction": st["pruned"] / max(1, st["candidates"]),
+           "terms_evaluated_fraction": st["terms_evaluated"] / max(1, st["terms_total"]),
+           "recall_planted": sum(1 for p in pl_test if p in kkeys) / len(pl_test),
+           "dense_detections_at_tau": len(dense), "cascade_detections_at_tau": len(kept_tau),
+           "ms_per_call_host_all_hypotheses": _host_ms(
+               lambda: tdpm.tdpm_detect_cascade(ctx, s_test, [d_test], t, -np.inf, stream=stream), 10),
+           "detect_ms_per_call_host_all_hypotheses": _host_ms(
+               lambda: tdpm.tdpm_detect(ctx, s_test, -np.inf, stream=stream), 10)}
+    tdpm.tdpm_release(ctx, s_test)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -827,6 +906,13 @@ def main():
                              "agreement_with_full_fp32": len(a & full_keys) / max(1, len(a | full_keys)),
                              "images_per_s": rate(run), "decompose_seconds": secs}
 
+    # ---- post-processing: NMS (f4) and convolution shortening (Sec. 4 / Algorithm 1, f1)
+    post = None
+    if form == tdpm.FORM_DECOMPOSED and args.mode == "per_filter" and not args.no_sweep and rank == 0:
+        tdpm.tdpm_decompose(ctx, mid, args.rank, dmode, max_iters=500, seed=1)  # the headline factors again
+        post = {"nms": nms_measure(tdpm, ctx, mid, dp, form, prec, tau, stream),
+                "cascade": cascade_measure(torch, tdpm, ctx, mid, wl, form, prec, tau, stream)}
+
     line = {"metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main_run["total_ms"] / args.steps, "p50_ms": p50, "p99_ms": p99,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -848,6 +934,7 @@ def main():
             "stages_ms_per_image": {k: v[0] / n_prof for k, v in stages.items()},
             "roofline": roofline, "rooflines": rooflines, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
             "compare": compare, "decomposition_report": rep, "rank_sweep": sweep, "auto_rank_sweep": auto_sweep,
+            "post_processing": post,
             "autotune": tdpm.tdpm_autotune_read(ctx),
             "wall_s_timed": main_run["wall_s"]}
     if rank == 0:
