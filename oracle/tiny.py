@@ -70,3 +70,43 @@ def hypothesis_score(root_level, part_level, root, parts, bias: float, y0: int, 
     for (filt, (vy, vx), d), (py, px) in zip(parts, positions):
         s += dot_at(part_level, filt, py, px) - deform_cost(d, px - (2 * x0 + vx), py - (2 * y0 + vy))
     return s
+
+
+def hog_features(obin, mag, sbin):
+    """Brute force of the HOG cell votes and features from per-pixel bins and magnitudes (nested lists): every
+    visible pixel votes bilinearly into its four cells, then each interior cell is normalised by its four 2x2 blocks
+    (E = sum of squared contrast-insensitive sums, N = 1 / sqrt(block E + 1e-4)), truncated at 0.2 and projected to
+    18 + 9 + 4 channels plus a zero channel."""
+    import math
+    h, w = len(mag), len(mag[0])
+    cy, cx = int(round(h / sbin)), int(round(w / sbin))
+    hist = [[[0.0] * 18 for _ in range(cx)] for _ in range(cy)]
+    for y in range(1, cy * sbin - 1):
+        for x in range(1, cx * sbin - 1):
+            yy, xx = min(y, h - 2), min(x, w - 2)
+            yp, xp = (y + 0.5) / sbin - 0.5, (x + 0.5) / sbin - 0.5
+            iy, ix = math.floor(yp), math.floor(xp)
+            for ty, wy in ((iy, 1.0 - (yp - iy)), (iy + 1, yp - iy)):
+                for tx, wx in ((ix, 1.0 - (xp - ix)), (ix + 1, xp - ix)):
+                    if 0 <= ty < cy and 0 <= tx < cx:
+                        hist[ty][tx][obin[yy][xx]] += wy * wx * mag[yy][xx]
+    E = [[sum((hist[a][b][o] + hist[a][b][o + 9]) ** 2 for o in range(9)) for b in range(cx)] for a in range(cy)]
+    out = []
+    for y in range(1, cy - 1):
+        row = []
+        for x in range(1, cx - 1):
+            norms = []
+            for a0, b0 in ((y, x), (y, x - 1), (y - 1, x), (y - 1, x - 1)):
+                s = E[a0][b0] + E[a0][b0 + 1] + E[a0 + 1][b0] + E[a0 + 1][b0 + 1]
+                norms.append(1.0 / math.sqrt(s + 1e-4))
+            hc = hist[y][x]
+            f = [0.0] * 32
+            for o in range(18):
+                f[o] = 0.5 * sum(min(hc[o] * n, 0.2) for n in norms)
+            for o in range(9):
+                f[18 + o] = 0.5 * sum(min((hc[o] + hc[o + 9]) * n, 0.2) for n in norms)
+            for k, n in enumerate(norms):
+                f[27 + k] = sum(min(hc[o] * n, 0.2) for o in range(18)) / math.sqrt(18.0)
+            row.append(f)
+        out.append(row)
+    return out

@@ -477,3 +477,97 @@ def test_cascade_thresholds_are_the_tightest_that_keep_every_positive():
     assert orc.cascade_walk(model, pyr, factors, big, recs[0]) == (True, 1)
     part = {2: np.array([-np.inf, np.inf, np.inf])}
     assert orc.cascade_walk(model, pyr, factors, part, recs[0]) == (True, 3 + 3 + 2)
+
+
+# ---------------------------------------------------------------------------------------------------------------------
+# feature extraction block: area-averaging resize and 32-channel HOG
+# ---------------------------------------------------------------------------------------------------------------------
+from oracle import hog as ohog  # noqa: E402
+
+
+def test_resize_identity_halving_and_mass():
+    rng = np.random.default_rng(3)
+    img = rng.uniform(0, 255, size=(12, 18, 3))
+    assert np.array_equal(ohog.resize(img, 1.0), img)
+    half = ohog.resize(img, 0.5)
+    np.testing.assert_allclose(half, 0.25 * (img[0::2, 0::2] + img[1::2, 0::2] + img[0::2, 1::2] + img[1::2, 1::2]),
+                               rtol=1e-13)
+    const = np.full((17, 23, 3), 7.25)
+    np.testing.assert_allclose(ohog.resize(const, 2 ** -0.3), 7.25, rtol=1e-13)
+    # 20 -> 16 pixels at s = 0.8: the output intervals tile the input, so the mass scales by 1 / s exactly
+    row = rng.uniform(0, 1, size=(1, 20, 1))
+    out = ohog.resize(np.repeat(row, 5, axis=0), 0.8)
+    assert out.shape == (4, 16, 1)
+    assert out[0, :, 0].sum() / 0.8 == pytest.approx(row.sum(), rel=1e-13)
+    # odd length halved: the last output pixel is the mean of the one input pixel its interval still covers
+    odd = rng.uniform(0, 1, size=(2, 5, 1))
+    assert ohog.resize(odd, 0.5)[0, 2, 0] == pytest.approx(0.5 * (odd[0, 4, 0] + odd[1, 4, 0]), rel=1e-13)
+
+
+def _ramp(h, w, a, b, boost=1):
+    """I = a x + b y in every channel, channel `boost` three times as steep."""
+    y, x = np.mgrid[0:h, 0:w].astype(np.float64)
+    img = np.stack([a * x + b * y] * 3, axis=2)
+    img[..., boost] = 3 * (a * x + b * y)
+    return img.astype(np.float32)
+
+
+@pytest.mark.parametrize("deg", [0.0, 13.0, 47.0, 95.0, 171.0, 200.0, 333.0])
+def test_hog_orientation_bin_of_a_ramp(deg):
+    """A ramp has one gradient (2a, 2b) (times 3 in the steepest channel, which wins) everywhere: every interior pixel
+    votes into the bin whose direction o * 20 degrees is nearest to the gradient's angle modulo 180, plus 9 when the
+    gradient points against it."""
+    th = math.radians(deg)
+    obin, mag = ohog.gradients(_ramp(12, 14, math.cos(th), math.sin(th)))
+    o_near = int(round(deg / 20.0)) % 18
+    want = o_near if o_near < 9 else o_near
+    assert np.all(obin[1:-1, 1:-1] == want)
+    assert np.allclose(mag[1:-1, 1:-1], 6.0, rtol=1e-5)   # |3 * (2 cos, 2 sin)| (FP32 image)
+    assert np.all(mag[0] == 0) and np.all(mag[:, -1] == 0)
+
+
+@pytest.mark.parametrize("slope,clipped", [(1.0, True), (3e-6, False)])
+def test_hog_features_of_a_ramp_closed_form(slope, clipped):
+    """Uniform gradient magnitude m in one bin o: every cell whose votes are complete holds h = sbin^2 m; a cell
+    surrounded by such cells has four blocks of energy 4 h^2, so each normalised value is h / sqrt(4 h^2 + 1e-4),
+    0.2 once truncated. Channel o and the contrast-insensitive channel o mod 9 are 0.5 * 4 * that value, the four
+    texture channels that value / sqrt(18), all others 0."""
+    sbin = 8
+    img = _ramp(8 * 9, 8 * 8, slope * math.cos(math.radians(40)), slope * math.sin(math.radians(40)))
+    f = ohog.hog(img, sbin)
+    assert f.shape == (7, 6, 32)
+    m = 3 * 2 * slope
+    h = sbin * sbin * m
+    v = h / math.sqrt(4 * h * h + 1e-4)
+    assert (v > 0.2) == clipped
+    v = min(v, 0.2)
+    want = np.zeros(32)
+    want[2] = want[18 + 2] = 2.0 * v
+    want[27:31] = v / math.sqrt(18.0)
+    for y in range(1, f.shape[0] - 1):
+        for x in range(1, f.shape[1] - 1):
+            np.testing.assert_allclose(f[y, x], want, rtol=2e-5, atol=1e-12)
+
+
+def test_hog_equals_brute_force_on_a_small_image():
+    rng = np.random.default_rng(8)
+    img = rng.integers(0, 256, size=(21, 27, 3)).astype(np.float32)
+    obin, mag = ohog.gradients(img)
+    for sbin in (4, 8):
+        got = ohog.hog(img, sbin)
+        want = np.array(tiny.hog_features(obin.tolist(), mag.tolist(), sbin))
+        assert got.shape == want.shape
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-14)
+
+
+def test_hog_pyramid_levels():
+    rng = np.random.default_rng(9)
+    img = rng.integers(0, 256, size=(96, 128, 3)).astype(np.float32)
+    lv = ohog.hog_pyramid(img, sbin=8, lam=3, min_cells=4)
+    np.testing.assert_allclose(lv[0], ohog.hog(img, 4), rtol=1e-12)         # 2x octave, scale 1
+    np.testing.assert_allclose(lv[3], ohog.hog(img, 8), rtol=1e-12)         # first root level, scale 1
+    np.testing.assert_allclose(lv[4], ohog.hog(ohog.resize(img, 2 ** (-1 / 3)), 8), rtol=1e-12)
+    np.testing.assert_allclose(lv[6], ohog.hog(ohog.resize(img, 0.5), 8), rtol=1e-12)
+    assert all(min(l.shape[:2]) >= 4 for l in lv[3:])
+    for j in range(3):   # every part level is at least twice its root level
+        assert lv[j].shape[0] >= 2 * lv[3 + j].shape[0] and lv[j].shape[1] >= 2 * lv[3 + j].shape[1]
