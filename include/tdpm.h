@@ -234,6 +234,42 @@ tdpm_status tdpm_detect_nms(tdpm_ctx *ctx, int32_t scores_id, float tau, const i
                             double overlap, double cell0, tdpm_detection *out, size_t capacity, size_t *n_out,
                             void *stream);
 
+/* ---------------------------------------------------------------- feature extraction block (Sec. 2): HOG pyramid */
+/* The paper scores DPM v5's HOG features and notes that extracting them costs about a twentieth of the scoring
+ * (Sec. 2). The library computes them on the device in that form (Felzenszwalb et al., PAMI 2010, Sec. 6), 32
+ * channels per cell: per pixel the colour channel with the largest squared central-difference gradient and the nearest
+ * of 18 oriented directions (both decided in FP32, products and sums rounded once), bilinear votes of the magnitude
+ * into cells of sbin pixels (floor(n / sbin + 1/2) cells per side), four 2x2-block normalisations per cell
+ * (1 / sqrt(block energy + 1e-4)), truncation at 0.2, and the projection to 18 contrast-sensitive, 9 -insensitive and
+ * 4 texture channels plus a zero channel; the outermost ring of cells is dropped. The pyramid resamples the image by
+ * area averaging at the lambda scales 2^(-i / lambda), then halves each octave into the next; levels 0..lambda-1 are
+ * the first octave at sbin / 2 (the part levels), then the root levels at sbin while both sides keep at least
+ * min_cells cells. */
+
+/* Level count, level sizes (level_hw[2 j], level_hw[2 j + 1] = rows, columns; may be NULL) and the bytes of the FP32
+ * NHWC output of an img_h x img_w image. sbin 4, 8 or 16; lambda 1..64. ERR_ARG for an image too small for one root
+ * level; ERR_CAPACITY when level_hw is given and max_levels is below the level count. */
+tdpm_status tdpm_hog_pyramid_shape(int32_t img_h, int32_t img_w, int32_t sbin, int32_t lambda, int32_t min_cells,
+                                   int32_t *n_levels, int32_t *level_hw, int32_t max_levels, size_t *out_bytes);
+
+/* The feature pyramid of a device 8-bit RGB image [img_h][img_w][3] into d_out (device, 16-byte aligned, at least
+ * the bytes tdpm_hog_pyramid_shape gives; caller-owned): levels[j] (host array of max_levels) receives each level's
+ * rows, columns and device pointer inside d_out, ready for tdpm_build_pyramid_scores. Asynchronous on `stream`; the
+ * context's scratch is reused by its next HOG call (ordered by an event). */
+tdpm_status tdpm_hog_pyramid(tdpm_ctx *ctx, const uint8_t *d_image, int32_t img_h, int32_t img_w, int32_t sbin,
+                             int32_t lambda, int32_t min_cells, float *d_out, size_t out_bytes, tdpm_level *levels,
+                             int32_t max_levels, int32_t *n_levels, void *stream);
+
+/* The features of one device FP32 RGB image [h][w][3] at cell size sbin (2, 4, 8 or 16) into d_out ([*out_h][*out_w]
+ * [32], 16-byte aligned). Synchronous. */
+tdpm_status tdpm_hog_features(tdpm_ctx *ctx, const float *d_img, int32_t h, int32_t w, int32_t sbin, float *d_out,
+                              size_t out_bytes, int32_t *out_h, int32_t *out_w, void *stream);
+
+/* Area-averaging resample of a device FP32 image [h][w][3] by scale in (0, 1] into d_dst ([*out_h][*out_w][3],
+ * floor(n scale + 1/2) per side). Asynchronous on `stream`. */
+tdpm_status tdpm_resize(tdpm_ctx *ctx, const float *d_src, int32_t h, int32_t w, double scale, float *d_dst,
+                        size_t dst_bytes, int32_t *out_h, int32_t *out_w, void *stream);
+
 /* ---------------------------------------------------------------- convolution shortening (Sec. 4, Algorithm 1) */
 /* A root hypothesis (a record's component, level, y, x) is pruned as soon as, for some filter of its component, the
  * partial sum of the filter's first q CP terms at the hypothesis falls below the filter's threshold t_q. Filters are

@@ -18,7 +18,7 @@ written from that description. Steps and the readings taken where the descriptio
                    (no gradient) votes into bin 0 with weight 0. These two decisions are taken in FP32, the precision
                    of the kernel, with each product and sum rounded once: the gradient in FP32 from the FP32 image,
                    the projections as fl(fl(u_x dx) + fl(u_y dy)) with u rounded to FP32.
-* ``cells``        c = round(n / sbin) cells per dimension; pixel x of the visible region 1 <= x <= c sbin - 2 reads
+* ``cells``        c = floor(n / sbin + 1/2) cells per dimension; pixel x of the visible region 1 <= x <= c sbin - 2 reads
                    the image at min(x, w - 2) (the last interior column repeats); its magnitude sqrt(dx^2 + dy^2)
                    votes bilinearly into the cells around xp = (x + 0.5) / sbin - 0.5 (and likewise in y).
 * ``features``     per interior cell (the outermost ring of cells is dropped: (cy - 2) x (cx - 2) cells), with
@@ -67,7 +67,8 @@ def resize(img: np.ndarray, s: float) -> np.ndarray:
     H, W = img.shape[:2]
     Ho, Wo = resized_size(H, s), resized_size(W, s)
     Wy, Wx = _weights(H, Ho, s), _weights(W, Wo, s)
-    return np.einsum("yi,ijc,xj->yxc", Wy, img.astype(np.float64), Wx)
+    rows = np.einsum("yi,ijc->yjc", Wy, img.astype(np.float64))     # along columns, then along rows
+    return np.einsum("yjc,xj->yxc", rows, Wx)
 
 
 def _orient_table() -> Tuple[np.ndarray, np.ndarray]:
@@ -110,7 +111,7 @@ def gradients(img: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
 def cell_histograms(obin: np.ndarray, mag: np.ndarray, sbin: int) -> np.ndarray:
     """Bilinear votes of the visible pixels into [cy][cx][18] cells (FP64; votes added in pixel order)."""
     h, w = mag.shape
-    cy, cx = int(round(h / sbin)), int(round(w / sbin))
+    cy, cx = (2 * h + sbin) // (2 * sbin), (2 * w + sbin) // (2 * sbin)   # floor(n / sbin + 1/2)
     hist = np.zeros((cy, cx, 2 * N_ORIENT), np.float64)
     ys = np.arange(1, cy * sbin - 1)
     xs = np.arange(1, cx * sbin - 1)

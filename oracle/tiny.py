@@ -79,7 +79,7 @@ def hog_features(obin, mag, sbin):
     18 + 9 + 4 channels plus a zero channel."""
     import math
     h, w = len(mag), len(mag[0])
-    cy, cx = int(round(h / sbin)), int(round(w / sbin))
+    cy, cx = (2 * h + sbin) // (2 * sbin), (2 * w + sbin) // (2 * sbin)   # floor(n / sbin + 1/2)
     hist = [[[0.0] * 18 for _ in range(cx)] for _ in range(cy)]
     for y in range(1, cy * sbin - 1):
         for x in range(1, cx * sbin - 1):

@@ -157,6 +157,9 @@ struct tdpm_ctx {
     std::unordered_map<uint64_t, size_t> det_last;  // plan uid -> detections of its last read-back (copy size hint)
     void *d_nms = nullptr;               // grow-only scratch of tdpm_detect_nms
     size_t nms_cap = 0;
+    void *d_hog = nullptr;               // grow-only scratch of the HOG pyramid calls (images, gradients, cells, tables)
+    size_t hog_cap = 0;
+    cudaEvent_t hog_done = nullptr;      // recorded after each HOG call's work; the next one waits before reusing d_hog
     bool use_graphs = true;
     bool fuse = true;                    // fused channel stage + separable passes where possible (tdpm_set_fusion)
     int zsep_form = -1;                  // fused kernel form forced by TDPM_ZSEP_FORM (-1: default / tuned)

@@ -264,6 +264,39 @@ struct CascArgs {
 };
 cudaError_t launch_cascade(const CascArgs &args, cudaStream_t s);
 
+// Feature extraction block: HOG pyramid (hog.cu).
+struct HogTap {
+    int i0, n, w;  // first input index, number of taps, offset of their weights in the weight table
+};
+struct HogResizeJob {
+    const void *src;  // [h][w][3], uint8 (octave 0) or FP32
+    int h, w;
+    float *dst;       // [ho][wo][3] FP32
+    int ho, wo;
+    const HogTap *ytaps, *xtaps;  // one per output row / column
+    const float *weights;
+};
+struct HogImage {
+    const float *img;  // [h][w][3]
+    int h, w;
+    float *mag;        // [h][w] gradient magnitude (0 on the border ring)
+    uint8_t *bin;      // [h][w] orientation bin 0..17
+};
+struct HogLevelJob {
+    const float *mag;
+    const uint8_t *bin;
+    int h, w;          // the image the level is computed from
+    int sbin, cy, cx;  // cell size and cells per column / row (including the border ring)
+    float *hist;       // [cy][cx][18] scratch
+    float *out;        // [cy - 2][cx - 2][32] FP32 features
+};
+cudaError_t hog_set_orientations(const float *ux, const float *uy);
+cudaError_t launch_hog_resize(const HogResizeJob *d_jobs, int n_jobs, long long max_pixels, bool from_u8,
+                              cudaStream_t s);
+cudaError_t launch_hog_grad(const HogImage *d_imgs, int n_imgs, long long max_pixels, cudaStream_t s);
+cudaError_t launch_hog_levels(const HogLevelJob *d_jobs, int n_jobs, long long max_cells, long long max_out_cells,
+                              cudaStream_t s);
+
 // Ordered compaction: the records whose flag is nonzero go to d_out in record order, their number to *d_n_out.
 // d_scratch: at least compact_scratch_bytes(n) bytes.
 size_t compact_scratch_bytes(long long n);

@@ -277,6 +277,8 @@ void tdpm_destroy(tdpm_ctx *ctx)
         cudaStreamDestroy(ctx->cap_stream);
         if (ctx->d_records) cudaFree(ctx->d_records);
         if (ctx->d_nms) cudaFree(ctx->d_nms);
+        if (ctx->d_hog) cudaFree(ctx->d_hog);
+        if (ctx->hog_done) cudaEventDestroy(ctx->hog_done);
         if (ctx->d_job_tau) cudaFree(ctx->d_job_tau);
         for (cudaStream_t st : ctx->side) cudaStreamDestroy(st);
         for (cudaEvent_t ev : ctx->join_ev) cudaEventDestroy(ev);

@@ -150,6 +150,14 @@ SIGNATURES = {
     "tdpm_detect_cascade": (_c_i32, [_VP, _c_i32, ctypes.POINTER(PyramidDesc), _c_i32, _VP, _c_i32, ctypes.c_float,
                                      _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(CascadeStats), _VP]),
+    "tdpm_hog_pyramid_shape": (_c_i32, [_c_i32, _c_i32, _c_i32, _c_i32, _c_i32, ctypes.POINTER(_c_i32), _VP, _c_i32,
+                                        ctypes.POINTER(ctypes.c_size_t)]),
+    "tdpm_hog_pyramid": (_c_i32, [_VP, _VP, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _VP, ctypes.c_size_t,
+                                  ctypes.POINTER(Level), _c_i32, ctypes.POINTER(_c_i32), _VP]),
+    "tdpm_hog_features": (_c_i32, [_VP, _VP, _c_i32, _c_i32, _c_i32, _VP, ctypes.c_size_t, ctypes.POINTER(_c_i32),
+                                   ctypes.POINTER(_c_i32), _VP]),
+    "tdpm_resize": (_c_i32, [_VP, _VP, _c_i32, _c_i32, ctypes.c_double, _VP, ctypes.c_size_t, ctypes.POINTER(_c_i32),
+                             ctypes.POINTER(_c_i32), _VP]),
     "tdpm_profile_read": (_c_i32, [_VP, _c_i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_c_i32)]),
     "tdpm_profile_reset": (_c_i32, [_VP]),
@@ -414,6 +422,71 @@ def tdpm_detect_cascade(ctx: int, scores_id: int, pyramids: Sequence[DevicePyram
                                      int(t.shape[1]), float(tau), out.ctypes.data if capacity else None,
                                      int(capacity), ctypes.byref(n), ctypes.byref(st), _stream_ptr(stream)))
     return out[: n.value], {f: getattr(st, f) for f, _ in CascadeStats._fields_}
+
+
+def tdpm_hog_pyramid_shape(img_h: int, img_w: int, sbin: int = 8, lam: int = 10,
+                           min_cells: int = 8) -> Tuple[List[Tuple[int, int]], int]:
+    """Level sizes (rows, columns) and output bytes of the HOG pyramid of an img_h x img_w image."""
+    n = _c_i32()
+    b = ctypes.c_size_t()
+    _check(lib().tdpm_hog_pyramid_shape(img_h, img_w, sbin, lam, min_cells, ctypes.byref(n), None, 0, ctypes.byref(b)))
+    hw = (_c_i32 * (2 * n.value))()
+    _check(lib().tdpm_hog_pyramid_shape(img_h, img_w, sbin, lam, min_cells, ctypes.byref(n), hw, n.value,
+                                        ctypes.byref(b)))
+    return [(hw[2 * j], hw[2 * j + 1]) for j in range(n.value)], b.value
+
+
+def tdpm_hog_pyramid(ctx: int, image, sbin: int = 8, lam: int = 10, min_cells: int = 8, out=None,
+                     stream=None) -> "DevicePyramid":
+    """HOG feature pyramid of a CUDA uint8 tensor [H][W][3]; the levels are views of one flat FP32 CUDA tensor (`out`
+    when given, else a new one), returned as a DevicePyramid ready for scoring."""
+    import torch
+    assert image.is_cuda and image.dtype == torch.uint8 and image.dim() == 3 and image.shape[2] == 3
+    image = image.contiguous()
+    H, W = int(image.shape[0]), int(image.shape[1])
+    shapes, nbytes = tdpm_hog_pyramid_shape(H, W, sbin, lam, min_cells)
+    if out is None:
+        out = torch.empty(nbytes // 4, dtype=torch.float32, device=image.device)
+    arr = (Level * len(shapes))()
+    n = _c_i32()
+    _check(lib().tdpm_hog_pyramid(ctx, _ptr(image), H, W, sbin, lam, min_cells, _ptr(out), out.numel() * 4, arr,
+                                  len(shapes), ctypes.byref(n), _stream_ptr(stream)))
+    levels, off = [], 0
+    for (h, w) in shapes:
+        levels.append(out[off:off + h * w * FEAT_DIM].view(h, w, FEAT_DIM))
+        off += h * w * FEAT_DIM
+    pyr = DevicePyramid(levels, lam)
+    pyr.flat = out
+    return pyr
+
+
+def tdpm_hog_features(ctx: int, img, sbin: int, stream=None):
+    """32-channel features of one CUDA FP32 image [h][w][3] at cell size sbin (a CUDA tensor [h'][w'][32])."""
+    import torch
+    assert img.is_cuda and img.dtype == torch.float32 and img.dim() == 3 and img.shape[2] == 3
+    img = img.contiguous()
+    h, w = int(img.shape[0]), int(img.shape[1])
+    cy, cx = (2 * h + sbin) // (2 * sbin), (2 * w + sbin) // (2 * sbin)
+    out = torch.empty((max(cy - 2, 0), max(cx - 2, 0), FEAT_DIM), dtype=torch.float32, device=img.device)
+    oh, ow = _c_i32(), _c_i32()
+    _check(lib().tdpm_hog_features(ctx, _ptr(img), h, w, sbin, _ptr(out) if out.numel() else _ptr(img),
+                                   out.numel() * 4, ctypes.byref(oh), ctypes.byref(ow), _stream_ptr(stream)))
+    return out
+
+
+def tdpm_resize(ctx: int, img, scale: float, stream=None):
+    """Area-averaging resample of a CUDA FP32 image [h][w][3] by scale in (0, 1]."""
+    import math as _m
+    import torch
+    assert img.is_cuda and img.dtype == torch.float32 and img.dim() == 3 and img.shape[2] == 3
+    img = img.contiguous()
+    h, w = int(img.shape[0]), int(img.shape[1])
+    ho, wo = int(_m.floor(h * scale + 0.5)), int(_m.floor(w * scale + 0.5))
+    out = torch.empty((max(ho, 1), max(wo, 1), 3), dtype=torch.float32, device=img.device)
+    oh, ow = _c_i32(), _c_i32()
+    _check(lib().tdpm_resize(ctx, _ptr(img), h, w, float(scale), _ptr(out), out.numel() * 4, ctypes.byref(oh),
+                             ctypes.byref(ow), _stream_ptr(stream)))
+    return out[: oh.value, : ow.value]
 
 
 def tdpm_build_batch_scores_subset(ctx: int, model_id: int, pyramids: Sequence[DevicePyramid],
