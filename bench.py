@@ -637,6 +637,63 @@ def nms_measure(tdpm, ctx, mid, dp, form, prec, tau, stream):
     return out
 
 
+def hog_measure(torch, tdpm, ctx, mid, form, prec, stream, score_ms, peaks, h=375, w=500, steps=200):
+    """The feature extraction block on a 500x375 8-bit image: HOG pyramid time on the device (inputs resident, CUDA
+    events), its share of the scoring time (the paper puts scoring at about 20x extraction), and image -> detections
+    end to end (image H2D from pinned memory, HOG pyramid, scoring, detection read-back)."""
+    img = synth.make_image(np.random.default_rng(21), h, w)
+    host = torch.from_numpy(img).pin_memory()
+    d_img = host.cuda()
+    shapes, nbytes = tdpm.tdpm_hog_pyramid_shape(h, w)
+    out = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    pyr = None
+    pyr = tdpm.HogPyramid(h, w, out=out)
+    for _ in range(5):
+        pyr.compute(ctx, d_img, stream)
+    torch.cuda.synchronize()
+    l0 = tdpm.tdpm_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        pyr.compute(ctx, d_img, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    hog_ms = e0.elapsed_time(e1) / steps
+    launches = (tdpm.tdpm_kernel_launches() - l0) / steps
+    # detections from the device pyramid, end to end
+    tau = None
+
+    def e2e():
+        d_img.copy_(host, non_blocking=True)
+        pyr.compute(ctx, d_img, stream)
+        sid = tdpm.tdpm_build_pyramid_scores(ctx, mid, pyr, form, prec, stream)
+        d = tdpm.tdpm_detect(ctx, sid, tau, stream=stream)
+        tdpm.tdpm_release(ctx, sid)
+        return d
+
+    sid = tdpm.tdpm_build_pyramid_scores(ctx, mid, pyr, form, prec, stream)
+    tau = float(np.percentile(tdpm.tdpm_detect(ctx, sid, -np.inf, stream=stream)["score"], 99.5))
+    tdpm.tdpm_release(ctx, sid)
+    for _ in range(5):
+        e2e()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    n_e2e = 100
+    for _ in range(n_e2e):
+        n_det = len(e2e())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    alg_bytes = h * w * 3 + nbytes  # the image read once, the features written once
+    hbm = (peaks or {}).get("hbm_gbs")
+    return {"image": f"{w}x{h}", "levels": len(shapes), "feature_bytes": nbytes, "hog_ms_per_image": hog_ms,
+            "launches_per_image": launches, "scoring_ms_over_hog_ms": score_ms / hog_ms,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / hog_ms / 1e6,
+                         "peak_gbs": hbm, "frac": (alg_bytes / hog_ms / 1e6 / hbm) if hbm else None},
+            "image_to_detections_images_per_s": 1e3 / e2e_ms, "image_to_detections_ms": e2e_ms,
+            "detections": n_det, "tau": tau, "h2d_bytes_per_step": h * w * 3}
+
+
 def cascade_measure(torch, tdpm, ctx, mid, wl, form, prec, tau, stream, n_train=4, per_comp=5):
     """Thresholds of Sec. 4 from planted positives on n_train training images of the workload's size (per_comp
     instances of every component each), then the cascade on the workload image with two planted instances per
@@ -911,7 +968,9 @@ def main():
     if form == tdpm.FORM_DECOMPOSED and args.mode == "per_filter" and not args.no_sweep and rank == 0:
         tdpm.tdpm_decompose(ctx, mid, args.rank, dmode, max_iters=500, seed=1)  # the headline factors again
         post = {"nms": nms_measure(tdpm, ctx, mid, dp, form, prec, tau, stream),
-                "cascade": cascade_measure(torch, tdpm, ctx, mid, wl, form, prec, tau, stream)}
+                "cascade": cascade_measure(torch, tdpm, ctx, mid, wl, form, prec, tau, stream),
+                "hog": hog_measure(torch, tdpm, ctx, mid, form, prec, stream, main_run["total_ms"] / args.steps,
+                                   peaks)}
 
     line = {"metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main_run["total_ms"] / args.steps, "p50_ms": p50, "p99_ms": p99,

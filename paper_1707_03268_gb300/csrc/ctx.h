@@ -160,6 +160,9 @@ struct tdpm_ctx {
     void *d_hog = nullptr;               // grow-only scratch of the HOG pyramid calls (images, gradients, cells, tables)
     size_t hog_cap = 0;
     cudaEvent_t hog_done = nullptr;      // recorded after each HOG call's work; the next one waits before reusing d_hog
+    std::string hog_key;                 // the pyramid call whose job tables d_hog holds ("" after any other HOG call)
+    cudaGraphExec_t hog_graph = nullptr; // that call's launches, captured once it repeats
+    int hog_graph_kernels = 0, hog_uses = 0;
     bool use_graphs = true;
     bool fuse = true;                    // fused channel stage + separable passes where possible (tdpm_set_fusion)
     int zsep_form = -1;                  // fused kernel form forced by TDPM_ZSEP_FORM (-1: default / tuned)

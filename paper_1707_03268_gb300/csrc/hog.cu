@@ -350,6 +350,16 @@ void axis_taps(int n_in, int n_out, double s, std::vector<HogTap> &T, std::vecto
     }
 }
 
+// Drops the cached pyramid tables and graph (the scratch is about to change).
+void hog_forget(tdpm_ctx *ctx)
+{
+    ctx->hog_key.clear();
+    if (ctx->hog_graph) cudaGraphExecDestroy(ctx->hog_graph);
+    ctx->hog_graph = nullptr;
+    ctx->hog_graph_kernels = 0;
+    ctx->hog_uses = 0;
+}
+
 tdpm_status hog_prepare(tdpm_ctx *ctx, cudaStream_t s, size_t need, char *&base)
 {
     static std::atomic<bool> orient_set[64];
@@ -377,6 +387,7 @@ tdpm_status hog_prepare(tdpm_ctx *ctx, cudaStream_t s, size_t need, char *&base)
         CUDA_TRY(cudaMalloc(&ctx->d_hog, need));
         ctx->hog_cap = need;
         ctx->used += need;
+        hog_forget(ctx);
     }
     base = static_cast<char *>(ctx->d_hog);
     return TDPM_OK;
@@ -421,6 +432,68 @@ tdpm_status tdpm_hog_pyramid_shape(int32_t img_h, int32_t img_w, int32_t sbin, i
     return TDPM_OK;
 }
 
+namespace {
+
+// Device layout of one pyramid call inside the scratch: images, gradients, cell histograms, then the tables (resize
+// jobs, images, levels first, so that their offsets follow from the plan alone; then the taps and their weights).
+struct HogLayout {
+    std::vector<size_t> img_off, mag_off, bin_off, hist_off;
+    size_t rj_off = 0, im_off = 0, lv_off = 0, taps_off = 0, bytes_fixed = 0;
+    long long max_px = 0, max_cells = 0, max_out = 0;
+    std::vector<long long> oct_max;  // per octave: the largest image
+};
+
+HogLayout hog_layout(const HogPlanH &P)
+{
+    const int NI = (int)P.img.size(), L = (int)P.lvl_img.size();
+    HogLayout Y;
+    Bumper b;
+    Y.img_off.resize(NI);
+    Y.mag_off.resize(NI);
+    Y.bin_off.resize(NI);
+    Y.hist_off.resize(L);
+    for (int k = 0; k < NI; ++k) Y.img_off[k] = b.take(sizeof(float) * 3 * (size_t)P.img[k].first * P.img[k].second);
+    for (int k = 0; k < NI; ++k) Y.mag_off[k] = b.take(sizeof(float) * (size_t)P.img[k].first * P.img[k].second);
+    for (int k = 0; k < NI; ++k) Y.bin_off[k] = b.take((size_t)P.img[k].first * P.img[k].second);
+    for (int j = 0; j < L; ++j) {
+        int cy, cx;
+        level_shape(P, j, cy, cx);
+        Y.hist_off[j] = b.take(sizeof(float) * 18 * (size_t)cy * cx);
+        Y.max_cells = std::max(Y.max_cells, (long long)cy * cx);
+        Y.max_out = std::max(Y.max_out, (long long)(cy - 2) * (cx - 2));
+    }
+    Y.rj_off = b.take(sizeof(HogResizeJob) * NI);
+    Y.im_off = b.take(sizeof(HogImage) * NI);
+    Y.lv_off = b.take(sizeof(HogLevelJob) * L);
+    Y.taps_off = b.take(0);
+    Y.bytes_fixed = Y.taps_off;
+    for (int k = 0; k < NI; ++k) {
+        const long long px = (long long)P.img[k].first * P.img[k].second;
+        Y.max_px = std::max(Y.max_px, px);
+        const size_t oct = (size_t)(k / P.lam);
+        if (Y.oct_max.size() <= oct) Y.oct_max.push_back(0);
+        Y.oct_max[oct] = std::max(Y.oct_max[oct], px);
+    }
+    return Y;
+}
+
+// The pyramid's launches: octave 0 from the 8-bit image, each further octave from the previous one, gradients of
+// every image, cells and features of every level.
+cudaError_t hog_enqueue(const HogPlanH &P, const HogLayout &Y, char *base, cudaStream_t s)
+{
+    const int NI = (int)P.img.size(), L = (int)P.lvl_img.size();
+    const auto *d_rj = reinterpret_cast<const HogResizeJob *>(base + Y.rj_off);
+    cudaError_t e = launch_hog_resize(d_rj, std::min(NI, P.lam), Y.oct_max[0], true, s);
+    for (int k0 = P.lam, oct = 1; e == cudaSuccess && k0 < NI; k0 += P.lam, ++oct)
+        e = launch_hog_resize(d_rj + k0, std::min(P.lam, NI - k0), Y.oct_max[oct], false, s);
+    if (e == cudaSuccess) e = launch_hog_grad(reinterpret_cast<const HogImage *>(base + Y.im_off), NI, Y.max_px, s);
+    if (e == cudaSuccess)
+        e = launch_hog_levels(reinterpret_cast<const HogLevelJob *>(base + Y.lv_off), L, Y.max_cells, Y.max_out, s);
+    return e;
+}
+
+}  // namespace
+
 tdpm_status tdpm_hog_pyramid(tdpm_ctx *ctx, const uint8_t *d_image, int32_t img_h, int32_t img_w, int32_t sbin,
                              int32_t lambda, int32_t min_cells, float *d_out, size_t out_bytes, tdpm_level *levels,
                              int32_t max_levels, int32_t *n_levels, void *stream)
@@ -434,10 +507,15 @@ tdpm_status tdpm_hog_pyramid(tdpm_ctx *ctx, const uint8_t *d_image, int32_t img_
     const int L = (int)P.lvl_img.size(), NI = (int)P.img.size();
     *n_levels = L;
     if (max_levels < L) return fail(TDPM_ERR_CAPACITY, "more levels than max_levels");
+    std::vector<size_t> out_off(L);
     size_t need_out = 0;
     for (int j = 0; j < L; ++j) {
         int cy, cx;
         level_shape(P, j, cy, cx);
+        out_off[j] = need_out;
+        levels[j].H = cy - 2;
+        levels[j].W = cx - 2;
+        levels[j].data = d_out + need_out / sizeof(float);
         need_out += (size_t)(cy - 2) * (cx - 2) * 32 * sizeof(float);
     }
     if (out_bytes < need_out) return fail(TDPM_ERR_CAPACITY, "d_out holds " + std::to_string(out_bytes) +
@@ -445,6 +523,44 @@ tdpm_status tdpm_hog_pyramid(tdpm_ctx *ctx, const uint8_t *d_image, int32_t img_
     std::lock_guard<std::mutex> lk(ctx->mu);
     if ((st = set_device(ctx))) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    const HogLayout Y = hog_layout(P);
+    const std::string key = std::to_string(img_h) + "x" + std::to_string(img_w) + ":" + std::to_string(sbin) + ":" +
+                            std::to_string(lambda) + ":" + std::to_string(min_cells) + ":" +
+                            std::to_string(reinterpret_cast<uintptr_t>(d_image)) + ":" +
+                            std::to_string(reinterpret_cast<uintptr_t>(d_out));
+    if (!ctx->hog_key.empty() && key == ctx->hog_key && ctx->d_hog) {
+        // the same call again: the tables on the device are current; from the second repeat on, one graph launch
+        char *base = static_cast<char *>(ctx->d_hog);
+        CUDA_TRY(cudaStreamWaitEvent(s, ctx->hog_done, 0));
+        if (!ctx->hog_graph && ctx->hog_uses >= 2 && ctx->use_graphs) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                int captured = 0;
+                t_capture_launches = &captured;
+                const cudaError_t eq = hog_enqueue(P, Y, base, ctx->cap_stream);
+                t_capture_launches = nullptr;
+                e = cudaStreamEndCapture(ctx->cap_stream, &g);
+                if (eq != cudaSuccess) e = eq;
+                ctx->hog_graph_kernels = captured;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->hog_graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                ctx->hog_graph = nullptr;
+            }
+        }
+        if (ctx->hog_graph) {
+            CUDA_TRY(cudaGraphLaunch(ctx->hog_graph, s));
+            note_launches(ctx->hog_graph_kernels);
+        } else {
+            CUDA_TRY(hog_enqueue(P, Y, base, s));
+        }
+        ctx->hog_uses++;
+        CUDA_TRY(cudaEventRecord(ctx->hog_done, s));
+        return TDPM_OK;
+    }
     // host tables: resize jobs with their taps, images, levels
     std::vector<HogResizeJob> rj(NI);
     std::vector<HogTap> taps_all;
@@ -452,87 +568,56 @@ tdpm_status tdpm_hog_pyramid(tdpm_ctx *ctx, const uint8_t *d_image, int32_t img_
     std::vector<size_t> ytap_off(NI), xtap_off(NI);
     for (int k = 0; k < NI; ++k) {
         const int oct = k / P.lam, i = k % P.lam;
-        const double sc = oct == 0 ? std::pow(2.0, -(double)i / P.lam) : 0.5;
+        const double sc = oct == 0 ? (i == 0 ? 1.0 : std::pow(2.0, -(double)i / P.lam)) : 0.5;
         const int hin = oct == 0 ? img_h : P.img[k - P.lam].first, win = oct == 0 ? img_w : P.img[k - P.lam].second;
         std::vector<HogTap> T;
         ytap_off[k] = taps_all.size();
-        axis_taps(hin, P.img[k].first, oct == 0 && i == 0 ? 1.0 : sc, T, wts);
+        axis_taps(hin, P.img[k].first, sc, T, wts);
         taps_all.insert(taps_all.end(), T.begin(), T.end());
         xtap_off[k] = taps_all.size();
-        axis_taps(win, P.img[k].second, oct == 0 && i == 0 ? 1.0 : sc, T, wts);
+        axis_taps(win, P.img[k].second, sc, T, wts);
         taps_all.insert(taps_all.end(), T.begin(), T.end());
         rj[k].h = hin;
         rj[k].w = win;
         rj[k].ho = P.img[k].first;
         rj[k].wo = P.img[k].second;
     }
-    // device scratch: images, magnitudes, bins, cell histograms, then the tables
-    Bumper b;
-    std::vector<size_t> img_off(NI), mag_off(NI), bin_off(NI), hist_off(L);
-    for (int k = 0; k < NI; ++k) img_off[k] = b.take(sizeof(float) * 3 * (size_t)P.img[k].first * P.img[k].second);
-    for (int k = 0; k < NI; ++k) mag_off[k] = b.take(sizeof(float) * (size_t)P.img[k].first * P.img[k].second);
-    for (int k = 0; k < NI; ++k) bin_off[k] = b.take((size_t)P.img[k].first * P.img[k].second);
-    long long max_cells = 0, max_out = 0;
-    for (int j = 0; j < L; ++j) {
-        int cy, cx;
-        level_shape(P, j, cy, cx);
-        hist_off[j] = b.take(sizeof(float) * 18 * (size_t)cy * cx);
-        max_cells = std::max(max_cells, (long long)cy * cx);
-        max_out = std::max(max_out, (long long)(cy - 2) * (cx - 2));
-    }
-    const size_t rj_off = b.take(sizeof(HogResizeJob) * NI), taps_off = b.take(sizeof(HogTap) * taps_all.size()),
-                 w_off = b.take(sizeof(float) * wts.size()), im_off = b.take(sizeof(HogImage) * NI),
-                 lv_off = b.take(sizeof(HogLevelJob) * L);
-    const size_t tables_begin = rj_off, tables_end = b.off;
+    const size_t w_off = align256(Y.taps_off + sizeof(HogTap) * taps_all.size());
+    const size_t total = w_off + sizeof(float) * wts.size();
     char *base = nullptr;
-    if ((st = hog_prepare(ctx, s, b.off, base))) return st;
+    hog_forget(ctx);
+    if ((st = hog_prepare(ctx, s, total, base))) return st;
     std::vector<HogImage> im(NI);
-    long long max_px = 0;
     for (int k = 0; k < NI; ++k) {
-        const int oct = k / P.lam;
-        rj[k].src = oct == 0 ? static_cast<const void *>(d_image) : static_cast<const void *>(base + img_off[k - P.lam]);
-        rj[k].dst = reinterpret_cast<float *>(base + img_off[k]);
-        rj[k].ytaps = reinterpret_cast<const HogTap *>(base + taps_off) + ytap_off[k];
-        rj[k].xtaps = reinterpret_cast<const HogTap *>(base + taps_off) + xtap_off[k];
+        rj[k].src = k < P.lam ? static_cast<const void *>(d_image) : static_cast<const void *>(base + Y.img_off[k - P.lam]);
+        rj[k].dst = reinterpret_cast<float *>(base + Y.img_off[k]);
+        rj[k].ytaps = reinterpret_cast<const HogTap *>(base + Y.taps_off) + ytap_off[k];
+        rj[k].xtaps = reinterpret_cast<const HogTap *>(base + Y.taps_off) + xtap_off[k];
         rj[k].weights = reinterpret_cast<const float *>(base + w_off);
-        im[k] = HogImage{rj[k].dst, P.img[k].first, P.img[k].second, reinterpret_cast<float *>(base + mag_off[k]),
-                         reinterpret_cast<uint8_t *>(base + bin_off[k])};
-        max_px = std::max(max_px, (long long)P.img[k].first * P.img[k].second);
+        im[k] = HogImage{rj[k].dst, P.img[k].first, P.img[k].second, reinterpret_cast<float *>(base + Y.mag_off[k]),
+                         reinterpret_cast<uint8_t *>(base + Y.bin_off[k])};
     }
     std::vector<HogLevelJob> lj(L);
-    size_t out_off = 0;
     for (int j = 0; j < L; ++j) {
         const int k = P.lvl_img[j];
         int cy, cx;
         level_shape(P, j, cy, cx);
         lj[j] = HogLevelJob{im[k].mag, im[k].bin, P.img[k].first, P.img[k].second, P.lvl_sbin[j], cy, cx,
-                            reinterpret_cast<float *>(base + hist_off[j]), d_out + out_off / sizeof(float)};
-        levels[j].H = cy - 2;
-        levels[j].W = cx - 2;
-        levels[j].data = d_out + out_off / sizeof(float);
-        out_off += (size_t)(cy - 2) * (cx - 2) * 32 * sizeof(float);
+                            reinterpret_cast<float *>(base + Y.hist_off[j]), d_out + out_off[j] / sizeof(float)};
     }
-    std::vector<char> blob(tables_end - tables_begin);
-    std::memcpy(blob.data() + (rj_off - tables_begin), rj.data(), sizeof(HogResizeJob) * NI);
-    if (!taps_all.empty()) std::memcpy(blob.data() + (taps_off - tables_begin), taps_all.data(), sizeof(HogTap) * taps_all.size());
-    if (!wts.empty()) std::memcpy(blob.data() + (w_off - tables_begin), wts.data(), sizeof(float) * wts.size());
-    std::memcpy(blob.data() + (im_off - tables_begin), im.data(), sizeof(HogImage) * NI);
-    std::memcpy(blob.data() + (lv_off - tables_begin), lj.data(), sizeof(HogLevelJob) * L);
-    CUDA_TRY(cudaMemcpyAsync(base + tables_begin, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
-    const auto *d_rj = reinterpret_cast<const HogResizeJob *>(base + rj_off);
-    // octave 0 from the 8-bit image, then each octave from the previous one
-    long long max0 = 0;
-    for (int k = 0; k < std::min(NI, P.lam); ++k) max0 = std::max(max0, (long long)P.img[k].first * P.img[k].second);
-    CUDA_TRY(launch_hog_resize(d_rj, std::min(NI, P.lam), max0, true, s));
-    for (int k0 = P.lam; k0 < NI; k0 += P.lam) {
-        const int n = std::min(P.lam, NI - k0);
-        long long mx = 0;
-        for (int k = k0; k < k0 + n; ++k) mx = std::max(mx, (long long)P.img[k].first * P.img[k].second);
-        CUDA_TRY(launch_hog_resize(d_rj + k0, n, mx, false, s));
-    }
-    CUDA_TRY(launch_hog_grad(reinterpret_cast<const HogImage *>(base + im_off), NI, max_px, s));
-    CUDA_TRY(launch_hog_levels(reinterpret_cast<const HogLevelJob *>(base + lv_off), L, max_cells, max_out, s));
+    // one transfer of every table, from pinned memory when the context has room for it
+    std::vector<char> blob(total - Y.rj_off);
+    std::memcpy(blob.data() + (Y.rj_off - Y.rj_off), rj.data(), sizeof(HogResizeJob) * NI);
+    std::memcpy(blob.data() + (Y.im_off - Y.rj_off), im.data(), sizeof(HogImage) * NI);
+    std::memcpy(blob.data() + (Y.lv_off - Y.rj_off), lj.data(), sizeof(HogLevelJob) * L);
+    if (!taps_all.empty())
+        std::memcpy(blob.data() + (Y.taps_off - Y.rj_off), taps_all.data(), sizeof(HogTap) * taps_all.size());
+    if (!wts.empty()) std::memcpy(blob.data() + (w_off - Y.rj_off), wts.data(), sizeof(float) * wts.size());
+    CUDA_TRY(cudaMemcpyAsync(base + Y.rj_off, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(hog_enqueue(P, Y, base, s));
     CUDA_TRY(cudaEventRecord(ctx->hog_done, s));
+    ctx->hog_key = key;
+    ctx->hog_uses = 1;
     return TDPM_OK;
 }
 
@@ -559,6 +644,7 @@ tdpm_status tdpm_hog_features(tdpm_ctx *ctx, const float *d_img, int32_t h, int3
                  hist_off = b.take(sizeof(float) * 18 * (size_t)cy * cx), im_off = b.take(sizeof(HogImage)),
                  lv_off = b.take(sizeof(HogLevelJob));
     char *base = nullptr;
+    hog_forget(ctx);
     if ((st = hog_prepare(ctx, s, b.off, base))) return st;
     HogImage im{d_img, h, w, reinterpret_cast<float *>(base + mag_off), reinterpret_cast<uint8_t *>(base + bin_off)};
     HogLevelJob lj{im.mag, im.bin, h, w, sbin, cy, cx, reinterpret_cast<float *>(base + hist_off), d_out};
@@ -599,6 +685,7 @@ tdpm_status tdpm_resize(tdpm_ctx *ctx, const float *d_src, int32_t h, int32_t w,
     const size_t j_off = b.take(sizeof(HogResizeJob)), ty_off = b.take(sizeof(HogTap) * ty.size()),
                  tx_off = b.take(sizeof(HogTap) * tx.size()), w_off = b.take(sizeof(float) * wts.size());
     char *base = nullptr;
+    hog_forget(ctx);
     if ((st = hog_prepare(ctx, s, b.off, base))) return st;
     HogResizeJob J{d_src, h, w, d_dst, ho, wo, reinterpret_cast<const HogTap *>(base + ty_off),
                    reinterpret_cast<const HogTap *>(base + tx_off), reinterpret_cast<const float *>(base + w_off)};

@@ -117,6 +117,8 @@ struct AsmJob {
 // Every launcher adds the number of kernels it launched to the process-wide counter (tdpm_kernel_launches) and
 // returns the launch error (cudaSuccess when the launch was accepted).
 void note_launches(int n);
+// While a thread captures a CUDA graph, its launches are counted here (they run at each replay) instead of now.
+extern thread_local int *t_capture_launches;
 
 // Raise a kernel's dynamic shared memory limit to the per-block maximum, once per device. Launches still request only
 // what they use; a fixed limit keeps captured CUDA graphs valid whatever order their launches were recorded in.

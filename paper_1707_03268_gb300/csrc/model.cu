@@ -279,6 +279,7 @@ void tdpm_destroy(tdpm_ctx *ctx)
         if (ctx->d_nms) cudaFree(ctx->d_nms);
         if (ctx->d_hog) cudaFree(ctx->d_hog);
         if (ctx->hog_done) cudaEventDestroy(ctx->hog_done);
+        if (ctx->hog_graph) cudaGraphExecDestroy(ctx->hog_graph);
         if (ctx->d_job_tau) cudaFree(ctx->d_job_tau);
         for (cudaStream_t st : ctx->side) cudaStreamDestroy(st);
         for (cudaEvent_t ev : ctx->join_ev) cudaEventDestroy(ev);

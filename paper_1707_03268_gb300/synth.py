@@ -191,6 +191,18 @@ def make_dpm_class(rng: np.random.Generator, kind: str = "dpm", **filter_kw) -> 
 
 
 # --------------------------------------------------------------------------------------------------------------------
+# images (input of the feature extraction block)
+# --------------------------------------------------------------------------------------------------------------------
+def make_image(rng: np.random.Generator, h: int, w: int) -> np.ndarray:
+    """An 8-bit RGB image [h][w][3]: smooth oriented structure (edges in every direction) plus pixel noise."""
+    y, x = np.mgrid[0:h, 0:w].astype(np.float64)
+    ph = rng.uniform(0, 2 * np.pi, size=4)
+    base = 120 + 60 * np.sin(x / 7.0 + 0.3 * y / 5.0 + ph[0]) + 40 * np.cos(y / 9.0 - x / 13.0 + ph[1])
+    img = np.stack([base, base * 0.8 + 20, 255 - base], axis=2) + rng.normal(0, 12, size=(h, w, 3))
+    return np.clip(np.rint(img), 0, 255).astype(np.uint8)
+
+
+# --------------------------------------------------------------------------------------------------------------------
 # planted object instances (positive examples for the thresholds of Sec. 4)
 # --------------------------------------------------------------------------------------------------------------------
 def plant_objects(rng: np.random.Generator, pyramid: Pyramid, model: Model,

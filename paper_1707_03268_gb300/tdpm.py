@@ -436,28 +436,46 @@ def tdpm_hog_pyramid_shape(img_h: int, img_w: int, sbin: int = 8, lam: int = 10,
     return [(hw[2 * j], hw[2 * j + 1]) for j in range(n.value)], b.value
 
 
+class HogPyramid(DevicePyramid):
+    """The device feature pyramid of an img_h x img_w image: level views of one flat FP32 CUDA tensor, filled by
+    ``compute`` (one library call; repeated calls with the same image buffer replay the library's cached launches)."""
+
+    def __init__(self, img_h: int, img_w: int, sbin: int = 8, lam: int = 10, min_cells: int = 8, out=None,
+                 device="cuda"):
+        import torch
+        shapes, nbytes = tdpm_hog_pyramid_shape(img_h, img_w, sbin, lam, min_cells)
+        if out is None:
+            out = torch.empty(nbytes // 4, dtype=torch.float32, device=device)
+        assert out.is_cuda and out.dtype == torch.float32 and out.numel() * 4 >= nbytes and out.is_contiguous()
+        levels, off = [], 0
+        for (h, w) in shapes:
+            levels.append(out[off:off + h * w * FEAT_DIM].view(h, w, FEAT_DIM))
+            off += h * w * FEAT_DIM
+        super().__init__(levels, lam)
+        self.flat, self.nbytes = out, nbytes
+        self.img_hw, self.sbin, self.min_cells = (img_h, img_w), sbin, min_cells
+        self._hog_levels = (Level * len(shapes))()
+        self._n = _c_i32()
+
+    def compute(self, ctx: int, image, stream=None) -> "HogPyramid":
+        """Fill the levels from a CUDA uint8 image [img_h][img_w][3] (contiguous)."""
+        assert tuple(image.shape) == (self.img_hw[0], self.img_hw[1], 3) and image.is_contiguous()
+        _check(lib().tdpm_hog_pyramid(ctx, image.data_ptr(), self.img_hw[0], self.img_hw[1], self.sbin, self.lam,
+                                      self.min_cells, self.flat.data_ptr(), self.nbytes, self._hog_levels,
+                                      len(self.levels), ctypes.byref(self._n), _stream_ptr(stream)))
+        return self
+
+
 def tdpm_hog_pyramid(ctx: int, image, sbin: int = 8, lam: int = 10, min_cells: int = 8, out=None,
-                     stream=None) -> "DevicePyramid":
-    """HOG feature pyramid of a CUDA uint8 tensor [H][W][3]; the levels are views of one flat FP32 CUDA tensor (`out`
-    when given, else a new one), returned as a DevicePyramid ready for scoring."""
+                     stream=None, pyramid: Optional["HogPyramid"] = None) -> "HogPyramid":
+    """HOG feature pyramid of a CUDA uint8 tensor [H][W][3] as a DevicePyramid ready for scoring (``pyramid``: one
+    made before for the same image size, reused)."""
     import torch
     assert image.is_cuda and image.dtype == torch.uint8 and image.dim() == 3 and image.shape[2] == 3
     image = image.contiguous()
-    H, W = int(image.shape[0]), int(image.shape[1])
-    shapes, nbytes = tdpm_hog_pyramid_shape(H, W, sbin, lam, min_cells)
-    if out is None:
-        out = torch.empty(nbytes // 4, dtype=torch.float32, device=image.device)
-    arr = (Level * len(shapes))()
-    n = _c_i32()
-    _check(lib().tdpm_hog_pyramid(ctx, _ptr(image), H, W, sbin, lam, min_cells, _ptr(out), out.numel() * 4, arr,
-                                  len(shapes), ctypes.byref(n), _stream_ptr(stream)))
-    levels, off = [], 0
-    for (h, w) in shapes:
-        levels.append(out[off:off + h * w * FEAT_DIM].view(h, w, FEAT_DIM))
-        off += h * w * FEAT_DIM
-    pyr = DevicePyramid(levels, lam)
-    pyr.flat = out
-    return pyr
+    if pyramid is None:
+        pyramid = HogPyramid(int(image.shape[0]), int(image.shape[1]), sbin, lam, min_cells, out, image.device)
+    return pyramid.compute(ctx, image, stream)
 
 
 def tdpm_hog_features(ctx: int, img, sbin: int, stream=None):

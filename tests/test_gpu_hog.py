@@ -113,3 +113,25 @@ def test_hog_argument_errors(torch, T, ctx):
         T.tdpm_hog_pyramid_shape(240, 320, 6, 10, 8)    # cell size not 4, 8 or 16
     with pytest.raises(T.TdpmError):
         T.tdpm_resize(ctx, torch.zeros((8, 8, 3), device="cuda"), 1.5)
+
+
+def test_repeated_pyramid_calls_replay_identically(torch, T, ctx):
+    """The second call with the same buffers reuses the device tables and later ones replay a captured graph; an
+    interleaved single-image call invalidates both. Every call writes the same bits."""
+    img = torch.from_numpy(_image(13, 150, 200)).cuda()
+    pyr = T.HogPyramid(150, 200)
+    l0 = T.tdpm_kernel_launches()
+    first = pyr.compute(ctx, img).flat.clone()
+    per_call = T.tdpm_kernel_launches() - l0   # one resize per octave, gradients, cells, features
+    assert per_call == 4                        # 150x200: every root level is in the first octave
+    l0 = T.tdpm_kernel_launches()
+    for _ in range(4):
+        pyr.compute(ctx, img)
+        torch.cuda.synchronize()
+        assert torch.equal(pyr.flat, first)
+    assert T.tdpm_kernel_launches() - l0 == 4 * per_call   # graph replays counted too
+    T.tdpm_hog_features(ctx, img.float(), 8)
+    pyr.flat.zero_()
+    pyr.compute(ctx, img)
+    torch.cuda.synchronize()
+    assert torch.equal(pyr.flat, first)
