@@ -104,25 +104,28 @@ __global__ void hog_grad_kernel(const HogImage *__restrict__ imgs)
 }
 
 // --------------------------------------------------------------------------------------------------- histogram
-// One thread per cell of one level; bins in shared memory, [bin][thread] so that a warp's updates of one bin fall in
-// distinct banks.
+// 2 sbin threads per cell, one per row of the 2 sbin x 2 sbin pixels that vote into it: each sums its row's votes into
+// its own 18 bins in shared memory ([bin][thread]: a warp's updates of one bin fall in distinct banks), then the rows
+// are added in a fixed tree order and the first thread writes the cell's bins and its energy
+// E = sum_{o<9} (h_o + h_{o+9})^2.
 __global__ void __launch_bounds__(HOG_HIST_THREADS) hog_hist_kernel(const HogLevelJob *__restrict__ jobs)
 {
     __shared__ float hs[18][HOG_HIST_THREADS];
     const HogLevelJob J = jobs[blockIdx.y];
     const int t = threadIdx.x;
-    const long long cell = (long long)blockIdx.x * HOG_HIST_THREADS + t;
-    if ((long long)blockIdx.x * HOG_HIST_THREADS >= (long long)J.cy * J.cx) return;  // uniform per block
-    const bool live = cell < (long long)J.cy * J.cx;
+    const int s = J.sbin, hs2 = s / 2, tpc = 2 * s;  // threads per cell (tpc divides the block)
+    const int cpb = HOG_HIST_THREADS / tpc;
+    const long long n_cells = (long long)J.cy * J.cx;
+    if ((long long)blockIdx.x * cpb >= n_cells) return;  // uniform per block
+    const int r = t % tpc;
+    const long long cell = (long long)blockIdx.x * cpb + t / tpc;
 #pragma unroll
     for (int o = 0; o < 18; ++o) hs[o][t] = 0.f;
-    if (live) {
+    if (cell < n_cells) {
         const int Y = (int)(cell / J.cx), X = (int)(cell - (long long)Y * J.cx);
-        const int s = J.sbin, hs2 = s / 2;
-        const float inv = 1.f / (float)s;  // s is a power of two: exact
-        const int y_lo = max(1, Y * s - hs2), y_hi = min(J.cy * s - 2, Y * s + s + hs2 - 1);
-        const int x_lo = max(1, X * s - hs2), x_hi = min(J.cx * s - 2, X * s + s + hs2 - 1);
-        for (int y = y_lo; y <= y_hi; ++y) {
+        const int y = Y * s - hs2 + r;
+        if (y >= 1 && y <= J.cy * s - 2) {
+            const float inv = 1.f / (float)s;  // s is a power of two: exact
             const float yp = ((float)y + 0.5f) * inv - 0.5f;
             const int iy = (int)floorf(yp);
             const float fy = yp - (float)iy;
@@ -130,6 +133,7 @@ __global__ void __launch_bounds__(HOG_HIST_THREADS) hog_hist_kernel(const HogLev
             const int yy = min(y, J.h - 2);
             const float *mrow = J.mag + (size_t)yy * J.w;
             const uint8_t *brow = J.bin + (size_t)yy * J.w;
+            const int x_lo = max(1, X * s - hs2), x_hi = min(J.cx * s - 2, X * s + s + hs2 - 1);
             for (int x = x_lo; x <= x_hi; ++x) {
                 const float xp = ((float)x + 0.5f) * inv - 0.5f;
                 const int ix = (int)floorf(xp);
@@ -139,24 +143,29 @@ __global__ void __launch_bounds__(HOG_HIST_THREADS) hog_hist_kernel(const HogLev
                 hs[brow[xx]][t] += wy * wx * mrow[xx];
             }
         }
+    }
+    __syncthreads();
+    for (int st = s; st >= 1; st >>= 1) {  // rows r and r + st of the same cell, in a fixed order
+        if (r < st)
+#pragma unroll
+            for (int o = 0; o < 18; ++o) hs[o][t] += hs[o][t + st];
+        __syncthreads();
+    }
+    if (r == 0 && cell < n_cells) {
         float *out = J.hist + (size_t)cell * 18;
+        float e = 0.f;
 #pragma unroll
         for (int o = 0; o < 18; ++o) out[o] = hs[o][t];
+#pragma unroll
+        for (int o = 0; o < 9; ++o) {
+            const float v = hs[o][t] + hs[o + 9][t];
+            e = fmaf(v, v, e);
+        }
+        J.energy[cell] = e;
     }
 }
 
 // ---------------------------------------------------------------------------------------------------- features
-__device__ __forceinline__ float hog_energy(const float *h)
-{
-    float e = 0.f;
-#pragma unroll
-    for (int o = 0; o < 9; ++o) {
-        const float s = h[o] + h[o + 9];
-        e = fmaf(s, s, e);
-    }
-    return e;
-}
-
 __global__ void hog_feat_kernel(const HogLevelJob *__restrict__ jobs)
 {
     const HogLevelJob J = jobs[blockIdx.y];
@@ -169,14 +178,23 @@ __global__ void hog_feat_kernel(const HogLevelJob *__restrict__ jobs)
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) E[a][b] = hog_energy(J.hist + ((size_t)(Y - 1 + a) * J.cx + (X - 1 + b)) * 18);
+        for (int b = 0; b < 3; ++b) E[a][b] = J.energy[(size_t)(Y - 1 + a) * J.cx + (X - 1 + b)];
     // blocks with top-left corner (Y, X), (Y, X - 1), (Y - 1, X), (Y - 1, X - 1)
     float n[4];
     n[0] = rsqrtf(E[1][1] + E[1][2] + E[2][1] + E[2][2] + HOG_EPS);
     n[1] = rsqrtf(E[1][0] + E[1][1] + E[2][0] + E[2][1] + HOG_EPS);
     n[2] = rsqrtf(E[0][1] + E[0][2] + E[1][1] + E[1][2] + HOG_EPS);
     n[3] = rsqrtf(E[0][0] + E[0][1] + E[1][0] + E[1][1] + HOG_EPS);
-    const float *h = J.hist + ((size_t)Y * J.cx + X) * 18;
+    float h[18];
+    {
+        const float2 *h2 = reinterpret_cast<const float2 *>(J.hist + ((size_t)Y * J.cx + X) * 18);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float2 v = h2[q];
+            h[2 * q] = v.x;
+            h[2 * q + 1] = v.y;
+        }
+    }
     float f[32];
     float tex[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -227,6 +245,12 @@ cudaError_t launch_hog_resize(const HogResizeJob *d_jobs, int n_jobs, long long 
     return cudaGetLastError();
 }
 
+int hog_hist_blocks(int cy, int cx, int sbin)
+{
+    const long long cpb = HOG_HIST_THREADS / (2 * sbin);
+    return (int)(((long long)cy * cx + cpb - 1) / cpb);
+}
+
 cudaError_t launch_hog_grad(const HogImage *d_imgs, int n_imgs, long long max_pixels, cudaStream_t s)
 {
     if (n_imgs <= 0 || max_pixels <= 0) return cudaSuccess;
@@ -235,14 +259,13 @@ cudaError_t launch_hog_grad(const HogImage *d_imgs, int n_imgs, long long max_pi
     return cudaGetLastError();
 }
 
-cudaError_t launch_hog_levels(const HogLevelJob *d_jobs, int n_jobs, long long max_cells, long long max_out_cells,
+cudaError_t launch_hog_levels(const HogLevelJob *d_jobs, int n_jobs, long long max_hist_blocks, long long max_out_cells,
                               cudaStream_t s)
 {
     if (n_jobs <= 0) return cudaSuccess;
     note_launches(2);
-    if (max_cells > 0)
-        hog_hist_kernel<<<dim3((unsigned)((max_cells + HOG_HIST_THREADS - 1) / HOG_HIST_THREADS), (unsigned)n_jobs),
-                          HOG_HIST_THREADS, 0, s>>>(d_jobs);
+    if (max_hist_blocks > 0)
+        hog_hist_kernel<<<dim3((unsigned)max_hist_blocks, (unsigned)n_jobs), HOG_HIST_THREADS, 0, s>>>(d_jobs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || max_out_cells <= 0) return e;
     hog_feat_kernel<<<dim3((unsigned)((max_out_cells + 127) / 128), (unsigned)n_jobs), 128, 0, s>>>(d_jobs);
@@ -437,9 +460,9 @@ namespace {
 // Device layout of one pyramid call inside the scratch: images, gradients, cell histograms, then the tables (resize
 // jobs, images, levels first, so that their offsets follow from the plan alone; then the taps and their weights).
 struct HogLayout {
-    std::vector<size_t> img_off, mag_off, bin_off, hist_off;
+    std::vector<size_t> img_off, mag_off, bin_off, hist_off, energy_off;
     size_t rj_off = 0, im_off = 0, lv_off = 0, taps_off = 0, bytes_fixed = 0;
-    long long max_px = 0, max_cells = 0, max_out = 0;
+    long long max_px = 0, max_hist_blocks = 0, max_out = 0;
     std::vector<long long> oct_max;  // per octave: the largest image
 };
 
@@ -452,6 +475,7 @@ HogLayout hog_layout(const HogPlanH &P)
     Y.mag_off.resize(NI);
     Y.bin_off.resize(NI);
     Y.hist_off.resize(L);
+    Y.energy_off.resize(L);
     for (int k = 0; k < NI; ++k) Y.img_off[k] = b.take(sizeof(float) * 3 * (size_t)P.img[k].first * P.img[k].second);
     for (int k = 0; k < NI; ++k) Y.mag_off[k] = b.take(sizeof(float) * (size_t)P.img[k].first * P.img[k].second);
     for (int k = 0; k < NI; ++k) Y.bin_off[k] = b.take((size_t)P.img[k].first * P.img[k].second);
@@ -459,7 +483,8 @@ HogLayout hog_layout(const HogPlanH &P)
         int cy, cx;
         level_shape(P, j, cy, cx);
         Y.hist_off[j] = b.take(sizeof(float) * 18 * (size_t)cy * cx);
-        Y.max_cells = std::max(Y.max_cells, (long long)cy * cx);
+        Y.energy_off[j] = b.take(sizeof(float) * (size_t)cy * cx);
+        Y.max_hist_blocks = std::max(Y.max_hist_blocks, (long long)hog_hist_blocks(cy, cx, P.lvl_sbin[j]));
         Y.max_out = std::max(Y.max_out, (long long)(cy - 2) * (cx - 2));
     }
     Y.rj_off = b.take(sizeof(HogResizeJob) * NI);
@@ -488,7 +513,8 @@ cudaError_t hog_enqueue(const HogPlanH &P, const HogLayout &Y, char *base, cudaS
         e = launch_hog_resize(d_rj + k0, std::min(P.lam, NI - k0), Y.oct_max[oct], false, s);
     if (e == cudaSuccess) e = launch_hog_grad(reinterpret_cast<const HogImage *>(base + Y.im_off), NI, Y.max_px, s);
     if (e == cudaSuccess)
-        e = launch_hog_levels(reinterpret_cast<const HogLevelJob *>(base + Y.lv_off), L, Y.max_cells, Y.max_out, s);
+        e = launch_hog_levels(reinterpret_cast<const HogLevelJob *>(base + Y.lv_off), L, Y.max_hist_blocks, Y.max_out,
+                              s);
     return e;
 }
 
@@ -603,7 +629,8 @@ tdpm_status tdpm_hog_pyramid(tdpm_ctx *ctx, const uint8_t *d_image, int32_t img_
         int cy, cx;
         level_shape(P, j, cy, cx);
         lj[j] = HogLevelJob{im[k].mag, im[k].bin, P.img[k].first, P.img[k].second, P.lvl_sbin[j], cy, cx,
-                            reinterpret_cast<float *>(base + Y.hist_off[j]), d_out + out_off[j] / sizeof(float)};
+                            reinterpret_cast<float *>(base + Y.hist_off[j]),
+                            reinterpret_cast<float *>(base + Y.energy_off[j]), d_out + out_off[j] / sizeof(float)};
     }
     // one transfer of every table, from pinned memory when the context has room for it
     std::vector<char> blob(total - Y.rj_off);
@@ -641,20 +668,22 @@ tdpm_status tdpm_hog_features(tdpm_ctx *ctx, const float *d_img, int32_t h, int3
     cudaStream_t s = (cudaStream_t)stream;
     Bumper b;
     const size_t mag_off = b.take(sizeof(float) * (size_t)h * w), bin_off = b.take((size_t)h * w),
-                 hist_off = b.take(sizeof(float) * 18 * (size_t)cy * cx), im_off = b.take(sizeof(HogImage)),
+                 hist_off = b.take(sizeof(float) * 18 * (size_t)cy * cx),
+                 energy_off = b.take(sizeof(float) * (size_t)cy * cx), im_off = b.take(sizeof(HogImage)),
                  lv_off = b.take(sizeof(HogLevelJob));
     char *base = nullptr;
     hog_forget(ctx);
     if ((st = hog_prepare(ctx, s, b.off, base))) return st;
     HogImage im{d_img, h, w, reinterpret_cast<float *>(base + mag_off), reinterpret_cast<uint8_t *>(base + bin_off)};
-    HogLevelJob lj{im.mag, im.bin, h, w, sbin, cy, cx, reinterpret_cast<float *>(base + hist_off), d_out};
+    HogLevelJob lj{im.mag, im.bin, h, w, sbin, cy, cx, reinterpret_cast<float *>(base + hist_off),
+                   reinterpret_cast<float *>(base + energy_off), d_out};
     char blob[512];
     static_assert(sizeof(HogImage) + sizeof(HogLevelJob) + 256 <= sizeof(blob), "blob");
     std::memcpy(blob, &im, sizeof im);
     std::memcpy(blob + (lv_off - im_off), &lj, sizeof lj);
     CUDA_TRY(cudaMemcpyAsync(base + im_off, blob, lv_off - im_off + sizeof lj, cudaMemcpyHostToDevice, s));
     CUDA_TRY(launch_hog_grad(reinterpret_cast<const HogImage *>(base + im_off), 1, (long long)h * w, s));
-    CUDA_TRY(launch_hog_levels(reinterpret_cast<const HogLevelJob *>(base + lv_off), 1, (long long)cy * cx,
+    CUDA_TRY(launch_hog_levels(reinterpret_cast<const HogLevelJob *>(base + lv_off), 1, hog_hist_blocks(cy, cx, sbin),
                                (long long)(*out_h) * (*out_w), s));
     CUDA_TRY(cudaEventRecord(ctx->hog_done, s));
     CUDA_TRY(cudaStreamSynchronize(s));  // the blob above lives on this stack frame

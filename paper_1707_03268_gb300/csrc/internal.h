@@ -290,13 +290,16 @@ struct HogLevelJob {
     int h, w;          // the image the level is computed from
     int sbin, cy, cx;  // cell size and cells per column / row (including the border ring)
     float *hist;       // [cy][cx][18] scratch
+    float *energy;     // [cy][cx] scratch: sum_{o<9} (h_o + h_{o+9})^2 per cell
     float *out;        // [cy - 2][cx - 2][32] FP32 features
 };
+// blocks of the cell kernel for one level (2 sbin threads per cell)
+int hog_hist_blocks(int cy, int cx, int sbin);
 cudaError_t hog_set_orientations(const float *ux, const float *uy);
 cudaError_t launch_hog_resize(const HogResizeJob *d_jobs, int n_jobs, long long max_pixels, bool from_u8,
                               cudaStream_t s);
 cudaError_t launch_hog_grad(const HogImage *d_imgs, int n_imgs, long long max_pixels, cudaStream_t s);
-cudaError_t launch_hog_levels(const HogLevelJob *d_jobs, int n_jobs, long long max_cells, long long max_out_cells,
+cudaError_t launch_hog_levels(const HogLevelJob *d_jobs, int n_jobs, long long max_hist_blocks, long long max_out_cells,
                               cudaStream_t s);
 
 // Ordered compaction: the records whose flag is nonzero go to d_out in record order, their number to *d_n_out.
