@@ -52,7 +52,8 @@ def test_nms_matches_oracle_one_image(torch, T, pct, overlap):
 
 
 def test_nms_batch_with_classes_and_bank(torch, T):
-    """A ragged batch scored with a small bank (4 classes of 6 components): groups are (image, class)."""
+    """A ragged batch scored with a small bank (4 classes of 6 components): groups are (image, class). Both NMS paths:
+    pairwise overlap masks (up to 16,384 detections) and the per-group walk above that."""
     ctx = T.tdpm_create(0)
     rng = np.random.default_rng(61)
     comps = []
@@ -71,6 +72,14 @@ def test_nms_batch_with_classes_and_bank(torch, T):
         want = _oracle_keep(dets, model, synth.LAMBDA, cls, overlap, 4.0)
         assert 0 < len(want) < len(dets)
         np.testing.assert_array_equal(kept, dets[want])
+    # more than 16,384 detections: each group's CTA walks its boxes itself instead of the pairwise masks
+    all_scores = np.sort(T.tdpm_detect(ctx, sid, -np.inf)["score"])
+    tau_low = float(all_scores[-20000])
+    dets = T.tdpm_detect(ctx, sid, tau_low).copy()
+    assert len(dets) > 16384
+    kept = T.tdpm_detect_nms(ctx, sid, tau_low, classes, 0.5, 4.0)
+    want = _oracle_keep(dets, model, synth.LAMBDA, classes, 0.5, 4.0)
+    np.testing.assert_array_equal(kept, dets[want])
     # nothing above the threshold: nothing kept
     assert len(T.tdpm_detect_nms(ctx, sid, 1e9, classes, 0.5, 4.0)) == 0
     with pytest.raises(T.TdpmError):
