@@ -416,14 +416,6 @@ tdpm_status hog_prepare(tdpm_ctx *ctx, cudaStream_t s, size_t need, char *&base)
     return TDPM_OK;
 }
 
-// Scratch and tables for a list of float images (with their device buffers already placed) and levels, then the
-// gradient and level launches. imgs[i].img must be set; mag, bin, hist and tables are placed here.
-struct HogRun {
-    std::vector<HogImage> imgs;
-    std::vector<HogLevelJob> lv;  // img index in .h (temporarily), out set
-    std::vector<int> lv_img;
-};
-
 }  // namespace
 
 }  // namespace tdpm

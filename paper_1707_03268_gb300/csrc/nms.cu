@@ -300,7 +300,7 @@ size_t align256z(size_t b) { return (b + 255) & ~(size_t)255; }
 namespace {
 // Flagged records per block of NMS_CBLOCK.
 __global__ void __launch_bounds__(NMS_CBLOCK) compact_count_kernel(const uint8_t *__restrict__ kept, long long n,
-                                                                     int *__restrict__ bcount)
+                                                                   int *__restrict__ bcount)
 {
     __shared__ int ws[NMS_CBLOCK / 32];
     const long long i = (long long)blockIdx.x * NMS_CBLOCK + threadIdx.x;
@@ -317,9 +317,9 @@ __global__ void __launch_bounds__(NMS_CBLOCK) compact_count_kernel(const uint8_t
 
 // The flagged records of each block at the block's offset, in record order.
 __global__ void __launch_bounds__(NMS_CBLOCK) compact_write_kernel(const tdpm_detection *__restrict__ rec,
-                                                               const uint8_t *__restrict__ kept, long long n,
-                                                               const int *__restrict__ boff,
-                                                               tdpm_detection *__restrict__ out)
+                                                                   const uint8_t *__restrict__ kept, long long n,
+                                                                   const int *__restrict__ boff,
+                                                                   tdpm_detection *__restrict__ out)
 {
     __shared__ int ws[NMS_CBLOCK / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
