@@ -49,6 +49,24 @@ RANK_SWEEP = {"per_filter": (4, 8, 16, 24, 32, 36), "joint": (16, 32, 64, 128, 2
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "bf16x3": 3}
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over the ranks (one all-reduce; x itself for one rank). The timed region's length is the slowest
+    rank's, so whole-job rates divide by this."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed (replicas: the same count on each) over the slowest
+    rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -835,15 +853,11 @@ def main():
             tdpm.tdpm_profile_enable(ctx, False)
             stages = tdpm.tdpm_profile_read(ctx)
         ms = [a.elapsed_time(b) for a, b in ev]
-        total_ms = sum(ms)
-        if world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(ms), world)
         return {"ms": ms, "total_ms": total_ms, "wall_s": wall, "launches": launches, "stages": stages}
 
     def rate(run):
-        return len(run["ms"]) * world / (run["total_ms"] / 1e3)
+        return job_rate(len(run["ms"]), world, run["total_ms"])
 
     rep = None
     if form == tdpm.FORM_DECOMPOSED:
@@ -921,12 +935,8 @@ def main():
         n_det = len(e2e_step(args.warmup + i))
     ev1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": args.steps * world / (e2e_ms / 1e3), "unit": "images/s", "h2d_bytes_per_step": h2d,
+    e2e_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    e2e = {"value": job_rate(args.steps, world, e2e_ms), "unit": "images/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": n_det * tdpm.DETECTION_DTYPE.itemsize + 8,
            "note": "the next image's pyramid transfer overlaps the current image's scoring (two device buffers)"}
 
