@@ -3,10 +3,10 @@
 // (root, then parts); a part is tested at its anchor, (2y + vy, 2x + vx) on the level lambda below. Term r of filter
 // k at window phi is lambda_r * sum_{dy,dx,c} phi[dy][dx][c] a_r[dy] b_r[dx] c_r[c].
 //
-// One warp per hypothesis, lane = channel: the window of the filter under test is staged once in the warp's slice of
-// shared memory (filters of up to CASC_MAX_CELLS cells; larger ones read it from global memory), then every term is
-// one pass over the window (sum over cells of a[dy] b[dx] phi, per lane) and one butterfly reduction of c_r[c] times
-// that over the lanes. The exit is uniform across the warp. The thresholds come from the same device function run
+// One warp per hypothesis, lane = channel: every term is one pass over the window of the filter under test (sum over
+// cells of a[dy] b[dx] phi, per lane) and one butterfly reduction of c_r[c] times that over the lanes. The first term
+// reads the window from global memory; a hypothesis that survives it has the window staged in the warp's slice of
+// shared memory for the rest (filters of up to CASC_MAX_CELLS cells; larger ones keep reading global memory). The exit is uniform across the warp. The thresholds come from the same device function run
 // without exits at positive examples, so a positive's own partial sums are never below them.
 #include <algorithm>
 
@@ -28,18 +28,31 @@ __device__ __forceinline__ float warp_sum_all(float v)
 
 // Partial sums of one filter at one window, in the filter's term order, with an early exit when thr is not null.
 // Returns the number of terms evaluated; *pruned is set when a partial sum fell below its threshold. partial (lane
-// 0 writes; may be null) receives every evaluated partial sum.
-__device__ int casc_filter(const CascFilter &F, const float *__restrict__ win, int win_stride, const float *thr,
-                           float *partial, bool *pruned)
+// 0 writes; may be null) receives every evaluated partial sum. The first term reads the window from global memory
+// (most hypotheses stop there); a hypothesis that goes on has its window staged in the warp's shared memory first
+// (swin, when not null). The arithmetic is the same either way.
+__device__ int casc_filter(const CascFilter &F, const float *__restrict__ gwin, int gstride, float *swin,
+                           const float *thr, float *partial, bool *pruned)
 {
     const int lane = threadIdx.x & 31;
+    const float *win = gwin;
+    int stride = gstride;
     float p = 0.f;
     for (int q = 0; q < F.nterms; ++q) {
+        if (q == 1 && swin) {
+            __syncwarp();
+            for (int dy = 0; dy < F.h; ++dy)
+                for (int dx = 0; dx < F.w; ++dx)
+                    swin[(dy * F.w + dx) * 32 + lane] = __ldg(gwin + (size_t)dy * gstride + dx * 32 + lane);
+            __syncwarp();
+            win = swin;
+            stride = F.w * 32;
+        }
         const int r = F.order[q];
         float acc = 0.f;
         for (int dy = 0; dy < F.h; ++dy) {
             const float ay = __ldg(F.A + (size_t)dy * F.R + r);
-            const float *row = win + (size_t)dy * win_stride;
+            const float *row = win + (size_t)dy * stride;
             for (int dx = 0; dx < F.w; ++dx) acc = fmaf(ay * __ldg(F.B + (size_t)dx * F.R + r), row[dx * 32 + lane], acc);
         }
         const float v = warp_sum_all(__ldg(F.Ct + (size_t)r * 32 + lane) * acc);
@@ -80,20 +93,9 @@ __global__ void __launch_bounds__(CASC_WARPS * 32) cascade_kernel(CascArgs a)
                 break;
             }
             const float *gwin = L.data + ((size_t)y0 * L.W + x0) * 32;
-            const float *win = gwin;
-            int stride = L.W * 32;
-            if (F.h * F.w <= CASC_MAX_CELLS) {
-                __syncwarp();
-                for (int k = 0; k < F.h * F.w; ++k) {
-                    const int dy = k / F.w, dx = k - dy * F.w;
-                    mywin[k * 32 + lane] = __ldg(gwin + ((size_t)dy * L.W + dx) * 32 + lane);
-                }
-                __syncwarp();
-                win = mywin;
-                stride = F.w * 32;
-            }
             float *part = a.partials ? a.partials + ((size_t)i * a.max_slots + s) * a.max_terms : nullptr;
-            evaluated += casc_filter(F, win, stride, a.apply_thr ? F.thr : nullptr, part, &pruned);
+            evaluated += casc_filter(F, gwin, L.W * 32, F.h * F.w <= CASC_MAX_CELLS ? mywin : nullptr,
+                                     a.apply_thr ? F.thr : nullptr, part, &pruned);
         }
         if (lane == 0) {
             if (a.alive) a.alive[i] = pruned ? 0 : 1;
