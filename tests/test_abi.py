@@ -88,3 +88,28 @@ def test_header_struct_sizes_match_the_binding(tmp_path):
     got = {l.split()[0]: int(l.split()[1]) for l in out if l.strip()}
     for name, cls in pairs.items():
         assert got[name] == ctypes.sizeof(cls), name
+
+
+@pytest.mark.parametrize("h,w,sbin,lam", [(96, 128, 8, 10), (150, 200, 8, 10), (131, 90, 8, 5), (200, 260, 16, 4)])
+def test_hog_pyramid_shape_matches_the_oracle(lib_path, h, w, sbin, lam):
+    """The library's HOG pyramid plan (a host computation: level count, sizes, output bytes) against the level
+    structure of the oracle's pyramid on an image of the same size."""
+    import numpy as np
+
+    from oracle import hog as ohog
+    from paper_1707_03268_gb300 import tdpm
+
+    img = np.random.default_rng(h + w).integers(0, 256, size=(h, w, 3)).astype(np.float32)
+    want = [tuple(l.shape[:2]) for l in ohog.hog_pyramid(img, sbin=sbin, lam=lam, min_cells=8)]
+    shapes, nbytes = tdpm.tdpm_hog_pyramid_shape(h, w, sbin, lam, 8)
+    assert shapes == want
+    assert nbytes == sum(a * b for a, b in shapes) * 32 * 4
+
+
+def test_hog_pyramid_shape_rejects_small_images_and_bad_cells(lib_path):
+    from paper_1707_03268_gb300 import tdpm
+
+    with pytest.raises(tdpm.TdpmError):
+        tdpm.tdpm_hog_pyramid_shape(61, 900, 8, 10, 8)   # no root level has 8 cells on each side
+    with pytest.raises(tdpm.TdpmError):
+        tdpm.tdpm_hog_pyramid_shape(200, 200, 6, 10, 8)  # cell size not 4, 8 or 16
