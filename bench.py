@@ -17,8 +17,12 @@ detections to the host.
           for 1..20 classes of the bank; p50/p99 latency from submission to results
 
 Reported beside the headline: the full form in FP32 (the GPU baseline the decomposed form must beat) and in the same
-precision, detection agreement with the FP64 oracle on the same factors (parity), and a rank sweep of the detection
-agreement of the decomposed form with the full FP32 form (the accuracy the decomposition gives up).
+precision, detection agreement with the FP64 oracle on the same factors (parity), a rank sweep of the detection
+agreement of the decomposed form with the full FP32 form (the accuracy the decomposition gives up), the rank
+detection of Sec. 4 at several constants e, and (`post_processing`) the steps around the scoring path: NMS of the
+headline detections, the convolution-shortening cascade with thresholds from planted positives, and the HOG pyramid
+of a 500x375 8-bit image with image-to-detections throughput. The end-to-end leg (`e2e`) copies each image's pyramid
+from pinned host memory on a copy stream, overlapping the previous image's scoring.
 
 Under torchrun every rank scores its own replica of the image (images are independent: no data-path collective); the
 barrier and the max-over-ranks timing use the process group.
