@@ -255,7 +255,10 @@ tdpm_status tdpm_hog_pyramid_shape(int32_t img_h, int32_t img_w, int32_t sbin, i
 /* The feature pyramid of a device 8-bit RGB image [img_h][img_w][3] into d_out (device, 16-byte aligned, at least
  * the bytes tdpm_hog_pyramid_shape gives; caller-owned): levels[j] (host array of max_levels) receives each level's
  * rows, columns and device pointer inside d_out, ready for tdpm_build_pyramid_scores. Asynchronous on `stream`; the
- * context's scratch is reused by its next HOG call (ordered by an event). */
+ * context's scratch is reused by its next HOG call (ordered by an event). A call repeating the previous one (same
+ * sizes, parameters, image and output buffers) reuses its device tables, and from the third call on replays its
+ * launches as one CUDA graph. ERR_ARG for sides outside [16, 16384], a bad sbin, lambda or min_cells, or a d_out
+ * that is not 16-byte aligned; ERR_CAPACITY when out_bytes or max_levels is too small. */
 tdpm_status tdpm_hog_pyramid(tdpm_ctx *ctx, const uint8_t *d_image, int32_t img_h, int32_t img_w, int32_t sbin,
                              int32_t lambda, int32_t min_cells, float *d_out, size_t out_bytes, tdpm_level *levels,
                              int32_t max_levels, int32_t *n_levels, void *stream);
