@@ -422,10 +422,10 @@ def _class_taus(dets, n_comp, comps_per_class=6, q=99.0):
 def run_bank(args):
     """c3 / c4: the 20-class bank on one 1280x720 image or on a batch of 64 images. Every variant is timed (one batch
     call + detection readback per step); agreement of each with the full FP32 form under per-class thresholds; error
-    of sampled filter maps against the FP64 oracle."""
+    of sampled filter maps against the full FP32 form's (the parity of these forms with the FP64 oracle is the tests'
+    job)."""
     import torch
     from paper_1707_03268_gb300 import tdpm
-    from oracle import oracle as orc
 
     torch.cuda.set_device(0)
     wl = synth.config_c3() if args.workload == "c3" else synth.config_c4()
@@ -483,7 +483,24 @@ def run_bank(args):
             head = variants[0]
     rng = np.random.default_rng(0)
     filters = wl.model.filters()
-    sample_maps = [(int(rng.integers(0, len(filters))), None) for _ in range(12)]
+    # sampled filter maps of image 0 in the full FP32 form (itself checked against the FP64 oracle by the tests): the
+    # reference of each variant's map error
+    pyr0 = wl.pyramids[0]
+    sample_maps = []
+    sid = tdpm.tdpm_build_batch_scores(ctx, mid, dps[:1], tdpm.FORM_FULL, tdpm.PREC_FP32, stream)
+    for _ in range(12):
+        fid = int(rng.integers(0, len(filters)))
+        f = filters[fid]
+        js = [j for j in range(len(pyr0.levels)) if pyr0.levels[j].shape[0] >= f.shape[0] and
+              pyr0.levels[j].shape[1] >= f.shape[1]]
+        j = js[len(js) // 3]
+        try:
+            ref = tdpm.tdpm_get_maps(ctx, sid, tdpm.MAP_FILTER_SCORE, fid, j, image=0).astype(np.float64)
+        except tdpm.TdpmError:
+            continue  # this filter's role does not score this level
+        if ref.size:
+            sample_maps.append((fid, j, ref))
+    tdpm.tdpm_release(ctx, sid)
     results = {}
     ref_keys = None
     for form_s, prec_s, r, mode in variants:
@@ -506,32 +523,19 @@ def run_bank(args):
         if ref_keys is None:
             ref_keys = k
         label = vlabel((form_s, prec_s, r, mode))
-        # error of sampled filter maps (image 0) against the FP64 oracle: the exact filters, and for the decomposed
-        # form also the filters rebuilt from the library's factors (parity of the arithmetic, same factors)
+        # error of the sampled filter maps (image 0) against the full FP32 form's: what the precision and, for the
+        # decomposed forms, the decomposition give up
         sid = tdpm.tdpm_build_batch_scores(ctx, mid, dps[:1], form, prec, stream)
-        rebuilt = factor_filters(tdpm, ctx, mid) if form == tdpm.FORM_DECOMPOSED else None
-        err_exact, err_same = 0.0, 0.0
-        pyr0 = wl.pyramids[0]
-        for fid, _ in sample_maps:
-            f = filters[fid]
-            js = [j for j in range(len(pyr0.levels)) if pyr0.levels[j].shape[0] >= f.shape[0] and
-                  pyr0.levels[j].shape[1] >= f.shape[1]]
-            j = js[len(js) // 3]
+        err_full = 0.0
+        for fid, j, ref in sample_maps:
             got = tdpm.tdpm_get_maps(ctx, sid, tdpm.MAP_FILTER_SCORE, fid, j, image=0)
-            if got.size == 0:
-                continue
-            ref = orc.correlate(pyr0.levels[j], f)
-            err_exact = max(err_exact, float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30)))
-            if rebuilt is not None:
-                ref2 = orc.correlate(pyr0.levels[j], rebuilt[fid])
-                err_same = max(err_same, float(np.max(np.abs(got - ref2)) / max(np.max(np.abs(ref2)), 1e-30)))
+            err_full = max(err_full, float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30)))
         tdpm.tdpm_release(ctx, sid)
         n_img = len(dps)
         results[label] = {"images_per_s": steps * n_img / (run["ms_sum"] / 1e3), "p50_ms_per_step": run["p50"],
                           "p99_ms_per_step": run["p99"], "detections": len(k),
                           "agreement_with_full_fp32": len(k & ref_keys) / max(1, len(k | ref_keys)),
-                          "max_rel_error_vs_fp64_exact_filters": err_exact,
-                          "max_rel_error_vs_fp64_same_factors": err_same if rebuilt is not None else None,
+                          "max_rel_error_vs_full_fp32_maps": err_full,
                           "stages_ms_per_step": stages, "decomposition_report": rep}
     hl = vlabel(head)
     h = results[hl]
