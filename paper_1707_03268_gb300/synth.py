@@ -211,7 +211,9 @@ def plant_objects(rng: np.random.Generator, pyramid: Pyramid, model: Model,
     """A copy of ``pyramid`` with an object instance at each placement (component, root level j, y, x): the root
     window at (y, x) on level j and every part window at its anchor (2y + vy, 2x + vx) on level j - lam are set to
     0.1 + 0.1 * strength * f / max|f| plus N(0, noise) per entry, clipped to [0, 0.2] (features that line up with
-    the filter f). Placements must be valid root positions (the root and every anchored part inside their levels)."""
+    the filter f). Windows are written root first, then the parts in model order, so where part windows overlap the
+    later part's pattern wins. Placements must be valid root positions (the root and every anchored part inside their
+    levels)."""
     levels = [l.copy() for l in pyramid.levels]
     for (c, j, y, x) in placements:
         comp = model.components[c]

@@ -38,3 +38,43 @@ def test_nms_division_free_rule_matches_the_division():
             assert fast == exact, (inter, area, overlap)
             n_band += int(abs(inter - overlap * area) <= overlap * area * 2.0 ** -50)
     assert n_band > 0  # the band (where the division decides) was exercised
+
+
+def test_planted_objects_line_up_with_their_filters():
+    """The cascade's positive examples: a planted instance raises the root's response at the placement, and the last
+    part's at its anchor (part windows may overlap; the later one is written over the earlier), far above the
+    background, and touches no other level."""
+    import pytest
+
+    from oracle import oracle as orc
+    from paper_1707_03268_gb300 import synth
+
+    rng = np.random.default_rng(4)
+    model = synth.Model(synth.make_dpm_class(np.random.default_rng(5))[:1])
+    comp = model.components[0]
+    base = synth.make_pyramid(rng, synth.pyramid_sizes(160, 200), synth.LAMBDA)
+    j = synth.LAMBDA + 2
+    y, x = 3, 4
+    planted = synth.plant_objects(rng, base, model, [(0, j, y, x)])
+    root_b = orc.correlate(base.levels[j], comp.root)
+    root_p = orc.correlate(planted.levels[j], comp.root)
+    assert root_p[y, x] > root_b[y, x] + 1.0 and root_p[y, x] > np.max(root_b) + 1.0
+    p = comp.parts[-1]
+    py, px = 2 * y + p.anchor[0], 2 * x + p.anchor[1]
+    s_b = orc.correlate(base.levels[j - synth.LAMBDA], p.filt)
+    s_p = orc.correlate(planted.levels[j - synth.LAMBDA], p.filt)
+    assert s_p[py, px] > np.max(s_b) + 0.5
+    untouched = [k for k in range(len(base.levels)) if k not in (j, j - synth.LAMBDA)]
+    assert all(np.array_equal(base.levels[k], planted.levels[k]) for k in untouched)
+    assert all(0.0 <= l.min() and l.max() <= 0.2 for l in planted.levels)
+    with pytest.raises(AssertionError):
+        synth.plant_objects(rng, base, model, [(0, j, 10 ** 4, 0)])
+
+
+def test_synthetic_images_are_seeded_8bit_rgb():
+    from paper_1707_03268_gb300 import synth
+
+    a = synth.make_image(np.random.default_rng(1), 37, 53)
+    b = synth.make_image(np.random.default_rng(1), 37, 53)
+    assert a.dtype == np.uint8 and a.shape == (37, 53, 3) and np.array_equal(a, b)
+    assert len(np.unique(a)) > 100  # structure and noise, not a flat image
