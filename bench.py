@@ -74,36 +74,72 @@ def job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: 20 at c3, 2000 at c2)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tdpm", choices=["tdpm", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c2", "c3", "c4", "c5"])
     ap.add_argument("--form", default=None, choices=["decomposed", "full"])
     ap.add_argument("--precision", default=None, choices=sorted(PRECISIONS))
-    ap.add_argument("--rank", type=int, default=None, help="CP rank per filter (per_filter) or per shape group (joint)")
+    ap.add_argument("--rank", type=int, default=None,
+                    help="one CP rank for every filter (per_filter) or per shape group (joint); default: the rank "
+                         "ladder (the cheapest root/part rank pair whose detections agree >= 99.5%% with full FP32)")
+    ap.add_argument("--ranks", default=None, help="per_filter: root and part ranks S,T (Sec. 5's (S, T) pairs)")
     ap.add_argument("--mode", default=None, choices=["per_filter", "joint"])
+    ap.add_argument("--als-iters", type=int, default=300, help="ALS cycles per decomposition")
     ap.add_argument("--variants", default=None,
-                    help="c3/c4: comma-separated subset of the variants to run, e.g. full_bf16,full_fp8")
+                    help="c4: comma-separated subset of the variants to run, e.g. full_bf16,full_fp8")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="c5: length of the arrival stream")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="c5: mean arrival rate (requests/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fuse", action="store_true",
                     help="decomposed per-filter form: channel stage and separable passes as two launches")
     ap.add_argument("--no-compare", action="store_true", help="skip the full-form comparison runs")
-    ap.add_argument("--no-sweep", action="store_true", help="skip the rank sweep")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the rank sweeps and the post-processing steps")
     args = ap.parse_args()
-    # per-workload defaults: the per-filter decomposition on the one-class model; the joint one on the class banks
-    dflt = {"c2": ("decomposed", "bf16x3", 8, "per_filter"), "c3": ("decomposed", "bf16", 32, "joint"),
-            "c4": ("decomposed", "bf16", 8, "joint"), "c5": ("decomposed", "bf16", 8, "joint")}[args.workload]
-    for k, v in zip(("form", "precision", "rank", "mode"), dflt):
+    # per-workload defaults: the per-filter decomposition in split BF16 (the precision that keeps >= 99.5% agreement)
+    dflt = {"c2": ("decomposed", "bf16x3", None, "per_filter"), "c3": ("decomposed", "bf16x3", None, "per_filter"),
+            "c4": ("decomposed", "bf16x3", None, "per_filter"), "c5": ("decomposed", "bf16x3", None, "per_filter")}
+    for k, v in zip(("form", "precision", "rank", "mode"), dflt[args.workload]):
         if getattr(args, k) is None:
             setattr(args, k, v)
+    if args.steps is None:
+        args.steps = {"c2": 2000, "c3": 20, "c4": 5, "c5": 0}[args.workload]
+    if args.mode == "joint" and args.rank is None:
+        args.rank = 32
     return args
+
+
+def load_taus(workload: str, n_comp: int) -> np.ndarray:
+    """Per-component detection thresholds from tests/golden/thresholds.json (written from the FP64 oracle's full-form
+    scores): one threshold for the one-class model (c2), one per class of six components for the bank (c3)."""
+    with open(os.path.join(ROOT, "tests", "golden", "thresholds.json")) as f:
+        g = json.load(f)
+    if workload == "c2":
+        return np.full(n_comp, float(g["c2"]["tau"]), dtype=np.float32)
+    per = int(g["c3"]["components_per_class"])
+    return np.repeat(np.asarray(g["c3"]["tau_per_class"], dtype=np.float32), per)[:n_comp]
 
 
 def load_tau():
     with open(os.path.join(ROOT, "tests", "golden", "thresholds.json")) as f:
         return float(json.load(f)["c2"]["tau"])
+
+
+# Sec. 5's (S, T) pairs: root rank S, part rank T; the ladder runs from the cheapest (the parts dominate the cost) and
+# stops at the first pair whose detections agree >= 99.5% with the full FP32 form. S = 64 is the exact slice form of
+# every root shape here (h*w <= 55).
+RANK_LADDER = ((16, 16), (24, 24), (64, 24), (32, 32), (64, 32), (64, 36))
+AGREEMENT_BAR = 0.995
+DEFAULT_PAIR = (64, 36)  # the batch and serving workloads: the (S, T) pair the bank's ladder reaches the bar with
+
+
+def filter_ranks(model, S: int, T: int) -> np.ndarray:
+    """Per-filter ranks in model order (root, then parts, per component), capped at the exact rank h*w."""
+    out = []
+    for c in model.components:
+        out.append(min(S, c.root.shape[0] * c.root.shape[1]))
+        out.extend(min(T, p.filt.shape[0] * p.filt.shape[1]) for p in c.parts)
+    return np.asarray(out, dtype=np.int32)
 
 
 # ------------------------------------------------------------------------------------------------ clocks
@@ -178,11 +214,16 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool, fuse
     sizes = pyr.sizes
     lam = pyr.lam
     L = len(sizes)
+    # rank: one rank for every filter (or the joint rank), or per-filter ranks in model order
+    per_rank = None if np.isscalar(rank) or rank is None else [int(r) for r in rank]
     groups = {}
+    fid = 0
     for comp in wl.model.components:
-        groups.setdefault((0,) + comp.root.shape[:2], []).append(comp.root)
-        for p in comp.parts:
-            groups.setdefault((1,) + p.filt.shape[:2], []).append(p.filt)
+        for f in [comp.root] + [p.filt for p in comp.parts]:
+            role = 0 if f is comp.root else 1
+            r_f = per_rank[fid] if per_rank is not None else (rank or 0)
+            groups.setdefault((role,) + f.shape[:2], []).append(min(r_f, f.shape[0] * f.shape[1]))
+            fid += 1
     tc = precision in ("bf16", "bf16x3", "fp8")
     fb = {"fp32": 4, "bf16": 2, "bf16x3": 4, "fp8": 1}[precision]  # feature bytes per channel read by the correlation
     corr = "corr_tc" if tc else "corr_f32"
@@ -197,20 +238,21 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool, fuse
         if joint:
             R = min(rank, h * w * 32)       # the joint form is exact from h*w*32 shared terms on
         else:
-            R = K * min(rank, h * w)        # per filter: exact from h*w terms (the slices) on
+            R = sum(fl)                     # per filter: exact from h*w terms (the slices) on
         js = range(lam, L) if role == 0 else range(0, L - lam)
         for j in js:
             H, W = sizes[j]
             Ho, Wo = H - h + 1, W - w + 1
             if Ho <= 0 or Wo <= 0:
                 continue
-            if form == "full":
+            # a per-filter group at its exact rank (every filter h*w terms) is scored by the full form's kernel
+            if form == "full" or (not joint and min(fl) >= h * w):
                 out[corr][0] += H * W * 32 * fb + K * Ho * Wo * 4
                 out[corr][1] += 2 * h * w * 32 * K * Ho * Wo
             elif (fused and not joint and precision in ("bf16", "bf16x3") and (h, w) in FUSED_SHAPES
-                  and min(rank, h * w) <= 64):
+                  and max(fl) <= 64):
                 out["zsep_tc"][0] += H * W * 32 * fb + K * Ho * Wo * 4
-                out["zsep_tc"][1] += 2 * K * Ho * Wo * (R // K) * (h + w + 1)
+                out["zsep_tc"][1] += 2 * Ho * Wo * R * (h + w + 1)
             else:
                 out[zproj][0] += H * W * 32 * fb + R * H * W * 4
                 out[zproj][1] += 2 * 32 * R * H * W
@@ -222,8 +264,8 @@ def stage_bytes(wl, pyr, form: str, precision: str, rank: int, joint: bool, fuse
                     out["recomb_tc"][1] += 2 * K * R * Ho * Wo
                 else:
                     out["sep"][0] += R * H * W * 4 + K * Ho * Wo * 4
-                    per_filter_terms = R if joint else R // K
-                    out["sep"][1] += 2 * K * Ho * Wo * per_filter_terms * (h + w + 1)
+                    terms = K * R if joint else R  # (filter, term) pairs
+                    out["sep"][1] += 2 * Ho * Wo * terms * (h + w + 1)
     for comp in wl.model.components:
         h0, w0 = comp.root.shape[:2]
         for j in range(lam, L):
@@ -276,9 +318,15 @@ def measured_traffic(workload: str, form: str, precision: str, mode: str, stage:
     return e.get("dram_bytes_per_image")
 
 
-def fp32_alu_peak_tflops(sm_mhz: float) -> float:
-    """FP32 FMA roofline: 152 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def sm_count() -> int:
+    """Streaming multiprocessors of device 0, read from the device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(0).multi_processor_count)
+
+
+def fp32_alu_peak_tflops(sm_mhz: float, sms: int) -> float:
+    """FP32 FMA roofline: SMs x 128 FP32 lanes x 2 flops per FMA x SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 TENSOR_STAGES = ("corr_tc", "zproj_tc", "recomb_tc")
@@ -297,7 +345,7 @@ def stage_roofline(name, ms_per_image, launches_per_image, model, peaks, sm_mhz)
     if name in TENSOR_STAGES:
         cand.append(("tensor", f / (tp * 1e12)))
     elif name in ALU_STAGES:
-        cand.append(("alu", f / (fp32_alu_peak_tflops(sm_mhz) * 1e12)))
+        cand.append(("alu", f / (fp32_alu_peak_tflops(sm_mhz, sm_count()) * 1e12)))
     bound = max(cand, key=lambda c: c[1])[0]
     out = {"kernel": name, "bound": bound, "launches_per_image": launches_per_image, "ms_per_image": ms_per_image,
            "traffic": None, "algorithmic_bytes_per_image": b, "algorithmic_flops_per_image": f}
@@ -308,14 +356,20 @@ def stage_roofline(name, ms_per_image, launches_per_image, model, peaks, sm_mhz)
                    peak_source="MEASURED_PEAKS.json bf16_tflops burst (of measured)" if "bf16_tflops" in peaks
                    else "fallback 1900 TFLOP/s")
     else:
-        pk = fp32_alu_peak_tflops(sm_mhz)
+        sms = sm_count()
+        pk = fp32_alu_peak_tflops(sm_mhz, sms)
         out.update(achieved=f / s / 1e12, peak=pk, unit="TFLOP/s",
-                   peak_source="derived: 152 SM x 128 FP32 lanes x 2 flop x median SM clock under load")
+                   peak_source=f"derived: {sms} SMs (read from the device) x 128 FP32 lanes x 2 flop x median SM "
+                               f"clock under load ({sm_mhz:.0f} MHz)")
     out["frac"] = out["achieved"] / out["peak"]
     return out
 
 
 # ------------------------------------------------------------------------------------------------ oracle legs
+def workload_of(name: str):
+    return {"c2": synth.config_c2, "c3": synth.config_c3, "c4": synth.config_c3, "c5": synth.config_c3}[name]()
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle on the host cores, same workload and metric (rank 0 of N only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -323,15 +377,16 @@ def run_reference(args):
         return
     from oracle import oracle as orc
 
-    wl = {"c2": synth.config_c2, "c3": synth.config_c3, "c4": synth.config_c3, "c5": synth.config_c3}[args.workload]()
+    wl = workload_of(args.workload)
     pyr = wl.pyramids[0]
     n_comp = len(wl.model.components)
-    tau = load_tau()
+    taus = load_taus("c2" if args.workload == "c2" else "c3", n_comp)
 
     def one_step(i):
         # one component of the model over the whole pyramid: 1/n_comp of an image
-        sub = synth.Model([wl.model.components[i % n_comp]])
-        orc.detect(orc.score_pyramid(sub, pyr), tau)
+        c = i % n_comp
+        sub = synth.Model([wl.model.components[c]])
+        orc.detect(orc.score_pyramid(sub, pyr), float(taus[c]))
 
     for i in range(args.warmup):
         one_step(i)
@@ -352,26 +407,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_oracle(wl, filters, gpu_keys, tau, budget_s: float = 15.0):
-    """The FP64 oracle as it stands, on this host's cores: the same whole image with the same filters (rebuilt from
-    the library's FP64 factors for the decomposed form), repeated within a time budget. Its detections also give the
-    parity agreement of the GPU's detections."""
+def cpu_baseline_oracle(wl, filters, gpu_dets, taus, budget_s: float = 15.0):
+    """The FP64 oracle as it stands, on this host's cores: the model's components one after another over the whole
+    pyramid (with the GPU run's filters, rebuilt from the library's FP64 factors for the decomposed form) until the
+    time budget is spent. Rate = the share of an image scored / time. Its detections give the parity agreement of
+    the GPU's detections of the same components."""
     from oracle import oracle as orc
     pyr = wl.pyramids[0]
+    comps = wl.model.components
+    fid0, starts = 0, []
+    for c in comps:
+        starts.append(fid0)
+        fid0 += 1 + len(c.parts)
     n = 0
+    ok = set()
     t0 = time.perf_counter()
-    dets = None
-    while True:
-        dets = orc.detect(orc.score_pyramid(wl.model, pyr, filters=filters), tau)
+    while n < len(comps):
+        c = comps[n]
+        sub = synth.Model([c])
+        fs = None if filters is None else filters[starts[n]:starts[n] + 1 + len(c.parts)]
+        for d in orc.detect(orc.score_pyramid(sub, pyr, filters=fs), float(taus[n])):
+            ok.add((n,) + tuple(d[1:4]))
         n += 1
-        if time.perf_counter() - t0 >= budget_s or n >= 20:
+        if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    ok = set(d[:4] for d in dets)
-    return {"value": n / dt, "unit": "images/s", "cores": orc.num_threads(), "kind": "oracle",
-            "sample": f"{n} whole 500x375 images (36 levels, 54 filters), FP64, same filters as the GPU run",
-            "parity_agreement_with_gpu": len(ok & gpu_keys) / max(1, len(ok | gpu_keys)),
-            "oracle_detections": len(ok)}
+    gk = set(k for k in gpu_dets if k[0] < n)
+    return {"value": (n / len(comps)) / dt, "unit": "images/s", "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{n} of the {len(comps)} components over the whole {len(pyr.levels)}-level pyramid "
+                      f"({n}/{len(comps)} of an image), FP64, the GPU run's filters",
+            "parity_agreement_with_gpu": len(ok & gk) / max(1, len(ok | gk)), "oracle_detections": len(ok),
+            "components_compared": n}
 
 
 def factor_filters(tdpm, ctx, mid):
@@ -420,15 +486,16 @@ def _class_taus(dets, n_comp, comps_per_class=6, q=99.0):
 
 
 def run_bank(args):
-    """c3 / c4: the 20-class bank on one 1280x720 image or on a batch of 64 images. Every variant is timed (one batch
-    call + detection readback per step); agreement of each with the full FP32 form under per-class thresholds; error
-    of sampled filter maps against the full FP32 form's (the parity of these forms with the FP64 oracle is the tests'
-    job)."""
+    """c4: the 20-class bank on a batch of 64 images. Every variant is timed (one batch call + detection readback per
+    step); agreement of each with the full FP32 form under per-class thresholds; error of sampled filter maps against
+    the full FP32 form's and against the FP64 oracle (the filters rebuilt from the library's factors for the decomposed
+    forms)."""
     import torch
+    from oracle import oracle as orc
     from paper_1707_03268_gb300 import tdpm
 
     torch.cuda.set_device(0)
-    wl = synth.config_c3() if args.workload == "c3" else synth.config_c4()
+    wl = synth.config_c4()
     n_comp = len(wl.model.components)
     ctx = tdpm.tdpm_create(0)
     tdpm.tdpm_set_fusion(ctx, not args.no_fuse)
@@ -461,21 +528,19 @@ def run_bank(args):
     taus = _class_taus(allp, n_comp)
     del allp
 
+    S, Tr = (int(v) for v in args.ranks.split(",")) if args.ranks else DEFAULT_PAIR
+    pair = f"{S}/{Tr}"
     variants = [("full", "fp32", None, None), ("full", "bf16", None, None), ("full", "bf16x3", None, None),
-                ("full", "fp8", None, None)]
-    if args.workload == "c3":
-        variants += [("decomposed", "bf16", r, "joint") for r in (8, 32, 128)]
-        variants += [("decomposed", "bf16x3", 32, "joint"), ("decomposed", "bf16", 8, "per_filter")]
-    else:
-        variants += [("decomposed", "bf16", 8, "joint"), ("decomposed", "bf16x3", 8, "joint")]
-    variants += [("decomposed", "bf16x3", 8, "per_filter")]
-    head = (args.form, args.precision, args.rank if args.form == "decomposed" else None,
-            args.mode if args.form == "decomposed" else None)
+                ("full", "fp8", None, None), ("decomposed", "bf16x3", pair, "per_filter"),
+                ("decomposed", "bf16", pair, "per_filter"), ("decomposed", "bf16", 8, "joint")]
+    head = ("decomposed", "bf16x3", pair, "per_filter") if args.form == "decomposed" and args.mode == "per_filter" \
+        else (args.form, args.precision, args.rank if args.form == "decomposed" else None,
+              args.mode if args.form == "decomposed" else None)
     if head not in variants:
         variants.append(head)
 
     def vlabel(v):
-        return f"{v[0]}_{v[1]}" + (f"_{v[3]}_r{v[2]}" if v[2] else "")
+        return f"{v[0]}_{v[1]}" + (f"_{v[3]}_r{str(v[2]).replace('/', '_')}" if v[2] else "")
     if args.variants:
         keep = set(args.variants.split(","))
         variants = [v for v in variants if vlabel(v) in keep]
@@ -499,7 +564,9 @@ def run_bank(args):
         except tdpm.TdpmError:
             continue  # this filter's role does not score this level
         if ref.size:
-            sample_maps.append((fid, j, ref))
+            # the FP64 oracle's map of the exact filter (what every form's error is measured against)
+            ref64 = orc.correlate(pyr0.levels[j], f.astype(np.float64))
+            sample_maps.append((fid, j, ref, ref64))
     tdpm.tdpm_release(ctx, sid)
     results = {}
     ref_keys = None
@@ -509,8 +576,12 @@ def run_bank(args):
         rep = None
         if form == tdpm.FORM_DECOMPOSED:
             t0 = time.perf_counter()
-            rep = tdpm.tdpm_decompose(ctx, mid, r, tdpm.DECOMP_JOINT if mode == "joint" else tdpm.DECOMP_PER_FILTER,
-                                      max_iters=30 if mode == "joint" else 100, seed=1)
+            if mode == "joint":
+                rep = tdpm.tdpm_decompose(ctx, mid, r, tdpm.DECOMP_JOINT, max_iters=30, seed=1)
+            else:
+                rs, rt = (int(v) for v in str(r).split("/"))
+                rep = tdpm.tdpm_decompose_ranks(ctx, mid, filter_ranks(wl.model, rs, rt), max_iters=args.als_iters,
+                                                seed=1)
             rep["seconds"] = time.perf_counter() - t0
         run = _timed_steps(torch, lambda: detections(form, prec, taus), steps, warmup, flush, stream)
         k = keys(run["last"])
@@ -526,16 +597,24 @@ def run_bank(args):
         # error of the sampled filter maps (image 0) against the full FP32 form's: what the precision and, for the
         # decomposed forms, the decomposition give up
         sid = tdpm.tdpm_build_batch_scores(ctx, mid, dps[:1], form, prec, stream)
-        err_full = 0.0
-        for fid, j, ref in sample_maps:
-            got = tdpm.tdpm_get_maps(ctx, sid, tdpm.MAP_FILTER_SCORE, fid, j, image=0)
-            err_full = max(err_full, float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-30)))
+        rebuilt = factor_filters(tdpm, ctx, mid) if form == tdpm.FORM_DECOMPOSED else None
+        err_full = err64 = err64_same = 0.0
+        for fid, j, ref, ref64 in sample_maps:
+            got = tdpm.tdpm_get_maps(ctx, sid, tdpm.MAP_FILTER_SCORE, fid, j, image=0).astype(np.float64)
+            scale = max(np.max(np.abs(ref64)), 1e-30)
+            err_full = max(err_full, float(np.max(np.abs(got - ref)) / scale))
+            err64 = max(err64, float(np.max(np.abs(got - ref64)) / scale))
+            if rebuilt is not None:
+                same = orc.correlate(pyr0.levels[j], rebuilt[fid])
+                err64_same = max(err64_same, float(np.max(np.abs(got - same)) / scale))
         tdpm.tdpm_release(ctx, sid)
         n_img = len(dps)
         results[label] = {"images_per_s": steps * n_img / (run["ms_sum"] / 1e3), "p50_ms_per_step": run["p50"],
                           "p99_ms_per_step": run["p99"], "detections": len(k),
                           "agreement_with_full_fp32": len(k & ref_keys) / max(1, len(k | ref_keys)),
                           "max_rel_error_vs_full_fp32_maps": err_full,
+                          "max_rel_error_vs_fp64_oracle_exact_filters": err64,
+                          "max_rel_error_vs_fp64_oracle_same_factors": err64_same if rebuilt is not None else None,
                           "stages_ms_per_step": stages, "decomposition_report": rep}
     hl = vlabel(head)
     h = results[hl]
@@ -571,9 +650,15 @@ def run_serve(args):
     bank = tdpm.tdpm_load_model(ctx, synth.Model(comps))
     form = tdpm.FORM_FULL if args.form == "full" else tdpm.FORM_DECOMPOSED
     prec = PRECISIONS[args.precision]
+    ranks_used = None
     if form == tdpm.FORM_DECOMPOSED:
-        tdpm.tdpm_decompose(ctx, bank, args.rank, tdpm.DECOMP_JOINT if args.mode == "joint" else tdpm.DECOMP_PER_FILTER,
-                            max_iters=30, seed=1)
+        if args.mode == "joint":
+            tdpm.tdpm_decompose(ctx, bank, args.rank, tdpm.DECOMP_JOINT, max_iters=30, seed=1)
+        else:
+            ranks_used = (tuple(int(v) for v in args.ranks.split(",")) if args.ranks
+                          else (args.rank, args.rank) if args.rank else DEFAULT_PAIR)
+            tdpm.tdpm_decompose_ranks(ctx, bank, filter_ranks(synth.Model(comps), *ranks_used),
+                                      max_iters=args.als_iters, seed=1)
     sizes = ((480, 640), (720, 1280), (1080, 1920))
     pyrs = {hw: tdpm.DevicePyramid([torch.from_numpy(l).cuda()
                                     for l in synth.make_pyramid(rng, synth.pyramid_sizes(*hw), synth.LAMBDA).levels],
@@ -630,7 +715,9 @@ def run_serve(args):
                        "requests": len(reqs), "warmup_requests_excluded": n_warm, "sizes": [f"{w}x{h}" for h, w in sizes],
                        "classes_per_request": "U{1..20} distinct of a 20-class bank (component subsets of one model)",
                        "form": args.form, "precision": args.precision,
-                       "rank": args.rank if form == tdpm.FORM_DECOMPOSED else None,
+                       "rank": (args.rank if args.mode == "joint" else None) if form == tdpm.FORM_DECOMPOSED else None,
+                       "rank_root_S": ranks_used[0] if ranks_used else None,
+                       "rank_part_T": ranks_used[1] if ranks_used else None,
                        "decomposition": args.mode if form == tdpm.FORM_DECOMPOSED else None,
                        "server": {"max_batch_images": 16, "max_inflight": 3, "max_wait_us": 500},
                        "tau": tau},
@@ -782,7 +869,7 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload in ("c3", "c4"):
+    if args.workload == "c4":
         run_bank(args)
         return
     if args.workload == "c5":
@@ -803,9 +890,10 @@ def main():
     prec = PRECISIONS[args.precision]
     joint = args.mode == "joint"
     dmode = tdpm.DECOMP_JOINT if joint else tdpm.DECOMP_PER_FILTER
-    wl = synth.config_c2()
+    wl = workload_of(args.workload)
     pyr = wl.pyramids[0]
-    tau = load_tau()
+    n_comp = len(wl.model.components)
+    taus = load_taus(args.workload, n_comp)
     ctx = tdpm.tdpm_create(local)
     tdpm.tdpm_set_fusion(ctx, not args.no_fuse)
     mid = tdpm.tdpm_load_model(ctx, wl.model)
@@ -819,17 +907,21 @@ def main():
     dp = tdpm.DevicePyramid(levels, pyr.lam)
     stream = torch.cuda.current_stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    cap = 1 << 16
+    cap = 1 << 20
     det_buf = pinned_records(torch, tdpm, cap)
+    tau_rows = np.ascontiguousarray(taus[None, :])
 
-    def step(f, p):
-        sid = tdpm.tdpm_build_pyramid_scores(ctx, mid, dp, f, p, stream)
-        dets = tdpm.tdpm_detect(ctx, sid, tau, capacity=cap, stream=stream, out=det_buf)
+    def step(f, p, pyramid=None):
+        sid = tdpm.tdpm_build_pyramid_scores(ctx, mid, pyramid or dp, f, p, stream)
+        dets = tdpm.tdpm_detect_thresholds(ctx, sid, tau_rows, capacity=cap, stream=stream, out=det_buf)
         tdpm.tdpm_release(ctx, sid)
         return dets
 
     def keys(d):
         return set(zip(d["component"].tolist(), d["level"].tolist(), d["y"].tolist(), d["x"].tolist()))
+
+    def agree(a, b):
+        return len(a & b) / max(1, len(a | b))
 
     def timed(f, p, steps, warmup, prof=False):
         for _ in range(warmup):
@@ -847,7 +939,7 @@ def main():
             dist.barrier()
         t0 = time.perf_counter()
         for i in range(steps):
-            flush.zero_()  # the pyramid is smaller than L2: evict it between steps (outside the events)
+            flush.zero_()  # evict the pyramid and the arena from L2 between steps (outside the events)
             ev[i][0].record(stream)
             step(f, p)
             ev[i][1].record(stream)
@@ -867,9 +959,35 @@ def main():
     def rate(run):
         return job_rate(len(run["ms"]), world, run["total_ms"])
 
-    rep = None
+    n_cmp = max(5, min(50, args.steps // 4))
+    # ---- the reference of the agreement: the full form in FP32 (the plain FP32 GPU baseline)
+    full32 = timed(tdpm.FORM_FULL, tdpm.PREC_FP32, n_cmp, 2)
+    full_keys = keys(step(tdpm.FORM_FULL, tdpm.PREC_FP32))
+
+    # ---- decomposition: a fixed rank, a fixed (S, T) pair, or the rank ladder
+    rep, ladder, ranks_used = None, None, None
     if form == tdpm.FORM_DECOMPOSED:
-        rep = tdpm.tdpm_decompose(ctx, mid, args.rank, dmode, max_iters=500, seed=1)
+        if joint:
+            rep = tdpm.tdpm_decompose(ctx, mid, args.rank, dmode, max_iters=args.als_iters, seed=1)
+        elif args.rank is not None or args.ranks is not None:
+            S, T = (args.rank, args.rank) if args.rank is not None else tuple(int(v) for v in args.ranks.split(","))
+            ranks_used = (S, T)
+            rep = tdpm.tdpm_decompose_ranks(ctx, mid, filter_ranks(wl.model, S, T), max_iters=args.als_iters, seed=1)
+        else:
+            ladder = []
+            for S, T in RANK_LADDER:
+                t0 = time.perf_counter()
+                rep = tdpm.tdpm_decompose_ranks(ctx, mid, filter_ranks(wl.model, S, T), max_iters=args.als_iters,
+                                                seed=1)
+                secs = time.perf_counter() - t0
+                a = agree(keys(step(form, prec)), full_keys)
+                run = timed(form, prec, 3, 1)
+                ladder.append({"S_root": S, "T_part": T, "agreement_with_full_fp32": a, "images_per_s": rate(run),
+                               "max_rel_error": rep["max_rel_error"], "mean_rel_error": rep["mean_rel_error"],
+                               "gain_formula_1": rep["gain"], "decompose_seconds": secs})
+                ranks_used = (S, T)
+                if a >= AGREEMENT_BAR:
+                    break
 
     # ---- headline run
     clocks = ClockSampler(local)
@@ -880,13 +998,17 @@ def main():
     ms_sorted = sorted(main_run["ms"])
     p50 = ms_sorted[len(ms_sorted) // 2]
     p99 = ms_sorted[min(len(ms_sorted) - 1, int(math.ceil(0.99 * len(ms_sorted))) - 1)]
-    head_keys = keys(step(form, prec))
+    head_dets = step(form, prec).copy()
+    head_keys = keys(head_dets)
+    agreement = agree(head_keys, full_keys)
 
     # ---- per-stage device time (same workload, CUDA events around each stage on its stream)
-    prof_run = timed(form, prec, max(10, args.steps // 4), 1, prof=True)
+    prof_run = timed(form, prec, max(5, min(20, args.steps // 4)), 1, prof=True)
     stages = prof_run["stages"]
     n_prof = len(prof_run["ms"])
-    model = stage_bytes(wl, pyr, args.form, args.precision, args.rank, joint, fused=not args.no_fuse)
+    rank_model = (filter_ranks(wl.model, *ranks_used) if ranks_used else args.rank) if form == tdpm.FORM_DECOMPOSED \
+        else None
+    model = stage_bytes(wl, pyr, args.form, args.precision, rank_model, joint, fused=not args.no_fuse)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -925,7 +1047,7 @@ def main():
         stream.wait_event(ready[cur])
         sid = tdpm.tdpm_build_pyramid_scores(ctx, mid, pyrs[cur], form, prec, stream)
         prefetch(1 - cur)  # queued after this step's job-table upload, so that upload does not wait behind it
-        dets = tdpm.tdpm_detect(ctx, sid, tau, capacity=cap, stream=stream, out=det_buf)
+        dets = tdpm.tdpm_detect_thresholds(ctx, sid, tau_rows, capacity=cap, stream=stream, out=det_buf)
         tdpm.tdpm_release(ctx, sid)
         return dets
 
@@ -948,49 +1070,40 @@ def main():
            "d2h_bytes_per_step": n_det * tdpm.DETECTION_DTYPE.itemsize + 8,
            "note": "the next image's pyramid transfer overlaps the current image's scoring (two device buffers)"}
 
-    # ---- full-form comparison runs on the same image
-    compare = None
+    # ---- the full form in the tensor-core precisions on the same image: speed and agreement with full FP32
+    compare = {"full_fp32_images_per_s": rate(full32), "full_fp32_p50_ms": sorted(full32["ms"])[len(full32["ms"]) // 2],
+               "speedup_vs_full_fp32": value / rate(full32), "agreement_with_full_fp32": agreement,
+               "detections": len(head_keys), "detections_full_fp32": len(full_keys)}
     if not args.no_compare:
-        n_cmp = max(10, args.steps // 4)
-        full32 = timed(tdpm.FORM_FULL, tdpm.PREC_FP32, n_cmp, 2)
-        full_keys = keys(step(tdpm.FORM_FULL, tdpm.PREC_FP32))
-        compare = {"full_fp32_images_per_s": rate(full32), "full_fp32_p50_ms": sorted(full32["ms"])[n_cmp // 2],
-                   "speedup_vs_full_fp32": value / rate(full32),
-                   "agreement_with_full_fp32": len(head_keys & full_keys) / max(1, len(head_keys | full_keys)),
-                   "detections": len(head_keys), "detections_full_fp32": len(full_keys)}
-        if prec != tdpm.PREC_FP32 or form != tdpm.FORM_FULL:
-            fullp = timed(tdpm.FORM_FULL, prec, n_cmp, 2)
-            compare[f"full_{args.precision}_images_per_s"] = rate(fullp)
-        # the other tensor-core operand formats of the full form: speed and agreement with the full FP32 form
-        for pname in ("bf16", "fp8"):
-            if pname == args.precision:
-                continue
+        for pname in ("bf16x3", "bf16", "fp8"):
             run = timed(tdpm.FORM_FULL, PRECISIONS[pname], n_cmp, 2)
             k = keys(step(tdpm.FORM_FULL, PRECISIONS[pname]))
             compare[f"full_{pname}_images_per_s"] = rate(run)
-            compare[f"full_{pname}_agreement_with_full_fp32"] = len(k & full_keys) / max(1, len(k | full_keys))
+            compare[f"full_{pname}_agreement_with_full_fp32"] = agree(k, full_keys)
+        if form == tdpm.FORM_DECOMPOSED:
+            compare["speedup_vs_full_bf16x3"] = value / compare["full_bf16x3_images_per_s"]
 
-    # ---- oracle leg: CPU baseline and parity of the headline detections (same factors)
+    # ---- oracle leg: CPU baseline and parity of the headline detections (same filters)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         filters = factor_filters(tdpm, ctx, mid) if form == tdpm.FORM_DECOMPOSED else None
-        cpu = cpu_baseline_oracle(wl, filters, head_keys, tau)
+        cpu = cpu_baseline_oracle(wl, filters, head_keys, taus)
 
-    # ---- accuracy given up by the decomposition: agreement with the full FP32 form per rank
+    # ---- accuracy given up by the decomposition: agreement with the full FP32 form per uniform rank
     sweep = None
-    if form == tdpm.FORM_DECOMPOSED and not args.no_sweep and compare is not None:
+    if form == tdpm.FORM_DECOMPOSED and not joint and not args.no_sweep and args.workload == "c2":
         sweep = {}
-        for r in RANK_SWEEP[args.mode]:
+        for r in RANK_SWEEP["per_filter"]:
             rr = tdpm.tdpm_decompose(ctx, mid, r, dmode, max_iters=500, seed=1)
             a = keys(step(form, prec))
             run = timed(form, prec, 50, 2)
-            sweep[r] = {"agreement_with_full_fp32": len(a & full_keys) / max(1, len(a | full_keys)),
-                        "images_per_s": rate(run), "max_rel_error": rr["max_rel_error"],
-                        "mean_rel_error": rr["mean_rel_error"], "gain_formula_1": rr["gain"]}
+            sweep[r] = {"agreement_with_full_fp32": agree(a, full_keys), "images_per_s": rate(run),
+                        "max_rel_error": rr["max_rel_error"], "mean_rel_error": rr["mean_rel_error"],
+                        "gain_formula_1": rr["gain"]}
 
     # ---- rank detection (Sec. 4): per filter the smallest rank meeting the error criterion with constant e
     auto_sweep = None
-    if form == tdpm.FORM_DECOMPOSED and args.mode == "per_filter" and not args.no_sweep and compare is not None:
+    if form == tdpm.FORM_DECOMPOSED and not joint and not args.no_sweep and args.workload == "c2":
         auto_sweep = {}
         for e in AUTO_RANK_E:
             t0 = time.perf_counter()
@@ -1001,13 +1114,14 @@ def main():
             auto_sweep[e] = {"ranks_mean": float(np.mean(ranks)), "ranks_min": int(ranks.min()),
                              "ranks_max": int(ranks.max()), "gain_formula_1": rr["gain"],
                              "max_rel_error": rr["max_rel_error"], "mean_rel_error": rr["mean_rel_error"],
-                             "agreement_with_full_fp32": len(a & full_keys) / max(1, len(a | full_keys)),
-                             "images_per_s": rate(run), "decompose_seconds": secs}
+                             "agreement_with_full_fp32": agree(a, full_keys), "images_per_s": rate(run),
+                             "decompose_seconds": secs}
 
-    # ---- post-processing: NMS (f4) and convolution shortening (Sec. 4 / Algorithm 1, f1)
+    # ---- post-processing on the one-class model: NMS (f4), convolution shortening (f1), HOG pyramid (f3)
     post = None
-    if form == tdpm.FORM_DECOMPOSED and args.mode == "per_filter" and not args.no_sweep and rank == 0:
-        tdpm.tdpm_decompose(ctx, mid, args.rank, dmode, max_iters=500, seed=1)  # the headline factors again
+    if form == tdpm.FORM_DECOMPOSED and not joint and not args.no_sweep and rank == 0 and args.workload == "c2":
+        tdpm.tdpm_decompose_ranks(ctx, mid, filter_ranks(wl.model, *ranks_used), max_iters=args.als_iters, seed=1)
+        tau = float(taus[0])
         post = {"nms": nms_measure(tdpm, ctx, mid, dp, form, prec, tau, stream),
                 "cascade": cascade_measure(torch, tdpm, ctx, mid, wl, form, prec, tau, stream),
                 "hog": hog_measure(torch, tdpm, ctx, mid, form, prec, stream, main_run["total_ms"] / args.steps,
@@ -1017,24 +1131,32 @@ def main():
             "warmup": args.warmup, "ms_per_step": main_run["total_ms"] / args.steps, "p50_ms": p50, "p99_ms": p99,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision if prec != tdpm.PREC_FP32 else "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "image": "500x375", "levels": len(pyr.levels),
-                       "components": len(wl.model.components), "filters": len(wl.model.filters()),
+            "config": {"workload": wl.name, "image": "x".join(str(v) for v in
+                                                             {"c2": (500, 375), "c3": (1280, 720)}[args.workload]),
+                       "levels": len(pyr.levels), "components": n_comp, "filters": len(wl.model.filters()),
                        "form": args.form, "precision": args.precision,
                        "precision_note": {"bf16x3": "BF16 tensor cores, operands split hi+lo (3 MMAs per product), "
                                                     "FP32 accumulation",
                                           "bf16": "BF16 tensor cores, FP32 accumulation",
                                           "fp8": "E4M3 tensor cores (per-tensor scales), FP32 accumulation",
                                           "fp32": "FP32 ALUs"}[args.precision],
-                       "rank": args.rank if form == tdpm.FORM_DECOMPOSED else None,
                        "decomposition": args.mode if form == tdpm.FORM_DECOMPOSED else None,
+                       "rank_root_S": ranks_used[0] if ranks_used else (args.rank if joint else None),
+                       "rank_part_T": ranks_used[1] if ranks_used else (args.rank if joint else None),
+                       "als_iters": args.als_iters if form == tdpm.FORM_DECOMPOSED else None,
+                       "thresholds": "per class: 99th percentile of the FP64 oracle's full-form scores"
+                                     if args.workload == "c3" else "99th percentile of the FP64 oracle's scores",
                        "fused": (not args.no_fuse) if form == tdpm.FORM_DECOMPOSED else None,
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world}"},
+            "agreement_with_full_fp32": agreement, "agreement_bar": AGREEMENT_BAR,
+            "agreement_met": agreement >= AGREEMENT_BAR,
+            "full_fp32_images_per_s": rate(full32), "speedup_vs_full_fp32": value / rate(full32),
             "gpu_launches": main_run["launches"],
             "stages_ms_per_image": {k: v[0] / n_prof for k, v in stages.items()},
             "roofline": roofline, "rooflines": rooflines, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
-            "compare": compare, "decomposition_report": rep, "rank_sweep": sweep, "auto_rank_sweep": auto_sweep,
-            "post_processing": post,
+            "compare": compare, "rank_ladder": ladder, "decomposition_report": rep, "rank_sweep": sweep,
+            "auto_rank_sweep": auto_sweep, "post_processing": post,
             "autotune": tdpm.tdpm_autotune_read(ctx),
             "wall_s_timed": main_run["wall_s"]}
     if rank == 0:

@@ -175,6 +175,14 @@ tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_
 tdpm_status tdpm_decompose_auto(tdpm_ctx *ctx, int32_t model_id, double e, int32_t max_rank, int32_t max_iters,
                                 double tol, uint64_t seed, int32_t *ranks, tdpm_decomp_report *report);
 
+/* Per-filter decomposition (Sec. 4) with a rank chosen for every filter, e.g. the (S, T) pairs of Sec. 5: rank S for
+ * the root filters and T for the part filters. ranks: host array indexed by filter id (tdpm_model_info's n_filters
+ * entries), each > 0; a rank >= h*w gives the exact slice form of that filter (error 0). Iterations, tolerance, seed
+ * and report are those of tdpm_decompose; the factors replace any earlier decomposition.
+ * Errors: ERR_ARG (NULL, a rank <= 0, max_iters <= 0), ERR_STATE (unknown model). */
+tdpm_status tdpm_decompose_ranks(tdpm_ctx *ctx, int32_t model_id, const int32_t *ranks, int32_t max_iters, double tol,
+                                 uint64_t seed, tdpm_decomp_report *report);
+
 /* FP64 factors of shape group g: A [h][R], B [w][R], C [32][R], Lambda [n_filters][R] (row-major). Any output may be
  * NULL. Errors: ERR_STATE (not decomposed). */
 tdpm_status tdpm_get_factors(tdpm_ctx *ctx, int32_t model_id, int32_t group, double *A, double *B, double *C,
@@ -349,12 +357,15 @@ tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int3
                     int32_t y_off, int32_t y_step, int32_t ny, float *D, int32_t *arg, void *scratch, void *stream);
 
 /* Allocation-free variant of tdpm_dt. The paper has no counterpart; this entry point exists for callers that must not
- * allocate device memory: code that runs while a stream is being captured into a CUDA graph (allocation calls are
- * not captured), latency-critical loops that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
- * imply, and applications whose device memory is owned entirely by another allocator.
- *   - Same arguments, layouts and results as tdpm_dt, without the scratch buffer: the x-pass intermediate lives in a
- *     fixed 4 MiB device array inside the library, which every GPU that loads the library holds until the process
- *     exits. H * nx may not exceed tdpm_dt_noalloc_max_elements() (524,224): larger sizes return TDPM_ERR_ARG.
+ * allocate device memory: applications whose device memory is owned entirely by another allocator (a framework's
+ * caching allocator or a memory pool that has reserved the GPU, where a stray cudaMalloc can fail or fragment it),
+ * and latency-critical loops that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may imply.
+ *   - Same arguments, layouts and results as tdpm_dt, without the scratch buffer: the job record and the x-pass
+ *     intermediate live in a fixed 4 MiB device array inside the library, which every GPU that loads the library
+ *     holds until the process exits. H * nx may not exceed tdpm_dt_noalloc_max_elements() (524,224): larger sizes
+ *     return TDPM_ERR_ARG.
+ *   - The job record reaches the array as a kernel argument, so the call copies nothing from host memory and does
+ *     not wait for the stream.
  *   - The first call on a device looks up that array's device address (with the device current); make that first
  *     call before any stream capture starts.
  *   - Every call on a device shares the one array and overwrites it: calls whose work overlaps on the GPU (other

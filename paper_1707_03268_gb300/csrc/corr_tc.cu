@@ -632,13 +632,13 @@ bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells
     return encode_tmap(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 8, const_cast<uint16_t *>(planar), cells, chunks);
 }
 
-bool encode_level_tmap_tiles(CUtensorMap *map, const uint16_t *planar, int H, int W)
+bool encode_level_tmap_tiles(CUtensorMap *map, const uint16_t *planar, int H, int W, int box_w, int box_h)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn || H <= 0 || W <= 0) return false;
     const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, 4};
     const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
-    const cuuint32_t box[4] = {8, 32, 4, 4};
+    const cuuint32_t box[4] = {8, (cuuint32_t)box_w, (cuuint32_t)box_h, 4};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(planar), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,

@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(DT_WARPS * 32, 4) dt_xy_kernel(const DtJob *__
 
 int dt_lines_per_cta() { return DT_WARPS; }
 int dt_strip_columns() { return DT_KS; }
+int dt_job_strips(int nx) { return (nx + DT_KS - 1) / DT_KS; }
 
 size_t dt_fused_smem_bytes(int max_W, int max_H, int nbuf)
 {
@@ -339,7 +340,7 @@ cudaError_t launch_dt_fused(const DtJob *d_jobs, int n_jobs, const int *d_cta_jo
                             cudaStream_t s)
 {
     if (n_jobs <= 0 || ctas <= 0) return cudaSuccess;
-    if (max_W > 800 || max_H > 800 || max_W < 1 || max_H < 1) return cudaErrorInvalidValue;
+    if (max_W > kDtMaxSide || max_H > kDtMaxSide || max_W < 1 || max_H < 1) return cudaErrorInvalidValue;
     const int nbuf = dt_fused_smem_bytes(max_W, max_H, 2) <= (size_t)kMaxDynamicSmem ? 2 : 1;
     const size_t smem = dt_fused_smem_bytes(max_W, max_H, nbuf);
     if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
@@ -353,7 +354,7 @@ cudaError_t launch_dt_fused(const DtJob *d_jobs, int n_jobs, const int *d_cta_jo
 cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_ctas, int y_ctas, int max_W, int max_H, cudaStream_t s)
 {
     if (n_jobs <= 0) return cudaSuccess;
-    if (max_W > 800 || max_H > 800) return cudaErrorInvalidValue;
+    if (max_W > kDtMaxSide || max_H > kDtMaxSide) return cudaErrorInvalidValue;
     const size_t smem_x = sizeof(float) * DT_WARPS * (size_t)max_W;
     // y pass: a column has H <= max_H values; outputs per column ny <= H
     const int colstride = max_H | 1, outstride = max_H | 1;

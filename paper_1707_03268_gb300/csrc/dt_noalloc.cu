@@ -41,6 +41,10 @@ tdpm_status scratch_address(void **out)
     return TDPM_OK;
 }
 
+// Writes the job record into the scratch array. The record travels as a kernel parameter, so the call makes no copy
+// from host memory: nothing waits for the stream, and no host buffer has to outlive the call.
+__global__ void dt_store_job_kernel(DtJob J, DtJob *dst) { *dst = J; }
+
 }  // namespace
 }  // namespace tdpm
 
@@ -59,7 +63,8 @@ tdpm_status tdpm_dt_noalloc(const float *S, int32_t H, int32_t W, const float d[
 {
     clear_error();
     if (!S || !d || !D || !arg) return fail(TDPM_ERR_ARG, "NULL argument");
-    if (H <= 0 || W <= 0 || H > 800 || W > 800) return fail(TDPM_ERR_ARG, "map sides must be in [1, 800]");
+    if (H <= 0 || W <= 0 || H > kDtMaxSide || W > kDtMaxSide)
+        return fail(TDPM_ERR_ARG, "map sides must be in [1, " + std::to_string(kDtMaxSide) + "]");
     for (int k = 0; k < 4; ++k)
         if (!std::isfinite(d[k])) return fail(TDPM_ERR_ARG, "non-finite deformation coefficient");
     if (!(d[1] > 0.f) || !(d[3] > 0.f)) return fail(TDPM_ERR_ARG, "quadratic coefficients must be > 0");
@@ -86,8 +91,9 @@ tdpm_status tdpm_dt_noalloc(const float *S, int32_t H, int32_t W, const float d[
     J.D = D; J.A = arg;
     J.xbegin = 0; J.ybegin = 0;
     cudaStream_t s = (cudaStream_t)stream;
-    // the job record is copied from this stack frame; a pageable copy is staged before cudaMemcpyAsync returns
-    CUDA_TRY(cudaMemcpyAsync(sb, &J, sizeof(DtJob), cudaMemcpyHostToDevice, s));
+    note_launches(1);
+    dt_store_job_kernel<<<1, 1, 0, s>>>(J, reinterpret_cast<DtJob *>(sb));
+    CUDA_TRY(cudaGetLastError());
     const int lpc = dt_lines_per_cta();
     CUDA_TRY(launch_dt(reinterpret_cast<const DtJob *>(sb), 1, (H + lpc - 1) / lpc, (nx + lpc - 1) / lpc, W, H, s));
     return TDPM_OK;

@@ -125,7 +125,7 @@ extern thread_local int *t_capture_launches;
 // slot: a distinct number per kernel (0 .. kSmemSlots-1) under which the setting is remembered.
 cudaError_t allow_max_dynamic_smem(const void *func, int slot);
 constexpr int kMaxDynamicSmem = 232448;
-constexpr int kSmemSlots = 32;
+constexpr int kSmemSlots = 48;
 
 // K8: FP32 SIMT direct correlation. filt_t: [h*w*32][Kpad] (filter index fastest), Kpad a multiple of 64.
 cudaError_t launch_corr_f32(const CorrJob *d_jobs, int n_jobs, int total_tiles, const float *filt_t, int K, int Kpad,
@@ -158,7 +158,7 @@ bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells
 bool encode_level_tmap_fp8(CUtensorMap *map, const uint8_t *planar, long long cells);
 
 // Tensor map of a BF16 planar level [4][H][W][8] as a 4-D array, box {8, 32 columns, 4 rows, 4 chunks}.
-bool encode_level_tmap_tiles(CUtensorMap *map, const uint16_t *planar, int H, int W);
+bool encode_level_tmap_tiles(CUtensorMap *map, const uint16_t *planar, int H, int W, int box_w = 32, int box_h = 4);
 
 // K2+K3+K4 fused (per-filter mode, BF16 or split-BF16 operands): the channel stage on the tensor cores and the
 // separable passes with the recombination, over `tiles` spatial tiles (records d_tiles, each naming its job) times
@@ -206,6 +206,21 @@ cudaError_t launch_sep(const SepJob *d_jobs, int n_jobs, long long total_items, 
 long long sep_job_items(int mode, int h, int w, int Ho, int Wo, int K, int *tiles_x, int *tiles_y);
 
 // K5/K6: distance transform passes (x_ctas / y_ctas: the CTA totals the jobs' xbegin / ybegin count; sides <= 800).
+// K2+K3+K4 with the CP terms on the MMA's M dimension (zsept_tc.cu), per-filter decomposition of 6x6 or 7x7 filters:
+// items = n_tiles spatial tiles (ZsTile: 16 x 16 cells of Z, 17 - w output columns, 17 - h output rows) x n_tg term
+// groups (consecutive filters, at most zsept_terms() terms); d_grec: n_tg records of zsept_record_bytes() bytes
+// (factors [16][128] floats: lambda a_r, b_r per term lane; then nf, k0, lane ranges); d_group_t0: first term of each
+// group in the channel bank (whose rows must extend zsept_terms() rows past it). The jobs' tensor maps use a
+// {8, 16, 16, 4} box.
+bool zsept_shape(int h, int w);
+int zsept_tile_side();
+int zsept_terms();
+int zsept_record_bytes();
+int zsept_factor_stride();
+cudaError_t launch_zsept_tc(const ZsJob *d_jobs, const ZsTile *d_tiles, int n_tiles, int n_tg, const void *d_grec,
+                            const int *d_group_t0, const void *cbank, const void *cbank_lo, int ld, int h, int w,
+                            int *d_err, cudaStream_t s);
+
 cudaError_t launch_dt(const DtJob *d_jobs, int n_jobs, int x_ctas, int y_ctas, int max_W, int max_H, cudaStream_t s);
 int dt_lines_per_cta();
 // K5+K6 fused: one CTA per (job, strip of dt_strip_columns() sampled columns), the jobs' xbegin counting those CTAs;
@@ -214,6 +229,9 @@ int dt_lines_per_cta();
 cudaError_t launch_dt_fused(const DtJob *d_jobs, int n_jobs, const int *d_cta_jobs, int ctas, int max_W, int max_H,
                             cudaStream_t s);
 int dt_strip_columns();
+int dt_job_strips(int nx);  // strips (CTAs) of a job with nx sampled columns
+// Largest side (rows or columns) of a part score map the distance transform accepts.
+constexpr int kDtMaxSide = 800;
 
 // K7: assembly (shift and sum), then detection count / scan / write.
 cudaError_t launch_assemble(const AsmJob *d_jobs, int n_jobs, long long total, cudaStream_t s);

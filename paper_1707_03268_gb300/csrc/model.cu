@@ -173,7 +173,8 @@ tdpm_status upload_factors(Group &g)
     if (ro.empty()) ro.assign(K + 1, 0);
     tdpm_status st = upload(&g.d_rank_off, ro);
     if (st) return st;
-    g.Rpad_tc = corr_tc_bank_rows(R);
+    // zero rows past the last term: the fused kernels' MMAs of a filter group read up to 128 rows from its first term
+    g.Rpad_tc = std::max(corr_tc_bank_rows(R), (R + 15) / 16 * 16 + zsept_terms());
     st = upload_tc_bank(&g.d_C_tc, &g.d_C_tc_lo, 1, g.Rpad_tc, R,
                         [&](int, int r, int c) { return (float)g.C[(size_t)c * R + r]; });
     if (!st)
@@ -435,7 +436,7 @@ double cp_abs_error(const std::vector<double> &T, const CpResult &cr, int n0, in
 // one CP per shape group of rank `rank`. ranks_out: the filters' ranks by filter id (per filter mode), may be null.
 tdpm_status decompose_model(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_t mode, bool autorank, double e,
                             int32_t max_rank, int32_t max_iters, double tol, uint64_t seed, int32_t *ranks_out,
-                            tdpm_decomp_report *report)
+                            tdpm_decomp_report *report, const int32_t *ranks_in = nullptr)
 {
     std::lock_guard<std::mutex> lk(ctx->mu);
     tdpm_status st = set_device(ctx);
@@ -453,6 +454,8 @@ tdpm_status decompose_model(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32
             // c_r = F[dy][dx][:]
             std::vector<CpResult> res(K);
             std::vector<int> Rk(K, rank >= hw ? hw : rank);
+            if (ranks_in)  // one rank per filter (by filter id); at least h*w is the exact slice form
+                for (int k = 0; k < K; ++k) Rk[k] = std::min(ranks_in[g.fids[k]], hw);
             const unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)K));
             std::vector<std::thread> pool;
             for (unsigned t = 0; t < nt; ++t)
@@ -620,6 +623,26 @@ tdpm_status tdpm_decompose(tdpm_ctx *ctx, int32_t model_id, int32_t rank, int32_
     if (max_iters <= 0) return fail(TDPM_ERR_ARG, "max_iters must be > 0");
     if (!(tol >= 0.0)) return fail(TDPM_ERR_ARG, "tol must be >= 0");
     return decompose_model(ctx, model_id, rank, mode, false, 0.0, 0, max_iters, tol, seed, nullptr, report);
+}
+
+tdpm_status tdpm_decompose_ranks(tdpm_ctx *ctx, int32_t model_id, const int32_t *ranks, int32_t max_iters, double tol,
+                                 uint64_t seed, tdpm_decomp_report *report)
+{
+    clear_error();
+    if (!ctx || !ranks) return fail(TDPM_ERR_ARG, "NULL argument");
+    if (max_iters <= 0) return fail(TDPM_ERR_ARG, "max_iters must be > 0");
+    if (!(tol >= 0.0)) return fail(TDPM_ERR_ARG, "tol must be >= 0");
+    int nf = 0;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        Model *m = get_model(ctx, model_id);
+        if (!m) return fail(TDPM_ERR_STATE, "unknown model id");
+        nf = (int)m->filters.size();
+    }
+    for (int i = 0; i < nf; ++i)
+        if (ranks[i] <= 0) return fail(TDPM_ERR_ARG, "every rank must be > 0");
+    return decompose_model(ctx, model_id, 1, TDPM_DECOMP_PER_FILTER, false, 0.0, 0, max_iters, tol, seed, nullptr,
+                           report, ranks);
 }
 
 tdpm_status tdpm_decompose_auto(tdpm_ctx *ctx, int32_t model_id, double e, int32_t max_rank, int32_t max_iters,

@@ -123,6 +123,10 @@ struct Plan {
     int dt_ctas = 0, max_W = 1, max_H = 1;  // CTAs of the fused distance transform (strips of sampled columns)
     std::vector<std::pair<size_t, int>> patches;  // blob offsets of caller level pointers
 
+    // decomposed per-filter groups whose every filter is at its exact rank (h*w, the slice form): scored by the full
+    // form's kernel on the original filters (the same function, in fewer flops than the slice form's passes)
+    std::vector<char> g_exact;
+    bool gdec(size_t gi) const { return dec && !g_exact[gi]; }
     // joint decomposition with tensor-core operands: the separable stage writes U_r and Lambda U runs as a GEMM
     bool rec_tc(const Group &g) const { return bf && dec && g.joint; }
     int sep_mode(const Group &g) const { return rec_tc(g) ? SEP_TERMS : (g.joint ? SEP_JOINT : SEP_PER_FILTER); }
@@ -147,6 +151,17 @@ std::string plan_key(int model_id, const Model &m, int form, int prec, const tdp
         }
     }
     return k;
+}
+
+// The terms-on-M fused kernel serves the shapes it has unless TDPM_ZSEPT=0 (then the tile kernel below does), or
+// unless a form of the tile kernel is forced (TDPM_ZSEP_FORM).
+bool zsept_enabled()
+{
+    static const bool on = [] {
+        const char *e = getenv("TDPM_ZSEPT");
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 // The filter groups of a per-filter decomposed shape group for the fused kernel: consecutive filters while their
@@ -204,12 +219,64 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
     }
     P->glv.resize(m.groups.size());
     const size_t ngr = m.groups.size();
+    P->g_exact.assign(ngr, 0);
+    for (size_t gi = 0; gi < ngr && P->dec; ++gi) {
+        const Group &g = m.groups[gi];
+        bool exact = !g.joint && (int)g.rank_off.size() == g.K + 1;
+        for (int k = 0; k < g.K && exact; ++k) exact = g.rank_off[k + 1] - g.rank_off[k] >= g.h * g.w;
+        P->g_exact[gi] = exact;
+    }
     P->g_fused.assign(ngr, 0); P->g_fg_off.assign(ngr, 0); P->g_tile_off.assign(ngr, 0); P->g_frec_off.assign(ngr, 0);
     P->g_frec.assign(ngr, {}); P->g_n_fg.assign(ngr, 0); P->g_nmax.assign(ngr, 0);
     P->g_fg.assign(ngr, {});
     for (size_t gi = 0; gi < ngr; ++gi) {
         // the fused kernel: BF16 or split-BF16 operands, per-filter factors, a compiled shape
         if (!fuse || !P->bf || P->fp8 || !P->dec) break;
+        if (P->g_exact[gi]) continue;
+        {
+            // terms on the M dimension (6x6 and 7x7 filters): term groups of consecutive filters, <= 128 terms each
+            const Group &g = m.groups[gi];
+            std::vector<ZsGroup> tg;
+            if (!g.joint && zsept_shape(g.h, g.w) && (int)g.rank_off.size() == g.K + 1 && zsep_form < 0 &&
+                zsept_enabled()) {
+                const int M = zsept_terms();
+                bool ok = true;
+                for (int k0 = 0; k0 < g.K && ok;) {
+                    const int t0 = g.rank_off[k0];
+                    int k1 = k0;
+                    while (k1 < g.K && g.rank_off[k1 + 1] - t0 <= M) ++k1;
+                    if (k1 == k0 || t0 + M > g.Rpad_tc) ok = false;  // a filter above 128 terms, or a short bank
+                    else tg.push_back(ZsGroup{k0, k1, t0, g.rank_off[k1] - t0});
+                    k0 = k1;
+                }
+                if (!ok) tg.clear();
+            }
+            if (!tg.empty()) {
+                P->g_fg[gi] = tg;
+                P->g_fused[gi] = 2;
+                P->g_n_fg[gi] = (int)tg.size();
+                P->g_nmax[gi] = zsept_terms();
+                const int rec = zsept_record_bytes(), M = zsept_terms();
+                std::vector<uint8_t> &out = P->g_frec[gi];
+                out.assign((size_t)rec * tg.size(), 0);
+                for (size_t f = 0; f < tg.size(); ++f) {
+                    const ZsGroup &G = tg[f];
+                    float *fv = reinterpret_cast<float *>(out.data() + f * rec);
+                    int *ri = reinterpret_cast<int *>(fv + (size_t)M * zsept_factor_stride());
+                    for (int k = G.k0; k < G.k1; ++k)
+                        for (int r = g.rank_off[k]; r < g.rank_off[k + 1]; ++r) {
+                            const int l = r - G.t0;
+                            const double lam = g.Lam[(size_t)k * g.R + r];
+                            for (int i = 0; i < g.h; ++i) fv[(size_t)i * M + l] = (float)(lam * g.A[(size_t)i * g.R + r]);
+                            for (int i = 0; i < g.w; ++i) fv[(size_t)(g.h + i) * M + l] = (float)g.B[(size_t)i * g.R + r];
+                        }
+                    ri[0] = G.k1 - G.k0;
+                    ri[1] = G.k0;
+                    for (int i = 0; i <= G.k1 - G.k0; ++i) ri[2 + i] = g.rank_off[G.k0 + i] - G.t0;
+                }
+                continue;
+            }
+        }
         int nmax = 0;
         P->g_fg[gi] = fused_groups(m.groups[gi], &nmax);
         if (P->g_fg[gi].empty()) continue;
@@ -247,7 +314,7 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
                 if (Ho <= 0 || Wo <= 0) continue;
                 GroupLevel gl{j, 0, 0, Ho, Wo};
                 gl.out_off = bump.take(sizeof(float) * (size_t)g.K * Ho * Wo);
-                if (P->dec && !P->g_fused[gi]) gl.z_off = bump.take(sizeof(float) * (size_t)g.R * H * W);
+                if (P->gdec(gi) && !P->g_fused[gi]) gl.z_off = bump.take(sizeof(float) * (size_t)g.R * H * W);
                 if (P->rec_tc(g)) {
                     gl.u_off = bump.take(sizeof(uint16_t) * (size_t)g.Upad * Ho * Wo);
                     if (P->split) gl.u_lo_off = bump.take(sizeof(uint16_t) * (size_t)g.Upad * Ho * Wo);
@@ -324,8 +391,20 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         const size_t nj = std::max<size_t>(1, P->glv[gi].size());
         const size_t job_bytes = P->g_fused[gi] ? sizeof(ZsJob)
                                  : P->bf        ? sizeof(TcJob)
-                                                : (P->dec ? sizeof(ZJob) : sizeof(CorrJob));
+                                                : (P->gdec(gi) ? sizeof(ZJob) : sizeof(CorrJob));
         P->g_jobs_off[gi] = jb.take(job_bytes * nj);
+        if (P->g_fused[gi] == 2) {
+            P->g_fg_off[gi] = jb.take(sizeof(int) * P->g_fg[gi].size());  // first term of every term group
+            const int T = zsept_tile_side(), tc = T - g.w + 1, tr = T - g.h + 1;
+            long long tiles = 0;
+            for (const GroupLevel &gl : P->glv[gi])
+                tiles += (long long)((gl.Wo + tc - 1) / tc) * ((gl.Ho + tr - 1) / tr);
+            P->g_tiles[gi] = (int)std::min<long long>(tiles, 0x7fffffff);
+            P->g_tile_off[gi] = jb.take(sizeof(ZsTile) * std::max(1, P->g_tiles[gi]));
+            P->g_frec_off[gi] = jb.take(P->g_frec[gi].size());
+            P->g_nt[gi] = 0;
+            continue;
+        }
         if (P->g_fused[gi]) {
             P->g_fg_off[gi] = jb.take(sizeof(ZsGroup) * P->g_fg[gi].size());
             int tc, tr;
@@ -344,23 +423,23 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
             }
             continue;
         }
-        if (P->dec) P->g_sep_off[gi] = jb.take(sizeof(SepJob) * nj);
+        if (P->gdec(gi)) P->g_sep_off[gi] = jb.take(sizeof(SepJob) * nj);
         if (P->rec_tc(g)) P->g_rec_off[gi] = jb.take(sizeof(TcJob) * nj);
         int tiles = 0, rec_tiles = 0;
         long long sep_tiles = 0;
         for (const GroupLevel &gl : P->glv[gi]) {
             const int H = P->sizes[gl.j].first, W = P->sizes[gl.j].second;
             if (P->bf) {
-                const long long span = P->dec ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
+                const long long span = P->gdec(gi) ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
                 tiles += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m());
-            } else if (P->dec) {
+            } else if (P->gdec(gi)) {
                 tiles += ((H * W + zproj_simt_cells_per_tile() - 1) / zproj_simt_cells_per_tile()) *
                          ((g.R + zproj_simt_r_chunk() - 1) / zproj_simt_r_chunk());
             } else {
                 tiles += ((gl.Wo + corr_f32_tile_x() - 1) / corr_f32_tile_x()) *
                          ((gl.Ho + corr_f32_tile_y() - 1) / corr_f32_tile_y()) * (g.Kpad / corr_f32_tile_k());
             }
-            if (P->dec) {
+            if (P->gdec(gi)) {
                 int tx, ty;
                 sep_tiles += sep_job_items(P->sep_mode(g), g.h, g.w, gl.Ho, gl.Wo, P->sep_k(g), &tx, &ty);
             }
@@ -373,23 +452,20 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         // untuned: the balanced width; the persistent form for split operands (three MMAs per step keep the tensor
         // cores busy enough for the accumulator double buffer to pay), the tile form otherwise
         const int persist = P->split ? kTcPersistent : 0;
-        P->g_nt[gi] = (P->dec ? corr_tc_default_nt(g.R, 1) : corr_tc_default_nt(g.K, g.h * g.w)) | persist;
+        P->g_nt[gi] = (P->gdec(gi) ? corr_tc_default_nt(g.R, 1) : corr_tc_default_nt(g.K, g.h * g.w)) | persist;
         P->g_rec_nt[gi] = P->rec_tc(g) ? corr_tc_default_nt(g.K, g.Upad / FD) | persist : 0;
     }
     P->dt_off = jb.take(sizeof(DtJob) * std::max<size_t>(1, P->dts.size()));
-    {
-        long long ctas = 0;
-        for (const DtPlan &p : P->dts) ctas += (p.X + dt_strip_columns() - 1) / dt_strip_columns();
-        P->dt_cta_off = jb.take(sizeof(int) * (size_t)std::max<long long>(1, ctas));
-    }
-    P->asm_off = jb.take(sizeof(AsmJob) * std::max<size_t>(1, P->asms.size()));
-    P->blob_bytes = align256(jb.off);
-    P->arena_bytes = P->blob_off + P->blob_bytes;
     for (const DtPlan &p : P->dts) {
-        P->dt_ctas += (p.X + dt_strip_columns() - 1) / dt_strip_columns();
         P->max_W = std::max(P->max_W, p.Ws);
         P->max_H = std::max(P->max_H, p.Hs);
     }
+    // one distance-transform CTA per strip of sampled columns (maps above the supported side are refused later)
+    for (const DtPlan &p : P->dts) P->dt_ctas += dt_job_strips(p.X);
+    P->dt_cta_off = jb.take(sizeof(int) * (size_t)std::max(1, P->dt_ctas));
+    P->asm_off = jb.take(sizeof(AsmJob) * std::max<size_t>(1, P->asms.size()));
+    P->blob_bytes = align256(jb.off);
+    P->arena_bytes = P->blob_off + P->blob_bytes;
     return P;
 }
 
@@ -417,24 +493,37 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
     for (size_t gi = 0; gi < m.groups.size(); ++gi) {
         const Group &g = m.groups[gi];
         if (P.g_fused[gi]) {
-            int tc, tr;
-            zsep_tile(g.h, g.w, &tc, &tr);
+            const bool zt = P.g_fused[gi] == 2;
+            int tc, tr, bw = 32, bh = 4;
+            if (zt) {
+                bw = bh = zsept_tile_side();
+                tc = bw - g.w + 1;
+                tr = bh - g.h + 1;
+            } else {
+                zsep_tile(g.h, g.w, &tc, &tr);
+            }
             ZsTile *tl = reinterpret_cast<ZsTile *>(hb + P.g_tile_off[gi]);
             for (size_t i = 0; i < P.glv[gi].size(); ++i) {
                 const GroupLevel &gl = P.glv[gi][i];
                 const int H = P.sizes[gl.j].first, W = P.sizes[gl.j].second;
                 ZsJob &z = reinterpret_cast<ZsJob *>(hb + P.g_jobs_off[gi])[i];
-                if (!encode_level_tmap_tiles(&z.tmap, reinterpret_cast<const uint16_t *>(base + P.bf_off[gl.j]), H, W) ||
+                if (!encode_level_tmap_tiles(&z.tmap, reinterpret_cast<const uint16_t *>(base + P.bf_off[gl.j]), H, W,
+                                             bw, bh) ||
                     (P.split && !encode_level_tmap_tiles(&z.tmap_lo,
                                                          reinterpret_cast<const uint16_t *>(base + P.bf_lo_off[gl.j]),
-                                                         H, W)))
+                                                         H, W, bw, bh)))
                     return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
                 z.out = reinterpret_cast<float *>(base + gl.out_off);
                 z.H = H; z.W = W; z.Ho = gl.Ho; z.Wo = gl.Wo;
                 for (int y0 = 0; y0 < gl.Ho; y0 += tr)
                     for (int x0 = 0; x0 < gl.Wo; x0 += tc) *tl++ = ZsTile{(int)i, x0, y0, std::min(tr, gl.Ho - y0)};
             }
-            std::memcpy(hb + P.g_fg_off[gi], P.g_fg[gi].data(), sizeof(ZsGroup) * P.g_fg[gi].size());
+            if (zt) {
+                int *t0s = reinterpret_cast<int *>(hb + P.g_fg_off[gi]);
+                for (size_t f = 0; f < P.g_fg[gi].size(); ++f) t0s[f] = P.g_fg[gi][f].t0;
+            } else {
+                std::memcpy(hb + P.g_fg_off[gi], P.g_fg[gi].data(), sizeof(ZsGroup) * P.g_fg[gi].size());
+            }
             std::memcpy(hb + P.g_frec_off[gi], P.g_frec[gi].data(), P.g_frec[gi].size());
             continue;
         }
@@ -454,14 +543,15 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
                 if (P.split && !encode_level_tmap(&t.tmap_lo, reinterpret_cast<const uint16_t *>(base + P.bf_lo_off[gl.j]),
                                                   (long long)H * W))
                     return fail(TDPM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-                t.out = P.dec ? reinterpret_cast<float *>(base + gl.z_off) : out;
+                const bool gd = P.gdec(gi);
+                t.out = gd ? reinterpret_cast<float *>(base + gl.z_off) : out;
                 t.H = H; t.W = W;
-                t.Ho = P.dec ? H : gl.Ho;
-                t.Wo = P.dec ? W : gl.Wo;
+                t.Ho = gd ? H : gl.Ho;
+                t.Wo = gd ? W : gl.Wo;
                 t.begin = begin;
-                const long long span = P.dec ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
+                const long long span = gd ? (long long)H * W : (long long)(gl.Ho - 1) * W + gl.Wo;
                 begin += (int)((span + corr_tc_tile_m() - 1) / corr_tc_tile_m());
-            } else if (P.dec) {
+            } else if (P.gdec(gi)) {
                 ZJob &z = reinterpret_cast<ZJob *>(hb + P.g_jobs_off[gi])[i];
                 z.feat = lv[gl.j]->data;
                 patches.push_back({P.g_jobs_off[gi] + sizeof(ZJob) * i + offsetof(ZJob, feat), gl.j});
@@ -481,7 +571,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
                 c.begin = begin;
                 begin += c.tiles_x * c.tiles_y * (g.Kpad / corr_f32_tile_k());
             }
-            if (P.dec) {
+            if (P.gdec(gi)) {
                 SepJob &sp = reinterpret_cast<SepJob *>(hb + P.g_sep_off[gi])[i];
                 sp.Z = reinterpret_cast<const float *>(base + gl.z_off);
                 sp.out = out;
@@ -523,7 +613,7 @@ tdpm_status fill_blob(const Plan &P, const Model &m, const std::vector<const tdp
         d.A = reinterpret_cast<int32_t *>(base + p.a_off);
         d.xbegin = xw;  // first CTA (strip of sampled columns) of the job in the fused launch
         d.ybegin = 0;
-        const int strips = (p.X + dt_strip_columns() - 1) / dt_strip_columns();
+        const int strips = dt_job_strips(p.X);
         int *cj = reinterpret_cast<int *>(hb + P.dt_cta_off) + xw;
         for (int t = 0; t < strips; ++t) cj[t] = (int)i;
         xw += strips;
@@ -562,12 +652,12 @@ cudaError_t launch_convert(const Plan &P, char *dblob, cudaStream_t s)
 // A shape group's tensor-core contraction over its m_tiles M tiles: the full correlation, or the channel stage of the
 // decomposed form, with the bank of the plan's operand format (FP8 results rescaled by the two per-tensor scales).
 // code: N tile width | kTcPersistent for the persistent form.
-cudaError_t launch_group_tc(const Plan &P, const Group &g, const TcJob *jobs, int nj, int m_tiles, int code, int *err,
-                            cudaStream_t s)
+cudaError_t launch_group_tc(const Plan &P, size_t gi, const Group &g, const TcJob *jobs, int nj, int m_tiles, int code,
+                            int *err, cudaStream_t s)
 {
     const int nt = code & 0xffff;
     const bool pers = (code & kTcPersistent) != 0;
-    if (P.dec) {
+    if (P.gdec(gi)) {
         if (P.fp8)
             return launch_corr_tc(jobs, nj, m_tiles, g.d_C_fp8, nullptr, g.R, g.Rpad_tc, nt, 1, 1, 1, err, s, true,
                                   1.f / (g.C_fp8_scale * kFp8FeatureScale), pers);
@@ -660,6 +750,17 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
         const int nj = (int)P.glv[gi].size();
         cudaError_t e = cudaSuccess;
         const char *jobs = dblob + P.g_jobs_off[gi];
+        if (P.g_fused[gi] == 2) {
+            Prof pr(ctx, gs, "zsep_tc");
+            e = launch_zsept_tc(reinterpret_cast<const ZsJob *>(jobs),
+                                reinterpret_cast<const ZsTile *>(dblob + P.g_tile_off[gi]), P.g_tiles[gi],
+                                P.g_n_fg[gi], dblob + P.g_frec_off[gi],
+                                reinterpret_cast<const int *>(dblob + P.g_fg_off[gi]), g.d_C_tc,
+                                P.split ? g.d_C_tc_lo : nullptr, g.Rpad_tc, g.h, g.w, ctx->d_err, gs);
+            if (e != cudaSuccess) return e;
+            pr.end();
+            return cudaSuccess;
+        }
         if (P.g_fused[gi]) {
             Prof pr(ctx, gs, "zsep_tc");
             e = launch_zsep_tc(reinterpret_cast<const ZsJob *>(jobs),
@@ -672,12 +773,12 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
             return cudaSuccess;
         }
         if (P.bf) {
-            Prof pr(ctx, gs, P.dec ? "zproj_tc" : "corr_tc");
-            e = launch_group_tc(P, g, reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], P.g_nt[gi], ctx->d_err,
+            Prof pr(ctx, gs, P.gdec(gi) ? "zproj_tc" : "corr_tc");
+            e = launch_group_tc(P, gi, g, reinterpret_cast<const TcJob *>(jobs), nj, P.g_tiles[gi], P.g_nt[gi], ctx->d_err,
                                 gs);
             if (e != cudaSuccess) return e;
             pr.end();
-        } else if (P.dec) {
+        } else if (P.gdec(gi)) {
             Prof pr(ctx, gs, "zproj_f32");
             e = launch_zproj_simt(reinterpret_cast<const ZJob *>(jobs), nj, P.g_tiles[gi], g.d_Ct, g.R, gs);
             if (e != cudaSuccess) return e;
@@ -689,7 +790,7 @@ cudaError_t enqueue(tdpm_ctx *ctx, const Plan &P, const Model &m, const Arena &A
             if (e != cudaSuccess) return e;
             pr.end();
         }
-        if (P.dec) {
+        if (P.gdec(gi)) {
             Prof pr(ctx, gs, "sep");
             e = launch_sep(reinterpret_cast<const SepJob *>(dblob + P.g_sep_off[gi]), nj, P.g_sep_tiles[gi], g.d_A,
                            g.d_B, g.d_lam, g.d_rank_off, P.sep_k(g), g.R, g.h, g.w, P.sep_mode(g), gs);
@@ -821,6 +922,7 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, Arena &A, cuda
         const Group &g = m.groups[gi];
         const int nj = (int)P.glv[gi].size();
         if (!nj) continue;
+        if (P.g_fused[gi] == 2) continue;  // one form
         if (P.g_fused[gi] && P.zsep_forced) continue;
         if (P.g_fused[gi]) {
             // the fused kernel: its forms (one CTA per item, or persistent with one or two feature stages / Z buffers)
@@ -840,13 +942,13 @@ cudaError_t autotune_plan(tdpm_ctx *ctx, Plan &P, const Model &m, Arena &A, cuda
         }
         const TcJob *jobs = reinterpret_cast<const TcJob *>(dblob + P.g_jobs_off[gi]);
         const char *op = P.fp8 ? "f8" : P.split ? "x3" : "x1";
-        if (P.dec)
+        if (P.gdec(gi))
             e = choose(tune_key("zproj", g.R, 1, op, P.g_tiles[gi]), g.R,
-                       [&](int nt) { return launch_group_tc(P, g, jobs, nj, P.g_tiles[gi], nt, ctx->d_err, s); },
+                       [&](int nt) { return launch_group_tc(P, gi, g, jobs, nj, P.g_tiles[gi], nt, ctx->d_err, s); },
                        &P.g_nt[gi]);
         else
             e = choose(tune_key("corr", g.K, g.h * g.w, op, P.g_tiles[gi]), g.K,
-                       [&](int nt) { return launch_group_tc(P, g, jobs, nj, P.g_tiles[gi], nt, ctx->d_err, s); },
+                       [&](int nt) { return launch_group_tc(P, gi, g, jobs, nj, P.g_tiles[gi], nt, ctx->d_err, s); },
                        &P.g_nt[gi]);
         if (e == cudaSuccess && P.rec_tc(g)) {
             const TcJob *rj = reinterpret_cast<const TcJob *>(dblob + P.g_rec_off[gi]);
@@ -1171,8 +1273,9 @@ tdpm_status tdpm_build_batch_scores_subset(tdpm_ctx *ctx, int32_t model_id, cons
         plan = pit->second;
     } else {
         plan = make_plan(*m, model_id, pyrs, n_images, form, precision, mask, ctx->fuse, ctx->zsep_form);
-        if (plan->max_W > 800 || plan->max_H > 800)
-            return fail(TDPM_ERR_ARG, "part score maps wider or taller than 800 cells are not supported");
+        if (plan->max_W > kDtMaxSide || plan->max_H > kDtMaxSide)
+            return fail(TDPM_ERR_ARG, "part score maps wider or taller than " + std::to_string(kDtMaxSide) +
+                                          " cells are not supported");
         if (ctx->plans.size() > 256) ctx->plans.clear();
         ctx->plans[key] = plan;
     }
@@ -1938,7 +2041,8 @@ tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int3
 {
     clear_error();
     if (!S || !d || !D || !arg || !scratch) return fail(TDPM_ERR_ARG, "NULL argument");
-    if (H <= 0 || W <= 0 || H > 800 || W > 800) return fail(TDPM_ERR_ARG, "map sides must be in [1, 800]");
+    if (H <= 0 || W <= 0 || H > kDtMaxSide || W > kDtMaxSide)
+        return fail(TDPM_ERR_ARG, "map sides must be in [1, " + std::to_string(kDtMaxSide) + "]");
     for (int k = 0; k < 4; ++k)
         if (!std::isfinite(d[k])) return fail(TDPM_ERR_ARG, "non-finite deformation coefficient");
     if (!(d[1] > 0.f) || !(d[3] > 0.f)) return fail(TDPM_ERR_ARG, "quadratic coefficients must be > 0");
@@ -1959,7 +2063,7 @@ tdpm_status tdpm_dt(const float *S, int32_t H, int32_t W, const float d[4], int3
     CUDA_TRY(cudaMemcpyAsync(sb, &J, sizeof(DtJob), cudaMemcpyHostToDevice, s));
     // the fused form (the scratch's V / IV areas stay unused; tdpm_dt_noalloc runs the two-pass form)
     CUDA_TRY(launch_dt_fused(reinterpret_cast<const DtJob *>(sb), 1, nullptr,
-                             (nx + dt_strip_columns() - 1) / dt_strip_columns(), W, H, s));
+                             dt_job_strips(nx), W, H, s));
     return TDPM_OK;
 }
 

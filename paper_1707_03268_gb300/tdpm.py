@@ -108,6 +108,8 @@ SIGNATURES = {
                                 ctypes.POINTER(DecompReport)]),
     "tdpm_decompose_auto": (_c_i32, [_VP, _c_i32, ctypes.c_double, _c_i32, _c_i32, ctypes.c_double, ctypes.c_uint64,
                                      _VP, ctypes.POINTER(DecompReport)]),
+    "tdpm_decompose_ranks": (_c_i32, [_VP, _c_i32, _VP, _c_i32, ctypes.c_double, ctypes.c_uint64,
+                                      ctypes.POINTER(DecompReport)]),
     "tdpm_get_factors": (_c_i32, [_VP, _c_i32, _c_i32] + [ctypes.POINTER(ctypes.c_double)] * 4),
     "tdpm_save_factors": (_c_i32, [_VP, _c_i32, ctypes.c_char_p]),
     "tdpm_load_factors": (_c_i32, [_VP, _c_i32, ctypes.c_char_p]),
@@ -275,6 +277,16 @@ def tdpm_decompose(ctx: int, model_id: int, rank: int, mode: int = DECOMP_PER_FI
     rep = DecompReport()
     _check(lib().tdpm_decompose(ctx, model_id, int(rank), int(mode), int(max_iters), float(tol), int(seed),
                                 ctypes.byref(rep)))
+    return {f: getattr(rep, f) for f, _ in DecompReport._fields_}
+
+
+def tdpm_decompose_ranks(ctx: int, model_id: int, ranks, max_iters: int = 500, tol: float = 1e-10,
+                         seed: int = 0) -> dict:
+    """Per-filter decomposition with one rank per filter (by filter id), e.g. Sec. 5's (S, T) root / part ranks."""
+    r = np.ascontiguousarray(np.asarray(ranks, dtype=np.int32))
+    rep = DecompReport()
+    _check(lib().tdpm_decompose_ranks(ctx, model_id, r.ctypes.data, int(max_iters), float(tol), int(seed),
+                                      ctypes.byref(rep)))
     return {f: getattr(rep, f) for f, _ in DecompReport._fields_}
 
 

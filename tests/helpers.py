@@ -63,3 +63,15 @@ def det_keys(dets) -> set:
 def agreement(a: set, b: set) -> float:
     u = a | b
     return 1.0 if not u else len(a & b) / len(u)
+
+
+# Two evaluations of the same decomposed filter map in FP32 that add the same products in different orders (the sum
+# over a filter's CP terms, and lambda_r folded into a_r or applied after the passes) differ by FP32 rounding only: a
+# few ulps of the partial sums per term, at most about 40 terms here. Relative to the map's largest value.
+SUM_ORDER_TOL = 2e-5
+
+
+def assert_same_sum(a: np.ndarray, b: np.ndarray, tol: float = SUM_ORDER_TOL) -> None:
+    assert a.shape == b.shape
+    if b.size:
+        assert rel_err(a, b.astype(np.float64)) <= tol, rel_err(a, b.astype(np.float64))

@@ -203,3 +203,78 @@ def test_class_subsets_of_a_bank(T, torch):
         _same(a, r["ref"])
         _same(m, r["ref"])
     T.tdpm_destroy(ctx)
+
+
+def test_served_detections_match_the_oracle(torch, T):
+    """Serving against the FP64 oracle (Algorithm 1's detection set D): a mix of requests with different image sizes,
+    class subsets of one bank model and thresholds taken from the oracle's own scores, submitted together and batched
+    by the server, each compared with the oracle's detections for the same image, components and threshold on the same
+    per-filter factors (split BF16: >= 99.5% agreement; matched detections carry the oracle's part positions up to
+    near-ties at the precision's tolerance, Sec. 2 argmax)."""
+    from helpers import agreement, dt_value
+    from oracle import oracle as orc
+
+    ctx = T.tdpm_create(0)
+    rng = np.random.default_rng(31)
+    comps = []
+    for _ in range(3):
+        comps.extend(synth.make_dpm_class(rng))  # three classes of six components: one bank model
+    bank = synth.Model(comps)
+    mid = T.tdpm_load_model(ctx, bank)
+    T.tdpm_decompose(ctx, mid, 8, T.DECOMP_PER_FILTER, max_iters=60, seed=5)
+    n_f, n_groups = T.tdpm_model_info(ctx, mid)
+    rebuilt = [None] * n_f
+    for gi in range(n_groups):
+        info = T.tdpm_group_info(ctx, mid, gi)
+        A, B, C, Lam = T.tdpm_get_factors(ctx, mid, gi)
+        F = orc.joint_reconstruct(Lam, A, B, C)
+        for k, fid in enumerate(info["filter_ids"]):
+            rebuilt[fid] = F[k]
+    first_fid = np.cumsum([0] + [1 + len(c.parts) for c in comps])
+    sizes = [(96, 128), (120, 160), (150, 200)]
+    host = [synth.make_pyramid(rng, synth.pyramid_sizes(h, w), synth.LAMBDA) for (h, w) in sizes]
+    dev = [device_pyramid(p, torch) for p in host]
+    subsets = [[0], [1, 2], [2, 0], [0, 1, 2], [1]]  # classes per request
+    reqs = []
+    for i, classes in enumerate(subsets):
+        img = i % len(sizes)
+        cs = [6 * c + k for c in classes for k in range(6)]
+        sub = synth.Model([comps[c] for c in cs])
+        fs = [rebuilt[f] for c in cs for f in range(first_fid[c], first_fid[c + 1])]
+        scored = orc.score_pyramid(sub, host[img], filters=fs)
+        tau = float(np.percentile(orc.all_scores(scored), 98))
+        ref = {(cs[d[0]],) + tuple(d[1:4]): d for d in orc.detect(scored, tau)}
+        reqs.append({"image": img, "components": cs, "tau": tau, "ref": ref, "sub": sub, "fs": fs})
+    T.tdpm_server_start(ctx, max_batch_images=8, max_inflight=2, max_wait_us=200)
+    tickets = [T.tdpm_submit(ctx, dev[r["image"]], [mid], T.FORM_DECOMPOSED, T.PREC_BF16X3, r["tau"],
+                             r["components"]) for r in reqs]
+    served = [T.tdpm_poll(ctx, t) for t in tickets]
+    T.tdpm_server_stop(ctx)
+    assert max(info["batch_images"] for _, info in served) > 1  # the requests really were batched together
+    n_parts_checked = 0
+    for r, (d, info) in zip(reqs, served):
+        assert info["status"] == T.OK
+        got = {(int(x["component"]), int(x["level"]), int(x["y"]), int(x["x"])): x for x in d}
+        assert set(k[0] for k in got) <= set(r["components"])
+        assert agreement(set(got), set(r["ref"])) >= 0.995
+        # part positions of the matched detections: equal, or a near-tie of the oracle's FP64 values within what split
+        # BF16 moves a part score (1e-4 of the map's largest value, for each of the two placements)
+        pyr = host[r["image"]]
+        for key in set(got) & set(r["ref"]):
+            c, j, y, x = key
+            comp = comps[c]
+            ref_d = r["ref"][key]
+            lp = j - pyr.lam
+            for i, part in enumerate(comp.parts):
+                gy, gx = int(got[key]["part_y"][i]), int(got[key]["part_x"][i])
+                oy, ox = ref_d[5][i], ref_d[6][i]
+                if (gy, gx) == (oy, ox):
+                    continue
+                S = orc.correlate(pyr.levels[lp], rebuilt[first_fid[c] + 1 + i])
+                py, px = 2 * y + part.anchor[0], 2 * x + part.anchor[1]
+                d4 = list(part.deform)
+                gap = dt_value(S, d4, oy, ox, py, px) - dt_value(S, d4, gy, gx, py, px)
+                assert gap <= 2e-4 * float(np.max(np.abs(S)))
+            n_parts_checked += 1
+    assert n_parts_checked > 100
+    T.tdpm_destroy(ctx)

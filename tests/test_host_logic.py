@@ -78,3 +78,30 @@ def test_synthetic_images_are_seeded_8bit_rgb():
     b = synth.make_image(np.random.default_rng(1), 37, 53)
     assert a.dtype == np.uint8 and a.shape == (37, 53, 3) and np.array_equal(a, b)
     assert len(np.unique(a)) > 100  # structure and noise, not a flat image
+
+
+def test_rank_pairs_and_class_thresholds_of_the_benchmark():
+    """The benchmark's (S, T) root / part rank pairs map to per-filter ranks in model order, capped at the exact rank
+    h*w; the bank's per-class thresholds (written by the oracle script) expand to one per component."""
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    from paper_1707_03268_gb300 import synth
+
+    wl = synth.config_c2()
+    r = bench.filter_ranks(wl.model, 64, 32)
+    shapes = [f.shape[:2] for f in wl.model.filters()]
+    assert len(r) == len(shapes)
+    i = 0
+    for c in wl.model.components:
+        assert r[i] == c.root.shape[0] * c.root.shape[1]  # S = 64 is past every root's exact rank
+        assert all(v == min(32, 36) for v in r[i + 1:i + 1 + len(c.parts)])
+        i += 1 + len(c.parts)
+    assert list(bench.filter_ranks(wl.model, 8, 40)[1:9]) == [36] * 8  # capped at 6 * 6
+    taus = bench.load_taus("c3", 120)
+    assert taus.shape == (120,) and np.all(taus[:6] == taus[0]) and taus[0] != taus[6]
+    assert np.all(bench.load_taus("c2", 6) == np.float32(bench.load_tau()))
+    # the ladder starts from the cheapest part rank and ends at the exact parts
+    assert bench.RANK_LADDER[-1][1] == 36 and bench.AGREEMENT_BAR == 0.995

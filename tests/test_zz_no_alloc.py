@@ -1,9 +1,11 @@
 """The allocation-free distance transform (tdpm_dt_noalloc) against the regular entry point (tdpm_dt).
 
-tdpm_dt_noalloc serves callers that may not allocate device memory (inside stream capture, latency-critical loops,
-applications whose memory belongs to another allocator); it keeps its scratch in a fixed device array inside the
-library. Both entry points run the same kernels, so their outputs must be identical. Two calls in a row check that the
-shared scratch is reused correctly. This file is collected last so that a failure here cannot hide another test's.
+tdpm_dt_noalloc serves callers that may not allocate device memory (applications whose memory belongs to another
+allocator, latency-critical loops that cannot take cudaMalloc's synchronisation); it keeps its scratch in a fixed device
+array inside the library. tdpm_dt runs the fused distance-transform kernel and tdpm_dt_noalloc the two-pass form
+(x pass, intermediate in the fixed array, y pass). The two forms run the same per-line scans in the same order, so
+their outputs must agree bit for bit; this test depends on that. Two calls in a row check that the shared scratch is
+reused correctly. This file is collected last so that a failure here cannot hide another test's.
 """
 import numpy as np
 import pytest
