@@ -198,6 +198,9 @@ tdpm_status tdpm_load_factors(tdpm_ctx *ctx, int32_t model_id, const char *path)
 /* Steps 1-3 for every component and root level of one pyramid: correlation in `form` and `precision`, distance
  * transform of every part map, shift-and-sum into per-(component, level) score maps. Enqueued on `stream`; returns
  * before the GPU finishes. The score buffers live in the context until tdpm_release(scores_id).
+ * Limit: a part filter's score map may be at most 800 cells wide and tall (the distance transform keeps a strip of
+ * its x-pass result for every row in shared memory), i.e. part levels of images up to about 3,200 pixels on a side at
+ * 4-pixel part cells; larger maps return ERR_ARG.
  * Errors: ERR_ARG, ERR_STATE (decomposed form before tdpm_decompose), ERR_OOM (budget). */
 tdpm_status tdpm_build_pyramid_scores(tdpm_ctx *ctx, int32_t model_id, const tdpm_pyramid *pyr, int32_t form,
                                       int32_t precision, void *stream, int32_t *scores_id);

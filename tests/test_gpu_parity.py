@@ -143,10 +143,12 @@ def test_dt_rejects_bad_arguments(torch, T):
 
 # ------------------------------------------------------------------------------------------------ whole path
 def _compare_pipeline(torch, T, ctx, wl, form, prec, filters=None, score_tol=1e-5, tau=None, model_id=None,
-                      check_parts=True, min_agree=0.995):
-    pyr = wl.pyramids[0]
+                      check_parts=True, min_agree=0.995, oracle_pyr=None):
+    """The library on the workload's FP32 pyramid against the oracle on oracle_pyr (default: the same pyramid; the
+    BF16-rounded one when the comparison is on rounded operands)."""
+    pyr = wl.pyramids[0] if oracle_pyr is None else oracle_pyr
     mid = model_id if model_id is not None else T.tdpm_load_model(ctx, wl.model)
-    dp = device_pyramid(pyr, torch)
+    dp = device_pyramid(wl.pyramids[0], torch)
     sid = T.tdpm_build_pyramid_scores(ctx, mid, dp, form, prec)
     scored = orc.score_pyramid(wl.model, pyr, filters=filters)
     worst = 0.0
@@ -212,13 +214,16 @@ def test_c2_full_fp32_end_to_end(torch, T, ctx):
     _compare_pipeline(torch, T, ctx, wl, T.FORM_FULL, T.PREC_FP32, tau=_tau("c2"))
 
 
-def _factor_filters(T, ctx, mid, model):
-    """Filters rebuilt by the oracle from the library's exported FP64 factors (model order)."""
+def _factor_filters(T, ctx, mid, model, round_c=None):
+    """Filters rebuilt by the oracle from the library's exported FP64 factors (model order); with round_c (the torch
+    module) the channel factors c_r are first rounded to BF16, the tensor cores' operand format."""
     n_f, n_g = T.tdpm_model_info(ctx, mid)
     out = [None] * n_f
     for g in range(n_g):
         info = T.tdpm_group_info(ctx, mid, g)
         A, B, C, Lam = T.tdpm_get_factors(ctx, mid, g)
+        if round_c is not None:
+            C = round_c.from_numpy(C.astype(np.float32)).bfloat16().double().numpy()
         F = orc.joint_reconstruct(Lam, A, B, C)
         for k, fid in enumerate(info["filter_ids"]):
             out[fid] = F[k]
@@ -236,12 +241,23 @@ def test_c1_decomposed_fp32_matches_oracle_on_same_factors(torch, T, ctx, rank, 
 
 
 def test_c2_decomposed_bf16_matches_oracle_on_same_factors(torch, T, ctx):
+    """Plain BF16 operands (features and channel factors rounded to BF16, FP32 accumulation and 1-D passes).
+    - Against the oracle on the same BF16-rounded operands (every BF16 product is exact in FP32, so what remains is
+      FP32 accumulation): scores within 1e-4, detections >= 99.5% with part positions checked.
+    - Against the oracle on the unrounded FP32 operands: scores within the stated BF16 bar, 1e-2. Detections are not
+      gated there: the BF16 rounding itself moves near-threshold scores (a reading of the precision bar, not of the
+      kernels)."""
     wl = synth.config_c2()
     mid = T.tdpm_load_model(ctx, wl.model)
     T.tdpm_decompose(ctx, mid, 8, T.DECOMP_PER_FILTER, max_iters=100, seed=1)
     filters = _factor_filters(T, ctx, mid, wl.model)
+    pyr = wl.pyramids[0]
+    rounded_pyr = synth.Pyramid([torch.from_numpy(l).bfloat16().float().numpy() for l in pyr.levels], pyr.lam)
+    rounded_f = _factor_filters(T, ctx, mid, wl.model, round_c=torch)
+    _compare_pipeline(torch, T, ctx, wl, T.FORM_DECOMPOSED, T.PREC_BF16, filters=rounded_f, model_id=mid,
+                      score_tol=1e-4, check_parts=True, min_agree=0.995, oracle_pyr=rounded_pyr)
     _compare_pipeline(torch, T, ctx, wl, T.FORM_DECOMPOSED, T.PREC_BF16, filters=filters, model_id=mid,
-                      score_tol=1e-2, check_parts=False, min_agree=0.95)
+                      score_tol=1e-2, check_parts=False, min_agree=0.0)
 
 
 def test_full_rank_decomposition_equals_full_form(torch, T, ctx):
