@@ -72,10 +72,10 @@ __device__ __forceinline__ void zt_ld_wait(uint32_t (&r)[16])
 
 // One Z row of a thread's half of the output columns: the x pass (b_r), the y pass into the ring of HH output rows
 // (lambda_r a_r, increasing dy), and the output row it completes into the term's reduction rows. C0: the half's first
-// output column; COWN: its first column this half writes (the two halves overlap by one column when TX is odd).
-template <int HH, int WW, int NC, int TY, int C0, int COWN>
+// output column and NC its number of columns (the first NC of the NCM accumulator columns).
+template <int HH, int WW, int NC, int NCM, int TY, int C0>
 __device__ __forceinline__ void zt_row(int y, const uint32_t (&zc)[16], const float (&a)[HH], const float (&bb)[WW],
-                                       float (&acc)[HH][NC], float *red_t)
+                                       float (&acc)[HH][NCM], float *red_t)
 {
     float X[NC];
 #pragma unroll
@@ -97,7 +97,7 @@ __device__ __forceinline__ void zt_row(int y, const uint32_t (&zc)[16], const fl
     if (o >= 0) {
         float *rr = red_t + (o % ZT_RR) * ZT_RS + C0;
 #pragma unroll
-        for (int c = COWN; c < NC; ++c) rr[c] = acc[o % HH][c];
+        for (int c = 0; c < NC; ++c) rr[c] = acc[o % HH][c];
     }
 }
 
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(ZT_THREADS, 2)
                     const uint8_t *__restrict__ cbank_lo, int ld, const int *__restrict__ group_t0, int *err)
 {
     constexpr int TX = ZT_T - WW + 1, TY = ZT_T - HH + 1;
-    constexpr int NC = (TX + 1) / 2;  // output columns per thread (the two halves overlap by 2 NC - TX)
+    constexpr int NC = (TX + 1) / 2;  // output columns of the first half; the second half takes the other TX - NC
     constexpr uint32_t NP = SPLIT ? 2 : 1;
     constexpr uint32_t REC = zt_record_bytes();
     extern __shared__ __align__(1024) uint8_t sm[];
@@ -222,15 +222,11 @@ __global__ void __launch_bounds__(ZT_THREADS, 2)
         float *out = J->out;
 
         float acc[HH][NC];
-        uint32_t zc[16], zn[16];
-        zt_ld16_nowait(tq, zc);
-        zt_ld_wait(zc);
-#pragma unroll
-        for (int y = 0; y < ZT_T; ++y) {
-            if (y + 1 < ZT_T) zt_ld16_nowait(tq + 16 * (y + 1), zn);
-            // the passes of Z row y for this thread's half (warp-uniform branch; each half has constant indices)
-            if (hf) zt_row<HH, WW, NC, TY, TX - NC, NC - (TX - NC)>(y, zc, a, bb, acc, red + t * ZT_TS);
-            else zt_row<HH, WW, NC, TY, 0, 0>(y, zc, a, bb, acc, red + t * ZT_TS);
+        // the passes of Z row y (held in zc) for this thread's half, and the reduction round it completes
+        auto row_step = [&](const int y, const uint32_t(&zc)[16]) {
+            // warp-uniform branch; each half has constant indices
+            if (hf) zt_row<HH, WW, TX - NC, NC, TY, NC>(y, zc, a, bb, acc, red + t * ZT_TS);
+            else zt_row<HH, WW, NC, NC, TY, 0>(y, zc, a, bb, acc, red + t * ZT_TS);
             const int o = y - (HH - 1);  // output row completed by this Z row
             if (o >= 0) {
                 if (o % ZT_RR == ZT_RR - 1 || o == TY - 1) {
@@ -265,11 +261,20 @@ __global__ void __launch_bounds__(ZT_THREADS, 2)
                     __syncthreads();
                 }
             }
-            if (y + 1 < ZT_T) {
-                zt_ld_wait(zn);
+        };
+        // two row buffers in turn: the next row's TMEM load is in flight during the current row's passes
+        static_assert(ZT_T % 2 == 0, "rows are taken in pairs");
+        uint32_t z0[16], z1[16];
+        zt_ld16_nowait(tq, z0);
+        zt_ld_wait(z0);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) zc[i] = zn[i];
-            }
+        for (int y = 0; y < ZT_T; y += 2) {
+            zt_ld16_nowait(tq + 16 * (y + 1), z1);
+            row_step(y, z0);
+            zt_ld_wait(z1);
+            if (y + 2 < ZT_T) zt_ld16_nowait(tq + 16 * (y + 2), z0);
+            row_step(y + 1, z1);
+            if (y + 2 < ZT_T) zt_ld_wait(z0);
         }
         // every TMEM read of this item is complete (the last round's barrier follows the last wait) before the next
         // item's MMAs overwrite the accumulator

@@ -178,11 +178,11 @@ def test_unfusable_groups_fall_back(torch, T, ctx):
     T.tdpm_release(ctx, plain)
 
 
-@pytest.mark.parametrize("ranks", [(40, 30), (55, 36), (64, 13)])
+@pytest.mark.parametrize("ranks", [(40, 30), (55, 36), (64, 13), (64, 32), (32, 32)])
 def test_terms_kernel_matches_oracle_at_high_rank(torch, T, ctx, ranks):
     """The terms-on-M kernel with groups whose filters span several warps of terms (30 terms: four filters per
-    128-term group, 40 terms: three; 13 terms: nine filters), with Sec. 5's (S, T) root / part rank pairs, against the oracle on the
-    same factors (split BF16: 1e-4 of the FP64 result), and the detections at >= 99.5% agreement. A group whose every
+    128-term group, 40 terms: three; 13 terms: nine filters; 32 terms: four, on 6x6 parts and, at (32, 32), on 7x7
+    roots), with Sec. 5's (S, T) root / part rank pairs, against the oracle on the same factors (split BF16: 1e-4 of the FP64 result), and the detections at >= 99.5% agreement. A group whose every
     filter is at its exact rank (h*w: the slice form; all of them at (55, 36)) is scored by the full form's kernel on
     the original filters, so its maps equal the full correlation's."""
     wl = synth.config_c2()
