@@ -164,6 +164,20 @@ bool zsept_enabled()
     return on;
 }
 
+// The untuned form of the tensor-core correlation launches: TDPM_CORR_FORM=tile or =persistent fixes it for every
+// precision (a profiling aid; the tuner, when on, still times both); -1 when unset.
+int corr_form_override()
+{
+    static const int v = [] {
+        const char *e = getenv("TDPM_CORR_FORM");
+        if (!e) return -1;
+        if (!strcmp(e, "tile")) return 0;
+        if (!strcmp(e, "persistent")) return 1;
+        return -1;
+    }();
+    return v;
+}
+
 // The filter groups of a per-filter decomposed shape group for the fused kernel: consecutive filters while their
 // terms fit nmax (and the bank rows an MMA of the rounded-up width reads exist). Empty when the group cannot be fused.
 std::vector<ZsGroup> fused_groups(const Group &g, int *nmax_out)
@@ -451,7 +465,8 @@ std::shared_ptr<Plan> make_plan(const Model &m, int model_id, const tdpm_pyramid
         P->g_rec_tiles[gi] = rec_tiles;
         // untuned: the balanced width; the persistent form for split operands (three MMAs per step keep the tensor
         // cores busy enough for the accumulator double buffer to pay), the tile form otherwise
-        const int persist = P->split ? kTcPersistent : 0;
+        const int form = corr_form_override();
+        const int persist = (form < 0 ? P->split : form == 1) ? kTcPersistent : 0;
         P->g_nt[gi] = (P->gdec(gi) ? corr_tc_default_nt(g.R, 1) : corr_tc_default_nt(g.K, g.h * g.w)) | persist;
         P->g_rec_nt[gi] = P->rec_tc(g) ? corr_tc_default_nt(g.K, g.Upad / FD) | persist : 0;
     }
