@@ -382,7 +382,9 @@ tdpm_status tdpm_dt_noalloc(const float *S, int32_t H, int32_t W, const float d[
 /* Correlation of K filters of one shape with one feature level (step 1, Sec. 2), on device buffers:
  *   out[k][y][x] = sum_{dy<h,dx<w,c<32} filt[k][dy][dx][c] * feat[y+dy][x+dx][c], y < H-h+1, x < W-w+1.
  * feat: device NHWC FP32; filt: HOST [K][h][w][32] FP32 (uploaded per call); out: device [K][H-h+1][W-w+1] FP32.
- * precision FP32 runs the FP32 SIMT kernel, BF16 the tcgen05 tensor-core kernel on BF16-rounded operands. */
+ * precision FP32 runs the FP32 SIMT kernel, BF16 the tcgen05 tensor-core kernel on BF16-rounded operands. The
+ * tensor-core precisions run the one-CTA-per-tile form, or the persistent form when the environment variable
+ * TDPM_CORR_FORM is "persistent" (read at each call); both give the same results. */
 tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float *filt_host, int32_t K, int32_t h,
                            int32_t w, int32_t precision, float *out, void *stream);
 

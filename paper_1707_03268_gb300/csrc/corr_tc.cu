@@ -10,10 +10,12 @@
 //
 // Positions are flattened over the full level width (p = y*W + x, so a 128-row M tile is one contiguous run of cells
 // and rows with x >= W-w+1 are computed and dropped). Features are stored as BF16 in a channel-chunk-planar layout
-// [4][H*W][8] (16 bytes per cell per chunk): a TMA box {8 ch, 128 cells, 4 chunks} at cell p0 + dy*W + dx lands in
-// shared memory as the no-swizzle K-major canonical layout of the A operand (core matrix = 8 cells x 16 bytes;
-// 8-row groups 128 bytes apart, K chunks 2048 bytes apart). Filter taps are stored [tap][4][N][8] and each tap's
-// N-tile slice is fetched with four 1-D bulk copies into the same layout for B. One thread issues the copies, one
+// [4][H*W][8] (16 bytes per cell per chunk). The taps of one filter row read the same cells shifted by dx, so one TMA
+// box {8 ch, 144 cells, 4 chunks} at cell p0 + dy*W serves up to 17 of them: it lands in shared memory as the
+// no-swizzle K-major canonical layout (core matrix = 8 cells x 16 bytes; 8-row groups 128 bytes apart, K chunks 2304
+// bytes apart), and the A operand of tap dx is that segment with its descriptor's start moved by 16 dx bytes. Filter
+// taps are stored [tap][4][N][8] and each tap's N-tile slice is fetched with four 1-D bulk copies into the same layout
+// for B. A segments and B slices have rings of their own. One thread issues the copies, one
 // issues the MMAs, and all four warps drain TMEM (32x32b loads) and store coalesced rows of the output maps.
 // Every mbarrier wait is bounded: on expiry the kernel raises the context's error flag and carries on to a clean exit.
 #include <cuda.h>
@@ -29,7 +31,9 @@ namespace tdpm {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr uint32_t A_PLANE_BYTES = TC_M * 16;  // one 8-channel chunk of 128 cells
+constexpr int TC_MS = 144;                        // cells of an A row segment: an M tile and up to 16 cells right of it
+constexpr int TC_DXS = TC_MS - TC_M + 1;          // filter width one segment serves (17, above the widest filter: 16)
+constexpr uint32_t A_SEG_PLANE = TC_MS * 16;      // one 16-byte K chunk of a segment
 
 template <class Job>
 __device__ __forceinline__ int find_job(const Job *jobs, int n, int idx)
@@ -58,9 +62,10 @@ __device__ __forceinline__ TileRef tile_ref(const TcJob *jobs, int n_jobs, int t
 }
 
 // Persistent: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... with three roles.
-//   warp 0 lane 0  producer: per tap of every tile, one TMA box of the input (128 cells x one tap's 32 channels) and
-//                  the tap's N-tile slice of the bank (1-D bulk copies), into a ring of `stages` shared-memory slots
-//                  that runs on across tile boundaries;
+//   warp 0 lane 0  producer: per filter row (and channel block) of every tile, one TMA box of the input (a row
+//                  segment of 144 cells x 32 channels, which serves up to 17 taps) into a ring of sa_n slots, and per
+//                  tap its N-tile slice of the bank (1-D bulk copies) into a ring of sb_n slots; both rings run on
+//                  across tile boundaries;
 //   warp 1 lane 0  MMA issuer: the tile's taps into one of two TMEM accumulators (tiles alternate), then a commit that
 //                  hands the accumulator to the epilogue;
 //   warps 2..      epilogue (TC_EPI warps): drain the accumulator with 32x32b loads (warp w reads TMEM lanes
@@ -82,29 +87,34 @@ __global__ void __launch_bounds__(TC_THREADS_P, 1) corr_tc_persistent_kernel(con
                                                                   int total_tiles, const uint8_t *__restrict__ filt,
                                                                   const uint8_t *__restrict__ filt_lo, int K, int ld,
                                                                   int NT, int n_tiles_n, int h, int w, int cb,
-                                                                  uint32_t acc_cols, int stages, float scale, int *err)
+                                                                  uint32_t acc_cols, int sa_n, int sb_n, float scale,
+                                                                  int *err)
 {
     static_assert(!(SPLIT && FP8), "split operands are BF16");
     extern __shared__ __align__(1024) uint8_t sm[];
     constexpr uint32_t NPART = SPLIT ? 2 : 1;
     constexpr int CHUNKS = FP8 ? 2 : 4;                              // 16-byte K chunks per tap
-    constexpr uint32_t A_BYTES = TC_M * 16 * CHUNKS;                  // one tap of A
+    constexpr uint32_t A_SEG_BYTES = A_SEG_PLANE * CHUNKS;            // one row segment of one channel block
     const uint32_t b_part_bytes = (uint32_t)NT * 16 * CHUNKS;
-    const uint32_t a_stage_bytes = NPART * A_BYTES, b_stage_bytes = NPART * b_part_bytes;
+    const uint32_t a_stage_bytes = NPART * A_SEG_BYTES, b_stage_bytes = NPART * b_part_bytes;
     uint8_t *a_smem = sm;
-    uint8_t *b_smem = sm + stages * a_stage_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + stages * b_stage_bytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 4);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + stages);
-    const uint32_t acc_full0 = smem_u32(bars + 2 * stages), acc_empty0 = smem_u32(bars + 2 * stages + 2);
+    uint8_t *b_smem = sm + sa_n * a_stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + sb_n * b_stage_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * sa_n + 2 * sb_n + 4);
+    const uint32_t afull0 = smem_u32(bars), aempty0 = smem_u32(bars + sa_n);
+    const uint32_t bfull0 = smem_u32(bars + 2 * sa_n), bempty0 = smem_u32(bars + 2 * sa_n + sb_n);
+    const uint32_t acc_full0 = smem_u32(bars + 2 * sa_n + 2 * sb_n), acc_empty0 = acc_full0 + 16;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int taps = h * w * cb;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < stages; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int s = 0; s < sa_n; ++s) {
+            mbar_init(afull0 + 8 * s, 1);
+            mbar_init(aempty0 + 8 * s, 1);
+        }
+        for (int s = 0; s < sb_n; ++s) {
+            mbar_init(bfull0 + 8 * s, 1);
+            mbar_init(bempty0 + 8 * s, 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full0 + 8 * b, 1);
@@ -124,69 +134,91 @@ __global__ void __launch_bounds__(TC_THREADS_P, 1) corr_tc_persistent_kernel(con
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // producer
-        int g = 0;
+        // producer: per filter row dy and channel block one TMA box of TC_MS cells (the row segment) into the A ring,
+        // then each tap's N-tile slice of the bank into the B ring; both rings run on across tiles
+        int ga = 0, gb = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             const TileRef T = tile_ref(jobs, n_jobs, tile, n_tiles_n, NT);
             const int W = T.J->W;
-            for (int t = 0; t < taps; ++t, ++g) {
-                const int s = g % stages;
-                if (g >= stages) mbar_wait(empty0 + 8 * s, ((g / stages) - 1) & 1, err);
-                const uint32_t full = full0 + 8 * s;
-                mbar_expect_tx(full, a_stage_bytes + b_stage_bytes);
-                const int ts = t / cb, blk = t - ts * cb;
-                const int dy = ts / w, dx = ts - dy * w;
-                const uint32_t adst = smem_u32(a_smem + s * a_stage_bytes);
-                tma_load_3d(adst, &T.J->tmap, 0, T.p0 + dy * W + dx, CHUNKS * blk, full);
-                if (SPLIT) tma_load_3d(adst + A_BYTES, &T.J->tmap_lo, 0, T.p0 + dy * W + dx, CHUNKS * blk, full);
-                const uint32_t bdst = smem_u32(b_smem + s * b_stage_bytes);
-                for (int kc = 0; kc < CHUNKS; ++kc) {
-                    const size_t off = (((size_t)t * CHUNKS + kc) * ld + T.n0) * 16;  // bytes
-                    bulk_load(bdst + kc * NT * 16, filt + off, (uint32_t)NT * 16, full);
-                    if (SPLIT) bulk_load(bdst + b_part_bytes + kc * NT * 16, filt_lo + off, (uint32_t)NT * 16, full);
+            for (int dy = 0; dy < h; ++dy)
+                for (int blk = 0; blk < cb; ++blk, ++ga) {
+                    const int sa = ga % sa_n;
+                    if (ga >= sa_n) mbar_wait(aempty0 + 8 * sa, ((ga / sa_n) - 1) & 1, err);
+                    const uint32_t afull = afull0 + 8 * sa;
+                    mbar_expect_tx(afull, a_stage_bytes);
+                    const uint32_t adst = smem_u32(a_smem + sa * a_stage_bytes);
+                    const int cell = T.p0 + dy * W;
+                    tma_load_3d(adst, &T.J->tmap, 0, cell, CHUNKS * blk, afull);
+                    if (SPLIT) tma_load_3d(adst + A_SEG_BYTES, &T.J->tmap_lo, 0, cell, CHUNKS * blk, afull);
+                    for (int dx = 0; dx < w; ++dx, ++gb) {
+                        const int sb = gb % sb_n;
+                        if (gb >= sb_n) mbar_wait(bempty0 + 8 * sb, ((gb / sb_n) - 1) & 1, err);
+                        const uint32_t bfull = bfull0 + 8 * sb;
+                        mbar_expect_tx(bfull, b_stage_bytes);
+                        const int t = (dy * w + dx) * cb + blk;
+                        const uint32_t bdst = smem_u32(b_smem + sb * b_stage_bytes);
+                        for (int kc = 0; kc < CHUNKS; ++kc) {
+                            const size_t off = (((size_t)t * CHUNKS + kc) * ld + T.n0) * 16;  // bytes
+                            bulk_load(bdst + kc * NT * 16, filt + off, (uint32_t)NT * 16, bfull);
+                            if (SPLIT)
+                                bulk_load(bdst + b_part_bytes + kc * NT * 16, filt_lo + off, (uint32_t)NT * 16,
+                                          bfull);
+                        }
+                    }
                 }
-            }
         }
         // the last fill of every slot has landed before the CTA can exit (immediate unless a wait gave up)
-        for (int k = g - stages < 0 ? 0 : g - stages; k < g; ++k) mbar_drain(full0 + 8 * (k % stages), (k / stages) & 1);
+        for (int k = ga - sa_n < 0 ? 0 : ga - sa_n; k < ga; ++k) mbar_drain(afull0 + 8 * (k % sa_n), (k / sa_n) & 1);
+        for (int k = gb - sb_n < 0 ? 0 : gb - sb_n; k < gb; ++k) mbar_drain(bfull0 + 8 * (k % sb_n), (k / sb_n) & 1);
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: BF16, two K=16 steps per tap (channel chunks {0,1} and {2,3}); FP8, one K=32 step
+        // MMA issuer: tap dx of a segment is its A operand shifted by dx cells (16 bytes per cell in every K chunk);
+        // BF16, two K=16 steps per tap (channel chunks {0,1} and {2,3}); FP8, one K=32 step
         const uint32_t idesc = FP8 ? instr_desc_e4m3(TC_M, NT) : instr_desc(TC_M, NT);
-        int g = 0, li = 0;
+        int ga = 0, gb = 0, li = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++li) {
             const int b = li & 1;
             if (li >= 2) mbar_wait(acc_empty0 + 8 * b, ((li >> 1) - 1) & 1, err);  // epilogue done with it
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc = tmem + (uint32_t)b * acc_cols;
-            for (int t = 0; t < taps; ++t, ++g) {
-                const int s = g % stages;
-                mbar_wait(full0 + 8 * s, (g / stages) & 1, err);
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a_base = smem_u32(a_smem + s * a_stage_bytes);
-                const uint32_t b_base = smem_u32(b_smem + s * b_stage_bytes);
-                if (FP8) {
-                    const uint64_t ad = smem_desc(a_base, A_PLANE_BYTES, 128);
-                    const uint64_t bd = smem_desc(b_base, (uint32_t)NT * 16, 128);
-                    mma_e4m3(acc, ad, bd, idesc, t != 0);
-                } else {
+            uint32_t accum = 0;  // the tile's first MMA overwrites the accumulator
+            for (int dy = 0; dy < h; ++dy)
+                for (int blk = 0; blk < cb; ++blk, ++ga) {
+                    const int sa = ga % sa_n;
+                    mbar_wait(afull0 + 8 * sa, (ga / sa_n) & 1, err);
+                    const uint32_t a_seg = smem_u32(a_smem + sa * a_stage_bytes);
+                    for (int dx = 0; dx < w; ++dx, ++gb) {
+                        const int sb = gb % sb_n;
+                        mbar_wait(bfull0 + 8 * sb, (gb / sb_n) & 1, err);
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a_base = a_seg + (uint32_t)dx * 16;
+                        const uint32_t b_base = smem_u32(b_smem + sb * b_stage_bytes);
+                        if (FP8) {
+                            const uint64_t ad = smem_desc(a_base, A_SEG_PLANE, 128);
+                            const uint64_t bd = smem_desc(b_base, (uint32_t)NT * 16, 128);
+                            mma_e4m3(acc, ad, bd, idesc, accum);
+                            accum = 1;
+                        } else {
 #pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
-                        const uint64_t ad = smem_desc(a_base + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
-                        const uint64_t bd = smem_desc(b_base + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
-                        mma_bf16(acc, ad, bd, idesc, (t | ks) != 0);
-                        if (SPLIT) {
-                            const uint64_t ad_lo =
-                                smem_desc(a_base + A_BYTES + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
-                            const uint64_t bd_lo =
-                                smem_desc(b_base + b_part_bytes + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
-                            mma_bf16(acc, ad, bd_lo, idesc, 1u);
-                            mma_bf16(acc, ad_lo, bd, idesc, 1u);
+                            for (int ks = 0; ks < 2; ++ks) {
+                                const uint64_t ad = smem_desc(a_base + ks * 2 * A_SEG_PLANE, A_SEG_PLANE, 128);
+                                const uint64_t bd = smem_desc(b_base + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
+                                mma_bf16(acc, ad, bd, idesc, accum);
+                                accum = 1;
+                                if (SPLIT) {
+                                    const uint64_t ad_lo = smem_desc(a_base + A_SEG_BYTES + ks * 2 * A_SEG_PLANE,
+                                                                     A_SEG_PLANE, 128);
+                                    const uint64_t bd_lo = smem_desc(b_base + b_part_bytes + ks * 2 * NT * 16,
+                                                                     (uint32_t)NT * 16, 128);
+                                    mma_bf16(acc, ad, bd_lo, idesc, 1u);
+                                    mma_bf16(acc, ad_lo, bd, idesc, 1u);
+                                }
+                            }
                         }
+                        mma_commit(bempty0 + 8 * sb);  // the B slot is free once these MMAs have read it
                     }
+                    mma_commit(aempty0 + 8 * sa);  // and the segment once its last tap's MMAs have
                 }
-                mma_commit(empty0 + 8 * s);  // the slot is free once these MMAs have read it
-            }
-            mma_commit(acc_full0 + 8 * b);   // the accumulator is complete once every MMA has finished
+            mma_commit(acc_full0 + 8 * b);  // the accumulator is complete once every MMA has finished
         }
     } else if (warp >= 2) {
         // epilogue: TMEM lane m of the accumulator holds position p0 + m; columns are the N tile's filters
@@ -229,7 +261,6 @@ __global__ void __launch_bounds__(TC_THREADS_P, 1) corr_tc_persistent_kernel(con
 }
 
 constexpr int TC_THREADS = 128;
-constexpr int TC_TILE_STAGES = 4;
 
 // Tile form: one CTA per (M tile, N tile), M tiles numbered across the jobs (a job's begin is its first M tile), so the job
 // tables do not depend on the N tiling; filt: [h*w*cb][4][ld][8] BF16 (tap-major, then channel block, ld rows per
@@ -244,20 +275,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_tile_kernel(const TcJob
                                                                 const uint8_t *__restrict__ filt,
                                                                 const uint8_t *__restrict__ filt_lo, int K, int ld,
                                                                 int NT, int n_tiles_n, int h, int w, int cb,
-                                                                uint32_t tmem_cols, int stages, float scale, int *err)
+                                                                uint32_t tmem_cols, int sa_n, int sb_n, float scale,
+                                                                int *err)
 {
     static_assert(!(SPLIT && FP8), "split operands are BF16");
     extern __shared__ __align__(1024) uint8_t sm[];
     constexpr uint32_t NPART = SPLIT ? 2 : 1;
     constexpr int CHUNKS = FP8 ? 2 : 4;                              // 16-byte K chunks per tap
-    constexpr uint32_t A_BYTES = TC_M * 16 * CHUNKS;                  // one tap of A
+    constexpr uint32_t A_SEG_BYTES = A_SEG_PLANE * CHUNKS;            // one row segment of one channel block
     const uint32_t b_part_bytes = (uint32_t)NT * 16 * CHUNKS;
-    const uint32_t a_stage_bytes = NPART * A_BYTES, b_stage_bytes = NPART * b_part_bytes;
+    const uint32_t a_stage_bytes = NPART * A_SEG_BYTES, b_stage_bytes = NPART * b_part_bytes;
     uint8_t *a_smem = sm;
-    uint8_t *b_smem = sm + stages * a_stage_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + stages * b_stage_bytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * stages + 1);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + stages), done = smem_u32(bars + 2 * stages);
+    uint8_t *b_smem = sm + sa_n * a_stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(b_smem + sb_n * b_stage_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * sa_n + 2 * sb_n + 1);
+    const uint32_t afull0 = smem_u32(bars), aempty0 = smem_u32(bars + sa_n);
+    const uint32_t bfull0 = smem_u32(bars + 2 * sa_n), bempty0 = smem_u32(bars + 2 * sa_n + sb_n);
+    const uint32_t done = smem_u32(bars + 2 * sa_n + 2 * sb_n);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nt = blockIdx.x % n_tiles_n, mg = blockIdx.x / n_tiles_n;
@@ -266,12 +300,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_tile_kernel(const TcJob
     const int mt = mg - J->begin;
     const int p0 = mt * TC_M, n0 = nt * NT;
     const int W = J->W, Ho = J->Ho, Wo = J->Wo;
-    const int taps = h * w * cb;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < stages; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int s = 0; s < sa_n; ++s) {
+            mbar_init(afull0 + 8 * s, 1);
+            mbar_init(aempty0 + 8 * s, 1);
+        }
+        for (int s = 0; s < sb_n; ++s) {
+            mbar_init(bfull0 + 8 * s, 1);
+            mbar_init(bempty0 + 8 * s, 1);
         }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -288,54 +325,80 @@ __global__ void __launch_bounds__(TC_THREADS, 1) corr_tc_tile_kernel(const TcJob
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // producer: one A box and four B chunk copies per tap
-        for (int t = 0; t < taps; ++t) {
-            const int s = t % stages;
-            if (t >= stages) mbar_wait(empty0 + 8 * s, ((t / stages) - 1) & 1, err);
-            const uint32_t full = full0 + 8 * s;
-            mbar_expect_tx(full, a_stage_bytes + b_stage_bytes);
-            const int ts = t / cb, blk = t - ts * cb;
-            const int dy = ts / w, dx = ts - dy * w;
-            const uint32_t adst = smem_u32(a_smem + s * a_stage_bytes);
-            tma_load_3d(adst, &J->tmap, 0, p0 + dy * W + dx, CHUNKS * blk, full);
-            if (SPLIT) tma_load_3d(adst + A_BYTES, &J->tmap_lo, 0, p0 + dy * W + dx, CHUNKS * blk, full);
-            const uint32_t bdst = smem_u32(b_smem + s * b_stage_bytes);
-            for (int kc = 0; kc < CHUNKS; ++kc) {
-                const size_t off = (((size_t)t * CHUNKS + kc) * ld + n0) * 16;  // bytes
-                bulk_load(bdst + kc * NT * 16, filt + off, (uint32_t)NT * 16, full);
-                if (SPLIT) bulk_load(bdst + b_part_bytes + kc * NT * 16, filt_lo + off, (uint32_t)NT * 16, full);
-            }
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: BF16, two K=16 steps per tap (channel chunks {0,1} and {2,3}); FP8, one K=32 step
-        const uint32_t idesc = FP8 ? instr_desc_e4m3(TC_M, NT) : instr_desc(TC_M, NT);
-        for (int t = 0; t < taps; ++t) {
-            const int s = t % stages;
-            mbar_wait(full0 + 8 * s, (t / stages) & 1, err);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_base = smem_u32(a_smem + s * a_stage_bytes);
-            const uint32_t b_base = smem_u32(b_smem + s * b_stage_bytes);
-            if (FP8) {
-                const uint64_t ad = smem_desc(a_base, A_PLANE_BYTES, 128);
-                const uint64_t bd = smem_desc(b_base, (uint32_t)NT * 16, 128);
-                mma_e4m3(tmem, ad, bd, idesc, t != 0);
-            } else {
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint64_t ad = smem_desc(a_base + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
-                    const uint64_t bd = smem_desc(b_base + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
-                    mma_bf16(tmem, ad, bd, idesc, (t | ks) != 0);
-                    if (SPLIT) {
-                        const uint64_t ad_lo = smem_desc(a_base + A_BYTES + ks * 2 * A_PLANE_BYTES, A_PLANE_BYTES, 128);
-                        const uint64_t bd_lo =
-                            smem_desc(b_base + b_part_bytes + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
-                        mma_bf16(tmem, ad, bd_lo, idesc, 1u);
-                        mma_bf16(tmem, ad_lo, bd, idesc, 1u);
+        // producer: one A row segment (TC_MS cells) per filter row and channel block, and each tap's N-tile slice of
+        // the bank
+        int ga = 0, gb = 0;
+        for (int dy = 0; dy < h; ++dy)
+            for (int blk = 0; blk < cb; ++blk, ++ga) {
+                const int sa = ga % sa_n;
+                if (ga >= sa_n) mbar_wait(aempty0 + 8 * sa, ((ga / sa_n) - 1) & 1, err);
+                const uint32_t afull = afull0 + 8 * sa;
+                mbar_expect_tx(afull, a_stage_bytes);
+                const uint32_t adst = smem_u32(a_smem + sa * a_stage_bytes);
+                const int cell = p0 + dy * W;
+                tma_load_3d(adst, &J->tmap, 0, cell, CHUNKS * blk, afull);
+                if (SPLIT) tma_load_3d(adst + A_SEG_BYTES, &J->tmap_lo, 0, cell, CHUNKS * blk, afull);
+                for (int dx = 0; dx < w; ++dx, ++gb) {
+                    const int sb = gb % sb_n;
+                    if (gb >= sb_n) mbar_wait(bempty0 + 8 * sb, ((gb / sb_n) - 1) & 1, err);
+                    const uint32_t bfull = bfull0 + 8 * sb;
+                    mbar_expect_tx(bfull, b_stage_bytes);
+                    const int t = (dy * w + dx) * cb + blk;
+                    const uint32_t bdst = smem_u32(b_smem + sb * b_stage_bytes);
+                    for (int kc = 0; kc < CHUNKS; ++kc) {
+                        const size_t off = (((size_t)t * CHUNKS + kc) * ld + n0) * 16;  // bytes
+                        bulk_load(bdst + kc * NT * 16, filt + off, (uint32_t)NT * 16, bfull);
+                        if (SPLIT)
+                            bulk_load(bdst + b_part_bytes + kc * NT * 16, filt_lo + off, (uint32_t)NT * 16, bfull);
                     }
                 }
             }
-            mma_commit(empty0 + 8 * s);
-        }
+        // the last fill of every slot has landed before the CTA can exit (immediate unless a wait gave up)
+        for (int k = ga - sa_n < 0 ? 0 : ga - sa_n; k < ga; ++k) mbar_drain(afull0 + 8 * (k % sa_n), (k / sa_n) & 1);
+        for (int k = gb - sb_n < 0 ? 0 : gb - sb_n; k < gb; ++k) mbar_drain(bfull0 + 8 * (k % sb_n), (k / sb_n) & 1);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: tap dx of a segment is its A operand shifted by dx cells; BF16, two K=16 steps per tap (channel
+        // chunks {0,1} and {2,3}); FP8, one K=32 step
+        const uint32_t idesc = FP8 ? instr_desc_e4m3(TC_M, NT) : instr_desc(TC_M, NT);
+        int ga = 0, gb = 0;
+        uint32_t accum = 0;  // the first MMA overwrites the accumulator
+        for (int dy = 0; dy < h; ++dy)
+            for (int blk = 0; blk < cb; ++blk, ++ga) {
+                const int sa = ga % sa_n;
+                mbar_wait(afull0 + 8 * sa, (ga / sa_n) & 1, err);
+                const uint32_t a_seg = smem_u32(a_smem + sa * a_stage_bytes);
+                for (int dx = 0; dx < w; ++dx, ++gb) {
+                    const int sb = gb % sb_n;
+                    mbar_wait(bfull0 + 8 * sb, (gb / sb_n) & 1, err);
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a_base = a_seg + (uint32_t)dx * 16;
+                    const uint32_t b_base = smem_u32(b_smem + sb * b_stage_bytes);
+                    if (FP8) {
+                        const uint64_t ad = smem_desc(a_base, A_SEG_PLANE, 128);
+                        const uint64_t bd = smem_desc(b_base, (uint32_t)NT * 16, 128);
+                        mma_e4m3(tmem, ad, bd, idesc, accum);
+                        accum = 1;
+                    } else {
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks) {
+                            const uint64_t ad = smem_desc(a_base + ks * 2 * A_SEG_PLANE, A_SEG_PLANE, 128);
+                            const uint64_t bd = smem_desc(b_base + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
+                            mma_bf16(tmem, ad, bd, idesc, accum);
+                            accum = 1;
+                            if (SPLIT) {
+                                const uint64_t ad_lo =
+                                    smem_desc(a_base + A_SEG_BYTES + ks * 2 * A_SEG_PLANE, A_SEG_PLANE, 128);
+                                const uint64_t bd_lo =
+                                    smem_desc(b_base + b_part_bytes + ks * 2 * NT * 16, (uint32_t)NT * 16, 128);
+                                mma_bf16(tmem, ad, bd_lo, idesc, 1u);
+                                mma_bf16(tmem, ad_lo, bd, idesc, 1u);
+                            }
+                        }
+                    }
+                    mma_commit(bempty0 + 8 * sb);
+                }
+                mma_commit(aempty0 + 8 * sa);
+            }
         mma_commit(done);
     }
     __syncwarp();
@@ -466,10 +529,30 @@ int corr_tc_bank_rows(int K)
     return rows;
 }
 
-size_t corr_tc_smem_bytes(int NT, bool split, bool fp8, int stages)
+// Shared memory of a dense launch: sa A row segments and sb B slices, their full / empty barriers, four more barriers
+// and the TMEM address.
+size_t corr_tc_smem_bytes(int NT, bool split, bool fp8, int sa, int sb)
 {
-    const size_t parts = split ? 2 : 1, tap_bytes = fp8 ? 32 : 64;  // bytes of one row of one tap
-    return stages * parts * (TC_M + (size_t)NT) * tap_bytes + 8 * (2 * stages + 4) + 16;
+    const size_t parts = split ? 2 : 1, tap_bytes = fp8 ? 32 : 64;  // bytes of one row (cell or filter) of one tap
+    return parts * tap_bytes * ((size_t)sa * TC_MS + (size_t)sb * NT) + 8 * (2 * (size_t)sa + 2 * (size_t)sb + 4) + 16;
+}
+
+// Ring depths within a shared-memory budget: two A segments when one segment serves several taps (one per tap
+// otherwise, so both rings advance together), and as many B slices as fit, 2..maxb.
+void corr_tc_rings(int NT, bool split, bool fp8, int w, size_t budget, int maxb, int *sa, int *sb)
+{
+    const size_t seg = corr_tc_smem_bytes(NT, split, fp8, 1, 0) - corr_tc_smem_bytes(NT, split, fp8, 0, 0);
+    const size_t slice = corr_tc_smem_bytes(NT, split, fp8, 0, 1) - corr_tc_smem_bytes(NT, split, fp8, 0, 0);
+    if (w > 1) {
+        *sa = 2;
+        const size_t base = corr_tc_smem_bytes(NT, split, fp8, 2, 0);
+        *sb = budget > base ? (int)std::min<size_t>((size_t)maxb, (budget - base) / slice) : 2;
+    } else {
+        *sb = (int)std::min<size_t>((size_t)maxb, budget / (seg + slice + 32));
+        *sa = *sb;
+    }
+    *sb = std::max(2, *sb);
+    *sa = std::max(2, *sa);
 }
 
 namespace {
@@ -498,6 +581,7 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const v
     const int n_tiles_n = corr_tc_n_tiles(K, NT);
     // every N tile's bulk copies stay inside the bank's ld rows
     if (NT % 16 != 0 || NT < 16 || NT > 256 || n_tiles_n * NT > ld) return cudaErrorInvalidValue;
+    if (w > TC_DXS) return cudaErrorInvalidValue;  // one row segment serves every tap of a filter row
     if ((long long)m_tiles * n_tiles_n > 0x7fffffffll) return cudaErrorInvalidValue;
     const int total_tiles = m_tiles * n_tiles_n;
     const uint8_t *fb = static_cast<const uint8_t *>(filt_tc), *fl = static_cast<const uint8_t *>(filt_tc_lo);
@@ -505,11 +589,14 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const v
         // tile form: one CTA per tile, at most 512 / cols CTAs per SM (TMEM), enforced through the shared memory
         // request
         const int taps = h * w * cb;
-        const int stages = taps < TC_TILE_STAGES ? taps : TC_TILE_STAGES;
         uint32_t cols = 32;
         while (cols < (uint32_t)NT) cols <<= 1;
         const int max_ctas = 512 / (int)cols;
-        size_t smem = corr_tc_smem_bytes(NT, split, fp8, stages);
+        // rings within the share of shared memory of one of the CTAs that fit in TMEM (at least 48 KB)
+        const size_t budget = std::max<size_t>((size_t)kMaxDynamicSmem / (size_t)max_ctas - 1024, 49152);
+        int sa = 2, sb = 2;
+        corr_tc_rings(NT, split, fp8, w, budget, std::max(2, std::min(8, taps)), &sa, &sb);
+        size_t smem = corr_tc_smem_bytes(NT, split, fp8, sa, sb);
         const size_t floor_bytes = 233472 / (size_t)(max_ctas + 1);
         if (smem < floor_bytes) smem = floor_bytes;
         if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
@@ -521,13 +608,13 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const v
         note_launches(1);
         if (split)
             corr_tc_tile_kernel<true, false><<<total_tiles, TC_THREADS, smem, s>>>(
-                d_jobs, n_jobs, fb, fl, K, ld, NT, n_tiles_n, h, w, cb, cols, stages, 1.f, d_err);
+                d_jobs, n_jobs, fb, fl, K, ld, NT, n_tiles_n, h, w, cb, cols, sa, sb, 1.f, d_err);
         else if (fp8)
             corr_tc_tile_kernel<false, true><<<total_tiles, TC_THREADS, smem, s>>>(
-                d_jobs, n_jobs, fb, nullptr, K, ld, NT, n_tiles_n, h, w, cb, cols, stages, scale, d_err);
+                d_jobs, n_jobs, fb, nullptr, K, ld, NT, n_tiles_n, h, w, cb, cols, sa, sb, scale, d_err);
         else
             corr_tc_tile_kernel<false, false><<<total_tiles, TC_THREADS, smem, s>>>(
-                d_jobs, n_jobs, fb, nullptr, K, ld, NT, n_tiles_n, h, w, cb, cols, stages, 1.f, d_err);
+                d_jobs, n_jobs, fb, nullptr, K, ld, NT, n_tiles_n, h, w, cb, cols, sa, sb, 1.f, d_err);
         return cudaGetLastError();
     }
     uint32_t acc_cols = 32;
@@ -535,13 +622,12 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const v
     // two accumulators per CTA; at most 512 / (2 acc_cols) CTAs per SM fit in TMEM, enforced through the shared
     // memory request so that no CTA waits in tcgen05.alloc
     const int max_ctas = 512 / (2 * (int)acc_cols);
-    // ring depth: as many slots as the shared memory of one of those CTAs holds (2..12); the ring runs on across tiles,
-    // so even a single-tap contraction keeps several tiles' operands in flight
+    // ring depths: as many slots as the shared memory of one of those CTAs holds (B: 2..12); the rings run on across
+    // tiles, so even a single-tap contraction keeps several tiles' operands in flight
     const size_t per_cta = (size_t)kMaxDynamicSmem / (size_t)max_ctas - 1024;
-    const size_t slot = corr_tc_smem_bytes(NT, split, fp8, 1) - corr_tc_smem_bytes(NT, split, fp8, 0);
-    int stages = (int)std::min<size_t>(12, (per_cta - corr_tc_smem_bytes(NT, split, fp8, 0)) / slot);
-    stages = std::max(2, stages);
-    size_t smem = corr_tc_smem_bytes(NT, split, fp8, stages);
+    int sa = 2, sb = 2;
+    corr_tc_rings(NT, split, fp8, w, per_cta, 12, &sa, &sb);
+    size_t smem = corr_tc_smem_bytes(NT, split, fp8, sa, sb);
     const size_t floor_bytes = 233472 / (size_t)(max_ctas + 1);
     if (smem < floor_bytes) smem = floor_bytes;
     if (smem > (size_t)kMaxDynamicSmem) return cudaErrorInvalidValue;
@@ -558,14 +644,14 @@ cudaError_t launch_corr_tc(const TcJob *d_jobs, int n_jobs, int m_tiles, const v
     note_launches(1);
     if (split)
         corr_tc_persistent_kernel<true, false><<<grid, TC_THREADS_P, smem, s>>>(d_jobs, n_jobs, total_tiles, fb, fl, K, ld, NT,
-                                                                     n_tiles_n, h, w, cb, acc_cols, stages, 1.f, d_err);
+                                                                     n_tiles_n, h, w, cb, acc_cols, sa, sb, 1.f, d_err);
     else if (fp8)
         corr_tc_persistent_kernel<false, true><<<grid, TC_THREADS_P, smem, s>>>(d_jobs, n_jobs, total_tiles, fb, nullptr, K, ld,
-                                                                     NT, n_tiles_n, h, w, cb, acc_cols, stages, scale,
+                                                                     NT, n_tiles_n, h, w, cb, acc_cols, sa, sb, scale,
                                                                      d_err);
     else
         corr_tc_persistent_kernel<false, false><<<grid, TC_THREADS_P, smem, s>>>(d_jobs, n_jobs, total_tiles, fb, nullptr, K, ld,
-                                                                      NT, n_tiles_n, h, w, cb, acc_cols, stages, 1.f,
+                                                                      NT, n_tiles_n, h, w, cb, acc_cols, sa, sb, 1.f,
                                                                       d_err);
     return cudaGetLastError();
 }
@@ -587,14 +673,14 @@ cudaError_t launch_to_fp8_planar(const ConvJob *d_jobs, int n_jobs, long long to
 }
 
 
-// Tensor map over one BF16 planar array: dims {8 channels, cells, chunks}, box {8, 128, 4}, zero fill outside.
+// Tensor map over one BF16 planar array: dims {8 channels, cells, chunks}, box {8, 144, 4}, zero fill outside.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 namespace {
 
-// dims {elems per 16-byte chunk, cells, chunks}, box {elems, 128, the chunks of one tap (32 channels)}, zero fill
+// dims {elems per 16-byte chunk, cells, chunks}, box {elems, 144, the chunks of one tap (32 channels)}, zero fill
 // outside; strides in bytes
 EncodeTiledFn encode_fn()
 {
@@ -619,7 +705,7 @@ bool encode_tmap(CUtensorMap *map, CUtensorMapDataType type, int elems, void *ba
     if (chunks < (int)tap_chunks || chunks % tap_chunks) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)elems, (cuuint64_t)cells, (cuuint64_t)chunks};
     const cuuint64_t strides[2] = {16, (cuuint64_t)cells * 16};
-    const cuuint32_t box[3] = {(cuuint32_t)elems, (cuuint32_t)TC_M, tap_chunks};
+    const cuuint32_t box[3] = {(cuuint32_t)elems, (cuuint32_t)TC_MS, tap_chunks};
     const cuuint32_t estr[3] = {1, 1, 1};
     return fn(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;

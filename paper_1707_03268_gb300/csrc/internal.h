@@ -152,9 +152,9 @@ int corr_tc_default_nt(int K, int taps);     // untuned N tile width for K filte
 int corr_tc_nt_candidates(int K, int *out);  // up to 4 widths a tuner may choose; returns their number
 int corr_tc_bank_rows(int K);                // bank rows (ld) that fit every candidate width
 constexpr int kTcPersistent = 1 << 16;       // tile configuration code: N tile width | kTcPersistent
-// Tensor map of a BF16 planar array [chunks][cells][8] (chunks a multiple of 4), box {8, 128, 4}.
+// Tensor map of a BF16 planar array [chunks][cells][8] (chunks a multiple of 4), box {8, 144, 4}: a row segment.
 bool encode_level_tmap(CUtensorMap *map, const uint16_t *planar, long long cells, int chunks = 4);
-// Tensor map of an E4M3 planar level [2][cells][16] bytes, box {16, 128, 2}.
+// Tensor map of an E4M3 planar level [2][cells][16] bytes, box {16, 144, 2}: a row segment.
 bool encode_level_tmap_fp8(CUtensorMap *map, const uint8_t *planar, long long cells);
 
 // Tensor map of a BF16 planar level [4][H][W][8] as a 4-D array, box {8, 32 columns, 4 rows, 4 chunks}.

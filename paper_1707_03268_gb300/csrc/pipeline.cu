@@ -165,17 +165,15 @@ bool zsept_enabled()
 }
 
 // The untuned form of the tensor-core correlation launches: TDPM_CORR_FORM=tile or =persistent fixes it for every
-// precision (a profiling aid; the tuner, when on, still times both); -1 when unset.
+// precision (a profiling and testing aid; the tuner, when on, still times both) and for tdpm_correlate; -1 when unset.
+// Read at each plan build and each tdpm_correlate call.
 int corr_form_override()
 {
-    static const int v = [] {
-        const char *e = getenv("TDPM_CORR_FORM");
-        if (!e) return -1;
-        if (!strcmp(e, "tile")) return 0;
-        if (!strcmp(e, "persistent")) return 1;
-        return -1;
-    }();
-    return v;
+    const char *e = getenv("TDPM_CORR_FORM");
+    if (!e) return -1;
+    if (!strcmp(e, "tile")) return 0;
+    if (!strcmp(e, "persistent")) return 1;
+    return -1;
 }
 
 // The filter groups of a per-filter decomposed shape group for the fused kernel: consecutive filters while their
@@ -2186,7 +2184,8 @@ tdpm_status tdpm_correlate(const float *feat, int32_t H, int32_t W, const float 
                     : launch_to_bf16_planar(reinterpret_cast<const ConvJob *>(cjd), 1, 4 * cells, s);
         if (e == cudaSuccess)
             e = launch_corr_tc(reinterpret_cast<const TcJob *>(tjd), 1, tiles, bank, bank_lo, K, Npad, NT, h, w, 1,
-                               d_err, s, fp8, fp8 ? 1.f / (fscale * kFp8FeatureScale) : 1.f);
+                               d_err, s, fp8, fp8 ? 1.f / (fscale * kFp8FeatureScale) : 1.f,
+                               corr_form_override() == 1);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(dmem);

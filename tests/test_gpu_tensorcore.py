@@ -56,6 +56,33 @@ def test_correlate_bf16_tensor_cores(torch, T, H, W, h, w, K):
         assert rel_err(got[k], orc.correlate(feat, filt[k])) <= 1e-2, k
 
 
+@pytest.mark.parametrize("form", ["tile", "persistent"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3", "fp8"])
+@pytest.mark.parametrize("H,W,h,w,K", [(10, 60, 2, 16, 17), (30, 50, 16, 3, 5), (12, 40, 6, 6, 40), (9, 17, 1, 16, 3)])
+def test_correlate_row_segments_both_forms(torch, T, H, W, h, w, K, prec, form, monkeypatch):
+    """One A row segment of 144 cells serves every tap of a filter row (each tap a 16-byte shift of it), up to the
+    widest filter (16 columns, the last tap reading cells 15..142 of the segment) and the tallest (16 rows, 16
+    segments per tile); both kernel forms, every tensor-core precision, against the oracle (on the rounded operands for
+    BF16 and FP8, unrounded for split BF16)."""
+    monkeypatch.setenv("TDPM_CORR_FORM", form)
+    rng = np.random.default_rng(H * 1000 + W * 10 + K + 29)
+    feat = rng.uniform(0, 0.2, size=(H, W, 32)).astype(np.float32)
+    filt = rng.normal(0, 0.05, size=(K, h, w, 32)).astype(np.float32)
+    out = torch.full((K, H - h + 1, W - w + 1), float("nan"), device="cuda")
+    p = {"bf16": T.PREC_BF16, "bf16x3": T.PREC_BF16X3, "fp8": T.PREC_FP8}[prec]
+    T.tdpm_correlate(torch.from_numpy(feat).cuda(), filt, out, precision=p)
+    got = out.cpu().numpy()
+    assert np.isfinite(got).all()
+    if prec == "bf16":
+        fr, kr, tol = bf16(feat, torch), bf16(filt, torch), 2e-5
+    elif prec == "fp8":
+        fr, kr, tol = e4m3(feat, FP8_FEATURE_SCALE, torch), e4m3(filt, bank_scale(filt), torch), 1e-5
+    else:
+        fr, kr, tol = feat, filt, 1e-4
+    for k in range(K):
+        assert rel_err(got[k], orc.correlate(fr, kr[k])) <= tol, k
+
+
 def _bf16_model(model, torch):
     comps = []
     for c in model.components:
