@@ -6,10 +6,10 @@
 // (the first strict maximum is the smallest maximiser), with the costs of those displacements taken once per line.
 // Then the result is checked against the line maximum M: on each side, beyond the cost's vertex, a cost above
 // (M - best) + margin at distance DT_R0 + 1 rules out every farther candidate (its f[q] - cost <= M - cost < best -
-// margin). With DPM-like deformation costs almost every output finishes there (away from the line ends the window
-// needs no bounds checks); an output whose window is wider continues with an outward scan over the exactly bounded
-// window (left candidates win ties, right ones must be strictly better). The margin covers FP32 rounding of the
-// evaluated values, so the result is the brute-force one.
+// margin). With DPM-like deformation costs most outputs finish there (away from the line ends the window needs no
+// bounds checks); an output whose window is wider continues outward, four distances per step, over the window that
+// its first result bounds (left candidates win ties, right ones must be strictly better). The margin covers FP32
+// rounding of the evaluated values, so the result is the brute-force one.
 //
 // x pass: one CTA per (job, 8 rows), one warp per row: the row is staged in shared memory, and the lanes take the
 //         sampled columns p = x_off + x_step*k; results V[y][k], IV[y][k] (row-major [H][nx]: the lanes of a warp
@@ -113,23 +113,24 @@ __device__ __forceinline__ void dt_scan(const DtLine &c, const float *L, int n, 
     if (!(done_l && done_r)) {
         int lo, hi;
         dt_window(c.lin, c.quad, c.mx, best, p, n, lo, hi);
-        for (int d = DT_R0 + 1; p - d >= lo || p + d <= hi; ++d) {
-            const float fd = (float)d;
-            if (p - d >= lo) {
-                // smallest index seen so far: it also wins a tie
-                const float v = L[p - d] - fmaf(c.quad, fd * fd, -c.lin * fd);
-                if (v >= best) {
-                    best = v;
+        // the window of the first result holds every candidate that can still win (a better value would only narrow
+        // it); four distances per step, at each distance the left candidate first: it is the smallest index seen so
+        // far and also wins a tie, the right one must be strictly better
+        const int dmax = max(p - lo, hi - p);
+        for (int d0 = DT_R0 + 1; d0 <= dmax; d0 += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int d = d0 + u;
+                const float fd = (float)d;
+                const float vl = p - d >= lo ? L[p - d] - fmaf(c.quad, fd * fd, -c.lin * fd) : -INFINITY;
+                const float vr = p + d <= hi ? L[p + d] - fmaf(c.quad, fd * fd, c.lin * fd) : -INFINITY;
+                if (vl >= best) {
+                    best = vl;
                     arg = p - d;
-                    dt_window(c.lin, c.quad, c.mx, best, p, n, lo, hi);
                 }
-            }
-            if (p + d <= hi) {
-                const float v = L[p + d] - fmaf(c.quad, fd * fd, c.lin * fd);
-                if (v > best) {
-                    best = v;
+                if (vr > best) {
+                    best = vr;
                     arg = p + d;
-                    dt_window(c.lin, c.quad, c.mx, best, p, n, lo, hi);
                 }
             }
         }
