@@ -258,7 +258,11 @@ __global__ void __launch_bounds__(ZT_THREADS, 2)
                         const int yy = TL.y0 + r, xx = TL.x0 + c;
                         if (r < TL.rows && xx < Wo) out[((size_t)(kf0 + f) * Ho + yy) * Wo + xx] = s;
                     }
+                    // the last round's barrier also ends the item: every TMEM read of it is complete (the last row's
+                    // load was waited for) before the next item's MMAs overwrite the accumulator
+                    if (o == TY - 1) asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncthreads();
+                    if (o == TY - 1) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 }
             }
         };
@@ -276,11 +280,7 @@ __global__ void __launch_bounds__(ZT_THREADS, 2)
             row_step(y + 1, z1);
             if (y + 2 < ZT_T) zt_ld_wait(z0);
         }
-        // every TMEM read of this item is complete (the last round's barrier follows the last wait) before the next
-        // item's MMAs overwrite the accumulator
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        static_assert(TY - 1 + HH - 1 == ZT_T - 1, "the last Z row completes the last output row and its round");
     }
     if (threadIdx.x == 0 && n_local > 0) {
         // only reached with copies or MMAs in flight when a wait above gave up
